@@ -1,0 +1,195 @@
+/*
+ * front.h -- C ABI of libfront.so, the GB300 (sm_103a) implementation of the
+ * front/fluid coupling of sharp front tracking (Gorges, Evrard, Chiodi,
+ * van Wachem, Denner; arXiv 2505.06932).
+ *
+ * Every time step a closed triangulated front is coupled to a uniform Cartesian
+ * fluid mesh only in the interfacial cells, in five steps:
+ *   front_bin              cells touched by each triangle           (Sec. 3.2)
+ *   front_volume_fraction  alpha_C = (1/V_C) int_C I dx              (Sec. 3.2)
+ *   front_curvature_ppic   PPIC volume fit -> curvature, normal      (Sec. 3.2,
+ *                          Eqs. volumefit, Wendland, volumefit2)
+ *   front_csf_force        S = sigma kappa grad alpha + smoothing    (Sec. 3.3,
+ *                          Eq. csf)
+ *   front_interp_velocity  divergence-preserving face -> vertex      (Sec. 3.1)
+ *
+ * Conventions (all calls):
+ *   - Array arguments are CUDA device pointers owned by the caller; the library
+ *     never frees or retains them beyond the call.  Host pointers are allowed
+ *     only where a parameter says "host".
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  They return FT_OK or a negative FT_ERR_* code
+ *     for errors detected on the host (bad arguments, allocation, launch).
+ *   - Errors found on the device (capacity, front outside the grid margin, open
+ *     or inverted front, bad vertex index, timeout) are OR-ed into the
+ *     workspace's status word as FT_ST_* bits; ft_status() synchronizes the
+ *     stream, returns them and clears the word.  Kernels never trap.
+ *   - Cell (i,j,k) of grid g spans origin + h*[i,i+1] x h*[j,j+1] x h*[k,k+1];
+ *     its key is (i*n1 + j)*n2 + k (k fastest).  Dense cell arrays are indexed
+ *     by key.  Fronts are closed 2-manifold triangle meshes whose triangles are
+ *     counter-clockwise seen from outside the region with indicator 1.
+ *   - A workspace is tied to one grid shape and one device, and is not safe to
+ *     use from two streams at once.
+ */
+#ifndef FRONT_H
+#define FRONT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Uniform grid of n[0] x n[1] x n[2] cubic cells of edge h starting at origin. */
+typedef struct {
+    int32_t n[3];
+    int32_t pad;
+    double origin[3];
+    double h;
+} ft_grid;
+
+/* Closed front: verts (nv, 3) float64 xyz, tris (nt, 3) int32 vertex indices. */
+typedef struct {
+    const double* verts;
+    int64_t nv;
+    const int32_t* tris;
+    int64_t nt;
+} ft_front;
+
+/* Method parameters (Sec. 3.2 and 3.3). */
+typedef struct {
+    double delta_h;      /* initial Wendland support radius / h (paper: 2.5)     */
+    double delta_growth; /* support growth factor while too few fragments (1.25) */
+    double delta_max_h;  /* largest support radius / h (4.0)                     */
+    double sigma;        /* surface tension coefficient of Eq. csf (1.0)         */
+    int32_t fit_min;     /* minimum fragments with non-zero weight (paper: 24)   */
+    int32_t precision;   /* FT_FP64 (plain) or FT_FP32C (FP32 + compensation)    */
+} ft_params;
+
+/* Workspace capacities; 0 selects a default derived from max_nt. */
+typedef struct {
+    int64_t max_nt;    /* most triangles of one front                          */
+    int64_t max_cand;  /* most (triangle, candidate cell) pairs (default 16*nt) */
+    int64_t max_cells; /* most interfacial cells (default max_cand)            */
+} ft_capacity;
+
+typedef struct ft_workspace ft_workspace; /* opaque; owns library device memory */
+
+enum {
+    FT_FP64 = 0,
+    FT_FP32C = 1
+};
+
+enum {
+    FT_OK = 0,
+    FT_ERR_ARG = -1,          /* null pointer, bad size, grid mismatch          */
+    FT_ERR_ALLOC = -2,        /* cudaMalloc failed                               */
+    FT_ERR_CAPACITY = -3,     /* a capacity was exceeded (see ft_counts)         */
+    FT_ERR_OUTSIDE_GRID = -4, /* front not inside the grid margin                */
+    FT_ERR_NOT_CLOSED = -5,   /* column parity residue > 1e-9: front not closed  */
+    FT_ERR_ORIENTATION = -6,  /* inverted front (negative enclosed volume)       */
+    FT_ERR_TIMEOUT = -7,      /* a bounded device wait gave up                   */
+    FT_ERR_CUDA = -8,         /* CUDA runtime error                              */
+    FT_ERR_STATE = -9         /* call order violated (e.g. no front_bin yet)     */
+};
+
+/* device status bits (ft_status) */
+#define FT_ST_CAPACITY 0x01u
+#define FT_ST_OUTSIDE_GRID 0x02u
+#define FT_ST_NOT_CLOSED 0x04u
+#define FT_ST_ORIENTATION 0x08u
+#define FT_ST_BAD_INDEX 0x10u
+#define FT_ST_TIMEOUT 0x20u
+
+/* per-cell fit_status bits of front_curvature_ppic */
+#define FT_FIT_GROWN 0x1     /* support radius was grown beyond delta_h          */
+#define FT_FIT_SINGULAR 0x2  /* normal equations singular: plane fit, kappa = 0  */
+#define FT_FIT_NORMAL 0x4    /* opposing sheets: normal of the largest fragment  */
+
+/* Create a workspace for grid *g on CUDA device `device`; *bytes (host, may be
+ * NULL) receives the device memory it holds.  The front must keep
+ * 2 + ceil(delta_max_h) cells from every grid face. */
+int ft_workspace_create(ft_workspace** ws, const ft_grid* g, const ft_capacity* cap, int device,
+                        size_t* bytes);
+int ft_workspace_destroy(ft_workspace* ws);
+
+/* Synchronize `stream`, write the accumulated FT_ST_* bits to *bits (host) and
+ * clear them. */
+int ft_status(ft_workspace* ws, void* stream, uint32_t* bits);
+
+/* Synchronize `stream` and write 5 host int64: interfacial cells M, binned
+ * (cell, triangle) pairs P, candidate pairs used, candidate pairs needed, and
+ * the (cell, fragment) pairs inside the support of the last PPIC call. */
+int ft_counts(ft_workspace* ws, void* stream, int64_t* out5);
+
+const char* ft_status_string(int code);
+
+/* Copy the sorted (cell key, triangle) pairs of the last front_bin into
+ * keys (uint32) and tris (int32), both of length >= cap (device pointers);
+ * pairs beyond cap are dropped (FT_ST_CAPACITY).  For inspection and tests. */
+int ft_bin_pairs(ft_workspace* ws, int64_t cap, uint32_t* keys, int32_t* tris, void* stream);
+
+/* (a1) Bin the front (Sec. 3.2, interfacial cells).  For every triangle, every
+ * cell whose closed box meets the triangle's bounding box is clipped against
+ * the triangle (Sutherland-Hodgman, planes x>=X_i, x<=X_i+1, y.., z..; crossing
+ * points prev + t (cur - prev) with t = (X - prev)/(cur - prev), all in IEEE
+ * binary64 without contraction); the cell keeps the triangle iff every stage
+ * leaves >= 3 vertices, the fan area vector is not zero, and the fragment does
+ * not lie entirely in one of the cell's upper faces.  The kept (cell, triangle)
+ * pairs are radix-sorted by cell key (triangles ascending within a cell); their
+ * fragment moments are kept in the workspace for the next steps.  Requires
+ * f->nt <= capacity.max_nt.  p->delta_max_h sets the grid margin. */
+int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* stream);
+
+/* (a2) Volume fraction (Sec. 3.2) of every cell into alpha (n0*n1*n2 float64,
+ * by key).  Interfacial cells: (1/h^3)[ int_{front in C} (z - Z_k) n_z dA
+ * + h int_{front above C in its column} n_z dA ]; other cells: the rounded
+ * column parity, exactly 0 or 1 (FT_ST_NOT_CLOSED if the residue > 1e-9).
+ * Results are clamped to [0,1].  Needs front_bin on this workspace. */
+int front_volume_fraction(ft_workspace* ws, double* alpha, void* stream);
+
+/* (a3) PPIC curvature (Sec. 3.2) in every interfacial cell, in ascending key
+ * order: cell_keys (M uint32), kappa (M float64, kappa = div n > 0 on a sphere,
+ * 2/R), normal (M x 3 float64, paraboloid normal at the local origin), coeffs
+ * (M x 6 float64, a1..a6 in the local frame with lengths in units of h; may be
+ * NULL) and fit_status (M int8, FT_FIT_* bits).  Local frame: n = normalized
+ * sum of the cell's fragment area vectors, (t1,t2) completing it (Duff et al.
+ * 2017); fit data: fragments of cells within ceil(delta - 1/2) cells whose area
+ * centroid lies closer than delta to the cell centre, Wendland weights, volume
+ * fit normal equations solved in float64.  `cap` is the length of the output
+ * arrays; M > cap sets FT_ST_CAPACITY and writes nothing.  Needs front_bin. */
+int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint32_t* cell_keys,
+                         double* kappa, double* normal, double* coeffs, int8_t* fit_status,
+                         void* stream);
+
+/* (a4) CSF source (Eq. csf, Sec. 3.3) into force (3 x n0*n1*n2 float64, SoA):
+ * S_P = sigma kappa_P grad alpha_P, grad by central differences with alpha = 0
+ * outside the grid; kappa_P is the cell's own curvature in interfacial cells
+ * and, elsewhere, sum_Q kappa_Q w_Q / sum_Q w_Q over interfacial Q among the 26
+ * neighbours with w_Q = |s_Q . n_Q| / |s_Q|.  kappa and normal are the M-long
+ * outputs of front_curvature_ppic for the same bins. */
+int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                    const double* normal, double* force, void* stream);
+
+/* (a5) Divergence-preserving velocity interpolation (Sec. 3.1) of the staggered
+ * face velocities U (n0+1,n1,n2), V (n0,n1+1,n2), W (n0,n1,n2+1) to the nv
+ * points verts (nv x 3) into vel (nv x 3).  The cell is floor((x - origin)/h)
+ * clamped to the grid; transverse face gradients are central differences,
+ * one-sided on the first and last face rows.  Needs no workspace. */
+int front_interp_velocity(const ft_grid* g, const double* U, const double* V, const double* W,
+                          const double* verts, int64_t nv, double* vel, void* stream);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * devices, all workspaces). */
+int64_t ft_launch_count(void);
+
+/* Throughput probe (no counterpart in the paper): runs dependent FMA chains on
+ * every SM (kind 0: float64, 1: float32) and writes the achieved FLOP/s
+ * (host *flops); used to state the ALU roofline of the kernels above. */
+int ft_probe_fma_rate(int kind, int device, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -452,14 +452,30 @@ static double og_wendland(double q) {
 
 double og_wendland_weight(double q) { return og_wendland(q); }
 
-/* Orthonormal basis (t1, t2) completing the unit normal n (Duff et al. 2017,
- * "Building an orthonormal basis, revisited"). */
+/* Orthonormal basis (t1, t2) completing the unit normal n.  The paper leaves
+ * the tangents open (the fit is isotropic in (t1, t2)); this reading applies
+ * the branchless construction of Duff et al. 2017 ("Building an orthonormal
+ * basis, revisited") to m = R n in a fixed rotated reference frame R, whose
+ * third row is (1,2,3)/sqrt(14), and rotates the tangents back.  Duff's
+ * construction switches with sign(m_z); in the rotated frame that switch no
+ * longer falls on fronts with an exactly vertical normal (n_z = 0), which
+ * axis-aligned or symmetric geometry produces routinely. */
+static const double OG_R[3][3] = {{0.9636241116594316, -0.14824986333222026, -0.22237479499833038},
+                                  {0.0, 0.8320502943378438, -0.5547001962252291},
+                                  {0.2672612419124244, 0.5345224838248488, 0.8017837257372732}};
+
 static void og_basis(const double* n, double* t1, double* t2) {
-    const double sg = copysign(1.0, n[2]);
-    const double a = -1.0 / (sg + n[2]);
-    const double b = n[0] * n[1] * a;
-    t1[0] = 1.0 + sg * n[0] * n[0] * a; t1[1] = sg * b; t1[2] = -sg * n[0];
-    t2[0] = b; t2[1] = sg + n[1] * n[1] * a; t2[2] = -n[1];
+    double m[3], u1[3], u2[3];
+    for (int r = 0; r < 3; r++) m[r] = OG_R[r][0] * n[0] + OG_R[r][1] * n[1] + OG_R[r][2] * n[2];
+    const double sg = copysign(1.0, m[2]);
+    const double a = -1.0 / (sg + m[2]);
+    const double b = m[0] * m[1] * a;
+    u1[0] = 1.0 + sg * m[0] * m[0] * a; u1[1] = sg * b; u1[2] = -sg * m[0];
+    u2[0] = b; u2[1] = sg + m[1] * m[1] * a; u2[2] = -m[1];
+    for (int c = 0; c < 3; c++) {
+        t1[c] = OG_R[0][c] * u1[0] + OG_R[1][c] * u1[1] + OG_R[2][c] * u1[2];
+        t2[c] = OG_R[0][c] * u2[0] + OG_R[1][c] * u2[1] + OG_R[2][c] * u2[2];
+    }
 }
 
 /* Gaussian elimination with partial pivoting on an n x n system (row-major). */

@@ -1,0 +1,268 @@
+"""ctypes binding of libfront.so (C ABI in include/front.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  The
+functions take torch CUDA tensors (device memory and the current stream come
+from PyTorch) and keep the C names.  There is no CPU fallback: if the library
+cannot be built or loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FT_FP64, FT_FP32C = 0, 1
+ST_BITS = {0x01: "capacity", 0x02: "outside_grid", 0x04: "not_closed", 0x08: "orientation",
+           0x10: "bad_index", 0x20: "timeout"}
+
+
+class FtGrid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("pad", C.c_int32), ("origin", C.c_double * 3), ("h", C.c_double)]
+
+
+class FtFront(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("nv", C.c_int64), ("tris", C.c_void_p), ("nt", C.c_int64)]
+
+
+class FtParams(C.Structure):
+    _fields_ = [("delta_h", C.c_double), ("delta_growth", C.c_double), ("delta_max_h", C.c_double),
+                ("sigma", C.c_double), ("fit_min", C.c_int32), ("precision", C.c_int32)]
+
+
+class FtCapacity(C.Structure):
+    _fields_ = [("max_nt", C.c_int64), ("max_cand", C.c_int64), ("max_cells", C.c_int64)]
+
+
+class FrontError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libfront.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            P, I64, I32 = C.c_void_p, C.c_int64, C.c_int
+            sig = {
+                "ft_workspace_create": (I32, [C.POINTER(P), P, P, I32, C.POINTER(C.c_size_t)]),
+                "ft_workspace_destroy": (I32, [P]),
+                "ft_status": (I32, [P, P, C.POINTER(C.c_uint32)]),
+                "ft_counts": (I32, [P, P, P]),
+                "ft_status_string": (C.c_char_p, [I32]),
+                "ft_bin_pairs": (I32, [P, I64, P, P, P]),
+                "front_bin": (I32, [P, P, P, P]),
+                "front_volume_fraction": (I32, [P, P, P]),
+                "front_curvature_ppic": (I32, [P, P, I64, P, P, P, P, P, P]),
+                "front_csf_force": (I32, [P, P, P, P, P, P, P]),
+                "front_interp_velocity": (I32, [P, P, P, P, P, I64, P, P]),
+                "ft_probe_fma_rate": (I32, [I32, I32, C.POINTER(C.c_double)]),
+                "ft_launch_count": (I64, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = lib().ft_status_string(rc).decode()
+        raise FrontError(f"{what}: {msg} ({rc})")
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor, dtype, what: str):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise FrontError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise FrontError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise FrontError(f"{what} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def make_grid(g) -> FtGrid:
+    s = FtGrid()
+    for d in range(3):
+        s.n[d] = int(g.n[d])
+        s.origin[d] = float(g.origin[d])
+    s.h = float(g.h)
+    return s
+
+
+def make_params(delta_h=2.5, delta_growth=1.25, delta_max_h=4.0, sigma=1.0, fit_min=24, precision=FT_FP64):
+    return FtParams(float(delta_h), float(delta_growth), float(delta_max_h), float(sigma), int(fit_min),
+                    int(precision))
+
+
+class Workspace:
+    """Library-owned device memory for one grid shape (ft_workspace_create)."""
+
+    def __init__(self, grid, max_nt: int, max_cand: int = 0, max_cells: int = 0, device: int = 0):
+        self.grid = grid
+        self._g = make_grid(grid)
+        cap = FtCapacity(int(max_nt), int(max_cand), int(max_cells))
+        h = C.c_void_p()
+        nbytes = C.c_size_t()
+        _check(lib().ft_workspace_create(C.byref(h), C.byref(self._g), C.byref(cap), int(device), C.byref(nbytes)),
+               "ft_workspace_create")
+        self.handle = h
+        self.bytes = int(nbytes.value)
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().ft_workspace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None) -> int:
+        bits = C.c_uint32()
+        _check(lib().ft_status(self.handle, _stream(stream), C.byref(bits)), "ft_status")
+        return int(bits.value)
+
+    def counts(self, stream=None) -> dict:
+        out = (C.c_int64 * 5)()
+        _check(lib().ft_counts(self.handle, _stream(stream), out), "ft_counts")
+        return dict(M=out[0], P=out[1], C=out[2], C_need=out[3], fit_pairs=out[4])
+
+
+def ft_bin_pairs(ws: Workspace, keys: torch.Tensor, tris: torch.Tensor, stream=None):
+    cap = min(keys.shape[0], tris.shape[0])
+    _check(lib().ft_bin_pairs(ws.handle, cap, _ptr(keys, torch.int32, "keys"), _ptr(tris, torch.int32, "tris"),
+                              _stream(stream)), "ft_bin_pairs")
+
+
+def status_names(bits: int):
+    return [v for k, v in ST_BITS.items() if bits & k]
+
+
+# ---------------------------------------------------------------------------
+# the five steps, one C call each
+# ---------------------------------------------------------------------------
+
+def front_bin(ws: Workspace, verts: torch.Tensor, tris: torch.Tensor, params: FtParams, stream=None):
+    f = FtFront(_ptr(verts, torch.float64, "verts"), verts.shape[0], _ptr(tris, torch.int32, "tris"), tris.shape[0])
+    _check(lib().front_bin(ws.handle, C.byref(f), C.byref(params), _stream(stream)), "front_bin")
+
+
+def front_volume_fraction(ws: Workspace, alpha: torch.Tensor, stream=None):
+    if alpha.numel() != ws.grid.ncells:
+        raise FrontError("alpha must hold n0*n1*n2 values")
+    _check(lib().front_volume_fraction(ws.handle, _ptr(alpha, torch.float64, "alpha"), _stream(stream)),
+           "front_volume_fraction")
+
+
+def front_curvature_ppic(ws: Workspace, params: FtParams, cell_keys, kappa, normal, coeffs, fit_status, stream=None):
+    cap = kappa.shape[0]
+    if cell_keys.shape[0] < cap or normal.shape[0] < cap or fit_status.shape[0] < cap:
+        raise FrontError("PPIC output arrays are shorter than kappa")
+    _check(lib().front_curvature_ppic(ws.handle, C.byref(params), cap, _ptr(cell_keys, torch.int32, "cell_keys"),
+                                      _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
+                                      _ptr(coeffs, torch.float64, "coeffs") if coeffs is not None else None,
+                                      _ptr(fit_status, torch.int8, "fit_status"), _stream(stream)),
+           "front_curvature_ppic")
+
+
+def front_csf_force(ws: Workspace, params: FtParams, alpha, kappa, normal, force, stream=None):
+    if force.numel() != 3 * ws.grid.ncells:
+        raise FrontError("force must hold 3*n0*n1*n2 values")
+    _check(lib().front_csf_force(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),
+                                 _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
+                                 _ptr(force, torch.float64, "force"), _stream(stream)), "front_csf_force")
+
+
+def front_interp_velocity(grid, U, V, W, verts, vel, stream=None):
+    g = make_grid(grid)
+    n = grid.n
+    if tuple(U.shape) != (n[0] + 1, n[1], n[2]) or tuple(V.shape) != (n[0], n[1] + 1, n[2]) \
+            or tuple(W.shape) != (n[0], n[1], n[2] + 1):
+        raise FrontError("face arrays have the wrong shapes")
+    _check(lib().front_interp_velocity(C.byref(g), _ptr(U, torch.float64, "U"), _ptr(V, torch.float64, "V"),
+                                       _ptr(W, torch.float64, "W"), _ptr(verts, torch.float64, "verts"),
+                                       verts.shape[0], _ptr(vel, torch.float64, "vel"), _stream(stream)),
+           "front_interp_velocity")
+
+
+def launch_count() -> int:
+    return int(lib().ft_launch_count())
+
+
+def probe_fma_rate(kind: int, device: int = 0) -> float:
+    out = C.c_double()
+    _check(lib().ft_probe_fma_rate(int(kind), int(device), C.byref(out)), "ft_probe_fma_rate")
+    return float(out.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience: device buffers for one front and the whole hot path
+# ---------------------------------------------------------------------------
+
+class FrontCoupling:
+    """Holds a workspace and device output buffers for fronts on one grid and
+    runs the five steps in order (bin, alpha, kappa, force, vertex velocity)."""
+
+    def __init__(self, grid, max_nt: int, max_nv: int, max_cand: int = 0, params: FtParams | None = None,
+                 device: int = 0):
+        self.grid = grid
+        self.params = params or make_params()
+        self.ws = Workspace(grid, max_nt, max_cand=max_cand, device=device)
+        dev = torch.device("cuda", device)
+        nc = grid.ncells
+        cap = max_cand if max_cand else 16 * max_nt + 1024
+        self.cap_cells = cap
+        self.alpha = torch.empty(nc, dtype=torch.float64, device=dev)
+        self.force = torch.empty(3 * nc, dtype=torch.float64, device=dev)
+        self.cell_keys = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.kappa = torch.empty(cap, dtype=torch.float64, device=dev)
+        self.normal = torch.empty((cap, 3), dtype=torch.float64, device=dev)
+        self.coeffs = torch.empty((cap, 6), dtype=torch.float64, device=dev)
+        self.fit_status = torch.empty(cap, dtype=torch.int8, device=dev)
+        self.vel = torch.empty((max_nv, 3), dtype=torch.float64, device=dev)
+
+    def step(self, verts, tris, faces, stream=None):
+        p = self.params
+        front_bin(self.ws, verts, tris, p, stream)
+        front_volume_fraction(self.ws, self.alpha, stream)
+        front_curvature_ppic(self.ws, p, self.cell_keys, self.kappa, self.normal, self.coeffs, self.fit_status, stream)
+        front_csf_force(self.ws, p, self.alpha, self.kappa, self.normal, self.force, stream)
+        front_interp_velocity(self.grid, faces[0], faces[1], faces[2], verts, self.vel[:verts.shape[0]], stream)
+
+    def results(self, nv: int):
+        """Synchronizes and returns host copies (numpy) of every output."""
+        c = self.ws.counts()
+        M = c["M"]
+        n = tuple(int(x) for x in self.grid.n)
+        return dict(
+            counts=c,
+            status=self.ws.status(),
+            alpha=self.alpha.view(n).cpu().numpy(),
+            cell_keys=self.cell_keys[:M].cpu().numpy().view("uint32"),
+            kappa=self.kappa[:M].cpu().numpy(),
+            normal=self.normal[:M].cpu().numpy(),
+            coeffs=self.coeffs[:M].cpu().numpy(),
+            fit_status=self.fit_status[:M].cpu().numpy(),
+            force=self.force.view((3,) + n).cpu().numpy(),
+            vel=self.vel[:nv].cpu().numpy(),
+        )

@@ -1,0 +1,104 @@
+// k_alpha.cu -- front_volume_fraction: alpha_C = (1/V_C) int_C I dx (Sec. 3.2).
+//
+// Divergence theorem along z: for a vertical line the length inside the
+// enclosed region and inside [Z_k, Z_k+1] is sum over front crossings of
+// sign(n_z)(clamp(z, Z_k, Z_k+1) - Z_k).  Integrated over the column cross-
+// section, with fragments f of cell C and the column above C:
+//   alpha_C h^3 = sum_{f in C} int_f (z - Z_k) n_z dA + h sum_{f above C} int_f n_z dA.
+// In units of h the first term is AN_z (c_z + 1/2) per fragment (area vector
+// AN, centroid c relative to the cell centre) and the second a suffix sum of
+// AN_z over the column.  Cells without fragments get the rounded suffix sum,
+// which is exactly 0 or 1 for a closed, outward-oriented front (the "column
+// parity fill" standing in for the paper's ray casting / flood fill).
+#include "ft_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// one warp per interfacial cell: L_C = sum AN_z (c_z + 1/2), P_C = sum AN_z
+__global__ void __launch_bounds__(kThreads) k_alpha_cells(const int* __restrict__ cell_off, const unsigned* __restrict__ vals,
+                                                          const ft_frag* __restrict__ rec, double* __restrict__ cell_L,
+                                                          double* __restrict__ cell_P, const ft_counters* ctr) {
+    const long long M = ctr->M;
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * kWarps;
+    for (long long m = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); m < M; m += nw) {
+        const int q0 = cell_off[m], q1 = cell_off[m + 1];
+        double L = 0.0, P = 0.0;
+        for (int q = q0 + lane; q < q1; q += 32) {
+            const ft_frag* f = rec + vals[q];
+            const double az = f->an[2];
+            L += az * (f->c[2] + 0.5);
+            P += az;
+        }
+        L = ft_warp_sum(L);
+        P = ft_warp_sum(P);
+        if (lane == 0) {
+            cell_L[m] = L;
+            cell_P[m] = P;
+        }
+    }
+}
+
+// one warp per (i, j) column, walking k downwards in chunks of 32 cells
+__global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* __restrict__ idx_map,
+                                                         const double* __restrict__ cell_L,
+                                                         const double* __restrict__ cell_P, double* __restrict__ alpha,
+                                                         ft_counters* ctr) {
+    const int lane = threadIdx.x & 31;
+    const long long ncol = (long long)g.n[0] * g.n[1];
+    const int n2 = g.n[2];
+    const long long nw = (long long)gridDim.x * kWarps;
+    unsigned err = 0;
+    for (long long col = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); col < ncol; col += nw) {
+        const long long base = col * n2;
+        double carry = 0.0;
+        for (int k0 = ((n2 - 1) / 32) * 32; k0 >= 0; k0 -= 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n2;
+            const int m = valid ? idx_map[base + k] : -1;
+            const double Pz = (m >= 0) ? cell_P[m] : 0.0;
+            const double L = (m >= 0) ? cell_L[m] : 0.0;
+            double x = Pz;  // inclusive suffix sum within the chunk
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_down_sync(0xffffffffu, x, o);
+                if (lane + o < 32) x += y;
+            }
+            double ex = __shfl_down_sync(0xffffffffu, x, 1);
+            if (lane == 31) ex = 0.0;
+            const double S = carry + ex;
+            carry += __shfl_sync(0xffffffffu, x, 0);
+            if (valid) {
+                double a;
+                if (m >= 0) {
+                    a = L + S;
+                } else {
+                    const double r = rint(S);
+                    if (fabs(S - r) > 1e-9) err |= FT_ST_NOT_CLOSED;
+                    if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
+                    a = r;
+                }
+                alpha[base + k] = fmin(fmax(a, 0.0), 1.0);
+            }
+        }
+    }
+    err = __reduce_or_sync(0xffffffffu, err);
+    if (err && lane == 0) ft_flag(ctr, err);
+}
+
+}  // namespace
+
+namespace ft {
+
+cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s) {
+    const unsigned* vals = ws->vals[ws->sorted_buf];
+    count_launches(2);
+    k_alpha_cells<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, ws->rec, ws->cell_L, ws->cell_P, ws->ctr);
+    k_alpha_fill<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->g, ws->idx_map, ws->cell_L, ws->cell_P, alpha, ws->ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace ft

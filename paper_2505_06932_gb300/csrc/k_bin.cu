@@ -1,0 +1,298 @@
+// k_bin.cu -- front_bin, part 1: candidate cells of every triangle and the
+// canonical clip predicate (Sec. 3.2, "interfacial cells"), with the fragment
+// moments that the volume fraction and the PPIC fit use later.
+//
+// The predicate is an exact definition, not an approximation: each arithmetic
+// step is one IEEE binary64 operation with round-to-nearest (the __d*_rn
+// intrinsics are never contracted into FMA), so every decision is reproducible
+// bit for bit by any implementation that follows the same definition.
+#include "ft_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Candidate range along one axis: cells whose closed extent [X_i, X_i+1] meets
+// [lo, hi]: i0 = min{i : X_i+1 >= lo}, i1 = max{i : X_i <= hi}.  The floor is
+// only a starting guess; the loops make the result exact.
+__device__ void cand_range(double o, double h, int n, double lo, double hi, int& i0, int& i1) {
+    double f = floor(__ddiv_rn(__dsub_rn(lo, o), h));
+    int e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
+    while (e > 0 && ft_plane(o, h, e) >= lo) e--;
+    while (e < n - 1 && ft_plane(o, h, e + 1) < lo) e++;
+    i0 = e;
+    f = floor(__ddiv_rn(__dsub_rn(hi, o), h));
+    e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
+    while (e < n - 1 && ft_plane(o, h, e + 1) <= hi) e++;
+    while (e > 0 && ft_plane(o, h, e) > hi) e--;
+    i1 = e;
+}
+
+__global__ void __launch_bounds__(kThreads) k_tri_setup(const double* __restrict__ verts, long long nv,
+                                                        const int* __restrict__ tris, long long T,
+                                                        ft_grid g, int margin, long long max_cand,
+                                                        int* __restrict__ tri_cnt, int* __restrict__ tri_box,
+                                                        ft_counters* ctr) {
+    const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+    if (t == 0) ctr->T = T;
+    if (t >= T) return;
+    int cnt = 0;
+    int box[6] = {0, 0, 0, 1, 1, 1};
+    unsigned err = 0;
+    int vi[3];
+    for (int c = 0; c < 3; c++) {
+        vi[c] = tris[3 * t + c];
+        if (vi[c] < 0 || vi[c] >= nv) err |= FT_ST_BAD_INDEX;
+    }
+    if (!err) {
+        double mn[3], mx[3];
+        for (int ax = 0; ax < 3; ax++) {
+            mn[ax] = INFINITY;
+            mx[ax] = -INFINITY;
+        }
+        bool finite = true;
+        for (int c = 0; c < 3; c++)
+            for (int ax = 0; ax < 3; ax++) {
+                const double x = verts[3 * (long long)vi[c] + ax];
+                finite = finite && isfinite(x);
+                mn[ax] = fmin(mn[ax], x);
+                mx[ax] = fmax(mx[ax], x);
+            }
+        if (!finite) err |= FT_ST_OUTSIDE_GRID;
+        long long total = 1;
+        for (int ax = 0; ax < 3 && !err; ax++) {
+            int i0, i1;
+            cand_range(g.origin[ax], g.h, g.n[ax], mn[ax], mx[ax], i0, i1);
+            if (i0 < margin || i1 > g.n[ax] - 1 - margin) err |= FT_ST_OUTSIDE_GRID;
+            box[ax] = i0;
+            box[3 + ax] = i1 - i0 + 1;
+            total *= (long long)(i1 - i0 + 1);
+        }
+        if (!err) {
+            if (total > max_cand) {
+                err |= FT_ST_CAPACITY;
+                total = max_cand + 1;  // still counted so that the total exceeds the capacity
+            }
+            cnt = (int)total;
+        }
+    }
+    if (err) ft_flag(ctr, err);
+    tri_cnt[t] = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
+    for (int d = 0; d < 6; d++) tri_box[6 * t + d] = box[d];
+}
+
+__global__ void __launch_bounds__(kThreads) k_expand(const int* __restrict__ tri_cnt, const int* __restrict__ tri_off,
+                                                     long long T, long long max_cand, int* __restrict__ cand_tri,
+                                                     ft_counters* ctr) {
+    const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const long long need = ctr->C_need;
+    const bool ok = need <= max_cand;
+    if (t == 0) {
+        ctr->C = ok ? need : 0;
+        if (!ok) ft_flag(ctr, FT_ST_CAPACITY);
+    }
+    if (!ok || t >= T) return;
+    const int off = tri_off[t], cnt = tri_cnt[t];
+    for (int l = 0; l < cnt; l++) cand_tri[off + l] = (int)t;
+}
+
+// ---------------------------------------------------------------------------
+// canonical clip
+// ---------------------------------------------------------------------------
+
+// One Sutherland-Hodgman step against coord[ax] >= pv (ge) or <= pv (!ge).
+// Returns false if the output would exceed MAXV vertices.
+template <int MAXV>
+__device__ __forceinline__ bool clip_half(const double (*in)[3], int n, double (*out)[3], int& m, int ax,
+                                          double pv, bool ge) {
+    m = 0;
+    for (int i = 0; i < n; i++) {
+        const double* cur = in[i];
+        const double* prev = in[i == 0 ? n - 1 : i - 1];
+        const bool cin = ge ? (cur[ax] >= pv) : (cur[ax] <= pv);
+        const bool pin = ge ? (prev[ax] >= pv) : (prev[ax] <= pv);
+        if (cin != pin) {
+            if (m >= MAXV) return false;
+            const double t = __ddiv_rn(__dsub_rn(pv, prev[ax]), __dsub_rn(cur[ax], prev[ax]));
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                out[m][c] = (c == ax) ? pv : __dadd_rn(prev[c], __dmul_rn(t, __dsub_rn(cur[c], prev[c])));
+            m++;
+        }
+        if (cin) {
+            if (m >= MAXV) return false;
+            out[m][0] = cur[0];
+            out[m][1] = cur[1];
+            out[m][2] = cur[2];
+            m++;
+        }
+    }
+    return true;
+}
+
+// Canonical clip of triangle v against cell (i,j,k).  Returns the vertex count
+// (>= 3) of the accepted fragment, 0 if rejected, -1 if MAXV was too small.
+template <int MAXV>
+__device__ int canon_clip(const double (*v)[3], const ft_grid& g, const int idx[3], double (*res)[3]) {
+    double A[MAXV][3], B[MAXV][3];
+    int n = 3;
+    for (int c = 0; c < 3; c++)
+        for (int d = 0; d < 3; d++) A[c][d] = v[c][d];
+    double(*src)[3] = A;
+    double(*dst)[3] = B;
+    for (int ax = 0; ax < 3; ax++) {
+        for (int side = 0; side < 2; side++) {
+            int m;
+            const double pv = ft_plane(g.origin[ax], g.h, idx[ax] + side);
+            if (!clip_half<MAXV>(src, n, dst, m, ax, pv, side == 0)) return -1;
+            if (m < 3) return 0;
+            n = m;
+            double(*tmp)[3] = src;
+            src = dst;
+            dst = tmp;
+        }
+    }
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int m = 1; m + 1 < n; m++) {
+        const double e1x = __dsub_rn(src[m][0], src[0][0]), e1y = __dsub_rn(src[m][1], src[0][1]),
+                     e1z = __dsub_rn(src[m][2], src[0][2]);
+        const double e2x = __dsub_rn(src[m + 1][0], src[0][0]), e2y = __dsub_rn(src[m + 1][1], src[0][1]),
+                     e2z = __dsub_rn(src[m + 1][2], src[0][2]);
+        s0 = __dadd_rn(s0, __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y)));
+        s1 = __dadd_rn(s1, __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z)));
+        s2 = __dadd_rn(s2, __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x)));
+    }
+    if (s0 == 0.0 && s1 == 0.0 && s2 == 0.0) return 0;
+    for (int ax = 0; ax < 3; ax++) {
+        const double up = ft_plane(g.origin[ax], g.h, idx[ax] + 1);
+        bool all = true;
+        for (int m = 0; m < n && all; m++) all = (src[m][ax] == up);
+        if (all) return 0;
+    }
+    for (int m = 0; m < n; m++)
+        for (int d = 0; d < 3; d++) res[m][d] = src[m][d];
+    return n;
+}
+
+__device__ __noinline__ int canon_clip_wide(const double (*v)[3], const ft_grid& g, const int idx[3],
+                                            double (*res)[3]) {
+    return canon_clip<32>(v, g, idx, res);
+}
+
+// Fragment moments in units of h relative to the fragment cell's centre, from
+// the fan triangles (p0, p_m, p_m+1) of the convex fragment polygon.
+__device__ void frag_moments(const double (*p)[3], int n, const double xc[3], double inv_h, ft_frag& f) {
+    double an[3] = {0.0, 0.0, 0.0};
+    for (int m = 1; m + 1 < n; m++) {
+        double e1[3], e2[3];
+        for (int d = 0; d < 3; d++) {
+            e1[d] = (p[m][d] - p[0][d]) * inv_h;
+            e2[d] = (p[m + 1][d] - p[0][d]) * inv_h;
+        }
+        an[0] += 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+        an[1] += 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+        an[2] += 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+    }
+    const double A = sqrt(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
+    double q0[3];
+    for (int d = 0; d < 3; d++) q0[d] = (p[0][d] - xc[d]) * inv_h;
+    double m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
+    if (A > 0.0) {
+        const double nh[3] = {an[0] / A, an[1] / A, an[2] / A};
+        for (int m = 1; m + 1 < n; m++) {
+            double e1[3], e2[3];
+            for (int d = 0; d < 3; d++) {
+                e1[d] = (p[m][d] - p[0][d]) * inv_h;
+                e2[d] = (p[m + 1][d] - p[0][d]) * inv_h;
+            }
+            const double cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+            const double cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+            const double cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+            const double a = 0.5 * (cr0 * nh[0] + cr1 * nh[1] + cr2 * nh[2]);
+            const double s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+            const double a3 = a * (1.0 / 3.0), a12 = a * (1.0 / 12.0);
+            for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
+            // int x_i x_j over a triangle with one vertex at the origin:
+            // (A/12) (s_i s_j + e1_i e1_j + e2_i e2_j)
+            m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+            m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+            m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+            m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+            m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+            m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
+        }
+        const double ia = 1.0 / A;
+        const double c[3] = {m1[0] * ia, m1[1] * ia, m1[2] * ia};
+        f.k[0] = m2[0] * ia - c[0] * c[0];
+        f.k[1] = m2[1] * ia - c[1] * c[1];
+        f.k[2] = m2[2] * ia - c[2] * c[2];
+        f.k[3] = m2[3] * ia - c[0] * c[1];
+        f.k[4] = m2[4] * ia - c[0] * c[2];
+        f.k[5] = m2[5] * ia - c[1] * c[2];
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d] + c[d];
+    } else {
+        for (int d = 0; d < 6; d++) f.k[d] = 0.0;
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d];
+    }
+    for (int d = 0; d < 3; d++) f.an[d] = an[d];
+}
+
+__global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ verts, const int* __restrict__ tris,
+                                                   ft_grid g, const int* __restrict__ cand_tri,
+                                                   const int* __restrict__ tri_off, const int* __restrict__ tri_box,
+                                                   unsigned* __restrict__ keys, unsigned* __restrict__ vals,
+                                                   ft_frag* __restrict__ rec, const ft_counters* ctr) {
+    const long long C = ctr->C;
+    const double inv_h = 1.0 / g.h;
+    for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < C; c += (long long)gridDim.x * kThreads) {
+        const int t = cand_tri[c];
+        const int l = (int)(c - tri_off[t]);
+        const int* bx = tri_box + 6 * (long long)t;
+        const int e1 = bx[4], e2 = bx[5];
+        const int idx[3] = {bx[0] + l / (e1 * e2), bx[1] + (l / e2) % e1, bx[2] + l % e2};
+        double v[3][3];
+        for (int a = 0; a < 3; a++) {
+            const long long vi = tris[3 * (long long)t + a];
+            for (int d = 0; d < 3; d++) v[a][d] = verts[3 * vi + d];
+        }
+        double poly[32][3];
+        int n = canon_clip<12>(v, g, idx, poly);
+        if (n < 0) n = canon_clip_wide(v, g, idx, poly);
+        unsigned key = FT_SENTINEL;
+        if (n >= 3) {
+            key = (unsigned)(((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
+            double xc[3];
+            for (int d = 0; d < 3; d++) xc[d] = ft_plane(g.origin[d], g.h, idx[d]) + 0.5 * g.h;
+            ft_frag f;
+            frag_moments(poly, n, xc, inv_h, f);
+            rec[c] = f;
+        }
+        keys[c] = key;
+        vals[c] = (unsigned)c;
+    }
+}
+
+}  // namespace
+
+namespace ft {
+
+cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s) {
+    const long long T = f->nt;
+    const int margin = 2 + (int)ceil(p->delta_max_h);
+    const unsigned nb = (unsigned)((T + kThreads - 1) / kThreads);
+    if (T > 0) {
+        k_tri_setup<<<nb, kThreads, 0, s>>>(f->verts, f->nv, f->tris, T, ws->g, margin, ws->max_cand, ws->tri_cnt,
+                                            ws->tri_box, ws->ctr);
+    } else {
+        cudaMemsetAsync(&ws->ctr->T, 0, sizeof(long long), s);
+    }
+    cudaError_t e = launch_scan_counts(ws, ws->tri_cnt, ws->tri_off, &ws->ctr->T, &ws->ctr->C_need, s);
+    if (e != cudaSuccess) return e;
+    count_launches(T > 0 ? 3 : 2);
+    k_expand<<<nb ? nb : 1, kThreads, 0, s>>>(ws->tri_cnt, ws->tri_off, T, ws->max_cand, ws->cand_tri, ws->ctr);
+    k_clip<<<ws->sm_count * 4, kThreads, 0, s>>>(f->verts, f->tris, ws->g, ws->cand_tri, ws->tri_off, ws->tri_box,
+                                                ws->keys[0], ws->vals[0], ws->rec, ws->ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace ft

@@ -1,0 +1,344 @@
+// k_sort.cu -- front_bin, part 2: device-wide exclusive scans, the stable LSD
+// radix sort of the (cell key, candidate slot) pairs and the run-length
+// encoding into the interfacial-cell list.
+//
+// Element counts live in device memory (no host round trip), so every kernel
+// here splits its range into gridDim.x contiguous segments computed on the
+// device.  No kernel waits on another block: each pass is reduce -> scan ->
+// scatter in separate launches.
+#include "ft_internal.cuh"
+
+namespace {
+
+constexpr int kB = 256;             // threads per block
+constexpr int kScanMax = 1024;      // most segments the partial scans take
+
+__device__ __forceinline__ long long seg_len(long long n, int G) {
+    long long s = (n + G - 1) / G;
+    return (s + kB - 1) / kB * kB;  // whole tiles per segment
+}
+
+// exclusive block scan of one int per thread; returns the block total
+__device__ __forceinline__ long long block_excl_scan(long long v, long long& excl, long long* sm_warp) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = (lane < kB / 32) ? sm_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kB / 32) sm_warp[lane] = t;
+    }
+    __syncthreads();
+    const long long before = (w > 0) ? sm_warp[w - 1] : 0;
+    const long long total = sm_warp[kB / 32 - 1];
+    excl = before + x - v;
+    __syncthreads();
+    return total;
+}
+
+struct LoadCounts {
+    const int* in;
+    __device__ long long operator()(long long i) const { return in[i]; }
+};
+struct LoadHeads {
+    const unsigned* keys;
+    __device__ long long operator()(long long i) const { return (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0; }
+};
+
+template <class L>
+__global__ void __launch_bounds__(kB) k_scan_reduce(L ld, const long long* n_ptr, long long* partials) {
+    __shared__ long long sm[kB / 32];
+    const long long n = *n_ptr;
+    const long long s = seg_len(n, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
+    long long acc = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += kB) acc += ld(i);
+    long long excl;
+    const long long tot = block_excl_scan(acc, excl, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// exclusive scan of the gridDim-of-the-reduce partials (<= 1024) in one block
+__global__ void __launch_bounds__(1024) k_scan_partials(long long* partials, int G, long long* total) {
+    __shared__ long long sm[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long v = (threadIdx.x < G) ? partials[threadIdx.x] : 0;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = sm[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sm[lane] = t;
+    }
+    __syncthreads();
+    const long long before = (w > 0) ? sm[w - 1] : 0;
+    if (threadIdx.x < G) partials[threadIdx.x] = before + x - v;
+    if (threadIdx.x == 0) *total = sm[31];
+}
+
+template <class L>
+__global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, const long long* partials,
+                                                  int* out) {
+    __shared__ long long sm[kB / 32];
+    const long long n = *n_ptr;
+    const long long s = seg_len(n, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
+    long long carry = partials[blockIdx.x];
+    for (long long base = b0; base < b1; base += kB) {
+        const long long i = base + threadIdx.x;
+        const long long v = (i < b1) ? ld(i) : 0;
+        long long excl;
+        const long long tot = block_excl_scan(v, excl, sm);
+        if (i < b1) out[i] = (int)(carry + excl);
+        carry += tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// radix sort: 8-bit digits, stable, segment per block
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ keys, const long long* n_ptr,
+                                                   int shift, int* __restrict__ hist) {
+    __shared__ int h[256];
+    const long long n = *n_ptr;
+    const long long s = seg_len(n, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long i = b0 + threadIdx.x; i < b1; i += kB) {
+        const unsigned k = keys[i];
+        if (k != FT_SENTINEL) atomicAdd(&h[(k >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];  // digit-major
+}
+
+// exclusive scan of the 256 x G digit-major histogram in one block
+__global__ void __launch_bounds__(1024) k_radix_scan(int* hist, int G, long long* total) {
+    __shared__ long long sm[32];
+    const int N = 256 * G;
+    const int per = (N + 1023) / 1024;
+    const int b0 = threadIdx.x * per, b1 = min(N, b0 + per);
+    long long acc = 0;
+    for (int i = b0; i < b1; i++) acc += hist[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long t = sm[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sm[lane] = t;
+    }
+    __syncthreads();
+    long long run = ((w > 0) ? sm[w - 1] : 0) + x - acc;
+    for (int i = b0; i < b1; i++) {
+        const int v = hist[i];
+        hist[i] = (int)run;
+        run += v;
+    }
+    if (threadIdx.x == 1023) *total = sm[31];
+}
+
+// Stable scatter: each block walks its segment in tiles of 256 keys in order;
+// a key's destination is the digit's offset for this block + the count of the
+// same digit earlier in the segment (earlier tiles, earlier warps, lower lanes).
+__global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
+                                                      unsigned* __restrict__ kout, unsigned* __restrict__ vout,
+                                                      const long long* n_ptr, int shift,
+                                                      const int* __restrict__ hist) {
+    __shared__ int base[256];
+    __shared__ int wcnt[kB / 32][256];
+    const long long n = *n_ptr;
+    const long long s = seg_len(n, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    base[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+    for (long long t0 = b0; t0 < b1; t0 += kB) {
+        for (int d = 0; d < kB / 32; d++) wcnt[d][threadIdx.x] = 0;
+        __syncthreads();
+        const long long i = t0 + threadIdx.x;
+        unsigned k = FT_SENTINEL, v = 0;
+        if (i < b1) {
+            k = kin[i];
+            v = vin[i];
+        }
+        const bool valid = (k != FT_SENTINEL);
+        const unsigned dig = valid ? ((k >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[w][dig] = __popc(peers);
+        __syncthreads();
+        // per digit: exclusive prefix over warps (thread = digit)
+        {
+            int run = 0;
+            for (int d = 0; d < kB / 32; d++) {
+                const int c = wcnt[d][threadIdx.x];
+                wcnt[d][threadIdx.x] = run;
+                run += c;
+            }
+            // the total of this tile for the digit is `run`
+            __syncthreads();
+            if (valid) {
+                const int dst = base[dig] + wcnt[w][dig] + rank;
+                kout[dst] = k;
+                vout[dst] = v;
+            }
+            __syncthreads();
+            base[threadIdx.x] += run;
+        }
+        __syncthreads();
+    }
+}
+
+// run-length encoding of the sorted keys: cells[m], cell_off[m], idx_map.
+// Writes nothing when M exceeds the capacity (k_cap_cells then resets M).
+__global__ void __launch_bounds__(kB) k_rle(const unsigned* __restrict__ keys, const int* __restrict__ head_idx,
+                                            unsigned* __restrict__ cells, int* __restrict__ cell_off,
+                                            int* __restrict__ idx_map, long long max_cells, const ft_counters* ctr) {
+    const long long P = ctr->P;
+    const long long M = ctr->M;  // computed by the head scan
+    if (M > max_cells) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cell_off[M] = (int)P;
+    for (long long q = (long long)blockIdx.x * kB + threadIdx.x; q < P; q += (long long)gridDim.x * kB) {
+        const unsigned k = keys[q];
+        if (q == 0 || keys[q - 1] != k) {
+            const int m = head_idx[q];
+            cells[m] = k;
+            cell_off[m] = (int)q;
+            idx_map[k] = m;
+        }
+    }
+}
+
+__global__ void k_cap_cells(long long max_cells, ft_counters* ctr) {
+    if (ctr->M > max_cells) {
+        ft_flag(ctr, FT_ST_CAPACITY);
+        ctr->M = 0;
+        ctr->P = 0;
+    }
+}
+
+// reset the index map entries of the previous bins
+__global__ void __launch_bounds__(kB) k_clear_map(const unsigned* __restrict__ cells, int* __restrict__ idx_map,
+                                                  const ft_counters* ctr) {
+    const long long M = ctr->M;
+    for (long long m = (long long)blockIdx.x * kB + threadIdx.x; m < M; m += (long long)gridDim.x * kB)
+        idx_map[cells[m]] = -1;
+}
+
+__global__ void __launch_bounds__(kB) k_export_pairs(const unsigned* __restrict__ skeys, const unsigned* __restrict__ svals,
+                                                     const int* __restrict__ cand_tri, long long cap,
+                                                     unsigned* __restrict__ keys, int* __restrict__ tris,
+                                                     ft_counters* ctr) {
+    const long long P = ctr->P;
+    if (P > cap && blockIdx.x == 0 && threadIdx.x == 0) ft_flag(ctr, FT_ST_CAPACITY);
+    const long long n = P < cap ? P : cap;
+    for (long long q = (long long)blockIdx.x * kB + threadIdx.x; q < n; q += (long long)gridDim.x * kB) {
+        keys[q] = skeys[q];
+        tris[q] = cand_tri[svals[q]];
+    }
+}
+
+}  // namespace
+
+namespace ft {
+
+cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s) {
+    count_launches(1);
+    k_export_pairs<<<ws->sm_count * 2, kB, 0, s>>>(ws->keys[ws->sorted_buf], ws->vals[ws->sorted_buf], ws->cand_tri,
+                                                   cap, keys, tris, ws->ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n, long long* total,
+                               cudaStream_t s) {
+    const int G = ws->grid_blocks;
+    long long* part = reinterpret_cast<long long*>(ws->partials);
+    LoadCounts ld{in};
+    count_launches(3);
+    k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
+    k_scan_partials<<<1, 1024, 0, s>>>(part, G, total);
+    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, const long long* n,
+                              long long* total, cudaStream_t s) {
+    const int G = ws->grid_blocks;
+    long long* part = reinterpret_cast<long long*>(ws->partials);
+    LoadHeads ld{keys};
+    count_launches(3);
+    k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
+    k_scan_partials<<<1, 1024, 0, s>>>(part, G, total);
+    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
+    const int G = ws->grid_blocks;
+    const int passes = (ws->key_bits + 7) / 8;
+    int src = 0;
+    for (int p = 0; p < passes; p++) {
+        // pass 0 reads the candidates (sentinels dropped) and counts the pairs
+        const long long* n = (p == 0) ? &ws->ctr->C : &ws->ctr->P;
+        long long* tot = (p == 0) ? &ws->ctr->P : &ws->ctr->pad2;
+        count_launches(3);
+        k_radix_hist<<<G, kB, 0, s>>>(ws->keys[src], n, 8 * p, ws->hist);
+        k_radix_scan<<<1, 1024, 0, s>>>(ws->hist, G, tot);
+        k_radix_scatter<<<G, kB, 0, s>>>(ws->keys[src], ws->vals[src], ws->keys[src ^ 1], ws->vals[src ^ 1], n,
+                                         8 * p, ws->hist);
+        src ^= 1;
+    }
+    ws->sorted_buf = src;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rle(ft_workspace* ws, cudaStream_t s) {
+    const unsigned* keys = ws->keys[ws->sorted_buf];
+    cudaError_t e = launch_scan_heads(ws, keys, ws->heads, &ws->ctr->P, &ws->ctr->M, s);
+    if (e != cudaSuccess) return e;
+    count_launches(2);
+    k_rle<<<ws->sm_count * 2, kB, 0, s>>>(keys, ws->heads, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
+                                          ws->ctr);
+    k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_map(ft_workspace* ws, cudaStream_t s) {
+    count_launches(1);
+    k_clear_map<<<ws->sm_count * 2, kB, 0, s>>>(ws->cells, ws->idx_map, ws->ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace ft

@@ -1,0 +1,212 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Bins, the interfacial-cell set and the parity fill must match bit for bit;
+floats within: |d alpha| <= 1e-12, |d kappa| <= 1e-9 max(|kappa|, 1),
+|d normal| <= 1e-9, |d S| <= 1e-9 max|S|, |d u| <= 1e-12 max|U|.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_06932_gb300 import inputs as I
+from gpucase import run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL_ALPHA = 1e-12
+TOL_KAPPA = 1e-9
+TOL_NORMAL = 1e-9
+TOL_FORCE = 1e-9
+TOL_VEL = 1e-12
+
+
+def _rotation(seed):
+    q, _ = np.linalg.qr(I.rng(seed).normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    return q
+
+
+def _box(rotate):
+    g = I.unit_grid(48)
+    L = 20 * g.h
+    v, t = I.box_front((0.5 - L / 2,) * 3, (0.5 + L / 2,) * 3, 40)
+    if rotate:
+        v = (v - 0.5) @ _rotation(5).T + 0.5
+    gen = I.rng(17)
+    faces, _ = I.solid_body_faces(g, np.array([0.5, 0.5, 0.5]), gen)
+    return dict(grid=g, verts=np.ascontiguousarray(v), tris=t, faces=faces)
+
+
+def _general_grid():
+    g = I.Grid((40, 36, 44), (-0.3, 0.2, 0.05), 1.0 / 37)
+    gen = I.rng(31)
+    c = np.array([-0.3 + 20 / 37, 0.2 + 18 / 37, 0.05 + 22 / 37]) + gen.uniform(0, 1 / 37, 3)
+    v, t = I.sh_deformed_front(4, 8.0 / 37, c, gen)
+    faces, _ = I.solid_body_faces(g, c, gen)
+    return dict(grid=g, verts=v, tris=t, faces=faces)
+
+
+CASES = {
+    "droplet_32": lambda: I.laplace_droplet_32(1),
+    "sphere_36_ragged": lambda: I.small_sphere(3, 0.3, 36, seed=4, noise_h=1e-3),
+    "sh_droplet_40": lambda: I.sh_droplet_256(seed=9, s=4, N=40),
+    "bubble_40": lambda: I.sh_droplet_256(seed=10, bubble=True, s=4, N=40),
+    "box_in_grid_planes": lambda: _box(False),
+    "box_rotated": lambda: _box(True),
+    "general_grid": _general_grid,
+}
+
+
+def _dump(name, gpu, orc):
+    import os
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    os.makedirs(d, exist_ok=True)
+    arrs = {}
+    for tag, r in (("gpu", gpu), ("orc", orc)):
+        for k, v in r.items():
+            if isinstance(v, np.ndarray):
+                arrs[f"{tag}_{k}"] = v
+    np.savez_compressed(os.path.join(d, f"fail_{name}.npz"), **arrs)
+
+
+def compare(gpu, orc, full=True, name=None):
+    try:
+        _compare(gpu, orc, full)
+    except AssertionError:
+        if name:
+            _dump(name, gpu, orc)
+        raise
+
+
+def _compare(gpu, orc, full=True):
+    assert gpu["status"] == 0, gpu["status"]
+    assert orc["status"] == 0
+    # bins: bit-exact pairs and interfacial set
+    assert np.array_equal(gpu["pair_keys"], orc["pair_keys"])
+    assert np.array_equal(gpu["pair_tris"], orc["pair_tris"])
+    assert np.array_equal(gpu["cell_keys"], orc["cells"])
+    # alpha: parity fill bit-exact, cut cells within 1e-12
+    ga, oa = gpu["alpha"], orc["alpha"]
+    inter = np.zeros(ga.size, bool)
+    inter[orc["cells"]] = True
+    assert np.array_equal(ga.reshape(-1)[~inter], oa.reshape(-1)[~inter])
+    assert np.max(np.abs(ga - oa)) <= TOL_ALPHA
+    if not full:
+        return
+    # kappa, normal, coefficients, fit status
+    k, ko = gpu["kappa"], orc["kappa"]
+    assert np.all(np.abs(k - ko) <= TOL_KAPPA * np.maximum(np.abs(ko), 1.0))
+    assert np.max(np.abs(gpu["normal"] - orc["normal"])) <= TOL_NORMAL
+    assert np.all(np.abs(gpu["coeffs"] - orc["coeffs"]) <= 1e-9 * np.maximum(np.abs(orc["coeffs"]), 1.0))
+    assert np.array_equal(gpu["fit_status"], orc["fit_status"])
+    # CSF force
+    fo = orc["force"]
+    assert np.max(np.abs(gpu["force"] - fo)) <= TOL_FORCE * max(np.abs(fo).max(), 1e-300)
+    # vertex velocities
+    if "vel" in orc:
+        umax = max(np.abs(f).max() for f in orc_faces(orc))
+        assert np.max(np.abs(gpu["vel"] - orc["vel"])) <= TOL_VEL * umax
+
+
+def orc_faces(orc):
+    return orc["_faces"]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_parity_small_cases(name):
+    w = CASES[name]()
+    gpu = run_gpu(w)
+    orc = run_oracle(w)
+    orc["_faces"] = w["faces"]
+    compare(gpu, orc, name=name)
+
+
+@pytest.mark.parametrize("make", [I.rough_sphere_128, I.ellipsoid_128], ids=["rough_sphere_128", "ellipsoid_128"])
+def test_parity_128(make):
+    """The 128^3 workloads (81,920 triangles) in full."""
+    w = make()
+    gpu = run_gpu(w)
+    orc = run_oracle(w)
+    orc["_faces"] = w["faces"]
+    compare(gpu, orc)
+
+
+@pytest.mark.parametrize("bubble", [False, True], ids=["sh_droplet_256", "bubble_256"])
+def test_parity_256_sampled(bubble):
+    """The 256^3 workloads (327,680 triangles): bins and alpha in full, PPIC on
+    a sample of 2,000 cells, velocities at every vertex."""
+    w = I.sh_droplet_256(seed=4, bubble=bubble)
+    gpu = run_gpu(w)
+    orc = run_oracle(w, need=("alpha", "interp"))
+    orc["_faces"] = w["faces"]
+    compare(gpu, orc, full=False)
+    sel = np.sort(I.rng(3).choice(len(orc["cells"]), size=2000, replace=False))
+    cells = orc["cells"][sel]
+    ko, no, co, so = oracle.ppic(w["verts"], w["tris"], w["grid"], cells)
+    assert np.all(np.abs(gpu["kappa"][sel] - ko) <= TOL_KAPPA * np.maximum(np.abs(ko), 1.0))
+    assert np.max(np.abs(gpu["normal"][sel] - no)) <= TOL_NORMAL
+    assert np.array_equal(gpu["fit_status"][sel], so)
+    umax = max(np.abs(f).max() for f in w["faces"])
+    assert np.max(np.abs(gpu["vel"] - orc["vel"])) <= TOL_VEL * umax
+
+
+def test_support_growth_parity():
+    """Coarse front with fit_min above the fragment count: delta grows."""
+    w = I.small_sphere(1, 0.25, 32, seed=2)
+    p = dict(fit_min=60)
+    gpu = run_gpu(w, params=p, max_cand=200000)
+    orc = run_oracle(w, params=p)
+    orc["_faces"] = w["faces"]
+    assert np.mean((gpu["fit_status"] & 1) != 0) > 0.5
+    compare(gpu, orc, name="growth")
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_front():
+    g = I.unit_grid(16)
+    w = dict(grid=g, verts=np.zeros((0, 3)), tris=np.zeros((0, 3), np.int32))
+    gpu = run_gpu(w)
+    assert gpu["status"] == 0
+    assert gpu["counts"]["M"] == 0 and gpu["counts"]["P"] == 0
+    assert np.all(gpu["alpha"] == 0.0) and np.all(gpu["force"] == 0.0)
+
+
+def test_outside_grid_flagged():
+    w = I.laplace_droplet_32(1)
+    w["verts"] = w["verts"] + np.array([0.3, 0.0, 0.0])
+    gpu = run_gpu(w)
+    assert gpu["status"] & 0x02
+
+
+def test_open_front_flagged():
+    w = I.laplace_droplet_32(2)
+    w["tris"] = np.ascontiguousarray(np.delete(w["tris"], 17, axis=0))
+    gpu = run_gpu(w)
+    assert gpu["status"] & 0x04
+
+
+def test_inverted_front_flagged():
+    w = I.laplace_droplet_32(2)
+    w["tris"] = np.ascontiguousarray(w["tris"][:, ::-1])
+    gpu = run_gpu(w)
+    assert gpu["status"] & 0x08
+
+
+def test_bad_vertex_index_flagged():
+    w = I.laplace_droplet_32(2)
+    t = w["tris"].copy()
+    t[5, 1] = len(w["verts"]) + 7
+    w["tris"] = t
+    gpu = run_gpu(w)
+    assert gpu["status"] & 0x10
+
+
+def test_capacity_overflow_flagged_not_faulting():
+    w = I.laplace_droplet_32(3)
+    gpu = run_gpu(w, max_cand=1000)
+    assert gpu["status"] & 0x01
+    assert gpu["counts"]["C_need"] > 1000 and gpu["counts"]["M"] == 0
