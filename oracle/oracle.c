@@ -456,13 +456,13 @@ double og_wendland_weight(double q) { return og_wendland(q); }
  * the tangents open (the fit is isotropic in (t1, t2)); this reading applies
  * the branchless construction of Duff et al. 2017 ("Building an orthonormal
  * basis, revisited") to m = R n in a fixed rotated reference frame R, whose
- * third row is (1,2,3)/sqrt(14), and rotates the tangents back.  Duff's
+ * third row is (sin 1 cos 1, sin 1 sin 1, cos 1), and rotates the tangents back.  Duff's
  * construction switches with sign(m_z); in the rotated frame that switch no
  * longer falls on fronts with an exactly vertical normal (n_z = 0), which
  * axis-aligned or symmetric geometry produces routinely. */
-static const double OG_R[3][3] = {{0.9636241116594316, -0.14824986333222026, -0.22237479499833038},
-                                  {0.0, 0.8320502943378438, -0.5547001962252291},
-                                  {0.2672612419124244, 0.5345224838248488, 0.8017837257372732}};
+static const double OG_R[3][3] = {{0.890670841215793, -0.3614406733922875, -0.2758008198422935},
+                                  {0.0, 0.6066239971779142, -0.7949888842291382},
+                                  {0.4546487134128409, 0.7080734182735712, 0.5403023058681398}};
 
 static void og_basis(const double* n, double* t1, double* t2) {
     double m[3], u1[3], u2[3];

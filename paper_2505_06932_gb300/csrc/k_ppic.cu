@@ -27,12 +27,13 @@ struct PpicArgs {
 
 // Tangents (t1, t2) completing the unit normal n: the branchless basis of Duff
 // et al. 2017 ("Building an orthonormal basis, revisited") built for m = R n in
-// a fixed rotated reference frame (third row of R: (1,2,3)/sqrt(14)) and rotated
+// a fixed rotated reference frame (third row of R: (sin 1 cos 1, sin 1 sin 1, cos 1), a
+// direction with no small-integer relation to axes or symmetric fronts) and rotated
 // back, so that the basis' switch on sign(m_z) does not fall on fronts with an
 // exactly vertical normal.
-__constant__ double kFrameR[3][3] = {{0.9636241116594316, -0.14824986333222026, -0.22237479499833038},
-                                     {0.0, 0.8320502943378438, -0.5547001962252291},
-                                     {0.2672612419124244, 0.5345224838248488, 0.8017837257372732}};
+__constant__ double kFrameR[3][3] = {{0.890670841215793, -0.3614406733922875, -0.2758008198422935},
+                                     {0.0, 0.6066239971779142, -0.7949888842291382},
+                                     {0.4546487134128409, 0.7080734182735712, 0.5403023058681398}};
 
 __device__ __forceinline__ void basis(const double n[3], double t1[3], double t2[3]) {
     double m[3], u1[3], u2[3];
