@@ -180,6 +180,39 @@ int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, c
 int front_interp_velocity(const ft_grid* g, const double* U, const double* V, const double* W,
                           const double* verts, int64_t nv, double* vel, void* stream);
 
+/* Allocation-free volume fraction (no counterpart in the paper).
+ *
+ * Some callers cannot allocate device memory while they run: a flow solver
+ * that owns all GPU memory through its own pool and fixes its budget before
+ * time stepping, a process under a hard per-process memory limit, or a time
+ * loop that cannot afford cudaMalloc's implicit device-wide synchronization.
+ * For them this call bins the front and writes its volume fraction (the same
+ * result as front_bin followed by front_volume_fraction) using only scratch
+ * that the library holds in one static device array of
+ * FT_NOALLOC_SCRATCH_BYTES, reserved on every device that loads the library
+ * until the process exits.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * Arguments: grid g and front f as for front_bin (device verts/tris), method
+ * parameters p (delta_max_h sets the grid margin), alpha (device, n0*n1*n2
+ * float64, by key) and status (device, one uint32 that receives the FT_ST_*
+ * bits of this call).  Runs on the current device and `stream`.
+ * Limits: n0*n1*n2 <= FT_NOALLOC_MAX_GRID_CELLS and nt <= FT_NOALLOC_MAX_TRIANGLES,
+ * else FT_ERR_CAPACITY is returned before any work; more than
+ * FT_NOALLOC_MAX_CANDIDATES (triangle, candidate cell) pairs or interfacial
+ * cells sets FT_ST_CAPACITY in *status and alpha is not valid.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call shares
+ * the one array and resets the parts that must start cleared, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller. */
+#define FT_NOALLOC_SCRATCH_BYTES 7340032
+#define FT_NOALLOC_MAX_GRID_CELLS 262144
+#define FT_NOALLOC_MAX_TRIANGLES 16384
+#define FT_NOALLOC_MAX_CANDIDATES 32768
+int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, const ft_params* p, double* alpha,
+                               uint32_t* status, void* stream);
+
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all workspaces). */
 int64_t ft_launch_count(void);

@@ -65,6 +65,7 @@ def lib():
                 "front_interp_velocity": (I32, [P, P, P, P, P, I64, P, P]),
                 "ft_probe_fma_rate": (I32, [I32, I32, C.POINTER(C.c_double)]),
                 "ft_launch_count": (I64, []),
+                "ft_volume_fraction_noalloc": (I32, [P, P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -203,6 +204,18 @@ def front_interp_velocity(grid, U, V, W, verts, vel, stream=None):
                                        _ptr(W, torch.float64, "W"), _ptr(verts, torch.float64, "verts"),
                                        verts.shape[0], _ptr(vel, torch.float64, "vel"), _stream(stream)),
            "front_interp_velocity")
+
+
+def ft_volume_fraction_noalloc(grid, verts, tris, params: FtParams, alpha, status, stream=None):
+    """Binning + volume fraction with the library's static scratch (no device
+    allocation); status is a 1-element int32 CUDA tensor receiving FT_ST_* bits."""
+    if alpha.numel() != grid.ncells or status.numel() < 1:
+        raise FrontError("alpha must hold n0*n1*n2 values and status one word")
+    g = make_grid(grid)
+    f = FtFront(_ptr(verts, torch.float64, "verts"), verts.shape[0], _ptr(tris, torch.int32, "tris"), tris.shape[0])
+    _check(lib().ft_volume_fraction_noalloc(C.byref(g), C.byref(f), C.byref(params),
+                                            _ptr(alpha, torch.float64, "alpha"), _ptr(status, torch.int32, "status"),
+                                            _stream(stream)), "ft_volume_fraction_noalloc")
 
 
 def launch_count() -> int:
