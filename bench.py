@@ -42,8 +42,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32c"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32c"], default="fp32c")
+    ap.add_argument("--alt-steps", type=int, default=30, help="steps timed for the other precision (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time eager launches instead of one CUDA graph per step")
+    ap.add_argument("--phase-steps", type=int, default=20, help="eager steps timed per phase")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -161,6 +165,9 @@ def cpu_baseline(fronts, budget_s=20.0):
                        f"{S} of its cells ({t4 - t3:.2f} s); cells/s = 1 / per-cell time"), (t0, t1, t2, M, S)
 
 
+PHASES = ("bin", "alpha", "ppic", "csf", "interp")
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -171,82 +178,147 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     fronts = workload()
     prec = F.FT_FP64 if a.precision == "fp64" else F.FT_FP32C
-    prm = F.make_params(precision=prec)
-    dfr, fcs = [], []
+    dfr = []
     for w in fronts:
         v = torch.from_numpy(w["verts"]).to(dev)
         t = torch.from_numpy(w["tris"]).to(dev)
         fa = [torch.from_numpy(f).to(dev) for f in w["faces"]]
         dfr.append((v, t, fa))
-        fcs.append(F.FrontCoupling(w["grid"], t.shape[0], v.shape[0], params=prm, device=local))
     stream = torch.cuda.current_stream()
-
-    def step(ppic_ev=None):
-        for (v, t, fa), fc in zip(dfr, fcs):
-            F.front_bin(fc.ws, v, t, prm)
-            F.front_volume_fraction(fc.ws, fc.alpha)
-            if ppic_ev is not None:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
-            if ppic_ev is not None:
-                e1.record(stream)
-                ppic_ev.append((e0, e1))
-            F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
-            F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
-
-    for _ in range(max(3, a.warmup)):
-        step()
-    torch.cuda.synchronize()
-    counts = [fc.ws.counts() for fc in fcs]
-    status = [fc.ws.status() for fc in fcs]
-    if any(status):
-        raise RuntimeError(f"device status after warm-up: {[F.status_names(s) for s in status]}")
-    cells_per_step = sum(c["M"] for c in counts)
-    fit_pairs = [c["fit_pairs"] for c in counts]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
-    clocks = Clocks(local)
-    barrier(ws)
-    torch.cuda.synchronize()
-    launches0 = F.launch_count()
-    evs, ppic_ev = [], []
-    for _ in range(a.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(ppic_ev)
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
-    barrier(ws)
-    launches = F.launch_count() - launches0
-    clk = clocks.stop()
-    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
-    ppic_ms = [e0.elapsed_time(e1) for e0, e1 in ppic_ev]
-    tmax = allmax(ws, total_ms)
-    all_cells = allsum(ws, cells_per_step * a.steps)
-    value = all_cells / (tmax * 1e-3)
+    def make(precision):
+        prm = F.make_params(precision=precision)
+        fcs = [F.FrontCoupling(w["grid"], w["tris"].shape[0], w["verts"].shape[0], params=prm, device=local)
+               for w in fronts]
+        return prm, fcs
 
-    # roofline of the dominant kernel (PPIC), ALU-bound
-    nf = len(fcs)
+    def step_one(prm, fc, v, t, fa, ev=None):
+        calls = (lambda: F.front_bin(fc.ws, v, t, prm),
+                 lambda: F.front_volume_fraction(fc.ws, fc.alpha),
+                 lambda: F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs,
+                                                fc.fit_status),
+                 lambda: F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force),
+                 lambda: F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]]))
+        for name, call in zip(PHASES, calls):
+            if ev is not None:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(torch.cuda.current_stream())
+                call()
+                e1.record(torch.cuda.current_stream())
+                ev[name].append((e0, e1))
+            else:
+                call()
+
+    def step(prm, fcs, ev=None):
+        for (v, t, fa), fc in zip(dfr, fcs):
+            step_one(prm, fc, v, t, fa, ev)
+
+    def capture(prm, fcs):
+        """One CUDA graph for a whole step; the fronts are independent, so each
+        runs on its own stream forked from (and joined back to) the capture stream."""
+        g = torch.cuda.CUDAGraph()
+        sides = [torch.cuda.Stream(device=dev) for _ in fcs]
+        with torch.cuda.graph(g):
+            cs = torch.cuda.current_stream()
+            for sd in sides:
+                sd.wait_stream(cs)
+            for (v, t, fa), fc, sd in zip(dfr, fcs, sides):
+                with torch.cuda.stream(sd):
+                    step_one(prm, fc, v, t, fa)
+            for sd in sides:
+                cs.wait_stream(sd)
+        return g
+
+    def measure(precision, steps, warmup, clocks=False):
+        prm, fcs = make(precision)
+        for _ in range(max(3, warmup)):
+            step(prm, fcs)
+        torch.cuda.synchronize()
+        counts = [fc.ws.counts() for fc in fcs]
+        status = [fc.ws.status() for fc in fcs]
+        if any(status):
+            raise RuntimeError(f"device status after warm-up: {[F.status_names(x) for x in status]}")
+        # eager steps with an event pair around every call: the per-phase breakdown
+        ph = {n: [] for n in PHASES}
+        l0 = F.launch_count()
+        for _ in range(a.phase_steps):
+            flush.zero_()
+            step(prm, fcs, ph)
+        torch.cuda.synchronize()
+        kernels_per_step = (F.launch_count() - l0) / max(1, a.phase_steps)
+        phase_ms = {n: sum(e0.elapsed_time(e1) for e0, e1 in ph[n]) / max(1, a.phase_steps) for n in PHASES}
+        ppic_ms_eager = [e0.elapsed_time(e1) for e0, e1 in ph["ppic"]]
+        graph = None if a.no_graph else capture(prm, fcs)
+        if graph is not None:
+            graph.replay()
+            torch.cuda.synchronize()
+            if any(fc.ws.status() for fc in fcs):
+                raise RuntimeError("device status after graph replay")
+        clk = Clocks(local) if clocks else None
+        barrier(ws)
+        torch.cuda.synchronize()
+        l0 = F.launch_count()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                step(prm, fcs)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier(ws)
+        launches = (kernels_per_step * steps) if graph is not None else (F.launch_count() - l0)
+        clk = clk.stop() if clk else None
+        total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        return dict(prm=prm, fcs=fcs, counts=counts, total_ms=total_ms, phase_ms=phase_ms,
+                    ppic_ms=ppic_ms_eager, launches=launches, clocks=clk, graph=graph)
+
+    r = measure(prec, a.steps, a.warmup, clocks=True)
+    counts = r["counts"]
+    cells_per_step = sum(c["M"] for c in counts)
+    fit_pairs = [c["fit_pairs"] for c in counts]
+    tmax = allmax(ws, r["total_ms"])
+    value = allsum(ws, cells_per_step * a.steps) / (tmax * 1e-3)
+
+    # roofline of the fit (k_ppic_acc + k_ppic_solve), ALU-bound
+    nf = len(fronts)
     flops = [FLOPS_PER_FIT_PAIR * fit_pairs[i] + FLOPS_PER_FIT_SOLVE * counts[i]["M"] for i in range(nf)]
+    ppic_ms = r["ppic_ms"]
     ach = sum(flops[i % nf] for i in range(len(ppic_ms))) / (sum(ppic_ms) * 1e-3) / 1e12
     peak = FP64_PEAK_TFLOPS if prec == F.FT_FP64 else FP32_PEAK_TFLOPS
-    probe = None
     try:
         probe = F.probe_fma_rate(0 if prec == F.FT_FP64 else 1, local) / 1e12
     except Exception:
         probe = None
-    roof = {"kernel": "k_ppic", "bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
-            "frac": round(ach / peak, 4), "traffic": None,
+    roof = {"kernel": "k_ppic_acc + k_ppic_solve", "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
             "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if prec == F.FT_FP64
-            else "152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz",
+            else "152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz (recipe unit counts and clock)",
             "probe_measured_peak": round(probe, 4) if probe else None,
-            "share_of_step": round(sum(ppic_ms) / total_ms, 4),
+            "share_of_step": round(r["phase_ms"]["ppic"] / sum(r["phase_ms"].values()), 4),
+            "timing": "CUDA events around front_curvature_ppic in eager steps",
             "flops_model": f"{FLOPS_PER_FIT_PAIR:.0f} per fit pair + {FLOPS_PER_FIT_SOLVE:.0f} per cell"}
+    phases = {n: round(v, 4) for n, v in r["phase_ms"].items()}
+
+    alt = None
+    if a.alt_steps > 0:
+        other = F.FT_FP64 if prec == F.FT_FP32C else F.FT_FP32C
+        ra = measure(other, a.alt_steps, 3)
+        ta = allmax(ws, ra["total_ms"])
+        alt = {"precision": "fp64" if other == F.FT_FP64 else "fp32c", "steps": a.alt_steps,
+               "value": round(allsum(ws, cells_per_step * a.alt_steps) / (ta * 1e-3), 1),
+               "ms_per_step": round(ta / a.alt_steps, 4),
+               "phases_ms": {n: round(v, 4) for n, v in ra["phase_ms"].items()}}
+        for fc in ra["fcs"]:
+            fc.ws.close()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    prm, fcs = r["prm"], r["fcs"]
     hin = []
     for w in fronts:
         hv = torch.from_numpy(w["verts"]).pin_memory()
@@ -302,13 +374,20 @@ def run_ours(a):
         "config": {"workload": "rough icosphere s6 R0.2 + ellipsoid (0.3,0.2,0.15), 128^3 grid, 81,920 tris each",
                    "fronts": [w["name"] for w in fronts], "cells_per_step": cells_per_step,
                    "pairs_per_step": sum(c["P"] for c in counts), "fit_pairs_per_step": sum(fit_pairs),
-                   "precision": a.precision, "l2": "flushed (512 MB write) before every timed step",
+                   "precision": a.precision,
+                   "stated_error": "FP32 form: |d alpha| <= 1e-6, |d kappa| <= 1e-4 rel. vs the FP64 oracle; "
+                                   "FP64 path: 1e-12 / 1e-9 (checked by tests/test_gpu_parity.py)",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "launch": "eager" if a.no_graph else "one CUDA graph per step, the two fronts on two streams",
                    "parallelism": f"replicas x{ws}"},
+        "phases_ms": phases,
+        "phases_note": "eager per-call CUDA-event times per step (sum over fronts), not the graph replay",
         "roofline": roof,
+        "alt_precision": alt,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps},
-        "gpu_launches": int(launches),
-        "clocks": clk,
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
     }
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cb, _ = cpu_baseline(fronts)

@@ -61,7 +61,7 @@ typedef struct {
 typedef struct {
     double delta_h;      /* initial Wendland support radius / h (paper: 2.5)     */
     double delta_growth; /* support growth factor while too few fragments (1.25) */
-    double delta_max_h;  /* largest support radius / h (4.0)                     */
+    double delta_max_h;  /* largest support radius / h (4.0; at most 7.0)        */
     double sigma;        /* surface tension coefficient of Eq. csf (1.0)         */
     int32_t fit_min;     /* minimum fragments with non-zero weight (paper: 24)   */
     int32_t precision;   /* FT_FP64 (plain) or FT_FP32C (FP32 + compensation)    */

@@ -30,7 +30,7 @@ bool grid_ok(const ft_grid* g) {
 }
 
 bool params_ok(const ft_params* p) {
-    return p && p->delta_h > 0.0 && p->delta_max_h >= p->delta_h && p->delta_max_h <= 64.0 &&
+    return p && p->delta_h > 0.0 && p->delta_max_h >= p->delta_h && p->delta_max_h <= 7.0 &&
            p->delta_growth > 1.0 && p->fit_min >= 0 && (p->precision == FT_FP64 || p->precision == FT_FP32C) &&
            isfinite(p->sigma);
 }
@@ -46,7 +46,8 @@ cudaError_t alloc(T** p, size_t n, size_t* total) {
 void release(ft_workspace* ws) {
     void* ptrs[] = {ws->ctr,     ws->idx_map, ws->tri_cnt,  ws->tri_off,  ws->tri_box, ws->cand_tri,
                     ws->keys[0], ws->keys[1], ws->vals[0],  ws->vals[1],  ws->rec,     ws->cells,
-                    ws->cell_off, ws->heads,  ws->cell_L,   ws->cell_P,   ws->partials, ws->hist};
+                    ws->cell_off, ws->heads,  ws->cell_L,   ws->cell_P,   ws->partials, ws->hist,
+                    ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -88,7 +89,8 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
         return FT_ERR_ARG;
     }
     cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, device);
-    ws->grid_blocks = ws->sm_count * 2 > 1024 ? 1024 : ws->sm_count * 2;
+    // segments of the scan / sort kernels; the sort stages 256 x grid_blocks counts in shared memory
+    ws->grid_blocks = ws->sm_count > 192 ? 192 : ws->sm_count;
     int bits = 1;
     while (bits < 32 && ((ws->ncells - 1) >> bits) > 0) bits++;
     ws->key_bits = bits < 8 ? 8 : bits;
@@ -106,6 +108,10 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
     e = e ? e : alloc(&ws->vals[0], C, &tot);
     e = e ? e : alloc(&ws->vals[1], C, &tot);
     e = e ? e : alloc(&ws->rec, C, &tot);
+    e = e ? e : alloc(&ws->rec32, C, &tot);
+    e = e ? e : alloc(&ws->cen32, C, &tot);
+    e = e ? e : alloc(&ws->sys, Mx, &tot);
+    e = e ? e : alloc(&ws->fit_info, 2 * Mx, &tot);
     e = e ? e : alloc(&ws->cells, Mx + 1, &tot);
     e = e ? e : alloc(&ws->cell_off, Mx + 1, &tot);
     e = e ? e : alloc(&ws->heads, C, &tot);
@@ -113,6 +119,7 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
     e = e ? e : alloc(&ws->cell_P, Mx, &tot);
     e = e ? e : alloc(&ws->partials, 2 * (size_t)(ws->grid_blocks + 1), &tot);
     e = e ? e : alloc(&ws->hist, 256 * (size_t)ws->grid_blocks, &tot);
+    if (e == cudaSuccess) e = ft::prepare_sort(ws->grid_blocks);
     if (e == cudaSuccess) e = cudaMemset(ws->ctr, 0, sizeof(ft_counters));
     if (e == cudaSuccess) e = cudaMemset(ws->idx_map, 0xff, sizeof(int) * (size_t)ws->ncells);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -179,7 +186,6 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     if (e == cudaSuccess) e = ft::launch_sort(ws, s);
     if (e == cudaSuccess) e = ft::launch_rle(ws, s);
     ws->binned = (e == cudaSuccess);
-    ws->last_precision = p->precision;
     return cuda_err(e);
 }
 

@@ -31,6 +31,21 @@ struct __align__(16) ft_frag {
     double k[6];
 };
 
+// The same record in float32 (the FP32-compensated form), 48 B.
+struct __align__(16) ft_frag32 {
+    float an[3];
+    float c[3];
+    float k[6];
+};
+
+// Per interfacial cell, the volume-fit normal equations left by the
+// accumulation kernel for the solve kernel: packed upper triangle of the 6x6
+// matrix (21), right-hand side (6), frame normal (3) -- as doubles (FP64) or as
+// hi/lo float pairs (FP32 form, 2 x 30 floats in the same 240 bytes).
+struct __align__(16) ft_cellsys {
+    double v[30];
+};
+
 struct ft_workspace {
     int device;
     int sm_count;
@@ -51,7 +66,11 @@ struct ft_workspace {
     int* cand_tri;         // max_cand
     unsigned* keys[2];     // max_cand
     unsigned* vals[2];     // max_cand
-    ft_frag* rec;          // max_cand
+    ft_frag* rec;          // max_cand (FP64 records)
+    ft_frag32* rec32;      // max_cand (FP32 records)
+    float4* cen32;         // max_cand: float copy of the FP64 centroids (support filter)
+    ft_cellsys* sys;       // max_cells: normal equations per cell
+    int* fit_info;         // max_cells x 2: fragments in support, status bits
     unsigned* cells;       // max_cells + 1
     int* cell_off;         // max_cells + 1
     int* heads;            // max_cand: cell index of each sorted pair (scan output)
@@ -73,6 +92,7 @@ cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const 
 cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, const long long* n,
                               long long* total, cudaStream_t s);
 cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s);
+cudaError_t prepare_sort(int grid_blocks);
 cudaError_t launch_rle(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_clear_map(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s);

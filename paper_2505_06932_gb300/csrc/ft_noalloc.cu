@@ -14,7 +14,7 @@ constexpr long long kMaxCells = FT_NOALLOC_MAX_GRID_CELLS;
 constexpr long long kMaxNt = FT_NOALLOC_MAX_TRIANGLES;
 constexpr long long kMaxCand = FT_NOALLOC_MAX_CANDIDATES;
 constexpr long long kMaxIcells = FT_NOALLOC_MAX_CANDIDATES;
-constexpr int kBlocks = 256;  // segments of the scan / sort kernels
+constexpr int kBlocks = 32;  // segments of the scan / sort kernels (histogram scan fits 48 KB of shared memory)
 
 constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -75,7 +75,7 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
         if (g->n[d] < 1 || !isfinite(g->origin[d])) return FT_ERR_ARG;
     if (!(g->h > 0.0) || !isfinite(g->h) || f->nt < 0 || f->nv < 0) return FT_ERR_ARG;
     if (f->nt > 0 && (!f->verts || !f->tris)) return FT_ERR_ARG;
-    if (!(p->delta_max_h >= 0.0) || p->delta_max_h > 64.0) return FT_ERR_ARG;
+    if (!(p->delta_max_h >= 0.0) || p->delta_max_h > 7.0) return FT_ERR_ARG;
     const long long ncells = (long long)g->n[0] * g->n[1] * g->n[2];
     if (ncells > kMaxCells || f->nt > kMaxNt) return FT_ERR_CAPACITY;  // beyond the static scratch
 

@@ -42,11 +42,58 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells(const int* __restrict_
     }
 }
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// FP32 form: float fragment terms, combined over the warp with compensated
+// (two-sum) accumulation, so each cell's L and P keep float64-like accuracy
+__global__ void __launch_bounds__(kThreads) k_alpha_cells32(const int* __restrict__ cell_off,
+                                                            const unsigned* __restrict__ vals,
+                                                            const ft_frag32* __restrict__ rec,
+                                                            double* __restrict__ cell_L, double* __restrict__ cell_P,
+                                                            const ft_counters* ctr) {
+    const long long M = ctr->M;
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * kWarps;
+    for (long long m = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); m < M; m += nw) {
+        const int q0 = cell_off[m], q1 = cell_off[m + 1];
+        float Lh = 0.f, Ll = 0.f, Ph = 0.f, Pl = 0.f;
+        for (int q = q0 + lane; q < q1; q += 32) {
+            const ft_frag32* f = rec + vals[q];
+            const float az = f->an[2];
+            float s, e;
+            two_sum(Lh, az * (f->c[2] + 0.5f), s, e);
+            Lh = s;
+            Ll += e;
+            two_sum(Ph, az, s, e);
+            Ph = s;
+            Pl += e;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float s, e;
+            two_sum(Lh, __shfl_xor_sync(0xffffffffu, Lh, o), s, e);
+            Ll += __shfl_xor_sync(0xffffffffu, Ll, o) + e;
+            Lh = s;
+            two_sum(Ph, __shfl_xor_sync(0xffffffffu, Ph, o), s, e);
+            Pl += __shfl_xor_sync(0xffffffffu, Pl, o) + e;
+            Ph = s;
+        }
+        if (lane == 0) {
+            cell_L[m] = (double)Lh + (double)Ll;
+            cell_P[m] = (double)Ph + (double)Pl;
+        }
+    }
+}
+
 // one warp per (i, j) column, walking k downwards in chunks of 32 cells
 __global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* __restrict__ idx_map,
                                                          const double* __restrict__ cell_L,
                                                          const double* __restrict__ cell_P, double* __restrict__ alpha,
-                                                         ft_counters* ctr) {
+                                                         double closure_tol, ft_counters* ctr) {
     const int lane = threadIdx.x & 31;
     const long long ncol = (long long)g.n[0] * g.n[1];
     const int n2 = g.n[2];
@@ -59,6 +106,23 @@ __global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* _
             const int k = k0 + lane;
             const bool valid = k < n2;
             const int m = valid ? idx_map[base + k] : -1;
+            if (__ballot_sync(0xffffffffu, m >= 0) == 0u) {
+                // no interfacial cell in this chunk: every cell takes the parity above it
+                const long long cb = __double_as_longlong(carry);
+                double r;
+                if (cb == __double_as_longlong(0.0) || cb == __double_as_longlong(1.0)) {
+                    r = carry;  // already exact: no float64 arithmetic needed
+                } else {
+                    r = rint(carry);
+                    if (fabs(carry - r) > closure_tol) err |= FT_ST_NOT_CLOSED;
+                    if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
+                    r = fmin(fmax(r, 0.0), 1.0);
+                    // below a closed stretch of front the parity is exact again
+                    if (fabs(carry - rint(carry)) <= closure_tol) carry = rint(carry);
+                }
+                if (valid) alpha[base + k] = r;
+                continue;
+            }
             const double Pz = (m >= 0) ? cell_P[m] : 0.0;
             const double L = (m >= 0) ? cell_L[m] : 0.0;
             double x = Pz;  // inclusive suffix sum within the chunk
@@ -77,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* _
                     a = L + S;
                 } else {
                     const double r = rint(S);
-                    if (fabs(S - r) > 1e-9) err |= FT_ST_NOT_CLOSED;
+                    if (fabs(S - r) > closure_tol) err |= FT_ST_NOT_CLOSED;
                     if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
                     a = r;
                 }
@@ -95,9 +159,18 @@ namespace ft {
 
 cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s) {
     const unsigned* vals = ws->vals[ws->sorted_buf];
+    const bool fp32 = ws->last_precision == FT_FP32C;
     count_launches(2);
-    k_alpha_cells<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, ws->rec, ws->cell_L, ws->cell_P, ws->ctr);
-    k_alpha_fill<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->g, ws->idx_map, ws->cell_L, ws->cell_P, alpha, ws->ctr);
+    if (fp32)
+        k_alpha_cells32<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, ws->rec32, ws->cell_L, ws->cell_P,
+                                                              ws->ctr);
+    else
+        k_alpha_cells<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, ws->rec, ws->cell_L, ws->cell_P,
+                                                            ws->ctr);
+    // the column parity of a closed front is an integer up to rounding of the fragment terms
+    const double closure_tol = fp32 ? 1e-5 : 1e-9;
+    k_alpha_fill<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->g, ws->idx_map, ws->cell_L, ws->cell_P, alpha,
+                                                       closure_tol, ws->ctr);
     return cudaGetLastError();
 }
 

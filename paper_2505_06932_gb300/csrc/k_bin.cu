@@ -237,11 +237,66 @@ __device__ void frag_moments(const double (*p)[3], int n, const double xc[3], do
     for (int d = 0; d < 3; d++) f.an[d] = an[d];
 }
 
+// The same moments in float32 (the FP32 form): vertex offsets from p0 and the
+// offset of p0 from the cell centre are formed in float64 and rounded once; all
+// products and sums are float32.
+__device__ void frag_moments32(const double (*p)[3], int n, const double xc[3], double inv_h, ft_frag32& f) {
+    float q0[3];
+    for (int d = 0; d < 3; d++) q0[d] = (float)((p[0][d] - xc[d]) * inv_h);
+    float an[3] = {0.f, 0.f, 0.f};
+    float e1[3], e2[3];
+    for (int d = 0; d < 3; d++) e1[d] = (float)((p[1][d] - p[0][d]) * inv_h);
+    for (int m = 1; m + 1 < n; m++) {
+        for (int d = 0; d < 3; d++) e2[d] = (float)((p[m + 1][d] - p[0][d]) * inv_h);
+        an[0] += 0.5f * (e1[1] * e2[2] - e1[2] * e2[1]);
+        an[1] += 0.5f * (e1[2] * e2[0] - e1[0] * e2[2]);
+        an[2] += 0.5f * (e1[0] * e2[1] - e1[1] * e2[0]);
+        for (int d = 0; d < 3; d++) e1[d] = e2[d];
+    }
+    const float A = sqrtf(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
+    float m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
+    if (A > 0.f) {
+        const float nh[3] = {an[0] / A, an[1] / A, an[2] / A};
+        for (int d = 0; d < 3; d++) e1[d] = (float)((p[1][d] - p[0][d]) * inv_h);
+        for (int m = 1; m + 1 < n; m++) {
+            for (int d = 0; d < 3; d++) e2[d] = (float)((p[m + 1][d] - p[0][d]) * inv_h);
+            const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+            const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+            const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+            const float a = 0.5f * (cr0 * nh[0] + cr1 * nh[1] + cr2 * nh[2]);
+            const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+            const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
+            for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
+            m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+            m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+            m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+            m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+            m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+            m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
+            for (int d = 0; d < 3; d++) e1[d] = e2[d];
+        }
+        const float ia = 1.f / A;
+        const float c[3] = {m1[0] * ia, m1[1] * ia, m1[2] * ia};
+        f.k[0] = m2[0] * ia - c[0] * c[0];
+        f.k[1] = m2[1] * ia - c[1] * c[1];
+        f.k[2] = m2[2] * ia - c[2] * c[2];
+        f.k[3] = m2[3] * ia - c[0] * c[1];
+        f.k[4] = m2[4] * ia - c[0] * c[2];
+        f.k[5] = m2[5] * ia - c[1] * c[2];
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d] + c[d];
+    } else {
+        for (int d = 0; d < 6; d++) f.k[d] = 0.f;
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d];
+    }
+    for (int d = 0; d < 3; d++) f.an[d] = an[d];
+}
+
 __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ verts, const int* __restrict__ tris,
                                                    ft_grid g, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
                                                    unsigned* __restrict__ keys, unsigned* __restrict__ vals,
-                                                   ft_frag* __restrict__ rec, const ft_counters* ctr) {
+                                                   ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
+                                                   float4* __restrict__ cen32, int fp32, const ft_counters* ctr) {
     const long long C = ctr->C;
     const double inv_h = 1.0 / g.h;
     for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < C; c += (long long)gridDim.x * kThreads) {
@@ -263,9 +318,16 @@ __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ ve
             key = (unsigned)(((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
             double xc[3];
             for (int d = 0; d < 3; d++) xc[d] = ft_plane(g.origin[d], g.h, idx[d]) + 0.5 * g.h;
-            ft_frag f;
-            frag_moments(poly, n, xc, inv_h, f);
-            rec[c] = f;
+            if (fp32) {
+                ft_frag32 f;
+                frag_moments32(poly, n, xc, inv_h, f);
+                rec32[c] = f;
+            } else {
+                ft_frag f;
+                frag_moments(poly, n, xc, inv_h, f);
+                rec[c] = f;
+                if (cen32) cen32[c] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
+            }
         }
         keys[c] = key;
         vals[c] = (unsigned)c;
@@ -290,8 +352,12 @@ cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, 
     if (e != cudaSuccess) return e;
     count_launches(T > 0 ? 3 : 2);
     k_expand<<<nb ? nb : 1, kThreads, 0, s>>>(ws->tri_cnt, ws->tri_off, T, ws->max_cand, ws->cand_tri, ws->ctr);
+    // the FP32 form needs float records; a workspace without them computes float64 records
+    const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
+    ws->last_precision = fp32 ? FT_FP32C : FT_FP64;
     k_clip<<<ws->sm_count * 4, kThreads, 0, s>>>(f->verts, f->tris, ws->g, ws->cand_tri, ws->tri_off, ws->tri_box,
-                                                ws->keys[0], ws->vals[0], ws->rec, ws->ctr);
+                                                ws->keys[0], ws->vals[0], ws->rec, ws->rec32, ws->cen32, fp32 ? 1 : 0,
+                                                ws->ctr);
     return cudaGetLastError();
 }
 

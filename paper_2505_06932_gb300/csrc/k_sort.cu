@@ -11,7 +11,6 @@
 namespace {
 
 constexpr int kB = 256;             // threads per block
-constexpr int kScanMax = 1024;      // most segments the partial scans take
 
 __device__ __forceinline__ long long seg_len(long long n, int G) {
     long long s = (n + G - 1) / G;
@@ -134,14 +133,22 @@ __global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ 
     hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];  // digit-major
 }
 
-// exclusive scan of the 256 x G digit-major histogram in one block
-__global__ void __launch_bounds__(1024) k_radix_scan(int* hist, int G, long long* total) {
-    __shared__ long long sm[32];
+// Exclusive scan of the 256 x G digit-major histogram in one block: the whole
+// histogram is staged in shared memory with coalesced loads (all in flight at
+// once), each thread scans a contiguous chunk, and a block scan of the chunk
+// totals supplies the offsets.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_radix_scan(int* hist, int G, long long* total) {
+    extern __shared__ int sh[];
+    __shared__ long long wsum[32];
     const int N = 256 * G;
-    const int per = (N + 1023) / 1024;
+    for (int i = threadIdx.x; i < N; i += kScanThreads) sh[i] = hist[i];
+    __syncthreads();
+    const int per = (N + kScanThreads - 1) / kScanThreads;
     const int b0 = threadIdx.x * per, b1 = min(N, b0 + per);
     long long acc = 0;
-    for (int i = b0; i < b1; i++) acc += hist[i];
+    for (int i = b0; i < b1; i++) acc += sh[i];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     long long x = acc;
 #pragma unroll
@@ -149,25 +156,27 @@ __global__ void __launch_bounds__(1024) k_radix_scan(int* hist, int G, long long
         const long long y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) sm[w] = x;
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
     if (w == 0) {
-        long long t = sm[lane];
+        long long t = wsum[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const long long y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
         }
-        sm[lane] = t;
+        wsum[lane] = t;
     }
     __syncthreads();
-    long long run = ((w > 0) ? sm[w - 1] : 0) + x - acc;
+    long long run = ((w > 0) ? wsum[w - 1] : 0) + x - acc;
     for (int i = b0; i < b1; i++) {
-        const int v = hist[i];
-        hist[i] = (int)run;
+        const int v = sh[i];
+        sh[i] = (int)run;
         run += v;
     }
-    if (threadIdx.x == 1023) *total = sm[31];
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += kScanThreads) hist[i] = sh[i];
+    if (threadIdx.x == 0) *total = wsum[31];
 }
 
 // Stable scatter: each block walks its segment in tiles of 256 keys in order;
@@ -305,6 +314,14 @@ cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, 
     return cudaGetLastError();
 }
 
+cudaError_t prepare_sort(int grid_blocks) {
+    // once per workspace, outside any stream capture: the histogram scan stages
+    // 256 x grid_blocks counts in dynamic shared memory
+    const size_t bytes = 256 * (size_t)grid_blocks * sizeof(int);
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_radix_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
     const int G = ws->grid_blocks;
     const int passes = (ws->key_bits + 7) / 8;
@@ -315,7 +332,7 @@ cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
         long long* tot = (p == 0) ? &ws->ctr->P : &ws->ctr->pad2;
         count_launches(3);
         k_radix_hist<<<G, kB, 0, s>>>(ws->keys[src], n, 8 * p, ws->hist);
-        k_radix_scan<<<1, 1024, 0, s>>>(ws->hist, G, tot);
+        k_radix_scan<<<1, kScanThreads, 256 * G * sizeof(int), s>>>(ws->hist, G, tot);
         k_radix_scatter<<<G, kB, 0, s>>>(ws->keys[src], ws->vals[src], ws->keys[src ^ 1], ws->vals[src ^ 1], n,
                                          8 * p, ws->hist);
         src ^= 1;
