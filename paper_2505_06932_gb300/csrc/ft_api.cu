@@ -47,7 +47,7 @@ void release(ft_workspace* ws) {
     void* ptrs[] = {ws->ctr,     ws->idx_map, ws->tri_cnt,  ws->tri_off,  ws->tri_box, ws->cand_tri,
                     ws->keys[0], ws->keys[1], ws->vals[0],  ws->vals[1],  ws->rec,     ws->cells,
                     ws->cell_off, ws->heads,  ws->cell_L,   ws->cell_P,   ws->partials, ws->hist,
-                    ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info};
+                    ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info, ws->srec, ws->srec32, ws->scen};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -110,6 +110,9 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
     e = e ? e : alloc(&ws->rec, C, &tot);
     e = e ? e : alloc(&ws->rec32, C, &tot);
     e = e ? e : alloc(&ws->cen32, C, &tot);
+    e = e ? e : alloc(&ws->srec, C, &tot);
+    e = e ? e : alloc(&ws->srec32, C, &tot);
+    e = e ? e : alloc(&ws->scen, C, &tot);
     e = e ? e : alloc(&ws->sys, Mx, &tot);
     e = e ? e : alloc(&ws->fit_info, 2 * Mx, &tot);
     e = e ? e : alloc(&ws->cells, Mx + 1, &tot);
@@ -185,6 +188,7 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     if (e == cudaSuccess) e = ft::launch_bin(ws, f, p, s);
     if (e == cudaSuccess) e = ft::launch_sort(ws, s);
     if (e == cudaSuccess) e = ft::launch_rle(ws, s);
+    if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
     return cuda_err(e);
 }

@@ -69,6 +69,9 @@ struct ft_workspace {
     ft_frag* rec;          // max_cand (FP64 records)
     ft_frag32* rec32;      // max_cand (FP32 records)
     float4* cen32;         // max_cand: float copy of the FP64 centroids (support filter)
+    ft_frag* srec;         // max_cand: FP64 records in sorted pair order
+    ft_frag32* srec32;     // max_cand: FP32 records in sorted pair order
+    float4* scen;          // max_cand: float centroids in sorted pair order (support filter)
     ft_cellsys* sys;       // max_cells: normal equations per cell
     int* fit_info;         // max_cells x 2: fragments in support, status bits
     unsigned* cells;       // max_cells + 1
@@ -94,6 +97,7 @@ cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, 
 cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s);
 cudaError_t prepare_sort(int grid_blocks);
 cudaError_t launch_rle(ft_workspace* ws, cudaStream_t s);
+cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_clear_map(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s);
 cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s);

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells(const int* __restrict_
         const int q0 = cell_off[m], q1 = cell_off[m + 1];
         double L = 0.0, P = 0.0;
         for (int q = q0 + lane; q < q1; q += 32) {
-            const ft_frag* f = rec + vals[q];
+            const ft_frag* f = rec + (vals ? vals[q] : (unsigned)q);
             const double az = f->an[2];
             L += az * (f->c[2] + 0.5);
             P += az;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells32(const int* __restric
         const int q0 = cell_off[m], q1 = cell_off[m + 1];
         float Lh = 0.f, Ll = 0.f, Ph = 0.f, Pl = 0.f;
         for (int q = q0 + lane; q < q1; q += 32) {
-            const ft_frag32* f = rec + vals[q];
+            const ft_frag32* f = rec + (vals ? vals[q] : (unsigned)q);
             const float az = f->an[2];
             float s, e;
             two_sum(Lh, az * (f->c[2] + 0.5f), s, e);
@@ -158,15 +158,17 @@ __global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* _
 namespace ft {
 
 cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s) {
-    const unsigned* vals = ws->vals[ws->sorted_buf];
     const bool fp32 = ws->last_precision == FT_FP32C;
+    // records in sorted pair order when front_bin gathered them, else through the slot index
+    const bool sorted = fp32 ? ws->srec32 != nullptr : ws->srec != nullptr;
+    const unsigned* vals = sorted ? nullptr : ws->vals[ws->sorted_buf];
     count_launches(2);
     if (fp32)
-        k_alpha_cells32<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, ws->rec32, ws->cell_L, ws->cell_P,
-                                                              ws->ctr);
+        k_alpha_cells32<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, sorted ? ws->srec32 : ws->rec32,
+                                                              ws->cell_L, ws->cell_P, ws->ctr);
     else
-        k_alpha_cells<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, ws->rec, ws->cell_L, ws->cell_P,
-                                                            ws->ctr);
+        k_alpha_cells<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, sorted ? ws->srec : ws->rec,
+                                                            ws->cell_L, ws->cell_P, ws->ctr);
     // the column parity of a closed front is an integer up to rounding of the fragment terms
     const double closure_tol = fp32 ? 1e-5 : 1e-9;
     k_alpha_fill<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->g, ws->idx_map, ws->cell_L, ws->cell_P, alpha,

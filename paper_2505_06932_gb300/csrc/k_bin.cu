@@ -12,19 +12,29 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Order-preserving integer key of a finite double: comparing keys as signed
+// 64-bit integers gives exactly the result of comparing the doubles (-0 and +0
+// map to the same key), on the integer pipe instead of the float64 one.
+__device__ __forceinline__ long long okey(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
 // Candidate range along one axis: cells whose closed extent [X_i, X_i+1] meets
-// [lo, hi]: i0 = min{i : X_i+1 >= lo}, i1 = max{i : X_i <= hi}.  The floor is
-// only a starting guess; the loops make the result exact.
-__device__ void cand_range(double o, double h, int n, double lo, double hi, int& i0, int& i1) {
-    double f = floor(__ddiv_rn(__dsub_rn(lo, o), h));
+// [lo, hi]: i0 = min{i : X_i+1 >= lo}, i1 = max{i : X_i <= hi}.  The product
+// with 1/h is only a starting guess; the exact comparisons make the result exact.
+__device__ void cand_range(double o, double h, double inv_h, int n, double lo, double hi, int& i0, int& i1) {
+    const long long klo = okey(lo), khi = okey(hi);
+    double f = floor((lo - o) * inv_h);
     int e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
-    while (e > 0 && ft_plane(o, h, e) >= lo) e--;
-    while (e < n - 1 && ft_plane(o, h, e + 1) < lo) e++;
+    while (e > 0 && okey(ft_plane(o, h, e)) >= klo) e--;
+    while (e < n - 1 && okey(ft_plane(o, h, e + 1)) < klo) e++;
     i0 = e;
-    f = floor(__ddiv_rn(__dsub_rn(hi, o), h));
+    f = floor((hi - o) * inv_h);
     e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
-    while (e < n - 1 && ft_plane(o, h, e + 1) <= hi) e++;
-    while (e > 0 && ft_plane(o, h, e) > hi) e--;
+    while (e < n - 1 && okey(ft_plane(o, h, e + 1)) <= khi) e++;
+    while (e > 0 && okey(ft_plane(o, h, e)) > khi) e--;
     i1 = e;
 }
 
@@ -45,24 +55,29 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(const double* __restrict
         if (vi[c] < 0 || vi[c] >= nv) err |= FT_ST_BAD_INDEX;
     }
     if (!err) {
+        // extent per axis by exact integer-key comparisons (no float64 arithmetic)
         double mn[3], mx[3];
-        for (int ax = 0; ax < 3; ax++) {
-            mn[ax] = INFINITY;
-            mx[ax] = -INFINITY;
-        }
         bool finite = true;
-        for (int c = 0; c < 3; c++)
-            for (int ax = 0; ax < 3; ax++) {
+        for (int ax = 0; ax < 3; ax++) {
+            double lo = 0.0, hi = 0.0;
+            long long klo = 0, khi = 0;
+            for (int c = 0; c < 3; c++) {
                 const double x = verts[3 * (long long)vi[c] + ax];
-                finite = finite && isfinite(x);
-                mn[ax] = fmin(mn[ax], x);
-                mx[ax] = fmax(mx[ax], x);
+                const long long b = __double_as_longlong(x);
+                finite = finite && ((b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
+                const long long kx = okey(x);
+                if (c == 0 || kx < klo) { klo = kx; lo = x; }
+                if (c == 0 || kx > khi) { khi = kx; hi = x; }
             }
+            mn[ax] = lo;
+            mx[ax] = hi;
+        }
         if (!finite) err |= FT_ST_OUTSIDE_GRID;
         long long total = 1;
+        const double inv_h = 1.0 / g.h;
         for (int ax = 0; ax < 3 && !err; ax++) {
             int i0, i1;
-            cand_range(g.origin[ax], g.h, g.n[ax], mn[ax], mx[ax], i0, i1);
+            cand_range(g.origin[ax], g.h, inv_h, g.n[ax], mn[ax], mx[ax], i0, i1);
             if (i0 < margin || i1 > g.n[ax] - 1 - margin) err |= FT_ST_OUTSIDE_GRID;
             box[ax] = i0;
             box[3 + ax] = i1 - i0 + 1;
@@ -106,11 +121,14 @@ template <int MAXV>
 __device__ __forceinline__ bool clip_half(const double (*in)[3], int n, double (*out)[3], int& m, int ax,
                                           double pv, bool ge) {
     m = 0;
+    const long long kp = okey(pv);
+    const long long kl = okey(in[n - 1][ax]);
+    bool pin = ge ? (kl >= kp) : (kl <= kp);
     for (int i = 0; i < n; i++) {
         const double* cur = in[i];
         const double* prev = in[i == 0 ? n - 1 : i - 1];
-        const bool cin = ge ? (cur[ax] >= pv) : (cur[ax] <= pv);
-        const bool pin = ge ? (prev[ax] >= pv) : (prev[ax] <= pv);
+        const long long kc = okey(cur[ax]);
+        const bool cin = ge ? (kc >= kp) : (kc <= kp);
         if (cin != pin) {
             if (m >= MAXV) return false;
             const double t = __ddiv_rn(__dsub_rn(pv, prev[ax]), __dsub_rn(cur[ax], prev[ax]));
@@ -126,14 +144,17 @@ __device__ __forceinline__ bool clip_half(const double (*in)[3], int n, double (
             out[m][2] = cur[2];
             m++;
         }
+        pin = cin;
     }
     return true;
 }
 
-// Canonical clip of triangle v against cell (i,j,k).  Returns the vertex count
-// (>= 3) of the accepted fragment, 0 if rejected, -1 if MAXV was too small.
+// The six clip stages of the canonical predicate for triangle v and cell idx,
+// followed by the upper-face test.  Returns the vertex count (>= 3) of the
+// surviving polygon in res, 0 if rejected, -1 if MAXV was too small.  The
+// remaining condition (fan area vector not zero) is checked by the caller.
 template <int MAXV>
-__device__ int canon_clip(const double (*v)[3], const ft_grid& g, const int idx[3], double (*res)[3]) {
+__device__ int canon_stages(const double (*v)[3], const ft_grid& g, const int idx[3], double (*res)[3]) {
     double A[MAXV][3], B[MAXV][3];
     int n = 3;
     for (int c = 0; c < 3; c++)
@@ -152,21 +173,10 @@ __device__ int canon_clip(const double (*v)[3], const ft_grid& g, const int idx[
             dst = tmp;
         }
     }
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int m = 1; m + 1 < n; m++) {
-        const double e1x = __dsub_rn(src[m][0], src[0][0]), e1y = __dsub_rn(src[m][1], src[0][1]),
-                     e1z = __dsub_rn(src[m][2], src[0][2]);
-        const double e2x = __dsub_rn(src[m + 1][0], src[0][0]), e2y = __dsub_rn(src[m + 1][1], src[0][1]),
-                     e2z = __dsub_rn(src[m + 1][2], src[0][2]);
-        s0 = __dadd_rn(s0, __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y)));
-        s1 = __dadd_rn(s1, __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z)));
-        s2 = __dadd_rn(s2, __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x)));
-    }
-    if (s0 == 0.0 && s1 == 0.0 && s2 == 0.0) return 0;
     for (int ax = 0; ax < 3; ax++) {
-        const double up = ft_plane(g.origin[ax], g.h, idx[ax] + 1);
+        const long long ku = okey(ft_plane(g.origin[ax], g.h, idx[ax] + 1));
         bool all = true;
-        for (int m = 0; m < n && all; m++) all = (src[m][ax] == up);
+        for (int m = 0; m < n && all; m++) all = (okey(src[m][ax]) == ku);
         if (all) return 0;
     }
     for (int m = 0; m < n; m++)
@@ -174,9 +184,25 @@ __device__ int canon_clip(const double (*v)[3], const ft_grid& g, const int idx[
     return n;
 }
 
-__device__ __noinline__ int canon_clip_wide(const double (*v)[3], const ft_grid& g, const int idx[3],
-                                            double (*res)[3]) {
-    return canon_clip<32>(v, g, idx, res);
+// The canonical fan area vector sum_m (p_m - p_0) x (p_m+1 - p_0), exactly as
+// defined (binary64, round to nearest, no contraction); true if not zero.
+__device__ bool canon_area_nonzero(const double (*p)[3], int n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int m = 1; m + 1 < n; m++) {
+        const double e1x = __dsub_rn(p[m][0], p[0][0]), e1y = __dsub_rn(p[m][1], p[0][1]),
+                     e1z = __dsub_rn(p[m][2], p[0][2]);
+        const double e2x = __dsub_rn(p[m + 1][0], p[0][0]), e2y = __dsub_rn(p[m + 1][1], p[0][1]),
+                     e2z = __dsub_rn(p[m + 1][2], p[0][2]);
+        s0 = __dadd_rn(s0, __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y)));
+        s1 = __dadd_rn(s1, __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z)));
+        s2 = __dadd_rn(s2, __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x)));
+    }
+    return !(s0 == 0.0 && s1 == 0.0 && s2 == 0.0);
+}
+
+__device__ __noinline__ int canon_stages_wide(const double (*v)[3], const ft_grid& g, const int idx[3],
+                                              double (*res)[3]) {
+    return canon_stages<32>(v, g, idx, res);
 }
 
 // Fragment moments in units of h relative to the fragment cell's centre, from
@@ -311,23 +337,34 @@ __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ ve
             for (int d = 0; d < 3; d++) v[a][d] = verts[3 * vi + d];
         }
         double poly[32][3];
-        int n = canon_clip<12>(v, g, idx, poly);
-        if (n < 0) n = canon_clip_wide(v, g, idx, poly);
+        int n = canon_stages<12>(v, g, idx, poly);
+        if (n < 0) n = canon_stages_wide(v, g, idx, poly);
         unsigned key = FT_SENTINEL;
         if (n >= 3) {
-            key = (unsigned)(((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
             double xc[3];
             for (int d = 0; d < 3; d++) xc[d] = ft_plane(g.origin[d], g.h, idx[d]) + 0.5 * g.h;
+            // The moments' own area vector certifies the canonical "area vector
+            // is not zero" condition whenever it exceeds its rounding bound by
+            // far (float32: 1e-4 h^2, float64: 1e-9 h^2); only smaller fragments
+            // evaluate the canonical sum.
+            bool accept;
             if (fp32) {
                 ft_frag32 f;
                 frag_moments32(poly, n, xc, inv_h, f);
-                rec32[c] = f;
+                const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
+                accept = (a > 1e-4f) || canon_area_nonzero(poly, n);
+                if (accept) rec32[c] = f;
             } else {
                 ft_frag f;
                 frag_moments(poly, n, xc, inv_h, f);
-                rec[c] = f;
-                if (cen32) cen32[c] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
+                const double a = fmax(fabs(f.an[0]), fmax(fabs(f.an[1]), fabs(f.an[2])));
+                accept = (a > 1e-9) || canon_area_nonzero(poly, n);
+                if (accept) {
+                    rec[c] = f;
+                    if (cen32) cen32[c] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
+                }
             }
+            if (accept) key = (unsigned)(((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
         }
         keys[c] = key;
         vals[c] = (unsigned)c;

@@ -13,8 +13,10 @@
 //   sum_f u_f v_f v_f^T a = sum_f u_f z_f v_f.
 //
 // Two kernels:
-//  * k_ppic_acc<T> -- one warp per cell: frame, candidate fragments of the
-//    cells within ceil(delta - 1/2), a float32 support test that appends the
+//  * k_ppic_acc<T> -- one warp per cell (fragment records in sorted pair
+//    order, so a cell's fragments are one contiguous range): frame, candidate
+//    fragments of the cells within ceil(delta - 1/2), a float32 support test
+//    on a compact centroid array that appends the
 //    fragments near or inside the support to a per-warp queue (so that the
 //    expensive part runs on full warps), the exact test and the accumulation in
 //    T (double: the plain path; float: the FP32 form), support growth, and a
@@ -166,9 +168,9 @@ __device__ __forceinline__ void accumulate(const Rec<T>& rec, unsigned ri, int d
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_ppic_acc(PpicArgs A, const unsigned* __restrict__ cells,
-                                                       const int* __restrict__ cell_off, const unsigned* __restrict__ vals,
-                                                       Rec<T> rec, const float4* __restrict__ cen32,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(PpicArgs A, const unsigned* __restrict__ cells,
+                                                       const int* __restrict__ cell_off, Rec<T> rec,
+                                                       const float4* __restrict__ cen,
                                                        const int* __restrict__ idx_map, ft_counters* ctr,
                                                        ft_cellsys* __restrict__ sys, int* __restrict__ fit_info) {
     __shared__ unsigned s_qr[kWarps][kQueue];
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kThreads) k_ppic_acc(PpicArgs A, const unsigne
         const int q0 = cell_off[m], q1 = cell_off[m + 1];
         for (int q = q0 + lane; q < q1; q += 32) {
             T an[3];
-            rec.load_an(vals[q], an);
+            rec.load_an(q, an);
             N[0] += an[0];
             N[1] += an[1];
             N[2] += an[2];
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_ppic_acc(PpicArgs A, const unsigne
                     bestq = oq;
                 }
             }
-            rec.load_an(vals[bestq], N);
+            rec.load_an(bestq, N);
             nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
             st |= FT_FIT_NORMAL;
         }
@@ -288,21 +290,11 @@ __global__ void __launch_bounds__(kThreads) k_ppic_acc(PpicArgs A, const unsigne
                     bool pass = false;
                     unsigned ri = 0;
                     if (fi < total) {
-                        ri = vals[fo + (fi - eo)];
-                        float cx, cy, cz;
-                        if (cen32) {
-                            const float4 c4 = cen32[ri];
-                            cx = c4.x;
-                            cy = c4.y;
-                            cz = c4.z;
-                        } else {
-                            cx = (float)rec.r[ri].c[0];
-                            cy = (float)rec.r[ri].c[1];
-                            cz = (float)rec.r[ri].c[2];
-                        }
-                        const float px = cx + (float)(((dc >> 8) & 15) - 8);
-                        const float py = cy + (float)(((dc >> 4) & 15) - 8);
-                        const float pz = cz + (float)((dc & 15) - 8);
+                        ri = (unsigned)(fo + (fi - eo));
+                        const float4 c4 = cen[ri];
+                        const float px = c4.x + (float)(((dc >> 8) & 15) - 8);
+                        const float py = c4.y + (float)(((dc >> 4) & 15) - 8);
+                        const float pz = c4.z + (float)((dc & 15) - 8);
                         pass = (px * px + py * py + pz * pz) < f_thr;
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -493,16 +485,16 @@ cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, uns
     A.delta_max_h = p->delta_max_h;
     A.fit_min = p->fit_min;
     cudaMemsetAsync(&ws->ctr->fit_pairs, 0, sizeof(long long), s);
-    const unsigned* vals = ws->vals[ws->sorted_buf];
     const bool fp32 = ws->last_precision == FT_FP32C;
     count_launches(2);
+    // fragments are read in sorted pair order (front_bin gathers them)
     if (fp32) {
-        Rec<float> r{ws->rec32};
-        k_ppic_acc<float><<<ws->sm_count * 4, kThreads, 0, s>>>(A, ws->cells, ws->cell_off, vals, r, nullptr,
+        Rec<float> r{ws->srec32};
+        k_ppic_acc<float><<<ws->sm_count * 4, kThreads, 0, s>>>(A, ws->cells, ws->cell_off, r, ws->scen,
                                                                 ws->idx_map, ws->ctr, ws->sys, ws->fit_info);
     } else {
-        Rec<double> r{ws->rec};
-        k_ppic_acc<double><<<ws->sm_count * 4, kThreads, 0, s>>>(A, ws->cells, ws->cell_off, vals, r, ws->cen32,
+        Rec<double> r{ws->srec};
+        k_ppic_acc<double><<<ws->sm_count * 4, kThreads, 0, s>>>(A, ws->cells, ws->cell_off, r, ws->scen,
                                                                  ws->idx_map, ws->ctr, ws->sys, ws->fit_info);
     }
     k_ppic_solve<<<ws->sm_count * 4, 128, 0, s>>>(ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, ws->g.h, cap,

@@ -279,9 +279,38 @@ __global__ void __launch_bounds__(kB) k_export_pairs(const unsigned* __restrict_
     }
 }
 
+// fragment records in sorted pair order, so later kernels read a cell's
+// fragments as one contiguous range (no indirection through the slot)
+__global__ void __launch_bounds__(kB) k_gather(const unsigned* __restrict__ svals, const ft_frag* __restrict__ rec,
+                                               const ft_frag32* __restrict__ rec32, ft_frag* __restrict__ srec,
+                                               ft_frag32* __restrict__ srec32, float4* __restrict__ scen, int fp32,
+                                               const ft_counters* ctr) {
+    const long long P = ctr->P;
+    for (long long q = (long long)blockIdx.x * kB + threadIdx.x; q < P; q += (long long)gridDim.x * kB) {
+        const unsigned c = svals[q];
+        if (fp32) {
+            const ft_frag32 f = rec32[c];
+            srec32[q] = f;
+            scen[q] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
+        } else {
+            const ft_frag f = rec[c];
+            srec[q] = f;
+            scen[q] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
+        }
+    }
+}
+
 }  // namespace
 
 namespace ft {
+
+cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s) {
+    if (!ws->srec || !ws->srec32 || !ws->scen) return cudaSuccess;  // a workspace without sorted copies
+    count_launches(1);
+    k_gather<<<ws->sm_count * 4, kB, 0, s>>>(ws->vals[ws->sorted_buf], ws->rec, ws->rec32, ws->srec, ws->srec32,
+                                             ws->scen, ws->last_precision == FT_FP32C ? 1 : 0, ws->ctr);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s) {
     count_launches(1);
