@@ -317,28 +317,180 @@ __device__ void frag_moments32(const double (*p)[3], int n, const double xc[3], 
     for (int d = 0; d < 3; d++) f.an[d] = an[d];
 }
 
+// One queued edge-plane crossing: the edge prev -> cur of a lane's polygon and
+// the plane value; the result q is written back for the owning lane.
+struct ClipJob {
+    double a[3], b[3], q[3], pv;
+};
+
+constexpr int kClipV = 12;     // polygon capacity of the warp-cooperative path
+constexpr int kClipJobs = 64;  // <= 2 crossings per lane and stage
+
+// Warp-cooperative canonical clip: lane l holds candidate cb + l.  Each stage
+// computes the inside flags per lane, queues every crossing of the warp in
+// shared memory and evaluates them on full lanes with the canonical operations
+// (t = (pv - a)/(b - a), q = a + t (b - a), clipped coordinate set to pv), then
+// each lane assembles its output in Sutherland-Hodgman order.  A stage with more
+// than two crossings in some lane (degenerate) is done lane by lane with
+// clip_half, and a polygon that outgrows kClipV is redone with the wide serial
+// clip: both give the same result as this path would.
+__device__ int clip_warp(const double (*v)[3], const ft_grid& g, const int idx[3], bool active, ClipJob* jobs,
+                         double (*res)[3]) {
+    const int lane = threadIdx.x & 31;
+    double A[kClipV][3], B[kClipV][3];
+    double(*src)[3] = A;
+    double(*dst)[3] = B;
+    int n = 3;
+    for (int c = 0; c < 3; c++)
+        for (int d = 0; d < 3; d++) A[c][d] = v[c][d];
+    bool alive = active, wide = false;
+    for (int st = 0; st < 6; st++) {
+        const int ax = st >> 1;
+        const bool ge = (st & 1) == 0;
+        const double pv = ft_plane(g.origin[ax], g.h, idx[ax] + (st & 1));
+        unsigned flags = 0, cross = 0;
+        int ncross = 0;
+        if (alive) {
+            const long long kp = okey(pv);
+            for (int i = 0; i < n; i++) {
+                const long long kc = okey(src[i][ax]);
+                if (ge ? (kc >= kp) : (kc <= kp)) flags |= 1u << i;
+            }
+            // edge (i-1 -> i) crosses iff the flags of its ends differ
+            const unsigned prevf = (flags << 1 | flags >> (n - 1)) & ((1u << n) - 1u);
+            cross = flags ^ prevf;
+            ncross = __popc(cross);
+        }
+        if (__any_sync(0xffffffffu, ncross > 2)) {
+            // degenerate stage somewhere in the warp: lane by lane, canonically
+            if (alive) {
+                int m;
+                if (!clip_half<kClipV>(src, n, dst, m, ax, pv, ge)) {
+                    wide = true;
+                    alive = false;
+                } else if (m < 3) {
+                    alive = false;
+                } else {
+                    n = m;
+                    double(*tmp)[3] = src;
+                    src = dst;
+                    dst = tmp;
+                }
+            }
+            continue;
+        }
+        int incl = ncross;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int base = incl - ncross;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (ncross) {
+            int k = 0;
+            for (int i = 0; i < n; i++) {
+                if (!((cross >> i) & 1u)) continue;
+                const int pi = (i == 0) ? n - 1 : i - 1;
+                ClipJob& J = jobs[base + k++];
+                for (int d = 0; d < 3; d++) {
+                    J.a[d] = src[pi][d];
+                    J.b[d] = src[i][d];
+                }
+                J.pv = pv;
+            }
+        }
+        __syncwarp();
+        for (int j = lane; j < total; j += 32) {
+            ClipJob& J = jobs[j];
+            const double t = __ddiv_rn(__dsub_rn(J.pv, J.a[ax]), __dsub_rn(J.b[ax], J.a[ax]));
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                J.q[c] = (c == ax) ? J.pv : __dadd_rn(J.a[c], __dmul_rn(t, __dsub_rn(J.b[c], J.a[c])));
+        }
+        __syncwarp();
+        if (alive) {
+            int m = 0, k = 0;
+            for (int i = 0; i < n && !wide; i++) {
+                if ((cross >> i) & 1u) {
+                    if (m >= kClipV) {
+                        wide = true;
+                        break;
+                    }
+                    const ClipJob& J = jobs[base + k++];
+                    dst[m][0] = J.q[0];
+                    dst[m][1] = J.q[1];
+                    dst[m][2] = J.q[2];
+                    m++;
+                }
+                if ((flags >> i) & 1u) {
+                    if (m >= kClipV) {
+                        wide = true;
+                        break;
+                    }
+                    dst[m][0] = src[i][0];
+                    dst[m][1] = src[i][1];
+                    dst[m][2] = src[i][2];
+                    m++;
+                }
+            }
+            if (wide || m < 3) {
+                alive = false;
+            } else {
+                n = m;
+                double(*tmp)[3] = src;
+                src = dst;
+                dst = tmp;
+            }
+        }
+        __syncwarp();
+    }
+    if (wide) return canon_stages_wide(v, g, idx, res);
+    if (!alive) return 0;
+    for (int ax = 0; ax < 3; ax++) {
+        const long long ku = okey(ft_plane(g.origin[ax], g.h, idx[ax] + 1));
+        bool all = true;
+        for (int m = 0; m < n && all; m++) all = (okey(src[m][ax]) == ku);
+        if (all) return 0;
+    }
+    for (int m = 0; m < n; m++)
+        for (int d = 0; d < 3; d++) res[m][d] = src[m][d];
+    return n;
+}
+
 __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ verts, const int* __restrict__ tris,
                                                    ft_grid g, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
                                                    unsigned* __restrict__ keys, unsigned* __restrict__ vals,
                                                    ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
                                                    float4* __restrict__ cen32, int fp32, const ft_counters* ctr) {
+    __shared__ ClipJob s_jobs[kThreads / 32][kClipJobs];
+    ClipJob* jobs = s_jobs[threadIdx.x >> 5];
     const long long C = ctr->C;
     const double inv_h = 1.0 / g.h;
-    for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < C; c += (long long)gridDim.x * kThreads) {
-        const int t = cand_tri[c];
-        const int l = (int)(c - tri_off[t]);
-        const int* bx = tri_box + 6 * (long long)t;
-        const int e1 = bx[4], e2 = bx[5];
-        const int idx[3] = {bx[0] + l / (e1 * e2), bx[1] + (l / e2) % e1, bx[2] + l % e2};
-        double v[3][3];
-        for (int a = 0; a < 3; a++) {
-            const long long vi = tris[3 * (long long)t + a];
-            for (int d = 0; d < 3; d++) v[a][d] = verts[3 * vi + d];
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (kThreads / 32);
+    for (long long cb = ((long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; cb < C; cb += nwarps * 32) {
+        const long long c = cb + lane;
+        const bool active = c < C;
+        int idx[3] = {0, 0, 0};
+        double v[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        if (active) {
+            const int t = cand_tri[c];
+            const int l = (int)(c - tri_off[t]);
+            const int* bx = tri_box + 6 * (long long)t;
+            const int e1 = bx[4], e2 = bx[5];
+            idx[0] = bx[0] + l / (e1 * e2);
+            idx[1] = bx[1] + (l / e2) % e1;
+            idx[2] = bx[2] + l % e2;
+            for (int a = 0; a < 3; a++) {
+                const long long vi = tris[3 * (long long)t + a];
+                for (int d = 0; d < 3; d++) v[a][d] = verts[3 * vi + d];
+            }
         }
         double poly[32][3];
-        int n = canon_stages<12>(v, g, idx, poly);
-        if (n < 0) n = canon_stages_wide(v, g, idx, poly);
+        const int n = clip_warp(v, g, idx, active, jobs, poly);
+        if (!active) continue;
         unsigned key = FT_SENTINEL;
         if (n >= 3) {
             double xc[3];
