@@ -40,10 +40,10 @@ struct __align__(16) ft_frag32 {
 
 // Per interfacial cell, the volume-fit normal equations left by the
 // accumulation kernel for the solve kernel: packed upper triangle of the 6x6
-// matrix (21), right-hand side (6), frame normal (3) -- as doubles (FP64) or as
-// hi/lo float pairs (FP32 form, 2 x 30 floats in the same 240 bytes).
+// matrix (21), right-hand side (6), frame normal (3) and the height shift z0 of
+// the fitted heights -- as doubles (FP64) or as hi/lo float pairs (FP32 form).
 struct __align__(16) ft_cellsys {
-    double v[30];
+    double v[32];
 };
 
 struct ft_workspace {

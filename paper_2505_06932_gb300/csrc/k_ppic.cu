@@ -126,12 +126,53 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
+// Transposed warp reduction of 32 values per lane: each round a lane keeps one
+// half of its vector and adds the partner's copy of that half, so after five
+// rounds lane l holds the warp total of value l (31 shuffles instead of 32 x 5).
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; i++) {
+            const double send = up ? v[i] : v[i + o];
+            const double keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+// The same with float (hi, lo) pairs combined by two-sum: the lanes' rounding
+// errors are carried along instead of being lost.
+__device__ __forceinline__ void warp_transpose_sum2(float (&h)[32], float (&l)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; i++) {
+            const float sh = up ? h[i] : h[i + o];
+            const float sl = up ? l[i] : l[i + o];
+            const float kh = up ? h[i + o] : h[i];
+            const float kl = up ? l[i + o] : l[i];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh, o);
+            const float rl = __shfl_xor_sync(0xffffffffu, sl, o);
+            float s, e;
+            two_sum(kh, rh, s, e);
+            h[i] = s;
+            l[i] = kl + rl + e;
+        }
+    }
+}
+
 // the expensive part for one queued fragment: exact support test, weight,
 // projected moments and the 27 accumulations
 template <typename T>
 __device__ __forceinline__ void accumulate(const Rec<T>& rec, unsigned ri, int dcode, T delta, T inv_delta,
                                           const T n[3], const T t1[3], const T t2[3], const T c11[6],
-                                          const T c12[6], const T c22[6], T S[21], T B[6], int& count) {
+                                          const T c12[6], const T c22[6], T z0, T S[21], T B[6], int& count) {
     T an[3], c[3], k[6];
     rec.load(ri, an, c, k);
     const T p[3] = {c[0] + (T)(((dcode >> 8) & 15) - 8), c[1] + (T)(((dcode >> 4) & 15) - 8),
@@ -146,7 +187,7 @@ __device__ __forceinline__ void accumulate(const Rec<T>& rec, unsigned ri, int d
     const T w = ((T)1 + (T)4 * q) * om2 * om2;
     const T x = t1[0] * p[0] + t1[1] * p[1] + t1[2] * p[2];
     const T y = t2[0] * p[0] + t2[1] * p[1] + t2[2] * p[2];
-    const T z = n[0] * p[0] + n[1] * p[1] + n[2] * p[2];
+    const T z = n[0] * p[0] + n[1] * p[1] + n[2] * p[2] - z0;
     const T sA = n[0] * an[0] + n[1] * an[1] + n[2] * an[2];
     T q11 = 0, q12 = 0, q22 = 0;
 #pragma unroll
@@ -190,17 +231,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
         int st = 0;
 
         // 1. local normal: normalized sum of the cell's fragment area vectors
-        T N[3] = {0, 0, 0}, sa = 0, best = -1;
+        T N[3] = {0, 0, 0}, sa = 0, best = -1, AC[3] = {0, 0, 0};
         int bestq = 0x7fffffff;
         const int q0 = cell_off[m], q1 = cell_off[m + 1];
         for (int q = q0 + lane; q < q1; q += 32) {
             T an[3];
             rec.load_an(q, an);
+            const float4 cq = cen[q];
             N[0] += an[0];
             N[1] += an[1];
             N[2] += an[2];
             const T a = sqrt(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
             sa += a;
+            AC[0] += a * (T)cq.x;
+            AC[1] += a * (T)cq.y;
+            AC[2] += a * (T)cq.z;
             if (a > best) {
                 best = a;
                 bestq = q;
@@ -212,6 +257,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
             N[1] += __shfl_xor_sync(0xffffffffu, N[1], o);
             N[2] += __shfl_xor_sync(0xffffffffu, N[2], o);
             sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            AC[0] += __shfl_xor_sync(0xffffffffu, AC[0], o);
+            AC[1] += __shfl_xor_sync(0xffffffffu, AC[1], o);
+            AC[2] += __shfl_xor_sync(0xffffffffu, AC[2], o);
         }
         T nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
         if (nn < (T)1e-3 * sa) {
@@ -230,6 +278,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
             st |= FT_FIT_NORMAL;
         }
         const T n[3] = {N[0] / nn, N[1] / nn, N[2] / nn};
+        // heights are fitted relative to the cell's own fragment centroid: a
+        // shift of z that leaves a2..a6 (and so kappa and n) unchanged but keeps
+        // the constant term small, which conditions the float32 form
+        const T z0 = (sa > 0) ? (n[0] * AC[0] + n[1] * AC[1] + n[2] * AC[2]) / sa : (T)0;
         T t1[3], t2[3], c11[6], c12[6], c22[6];
         basis<T>(n, t1, t2);
         qform<T>(t1, t1, c11);
@@ -307,14 +359,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
                     __syncwarp();
                     if (qn >= 32) {
                         const int e = qn - 32 + lane;
-                        accumulate<T>(rec, qr[e], qd[e], delta, inv_delta, n, t1, t2, c11, c12, c22, S, B, count);
+                        accumulate<T>(rec, qr[e], qd[e], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, S, B, count);
                         qn -= 32;
                         __syncwarp();
                     }
                 }
             }
             if (lane < qn)
-                accumulate<T>(rec, qr[lane], qd[lane], delta, inv_delta, n, t1, t2, c11, c12, c22, S, B, count);
+                accumulate<T>(rec, qr[lane], qd[lane], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, S, B, count);
             __syncwarp();
             ctot = ft_warp_sum_i(count);
             if (ctot >= A.fit_min || (double)delta >= A.delta_max_h) break;
@@ -323,41 +375,39 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
         }
         pairs_total += (unsigned long long)ctot;
 
-        // 5. reduce the 27 sums over the warp and leave them for the solve kernel
+        // 5. reduce the 27 sums over the warp (transposed: lane r ends with sum r)
+        //    and leave them for the solve kernel
         ft_cellsys* out = sys + m;
         if (sizeof(T) == 8) {
+            double v[32];
 #pragma unroll
-            for (int r = 0; r < 21; r++) S[r] = (T)ft_warp_sum((double)S[r]);
+            for (int r = 0; r < 21; r++) v[r] = (double)S[r];
 #pragma unroll
-            for (int r = 0; r < 6; r++) B[r] = (T)ft_warp_sum((double)B[r]);
+            for (int r = 0; r < 6; r++) v[21 + r] = (double)B[r];
+#pragma unroll
+            for (int r = 27; r < 32; r++) v[r] = 0.0;
+            const double tot = warp_transpose_sum(v);
+            if (lane < 27) out->v[lane] = tot;
             if (lane == 0) {
 #pragma unroll
-                for (int r = 0; r < 21; r++) out->v[r] = (double)S[r];
-#pragma unroll
-                for (int r = 0; r < 6; r++) out->v[21 + r] = (double)B[r];
-#pragma unroll
                 for (int r = 0; r < 3; r++) out->v[27 + r] = (double)n[r];
+                out->v[30] = (double)z0;
             }
         } else {
-            // compensated (hi, lo) butterfly: the lanes' float partial sums are
-            // combined without losing their rounding errors
+            float hv[32], lv[32];
+#pragma unroll
+            for (int r = 0; r < 21; r++) hv[r] = (float)S[r];
+#pragma unroll
+            for (int r = 0; r < 6; r++) hv[21 + r] = (float)B[r];
+#pragma unroll
+            for (int r = 27; r < 32; r++) hv[r] = 0.f;
+#pragma unroll
+            for (int r = 0; r < 32; r++) lv[r] = 0.f;
+            warp_transpose_sum2(hv, lv);
             float* o32 = reinterpret_cast<float*>(out->v);
-#pragma unroll
-            for (int r = 0; r < 27; r++) {
-                float hi = (r < 21) ? (float)S[r] : (float)B[r - 21], lo = 0.f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-                    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-                    float s, e;
-                    two_sum(hi, oh, s, e);
-                    hi = s;
-                    lo = lo + ol + e;
-                }
-                if (lane == 0) {
-                    o32[2 * r] = hi;
-                    o32[2 * r + 1] = lo;
-                }
+            if (lane < 27) {
+                o32[2 * lane] = hv[0];
+                o32[2 * lane + 1] = lv[0];
             }
             if (lane == 0) {
 #pragma unroll
@@ -365,6 +415,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
                     o32[54 + 2 * r] = (float)n[r];
                     o32[55 + 2 * r] = 0.f;
                 }
+                o32[60] = (float)z0;
             }
         }
         if (lane == 0) {
@@ -427,18 +478,20 @@ __global__ void __launch_bounds__(128) k_ppic_solve(const ft_cellsys* __restrict
         return;
     }
     for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
-        double S[21], B[6], n[3];
+        double S[21], B[6], n[3], z0;
         if (fp32) {
             const float* v = reinterpret_cast<const float*>(sys[m].v);
             for (int r = 0; r < 21; r++) S[r] = (double)v[2 * r] + (double)v[2 * r + 1];
             for (int r = 0; r < 6; r++) B[r] = (double)v[42 + 2 * r] + (double)v[43 + 2 * r];
             for (int r = 0; r < 3; r++) n[r] = (double)v[54 + 2 * r];
+            z0 = (double)v[60];
             const double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
             for (int r = 0; r < 3; r++) n[r] /= nl;
         } else {
             for (int r = 0; r < 21; r++) S[r] = sys[m].v[r];
             for (int r = 0; r < 6; r++) B[r] = sys[m].v[21 + r];
             for (int r = 0; r < 3; r++) n[r] = sys[m].v[27 + r];
+            z0 = sys[m].v[30];
         }
         int st = fit_info[2 * m + 1];
         double t1[3], t2[3];
@@ -456,6 +509,7 @@ __global__ void __launch_bounds__(128) k_ppic_solve(const ft_cellsys* __restrict
             }
             st |= FT_FIT_SINGULAR;
         }
+        a[0] += z0;  // undo the height shift (it changes a1 only)
         // mean curvature of the graph z = P(x, y) at the origin, kappa = div n
         const double g2 = 1.0 + a[1] * a[1] + a[2] * a[2];
         const double kl = -(2.0 * a[3] * (1.0 + a[2] * a[2]) - 2.0 * a[1] * a[2] * a[4] +
