@@ -76,6 +76,8 @@ def lib():
             L.og_csf.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P]
             L.og_interp.restype = None
             L.og_interp.argtypes = [P, P, P, P, P, C.c_int64, P]
+            L.og_advect_rk4.restype = None
+            L.og_advect_rk4.argtypes = [P, P, P, P, P, C.c_int64, C.c_double, P, P]
             L.og_green_moments.restype = None
             L.og_green_moments.argtypes = [P, P, C.c_int, P]
             L.og_signed_volume.restype = C.c_double
@@ -219,6 +221,19 @@ def interp(g, faces, pts):
     gs = _grid(g)
     lib().og_interp(C.byref(gs), _ptr(U), _ptr(V), _ptr(W), _ptr(p), p.shape[0], _ptr(out))
     return out
+
+
+def advect_rk4(g, faces, pts, dt):
+    """One classical RK4 step of the points in the interpolated velocity of the
+    (fixed) face field: returns (new positions (np, 3), k1 velocities (np, 3))."""
+    U, V, W = (np.ascontiguousarray(f, dtype=np.float64) for f in faces)
+    p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    out = np.empty_like(p)
+    vel = np.empty_like(p)
+    gs = _grid(g)
+    lib().og_advect_rk4(C.byref(gs), _ptr(U), _ptr(V), _ptr(W), _ptr(p), p.shape[0], C.c_double(dt), _ptr(out),
+                        _ptr(vel))
+    return out, vel
 
 
 def green_moments(x, y):

@@ -15,6 +15,8 @@
  *   og_csf      -- S = sigma kappa grad alpha (Eq. csf) + curvature smoothing
  *                  (Sec. 3.3)
  *   og_interp   -- divergence-preserving velocity interpolation (Sec. 3.1)
+ *   og_advect_rk4 -- one fourth-order Runge-Kutta step of the front vertices
+ *                  in the interpolated velocity (Sec. 3.1)
  */
 #include "oracle.h"
 
@@ -787,54 +789,86 @@ static double og_tgrad(const double* A, const int64_t e[3], int dir, int64_t i, 
     return (vh - vl) / span;
 }
 
+/* the interpolated velocity at one point x (Sec. 3.1) */
+static void og_interp_one(const og_grid* g, const double* const F[3], const int64_t* const E[3], const double* x,
+                          double* vel) {
+    const double h = g->h;
+    int64_t c[3];
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; d++) {
+        double f = floor((x[d] - g->origin[d]) / h);
+        const int64_t nd = g->n[d];
+        c[d] = (f >= 0.0) ? ((f <= (double)(nd - 1)) ? (int64_t)f : nd - 1) : 0;
+        lo[d] = og_plane(g, d, c[d]);
+        hi[d] = og_plane(g, d, c[d] + 1);
+    }
+    /* component d along its own axis: faces c[d] (minus) and c[d]+1 (plus) */
+    for (int d = 0; d < 3; d++) {
+        const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+        const double* A = F[d];
+        const int64_t* ext = E[d];
+        int64_t im[3] = {c[0], c[1], c[2]}, ip[3] = {c[0], c[1], c[2]};
+        ip[d] += 1;
+        const double Am = og_at(A, ext[1], ext[2], im[0], im[1], im[2]);
+        const double Ap = og_at(A, ext[1], ext[2], ip[0], ip[1], ip[2]);
+        const double g1m = og_tgrad(A, ext, e1, im[0], im[1], im[2], h);
+        const double g2m = og_tgrad(A, ext, e2, im[0], im[1], im[2], h);
+        const double g1p = og_tgrad(A, ext, e1, ip[0], ip[1], ip[2], h);
+        const double g2p = og_tgrad(A, ext, e2, ip[0], ip[1], ip[2], h);
+        const double y1 = x[e1] - (lo[e1] + hi[e1]) / 2.0;
+        const double y2 = x[e2] - (lo[e2] + hi[e2]) / 2.0;
+        /* transverse derivatives along d of the two other components on their own faces */
+        double corr = 0.0;
+        for (int s = 1; s <= 2; s++) {
+            const int o = (d + s) % 3;
+            const double* B = F[o];
+            const int64_t* eb = E[o];
+            int64_t bm[3] = {c[0], c[1], c[2]}, bp[3] = {c[0], c[1], c[2]};
+            bp[o] += 1;
+            corr += og_tgrad(B, eb, d, bp[0], bp[1], bp[2], h) - og_tgrad(B, eb, d, bm[0], bm[1], bm[2], h);
+        }
+        const double xi = x[d];
+        vel[d] = (xi - lo[d]) / h * (Ap + y1 * g1p + y2 * g2p) + (hi[d] - xi) / h * (Am + y1 * g1m + y2 * g2m) +
+                 (hi[d] - xi) * (xi - lo[d]) / (2.0 * h) * corr;
+    }
+}
+
 void og_interp(const og_grid* g, const double* U, const double* V, const double* W, const double* pts,
                int64_t np, double* vel) {
     const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
-    const double h = g->h;
     const int64_t eU[3] = {n0 + 1, n1, n2}, eV[3] = {n0, n1 + 1, n2}, eW[3] = {n0, n1, n2 + 1};
-    const double* F[3] = {U, V, W};
-    const int64_t* E[3] = {eU, eV, eW};
+    const double* const F[3] = {U, V, W};
+    const int64_t* const E[3] = {eU, eV, eW};
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < np; p++) og_interp_one(g, F, E, pts + 3 * p, vel + 3 * p);
+}
+
+/* One step of the classical fourth-order Runge-Kutta scheme for dx/dt = u(x)
+ * (Sec. 3.1), u the interpolated velocity of the face field, which is held
+ * fixed during the step:
+ *   k1 = u(x), k2 = u(x + dt/2 k1), k3 = u(x + dt/2 k2), k4 = u(x + dt k3),
+ *   x_new = x + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ * vel (may be NULL) receives k1, the interpolated velocity at the start. */
+void og_advect_rk4(const og_grid* g, const double* U, const double* V, const double* W, const double* pts,
+                   int64_t np, double dt, double* out, double* vel) {
+    const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+    const int64_t eU[3] = {n0 + 1, n1, n2}, eV[3] = {n0, n1 + 1, n2}, eW[3] = {n0, n1, n2 + 1};
+    const double* const F[3] = {U, V, W};
+    const int64_t* const E[3] = {eU, eV, eW};
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < np; p++) {
         const double* x = pts + 3 * p;
-        int64_t c[3];
-        double lo[3], hi[3];
+        double k1[3], k2[3], k3[3], k4[3], y[3];
+        og_interp_one(g, F, E, x, k1);
+        for (int d = 0; d < 3; d++) y[d] = x[d] + 0.5 * dt * k1[d];
+        og_interp_one(g, F, E, y, k2);
+        for (int d = 0; d < 3; d++) y[d] = x[d] + 0.5 * dt * k2[d];
+        og_interp_one(g, F, E, y, k3);
+        for (int d = 0; d < 3; d++) y[d] = x[d] + dt * k3[d];
+        og_interp_one(g, F, E, y, k4);
         for (int d = 0; d < 3; d++) {
-            double f = floor((x[d] - g->origin[d]) / h);
-            const int64_t nd = g->n[d];
-            c[d] = (f >= 0.0) ? ((f <= (double)(nd - 1)) ? (int64_t)f : nd - 1) : 0;
-            lo[d] = og_plane(g, d, c[d]);
-            hi[d] = og_plane(g, d, c[d] + 1);
-        }
-        /* component d along its own axis: faces c[d] (minus) and c[d]+1 (plus) */
-        for (int d = 0; d < 3; d++) {
-            const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-            const double* A = F[d];
-            const int64_t* ext = E[d];
-            int64_t im[3] = {c[0], c[1], c[2]}, ip[3] = {c[0], c[1], c[2]};
-            ip[d] += 1;
-            const double Am = og_at(A, ext[1], ext[2], im[0], im[1], im[2]);
-            const double Ap = og_at(A, ext[1], ext[2], ip[0], ip[1], ip[2]);
-            const double g1m = og_tgrad(A, ext, e1, im[0], im[1], im[2], h);
-            const double g2m = og_tgrad(A, ext, e2, im[0], im[1], im[2], h);
-            const double g1p = og_tgrad(A, ext, e1, ip[0], ip[1], ip[2], h);
-            const double g2p = og_tgrad(A, ext, e2, ip[0], ip[1], ip[2], h);
-            const double y1 = x[e1] - (lo[e1] + hi[e1]) / 2.0;
-            const double y2 = x[e2] - (lo[e2] + hi[e2]) / 2.0;
-            /* transverse derivatives along d of the two other components on their own faces */
-            double corr = 0.0;
-            for (int s = 1; s <= 2; s++) {
-                const int o = (d + s) % 3;
-                const double* B = F[o];
-                const int64_t* eb = E[o];
-                int64_t bm[3] = {c[0], c[1], c[2]}, bp[3] = {c[0], c[1], c[2]};
-                bp[o] += 1;
-                corr += og_tgrad(B, eb, d, bp[0], bp[1], bp[2], h) - og_tgrad(B, eb, d, bm[0], bm[1], bm[2], h);
-            }
-            const double xi = x[d];
-            vel[3 * p + d] = (xi - lo[d]) / h * (Ap + y1 * g1p + y2 * g2p) +
-                             (hi[d] - xi) / h * (Am + y1 * g1m + y2 * g2m) +
-                             (hi[d] - xi) * (xi - lo[d]) / (2.0 * h) * corr;
+            out[3 * p + d] = x[d] + dt / 6.0 * (k1[d] + 2.0 * k2[d] + 2.0 * k3[d] + k4[d]);
+            if (vel) vel[3 * p + d] = k1[d];
         }
     }
 }

@@ -92,6 +92,12 @@ int og_csf(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t
 void og_interp(const og_grid* g, const double* U, const double* V, const double* W,
                const double* pts, int64_t np, double* vel);
 
+/* One classical RK4 step of dx/dt = u(x) (Sec. 3.1) in the interpolated velocity
+ * of the fixed face field: out (np, 3) = new positions; vel (np, 3, may be NULL)
+ * = k1, the velocity at the start. */
+void og_advect_rk4(const og_grid* g, const double* U, const double* V, const double* W,
+                   const double* pts, int64_t np, double dt, double* out, double* vel);
+
 /* Helpers exposed for pin tests. */
 void og_green_moments(const double* x, const double* y, int n, double* m6);
 double og_signed_volume(const double* verts, const int32_t* tris, int64_t nt);

@@ -13,6 +13,7 @@ Every generator draws from ``numpy.random.Generator(PCG64(seed))``.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass
 
@@ -49,6 +50,17 @@ def rng(seed: int) -> np.random.Generator:
 # ----------------------------------------------------------------------------
 
 def icosphere(s: int):
+    """Unit icosphere after ``s`` 4-to-1 subdivisions (fresh copies of a cached mesh).
+
+    Returns ``verts (10*4^s+2, 3) float64`` on the unit sphere and
+    ``tris (20*4^s, 3) int32`` ordered counter-clockwise seen from outside.
+    """
+    v, t = _icosphere(s)
+    return v.copy(), t.copy()
+
+
+@functools.lru_cache(maxsize=None)
+def _icosphere(s: int):
     """Unit icosphere after ``s`` 4-to-1 subdivisions.
 
     Returns ``verts (10*4^s+2, 3) float64`` on the unit sphere and
@@ -297,3 +309,52 @@ def small_sphere(s: int, R: float, N: int, seed: int = 0, noise_h: float = 0.0):
     faces, omega = solid_body_faces(g, centre, gen)
     return dict(name=f"icosphere_s{s}_R{R}_{N}^3", grid=g, verts=verts, tris=tris,
                 faces=faces, centre=centre, R=R, omega=omega)
+
+
+# ----------------------------------------------------------------------------
+# batched form: many independent fronts of uneven size
+# ----------------------------------------------------------------------------
+
+def batch_fronts(seed: int = 5, count: int = 512, delta_max_h: float = 4.0, s_choices=(3, 4, 5, 6),
+                 n_choices=(32, 48, 64, 96), rmin_h: float = 3.0, rmax_h: float = 20.0, noise_h: float = 1e-3):
+    """``count`` independent rough icospheres, each on its own unit grid:
+    subdivision s ~ U(s_choices), N ~ U(n_choices), radius log-uniform in
+    [rmin_h h, rmax_h h] capped so that the front keeps the grid margin
+    2 + ceil(delta_max/h) (plus one cell), centre uniform where it fits,
+    radial roughness U[-noise_h h, noise_h h] per vertex.  Returns a list of
+    dicts (grid, verts, tris, centre, R, s, omega: the solid-body rotation
+    vector used for face velocities, capped: whether the radius was capped)."""
+    gen = rng(seed)
+    margin = 2 + math.ceil(delta_max_h)
+    out = []
+    for b in range(count):
+        s = int(gen.choice(s_choices))
+        N = int(gen.choice(n_choices))
+        g = unit_grid(N)
+        h = g.h
+        r = math.exp(gen.uniform(math.log(rmin_h * h), math.log(rmax_h * h)))
+        rcap = (N / 2 - margin - 2) * h
+        capped = r > rcap
+        r = min(r, rcap)
+        lo = (margin + 1) * h + r + 2 * noise_h * h
+        hi = 1.0 - lo
+        centre = np.array([gen.uniform(lo, hi) if hi > lo else 0.5 for _ in range(3)])
+        verts, tris = sphere_front(s, r, centre, radial_noise=noise_h * h, gen=gen)
+        a = gen.normal(size=3)
+        a /= np.linalg.norm(a)
+        out.append(dict(name=f"batch{b}_s{s}_N{N}", grid=g, verts=verts, tris=tris, centre=centre, R=r, s=s,
+                        omega=a, capped=capped))
+    return out
+
+
+def solid_body_faces_exact(g: Grid, centre, omega):
+    """Noise-free solid-body rotation u = omega x (x - c) at the face centres
+    (a linear divergence-free field, reproduced exactly by the interpolation)."""
+    w = np.asarray(omega, dtype=np.float64)
+    c = np.asarray(centre, dtype=np.float64)
+    out = []
+    for axis in range(3):
+        X, Y, Z = face_centres(g, axis)
+        r = np.stack([X - c[0], Y - c[1], Z - c[2]], -1)
+        out.append(np.ascontiguousarray(np.cross(np.broadcast_to(w, r.shape), r)[..., axis]))
+    return tuple(out)
