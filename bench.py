@@ -49,6 +49,12 @@ def parse():
                     help="time eager launches instead of one CUDA graph per step")
     ap.add_argument("--phase-steps", type=int, default=20, help="eager steps timed per phase")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=5,
+                    help="timed steps of the batched form (512 fronts); 0: skip")
+    ap.add_argument("--batch-fronts", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per served run; 0: skip")
+    ap.add_argument("--serve-rates", type=str, default="10,100,1000", help="Poisson arrival rates (req/s)")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="device memory for resident requests")
     return ap.parse_args()
 
 
@@ -389,13 +395,186 @@ def run_ours(a):
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }
+    for fc in fcs:
+        fc.ws.close()
+    if a.batch_steps > 0:
+        line["batched"] = run_batched(a, dev, local, flush)
+        torch.cuda.empty_cache()
+    if a.serve_requests > 0:
+        line["served"] = run_served(a, local)
+        torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cb, _ = cpu_baseline(fronts)
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for fc in fcs:
+
+
+def device_faces(f, dev):
+    """Noise-free solid-body rotation u = omega x (x - c) at the face centres of
+    front f's grid, built on the device (the batched workload's face velocities)."""
+    import torch
+    g = f["grid"]
+    c = [float(x) for x in f["centre"]]
+    w = [float(x) for x in f["omega"]]
+    out = []
+    for ax in range(3):
+        n = list(g.n)
+        n[ax] += 1
+        xs = [g.origin[d] + g.h * (torch.arange(n[d], device=dev, dtype=torch.float64) + (0.0 if d == ax else 0.5))
+              - c[d] for d in range(3)]
+        X, Y, Z = torch.meshgrid(*xs, indexing="ij")
+        u = (w[1] * Z - w[2] * Y, w[2] * X - w[0] * Z, w[0] * Y - w[1] * X)[ax]
+        out.append(u.contiguous())
+    return out
+
+
+def run_batched(a, dev, local, flush):
+    """The batched form: the 512-front workload (icospheres s3-6 on 32^3-96^3
+    grids) through the batched entry points, one CUDA graph per step, launch
+    shapes from ft_autotune; FP32-compensated and FP64, and the same fronts
+    through the one-front entry points in a loop for comparison."""
+    import torch
+    from paper_2505_06932_gb300 import _front as F
+    from paper_2505_06932_gb300 import inputs as I
+    fr = I.batch_fronts(5, a.batch_fronts)
+    dl = []
+    for f in fr:
+        U, V, W = device_faces(f, dev)
+        dl.append(dict(grid=f["grid"], verts=torch.from_numpy(f["verts"]).to(dev),
+                       tris=torch.from_numpy(f["tris"]).to(dev), U=U, V=V, W=W))
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{len(fr)} fronts: icosphere s3-6, grids 32^3/48^3/64^3/96^3, radius log-uniform in "
+                       f"[3h, 20h] (capped at (N/2-8)h), radial roughness 1e-3 h",
+           "fronts": len(fr), "triangles": int(sum(f["tris"].shape[0] for f in fr)),
+           "grid_cells": int(sum(f["grid"].ncells for f in fr)),
+           "radius_capped": int(sum(f["capped"] for f in fr)),
+           "launch": "one CUDA graph per step: front_bin_batch, front_volume_fraction_batch, "
+                     "front_curvature_ppic, front_csf_force_batch, ft_batch_cell_ranges, "
+                     "front_interp_velocity_batch",
+           "l2": "inputs larger than L2 (dense fields alone 1.4 GB) and a 512 MB flush before every timed step"}
+    tuning = None
+    for prec, tag in ((F.FT_FP32C, "fp32c"), (F.FT_FP64, "fp64")):
+        prm = F.make_params(precision=prec)
+        bc = F.BatchCoupling(dl, params=prm, headroom=1.02, device=local)
+        if tuning is None:
+            tuning = F.ft_autotune(bc.ws, prm, reps=2)
+            out["tuning"] = {k: tuning[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm",
+                                                    "csf_blocks_per_sm", "fill_blocks_per_sm", "ppic_min_blocks",
+                                                    "ppic_dynamic")}
+        else:
+            F.ft_set_tuning(bc.ws, clip=tuning["clip_blocks_per_sm"], ppic=tuning["ppic_blocks_per_sm"],
+                            csf=tuning["csf_blocks_per_sm"], fill=tuning["fill_blocks_per_sm"],
+                            ppic_min_blocks=tuning["ppic_min_blocks"], ppic_dynamic=tuning["ppic_dynamic"])
+        for _ in range(3):
+            bc.step()
+        torch.cuda.synchronize()
+        st = bc.ws.status()
+        fst = bc.ws.front_status()
+        if st or any(fst):
+            raise RuntimeError(f"batched form: device status {F.status_names(st)}")
+        c = bc.ws.counts()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bc.step()
+        g.replay()
+        torch.cuda.synchronize()
+        steps = a.batch_steps if prec == F.FT_FP32C else max(1, a.batch_steps // 2)
+        l0 = F.launch_count()
+        bc.step()
+        torch.cuda.synchronize()
+        per_step = F.launch_count() - l0
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        if bc.ws.status() or any(bc.ws.front_status()):
+            raise RuntimeError("batched form: device status after the timed steps")
+        out[tag] = {"value": round(c["M"] * steps / (tot * 1e-3), 1), "ms_per_step": round(tot / steps, 3),
+                    "steps": steps, "cells_per_step": c["M"], "pairs_per_step": c["P"],
+                    "fit_pairs_per_step": c["fit_pairs"], "kernels_per_step": per_step,
+                    "workspace_bytes": bc.ws.bytes}
+        del g
+        bc.ws.close()
+        del bc
+        torch.cuda.empty_cache()
+    # the same fronts through the one-front entry points, front after front (eager)
+    prm = F.make_params(precision=F.FT_FP32C)
+    fcs = {}
+    for f, d in zip(fr, dl):
+        N = f["grid"].n[0]
+        if N not in fcs:
+            mt = max(x["tris"].shape[0] for x in fr if x["grid"].n[0] == N)
+            mv = max(x["verts"].shape[0] for x in fr if x["grid"].n[0] == N)
+            fcs[N] = F.FrontCoupling(f["grid"], mt, mv, params=prm, device=local)
+    for _ in range(2):
+        for f, d in zip(fr, dl):
+            fcs[f["grid"].n[0]].step(d["verts"], d["tris"], (d["U"], d["V"], d["W"]))
+    torch.cuda.synchronize()
+    loop_steps = max(1, a.batch_steps // 2)
+    tot = 0.0
+    for _ in range(loop_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for f, d in zip(fr, dl):
+            fcs[f["grid"].n[0]].step(d["verts"], d["tris"], (d["U"], d["V"], d["W"]))
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    M = out["fp32c"]["cells_per_step"]
+    out["per_front_loop_fp32c"] = {"value": round(M * loop_steps / (tot * 1e-3), 1),
+                                   "ms_per_step": round(tot / loop_steps, 3), "steps": loop_steps,
+                                   "launch": "eager, one-front entry points, fronts in sequence"}
+    for fc in fcs.values():
         fc.ws.close()
+    return out
+
+
+def run_served(a, local):
+    """The served form: request streams (Poisson arrivals) of SH-deformed fronts
+    on 32^3-512^3 grids, 1-50 steps each, served with continuous batching in the
+    FP32 form; the same stream served by the plain FP64 path one request at a
+    time.  Latency = arrival -> end of the request's last step (wall clock)."""
+    import torch
+    from paper_2505_06932_gb300 import _front as F
+    from paper_2505_06932_gb300 import inputs as I
+    from paper_2505_06932_gb300 import serve as S
+
+    def requests(rate):
+        rq = I.served_requests(11, a.serve_requests, rate)
+        return [S.Request(r["rid"], r["grid"], r["verts"], r["tris"], r["steps"], r["arrival"], r["dt"],
+                          tuple(r["centre"]), tuple(r["omega"])) for r in rq]
+
+    rates = [float(x) for x in a.serve_rates.split(",") if x]
+    budget = int(a.serve_budget_gb * 2 ** 30)
+    probe = requests(rates[0])
+    cap = S.Capacity(budget_bytes=budget, max_fronts=256,
+                     max_grid_cells=min(2 ** 32 - 2, budget // 56),
+                     max_nt=sum(r.tris.shape[0] for r in probe),
+                     max_cand=sum(S.candidate_estimate(r) for r in probe))
+    out = {"workload": f"{a.serve_requests} requests per rate: icosphere s4-7 with real SH deformation "
+                       f"(l 2-8, c ~ N(0,(0.05R)^2)), grids 32^3-512^3, 1-50 steps of dt = 0.25h each "
+                       f"(bin, alpha, PPIC, CSF, RK4 advection), solid-body rotation about the front centre",
+           "budget_bytes": budget, "admission": "FIFO by device footprint and batch capacities",
+           "precision": "fp32c", "rates": {}}
+    ex = S.BatchExecutor(cap, F.make_params(precision=F.FT_FP32C), device=local)
+    S.serve(requests(rates[0])[:2], ex, cap, realtime=False)          # warm-up
+    for rate in rates:
+        torch.cuda.synchronize()
+        _, st = S.serve(requests(rate), ex, cap, realtime=True)
+        out["rates"][str(int(rate))] = st
+    ex.close()
+    seq = S.SequentialExecutor(F.make_params(precision=F.FT_FP64), device=local)
+    _, st = S.serve_sequential(requests(rates[0]), seq, realtime=True)
+    st["rate"] = rates[0]
+    out["plain_fp64_one_at_a_time"] = st
+    return out
 
 
 def run_reference(a):

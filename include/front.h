@@ -180,6 +180,16 @@ int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, c
 int front_interp_velocity(const ft_grid* g, const double* U, const double* V, const double* W,
                           const double* verts, int64_t nv, double* vel, void* stream);
 
+/* Front advection (Sec. 3.1): one classical fourth-order Runge-Kutta step of
+ * dx/dt = u(x) for the nv points verts, u the interpolated velocity of
+ * front_interp_velocity with the face field U, V, W held fixed during the step:
+ * k1 = u(x), k2 = u(x + dt/2 k1), k3 = u(x + dt/2 k2), k4 = u(x + dt k3),
+ * verts_out = x + dt/6 (k1 + 2 k2 + 2 k3 + k4).  verts_out (nv x 3) may be verts
+ * itself (each point's stages read only that point); vel (nv x 3, may be NULL)
+ * receives k1.  Points must stay inside the grid. */
+int front_advect_rk4(const ft_grid* g, const double* U, const double* V, const double* W, const double* verts,
+                     int64_t nv, double dt, double* verts_out, double* vel, void* stream);
+
 /* Allocation-free volume fraction (no counterpart in the paper).
  *
  * Some callers cannot allocate device memory while they run: a flow solver
@@ -212,6 +222,130 @@ int front_interp_velocity(const ft_grid* g, const double* U, const double* V, co
 #define FT_NOALLOC_MAX_CANDIDATES 32768
 int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, const ft_params* p, double* alpha,
                                uint32_t* status, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched form (no counterpart in the paper, which couples one front per
+ * simulation).  Many independent fronts, each with its own grid, run through
+ * one launch sequence: their cells share one batch-global key space (front b's
+ * cell with local key q has key key_base[b] + q, key_base[b] = sum of the
+ * earlier fronts' n0*n1*n2), one radix sort and one interfacial-cell worklist,
+ * so small fronts do not each pay a launch sequence.  Every front's results are
+ * bit for bit those of the one-front calls on that front alone (each cell's
+ * sums run over the same fragments in the same order).  Errors of one front (outside
+ * the grid, bad index, not closed, inverted) skip or flag that front only and
+ * are reported per front by ft_batch_status; capacity errors concern the batch.
+ * --------------------------------------------------------------------------- */
+
+/* One front of a batch: its grid and its device arrays, owned by the caller and
+ * kept alive while the table is in use.  alpha (n0*n1*n2 float64) is written by
+ * front_volume_fraction_batch and read by front_csf_force_batch; force
+ * (3 x n0*n1*n2 SoA) is written by front_csf_force_batch; U, V, W (faces as in
+ * front_interp_velocity) are read and vel (nv x 3) written by
+ * front_interp_velocity_batch and front_advect_rk4_batch, which writes the
+ * advected positions to verts_next.  Pointers of steps that are not called may
+ * be NULL. */
+typedef struct {
+    ft_grid grid;
+    const double* verts;
+    int64_t nv;
+    const int32_t* tris; /* indices into this front's verts */
+    int64_t nt;
+    double* alpha;
+    double* force;
+    const double* U;
+    const double* V;
+    const double* W;
+    double* vel;
+    double* verts_next; /* front_advect_rk4_batch output positions (may equal verts) */
+    double dt;          /* front_advect_rk4_batch time step of this front            */
+} ft_batch_front;
+
+/* Capacities of a batch workspace; 0 selects the default of ft_capacity. */
+typedef struct {
+    int32_t max_fronts;     /* fronts in one table                                 */
+    int32_t pad;
+    int64_t max_grid_cells; /* sum of n0*n1*n2 over the table (< 2^32 - 1)          */
+    int64_t max_nt;         /* sum of triangles over the table                      */
+    int64_t max_cand;       /* (triangle, candidate cell) pairs (default 16*max_nt) */
+    int64_t max_cells;      /* interfacial cells (default max_cand)                 */
+} ft_batch_capacity;
+
+/* Create a batch workspace on `device`; *bytes (host, may be NULL) receives the
+ * device memory it holds (the index map takes 4 B per grid cell). */
+int ft_batch_workspace_create(ft_workspace** ws, const ft_batch_capacity* cap, int device, size_t* bytes);
+
+/* Install the table of nf fronts (host array) on the workspace: copies the
+ * descriptors to the device on `stream` and synchronizes it.  Returns
+ * FT_ERR_CAPACITY if the table exceeds the workspace.  Not capturable in a CUDA
+ * graph; graphs captured earlier keep the previous table's launch sizes and
+ * must be captured again. */
+int ft_batch_set(ft_workspace* ws, int32_t nf, const ft_batch_front* fronts, void* stream);
+
+/* (a1) front_bin over every front of the table; cell keys are batch-global. */
+int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream);
+
+/* (a2) front_volume_fraction of every front into its own alpha array. */
+int front_volume_fraction_batch(ft_workspace* ws, void* stream);
+
+/* (a3) is front_curvature_ppic itself: on a batch workspace its M outputs cover
+ * every front in ascending batch-global key order, so front b's cells are the
+ * rows [off[b], off[b+1]) given by ft_batch_cell_ranges. */
+
+/* (a4) front_csf_force of every front from its alpha into its force. */
+int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                          void* stream);
+
+/* (a5) front_interp_velocity of every front (its U, V, W, verts -> vel). */
+int front_interp_velocity_batch(ft_workspace* ws, void* stream);
+
+/* Front advection of every front of the table: front_advect_rk4 with its
+ * verts, U, V, W and dt into verts_next (vel, if not NULL, receives k1). */
+int front_advect_rk4_batch(ft_workspace* ws, void* stream);
+
+/* off (device, nf + 1 int64): first row of each front in the outputs of
+ * front_curvature_ppic; off[nf] = M.  Needs front_bin_batch. */
+int ft_batch_cell_ranges(ft_workspace* ws, int64_t* off, void* stream);
+
+/* Synchronize `stream`, write the FT_ST_* bits of each front (host, nf
+ * uint32) and clear them (the workspace-wide word of ft_status is separate). */
+int ft_batch_status(ft_workspace* ws, void* stream, uint32_t* bits);
+
+/* ---------------------------------------------------------------------------
+ * Launch tuning (no counterpart in the paper).  The grid sizes of the kernels
+ * whose work is distributed over a grid-stride or work-counter loop (any value
+ * from 1 to 32), the register/occupancy variant and the cell schedule of the
+ * PPIC accumulation; every choice gives the same results.  ft_autotune picks
+ * them by timing.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+    int32_t clip_blocks_per_sm; /* canonical clip (front_bin), default 4            */
+    int32_t ppic_blocks_per_sm; /* PPIC accumulation, default 4                      */
+    int32_t csf_blocks_per_sm;  /* CSF dense pass, default 16                        */
+    int32_t fill_blocks_per_sm; /* column parity fill, default 8                     */
+    int32_t ppic_min_blocks;    /* FP32 PPIC accumulation compiled for 4 (default) or
+                                   6 resident blocks per SM (fewer registers each)   */
+    int32_t ppic_dynamic;       /* PPIC cells from a global work counter (1) or
+                                   interleaved over the warps (0, default)           */
+    /* outputs of ft_autotune: what the tuned workload needed, for sizing a
+     * workspace (ft_capacity / ft_batch_capacity) to it */
+    int64_t cand_need;
+    int64_t cells_need;
+    int64_t fit_pairs;
+    double step_ms;             /* bin + alpha + PPIC + CSF time with the result  */
+} ft_tuning;
+
+int ft_set_tuning(ft_workspace* ws, const ft_tuning* t);
+int ft_get_tuning(ft_workspace* ws, ft_tuning* t);
+
+/* Time bin + volume fraction + PPIC + CSF on this workspace for a set of launch
+ * shapes (coordinate by coordinate, `reps` timed runs each after one warm-up,
+ * median time) and install the fastest; *best (host) receives it.  f is the
+ * front for a one-front workspace and NULL for a batch workspace (the table's
+ * alpha and force arrays are overwritten).  Allocates and frees temporary
+ * device memory for the outputs and synchronizes `stream`: call it at set-up,
+ * not inside a capture. */
+int ft_autotune(ft_workspace* ws, const ft_front* f, const ft_params* p, int32_t reps, ft_tuning* best,
+                void* stream);
 
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all workspaces). */

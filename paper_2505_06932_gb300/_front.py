@@ -39,6 +39,27 @@ class FtCapacity(C.Structure):
     _fields_ = [("max_nt", C.c_int64), ("max_cand", C.c_int64), ("max_cells", C.c_int64)]
 
 
+class FtBatchFront(C.Structure):
+    _fields_ = [("grid", FtGrid), ("verts", C.c_void_p), ("nv", C.c_int64), ("tris", C.c_void_p), ("nt", C.c_int64),
+                ("alpha", C.c_void_p), ("force", C.c_void_p), ("U", C.c_void_p), ("V", C.c_void_p),
+                ("W", C.c_void_p), ("vel", C.c_void_p), ("verts_next", C.c_void_p), ("dt", C.c_double)]
+
+
+class FtBatchCapacity(C.Structure):
+    _fields_ = [("max_fronts", C.c_int32), ("pad", C.c_int32), ("max_grid_cells", C.c_int64),
+                ("max_nt", C.c_int64), ("max_cand", C.c_int64), ("max_cells", C.c_int64)]
+
+
+class FtTuning(C.Structure):
+    _fields_ = [("clip_blocks_per_sm", C.c_int32), ("ppic_blocks_per_sm", C.c_int32),
+                ("csf_blocks_per_sm", C.c_int32), ("fill_blocks_per_sm", C.c_int32),
+                ("ppic_min_blocks", C.c_int32), ("ppic_dynamic", C.c_int32), ("cand_need", C.c_int64), ("cells_need", C.c_int64), ("fit_pairs", C.c_int64),
+                ("step_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FrontError(RuntimeError):
     pass
 
@@ -66,6 +87,19 @@ def lib():
                 "ft_probe_fma_rate": (I32, [I32, I32, C.POINTER(C.c_double)]),
                 "ft_launch_count": (I64, []),
                 "ft_volume_fraction_noalloc": (I32, [P, P, P, P, P, P]),
+                "ft_batch_workspace_create": (I32, [C.POINTER(P), P, I32, C.POINTER(C.c_size_t)]),
+                "ft_batch_set": (I32, [P, I32, P, P]),
+                "front_bin_batch": (I32, [P, P, P]),
+                "front_volume_fraction_batch": (I32, [P, P]),
+                "front_csf_force_batch": (I32, [P, P, P, P, P]),
+                "front_interp_velocity_batch": (I32, [P, P]),
+                "ft_batch_cell_ranges": (I32, [P, P, P]),
+                "ft_batch_status": (I32, [P, P, P]),
+                "ft_set_tuning": (I32, [P, P]),
+                "ft_get_tuning": (I32, [P, P]),
+                "ft_autotune": (I32, [P, P, P, I32, P, P]),
+                "front_advect_rk4": (I32, [P, P, P, P, P, I64, C.c_double, P, P, P]),
+                "front_advect_rk4_batch": (I32, [P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -149,6 +183,61 @@ class Workspace:
         return dict(M=out[0], P=out[1], C=out[2], C_need=out[3], fit_pairs=out[4])
 
 
+class BatchWorkspace(Workspace):
+    """Library-owned device memory for a batch of fronts (ft_batch_workspace_create).
+    ``set_fronts`` installs the table; the tensors it references are kept alive here."""
+
+    def __init__(self, max_fronts: int, max_grid_cells: int, max_nt: int, max_cand: int = 0, max_cells: int = 0,
+                 device: int = 0):
+        cap = FtBatchCapacity(int(max_fronts), 0, int(max_grid_cells), int(max_nt), int(max_cand), int(max_cells))
+        h = C.c_void_p()
+        nbytes = C.c_size_t()
+        _check(lib().ft_batch_workspace_create(C.byref(h), C.byref(cap), int(device), C.byref(nbytes)),
+               "ft_batch_workspace_create")
+        self.handle = h
+        self.bytes = int(nbytes.value)
+        self.device = device
+        self.grid = None
+        self.nf = 0
+        self._keep = []
+
+    def set_fronts(self, fronts, stream=None):
+        """fronts: list of dicts with keys grid, verts, tris and optionally
+        alpha, force, U, V, W, vel (CUDA tensors)."""
+        arr = (FtBatchFront * len(fronts))()
+        keep = []
+        for b, f in enumerate(fronts):
+            e = arr[b]
+            e.grid = make_grid(f["grid"])
+            n = f["grid"].n
+            e.verts = _ptr(f["verts"], torch.float64, "verts")
+            e.nv = f["verts"].shape[0]
+            e.tris = _ptr(f["tris"], torch.int32, "tris")
+            e.nt = f["tris"].shape[0]
+            nc = int(n[0]) * int(n[1]) * int(n[2])
+            for name, size in (("alpha", nc), ("force", 3 * nc), ("vel", 3 * e.nv), ("verts_next", 3 * e.nv)):
+                t = f.get(name)
+                if t is not None and t.numel() != size:
+                    raise FrontError(f"front {b}: {name} must hold {size} values")
+                setattr(e, name, _ptr(t, torch.float64, name) if t is not None else None)
+            for name, shp in (("U", (n[0] + 1, n[1], n[2])), ("V", (n[0], n[1] + 1, n[2])),
+                              ("W", (n[0], n[1], n[2] + 1))):
+                t = f.get(name)
+                if t is not None and tuple(t.shape) != tuple(int(x) for x in shp):
+                    raise FrontError(f"front {b}: {name} has the wrong shape")
+                setattr(e, name, _ptr(t, torch.float64, name) if t is not None else None)
+            e.dt = float(f.get("dt", 0.0))
+            keep.append(f)
+        _check(lib().ft_batch_set(self.handle, len(fronts), arr, _stream(stream)), "ft_batch_set")
+        self._keep = keep
+        self.nf = len(fronts)
+
+    def front_status(self, stream=None):
+        out = (C.c_uint32 * max(self.nf, 1))()
+        _check(lib().ft_batch_status(self.handle, _stream(stream), out), "ft_batch_status")
+        return [int(out[b]) for b in range(self.nf)]
+
+
 def ft_bin_pairs(ws: Workspace, keys: torch.Tensor, tris: torch.Tensor, stream=None):
     cap = min(keys.shape[0], tris.shape[0])
     _check(lib().ft_bin_pairs(ws.handle, cap, _ptr(keys, torch.int32, "keys"), _ptr(tris, torch.int32, "tris"),
@@ -206,6 +295,27 @@ def front_interp_velocity(grid, U, V, W, verts, vel, stream=None):
            "front_interp_velocity")
 
 
+def front_advect_rk4(grid, U, V, W, verts, dt, verts_out, vel=None, stream=None):
+    """One RK4 step of the points (verts_out may be verts; vel receives k1)."""
+    g = make_grid(grid)
+    n = grid.n
+    if tuple(U.shape) != (n[0] + 1, n[1], n[2]) or tuple(V.shape) != (n[0], n[1] + 1, n[2]) \
+            or tuple(W.shape) != (n[0], n[1], n[2] + 1):
+        raise FrontError("face arrays have the wrong shapes")
+    if verts_out.shape != verts.shape or (vel is not None and vel.shape != verts.shape):
+        raise FrontError("verts_out and vel must have the shape of verts")
+    _check(lib().front_advect_rk4(C.byref(g), _ptr(U, torch.float64, "U"), _ptr(V, torch.float64, "V"),
+                                  _ptr(W, torch.float64, "W"), _ptr(verts, torch.float64, "verts"), verts.shape[0],
+                                  float(dt), _ptr(verts_out, torch.float64, "verts_out"),
+                                  _ptr(vel, torch.float64, "vel") if vel is not None else None, _stream(stream)),
+           "front_advect_rk4")
+
+
+def front_advect_rk4_batch(ws: "BatchWorkspace", stream=None):
+    """RK4 step of every front of the table with its own dt."""
+    _check(lib().front_advect_rk4_batch(ws.handle, _stream(stream)), "front_advect_rk4_batch")
+
+
 def ft_volume_fraction_noalloc(grid, verts, tris, params: FtParams, alpha, status, stream=None):
     """Binning + volume fraction with the library's static scratch (no device
     allocation); status is a 1-element int32 CUDA tensor receiving FT_ST_* bits."""
@@ -216,6 +326,56 @@ def ft_volume_fraction_noalloc(grid, verts, tris, params: FtParams, alpha, statu
     _check(lib().ft_volume_fraction_noalloc(C.byref(g), C.byref(f), C.byref(params),
                                             _ptr(alpha, torch.float64, "alpha"), _ptr(status, torch.int32, "status"),
                                             _stream(stream)), "ft_volume_fraction_noalloc")
+
+
+def front_bin_batch(ws: BatchWorkspace, params: FtParams, stream=None):
+    _check(lib().front_bin_batch(ws.handle, C.byref(params), _stream(stream)), "front_bin_batch")
+
+
+def front_volume_fraction_batch(ws: BatchWorkspace, stream=None):
+    _check(lib().front_volume_fraction_batch(ws.handle, _stream(stream)), "front_volume_fraction_batch")
+
+
+def front_csf_force_batch(ws: BatchWorkspace, params: FtParams, kappa, normal, stream=None):
+    _check(lib().front_csf_force_batch(ws.handle, C.byref(params), _ptr(kappa, torch.float64, "kappa"),
+                                       _ptr(normal, torch.float64, "normal"), _stream(stream)),
+           "front_csf_force_batch")
+
+
+def front_interp_velocity_batch(ws: BatchWorkspace, stream=None):
+    _check(lib().front_interp_velocity_batch(ws.handle, _stream(stream)), "front_interp_velocity_batch")
+
+
+def ft_batch_cell_ranges(ws: BatchWorkspace, off: torch.Tensor, stream=None):
+    if off.numel() < ws.nf + 1:
+        raise FrontError("off must hold nf + 1 values")
+    _check(lib().ft_batch_cell_ranges(ws.handle, _ptr(off, torch.int64, "off"), _stream(stream)),
+           "ft_batch_cell_ranges")
+
+
+def ft_set_tuning(ws: Workspace, clip=4, ppic=4, csf=16, fill=8, ppic_min_blocks=4, ppic_dynamic=0):
+    t = FtTuning(int(clip), int(ppic), int(csf), int(fill), int(ppic_min_blocks), int(ppic_dynamic), 0, 0, 0, 0.0)
+    _check(lib().ft_set_tuning(ws.handle, C.byref(t)), "ft_set_tuning")
+
+
+def ft_get_tuning(ws: Workspace) -> dict:
+    t = FtTuning()
+    _check(lib().ft_get_tuning(ws.handle, C.byref(t)), "ft_get_tuning")
+    return t.as_dict()
+
+
+def ft_autotune(ws: Workspace, params: FtParams, reps: int = 5, verts=None, tris=None, stream=None) -> dict:
+    """Times launch shapes on the workspace's workload and installs the fastest
+    (verts/tris for a one-front workspace; None for a batch workspace)."""
+    t = FtTuning()
+    if verts is not None:
+        f = FtFront(_ptr(verts, torch.float64, "verts"), verts.shape[0], _ptr(tris, torch.int32, "tris"),
+                    tris.shape[0])
+        fp = C.byref(f)
+    else:
+        fp = None
+    _check(lib().ft_autotune(ws.handle, fp, C.byref(params), int(reps), C.byref(t), _stream(stream)), "ft_autotune")
+    return t.as_dict()
 
 
 def launch_count() -> int:
@@ -279,3 +439,79 @@ class FrontCoupling:
             force=self.force.view((3,) + n).cpu().numpy(),
             vel=self.vel[:nv].cpu().numpy(),
         )
+
+
+class BatchCoupling:
+    """A batch workspace, per-front device outputs (alpha, force, vel) and the
+    batch-wide PPIC outputs; runs the five steps over every front at once."""
+
+    def __init__(self, fronts, params: FtParams | None = None, max_cand: int = 0, max_cells: int = 0,
+                 device: int = 0, headroom: float = 1.0):
+        """fronts: list of dicts with grid, verts, tris and optional U, V, W.
+        max_cand = 0 sizes the candidate buffers exactly: a first binning on a
+        small workspace reports the pairs needed (ft_counts), times headroom."""
+        self.params = params or make_params()
+        dev = torch.device("cuda", device)
+        cells = sum(int(f["grid"].ncells) for f in fronts)
+        nt = sum(int(f["tris"].shape[0]) for f in fronts)
+        if not max_cand:
+            # per-triangle counts are exact up to the probe's capacity
+            probe = BatchWorkspace(len(fronts), cells, max(nt, 1), max_cand=1 << 20, max_cells=1024, device=device)
+            probe.set_fronts([dict(grid=f["grid"], verts=f["verts"], tris=f["tris"]) for f in fronts])
+            front_bin_batch(probe, self.params)
+            max_cand = int(probe.counts()["C_need"] * headroom) + 1024
+            probe.status()
+            probe.front_status()
+            probe.close()
+        self.ws = BatchWorkspace(len(fronts), int(cells * headroom) + 1, int(nt * headroom) + 1,
+                                 max_cand=max_cand, max_cells=max_cells, device=device)
+        cap = max_cand if max_cand else 16 * (int(nt * headroom) + 1) + 1024
+        self.cap_cells = max_cells if max_cells else cap
+        self.fronts = []
+        for f in fronts:
+            g = f["grid"]
+            d = dict(f)
+            d.setdefault("alpha", torch.empty(g.ncells, dtype=torch.float64, device=dev))
+            d.setdefault("force", torch.empty(3 * g.ncells, dtype=torch.float64, device=dev))
+            if "U" in f:
+                d.setdefault("vel", torch.empty((f["verts"].shape[0], 3), dtype=torch.float64, device=dev))
+            self.fronts.append(d)
+        self.ws.set_fronts(self.fronts)
+        M = self.cap_cells
+        self.cell_keys = torch.empty(M, dtype=torch.int32, device=dev)
+        self.kappa = torch.empty(M, dtype=torch.float64, device=dev)
+        self.normal = torch.empty((M, 3), dtype=torch.float64, device=dev)
+        self.coeffs = torch.empty((M, 6), dtype=torch.float64, device=dev)
+        self.fit_status = torch.empty(M, dtype=torch.int8, device=dev)
+        self.off = torch.empty(len(fronts) + 1, dtype=torch.int64, device=dev)
+
+    def step(self, stream=None, interp: bool = True):
+        p, ws = self.params, self.ws
+        front_bin_batch(ws, p, stream)
+        front_volume_fraction_batch(ws, stream)
+        front_curvature_ppic(ws, p, self.cell_keys, self.kappa, self.normal, self.coeffs, self.fit_status, stream)
+        front_csf_force_batch(ws, p, self.kappa, self.normal, stream)
+        ft_batch_cell_ranges(ws, self.off, stream)
+        if interp and all("U" in f for f in self.fronts):
+            front_interp_velocity_batch(ws, stream)
+
+    def results(self, b: int):
+        """Synchronizes and returns host copies (numpy) of front b's outputs,
+        with its cell keys made front-local."""
+        off = self.off.cpu().numpy()
+        lo, hi = int(off[b]), int(off[b + 1])
+        f = self.fronts[b]
+        n = tuple(int(x) for x in f["grid"].n)
+        kb = sum(int(x["grid"].ncells) for x in self.fronts[:b])
+        out = dict(
+            alpha=f["alpha"].view(n).cpu().numpy(),
+            cell_keys=(self.cell_keys[lo:hi].cpu().numpy().view("uint32").astype("int64") - kb).astype("uint32"),
+            kappa=self.kappa[lo:hi].cpu().numpy(),
+            normal=self.normal[lo:hi].cpu().numpy(),
+            coeffs=self.coeffs[lo:hi].cpu().numpy(),
+            fit_status=self.fit_status[lo:hi].cpu().numpy(),
+            force=f["force"].view((3,) + n).cpu().numpy(),
+        )
+        if "vel" in f:
+            out["vel"] = f["vel"].cpu().numpy()
+        return out

@@ -47,9 +47,82 @@ void release(ft_workspace* ws) {
     void* ptrs[] = {ws->ctr,     ws->idx_map, ws->tri_cnt,  ws->tri_off,  ws->tri_box, ws->cand_tri,
                     ws->keys[0], ws->keys[1], ws->vals[0],  ws->vals[1],  ws->rec,     ws->cells,
                     ws->cell_off, ws->heads,  ws->cell_L,   ws->cell_P,   ws->partials, ws->hist,
-                    ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info, ws->srec, ws->srec32, ws->scen};
+                    ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info, ws->srec, ws->srec32, ws->scen,
+                    ws->fdesc,   ws->fbase,   ws->fstatus, ws->tri_nrm, ws->planes};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (ws->h_fdesc) cudaFreeHost(ws->h_fdesc);
+    if (ws->h_fbase) cudaFreeHost(ws->h_fbase);
+}
+
+int key_bits_for(long long ncells) {
+    int bits = 1;
+    while (bits < 32 && ((ncells - 1) >> bits) > 0) bits++;
+    return bits < 8 ? 8 : bits;
+}
+
+// Device memory of a workspace for `map_cells` index-map entries, once the
+// capacities are set; frees everything and returns FT_ERR_ALLOC on failure.
+int allocate(ft_workspace* ws, long long map_cells) {
+    cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, ws->device);
+    // segments of the scan / sort kernels; the sort stages 256 x grid_blocks counts in shared memory
+    ws->grid_blocks = ws->sm_count > 192 ? 192 : ws->sm_count;
+    ws->tune = ft_tune{4, 4, 16, 8, 4, 0};
+    size_t tot = 0;
+    cudaError_t e = cudaSuccess;
+    const size_t C = (size_t)ws->max_cand, Mx = (size_t)ws->max_cells, T = (size_t)ws->max_nt;
+    e = e ? e : alloc(&ws->ctr, 1, &tot);
+    e = e ? e : alloc(&ws->idx_map, (size_t)map_cells, &tot);
+    e = e ? e : alloc(&ws->tri_cnt, T, &tot);
+    e = e ? e : alloc(&ws->tri_off, T, &tot);
+    e = e ? e : alloc(&ws->tri_box, 8 * T, &tot);
+    e = e ? e : alloc(&ws->tri_nrm, 4 * T, &tot);
+    if (!ws->batch) {
+        ws->planes_cap = ft_plane_count(ws->g);
+        e = e ? e : alloc(&ws->planes, (size_t)ws->planes_cap, &tot);
+        if (e == cudaSuccess) e = ft::launch_planes_one(ws, 0);
+    }
+    e = e ? e : alloc(&ws->cand_tri, C, &tot);
+    e = e ? e : alloc(&ws->keys[0], C, &tot);
+    e = e ? e : alloc(&ws->keys[1], C, &tot);
+    e = e ? e : alloc(&ws->vals[0], C, &tot);
+    e = e ? e : alloc(&ws->vals[1], C, &tot);
+    e = e ? e : alloc(&ws->rec, C, &tot);
+    e = e ? e : alloc(&ws->rec32, C, &tot);
+    e = e ? e : alloc(&ws->cen32, C, &tot);
+    e = e ? e : alloc(&ws->srec, C, &tot);
+    e = e ? e : alloc(&ws->srec32, C, &tot);
+    e = e ? e : alloc(&ws->scen, C, &tot);
+    e = e ? e : alloc(&ws->sys, Mx, &tot);
+    e = e ? e : alloc(&ws->fit_info, 2 * Mx, &tot);
+    e = e ? e : alloc(&ws->cells, Mx + 1, &tot);
+    e = e ? e : alloc(&ws->cell_off, Mx + 1, &tot);
+    e = e ? e : alloc(&ws->heads, C, &tot);
+    e = e ? e : alloc(&ws->cell_L, Mx, &tot);
+    e = e ? e : alloc(&ws->cell_P, Mx, &tot);
+    e = e ? e : alloc(&ws->partials, 2 * (size_t)(ws->grid_blocks + 1), &tot);
+    e = e ? e : alloc(&ws->hist, 256 * (size_t)ws->grid_blocks, &tot);
+    if (ws->batch) {
+        const size_t F = (size_t)ws->max_fronts;
+        e = e ? e : alloc(&ws->fdesc, F, &tot);
+        e = e ? e : alloc(&ws->fbase, 4 * (F + 1), &tot);
+        e = e ? e : alloc(&ws->fstatus, F, &tot);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&ws->h_fdesc), F * sizeof(ft_fdesc));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(reinterpret_cast<void**>(&ws->h_fbase), 4 * (F + 1) * sizeof(long long));
+        if (e == cudaSuccess) e = cudaMemset(ws->fstatus, 0, F * sizeof(unsigned));
+    }
+    if (e == cudaSuccess) e = ft::prepare_sort(ws->grid_blocks);
+    if (e == cudaSuccess) e = cudaMemset(ws->ctr, 0, sizeof(ft_counters));
+    if (e == cudaSuccess) e = cudaMemset(ws->idx_map, 0xff, sizeof(int) * (size_t)map_cells);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        release(ws);
+        cudaGetLastError();
+        return FT_ERR_ALLOC;
+    }
+    ws->bytes = tot;
+    return FT_OK;
 }
 
 }  // namespace
@@ -88,53 +161,132 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
         free(ws);
         return FT_ERR_ARG;
     }
-    cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, device);
-    // segments of the scan / sort kernels; the sort stages 256 x grid_blocks counts in shared memory
-    ws->grid_blocks = ws->sm_count > 192 ? 192 : ws->sm_count;
-    int bits = 1;
-    while (bits < 32 && ((ws->ncells - 1) >> bits) > 0) bits++;
-    ws->key_bits = bits < 8 ? 8 : bits;
-    size_t tot = 0;
-    cudaError_t e = cudaSuccess;
-    const size_t C = (size_t)ws->max_cand, Mx = (size_t)ws->max_cells, T = (size_t)ws->max_nt;
-    e = e ? e : alloc(&ws->ctr, 1, &tot);
-    e = e ? e : alloc(&ws->idx_map, (size_t)ws->ncells, &tot);
-    e = e ? e : alloc(&ws->tri_cnt, T, &tot);
-    e = e ? e : alloc(&ws->tri_off, T, &tot);
-    e = e ? e : alloc(&ws->tri_box, 6 * T, &tot);
-    e = e ? e : alloc(&ws->cand_tri, C, &tot);
-    e = e ? e : alloc(&ws->keys[0], C, &tot);
-    e = e ? e : alloc(&ws->keys[1], C, &tot);
-    e = e ? e : alloc(&ws->vals[0], C, &tot);
-    e = e ? e : alloc(&ws->vals[1], C, &tot);
-    e = e ? e : alloc(&ws->rec, C, &tot);
-    e = e ? e : alloc(&ws->rec32, C, &tot);
-    e = e ? e : alloc(&ws->cen32, C, &tot);
-    e = e ? e : alloc(&ws->srec, C, &tot);
-    e = e ? e : alloc(&ws->srec32, C, &tot);
-    e = e ? e : alloc(&ws->scen, C, &tot);
-    e = e ? e : alloc(&ws->sys, Mx, &tot);
-    e = e ? e : alloc(&ws->fit_info, 2 * Mx, &tot);
-    e = e ? e : alloc(&ws->cells, Mx + 1, &tot);
-    e = e ? e : alloc(&ws->cell_off, Mx + 1, &tot);
-    e = e ? e : alloc(&ws->heads, C, &tot);
-    e = e ? e : alloc(&ws->cell_L, Mx, &tot);
-    e = e ? e : alloc(&ws->cell_P, Mx, &tot);
-    e = e ? e : alloc(&ws->partials, 2 * (size_t)(ws->grid_blocks + 1), &tot);
-    e = e ? e : alloc(&ws->hist, 256 * (size_t)ws->grid_blocks, &tot);
-    if (e == cudaSuccess) e = ft::prepare_sort(ws->grid_blocks);
-    if (e == cudaSuccess) e = cudaMemset(ws->ctr, 0, sizeof(ft_counters));
-    if (e == cudaSuccess) e = cudaMemset(ws->idx_map, 0xff, sizeof(int) * (size_t)ws->ncells);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-        release(ws);
+    ws->key_bits = key_bits_for(ws->ncells);
+    const int r = allocate(ws, ws->ncells);
+    if (r != FT_OK) {
         free(ws);
-        cudaGetLastError();
-        return FT_ERR_ALLOC;
+        return r;
     }
-    ws->bytes = tot;
-    if (bytes) *bytes = tot;
+    if (bytes) *bytes = ws->bytes;
     *out = ws;
+    return FT_OK;
+}
+
+int ft_batch_workspace_create(ft_workspace** out, const ft_batch_capacity* cap, int device, size_t* bytes) {
+    if (!out || !cap || cap->max_fronts < 1 || cap->max_grid_cells < 1 || cap->max_grid_cells >= 0xffffffffLL ||
+        cap->max_nt < 0 || cap->max_cand < 0 || cap->max_cells < 0)
+        return FT_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return FT_ERR_CUDA;
+    ft_workspace* ws = (ft_workspace*)calloc(1, sizeof(ft_workspace));
+    if (!ws) return FT_ERR_ALLOC;
+    ws->device = device;
+    ws->batch = true;
+    ws->max_fronts = cap->max_fronts;
+    ws->max_grid_cells = cap->max_grid_cells;
+    ws->max_nt = cap->max_nt > 0 ? cap->max_nt : 1;
+    ws->max_cand = cap->max_cand > 0 ? cap->max_cand : 16 * ws->max_nt + 1024;
+    ws->max_cells = cap->max_cells > 0 ? cap->max_cells : ws->max_cand;
+    if (ws->max_cand > 0x7fffffffLL - 1 || ws->max_cells > ws->max_cand) {
+        free(ws);
+        return FT_ERR_ARG;
+    }
+    ws->key_bits = 8;
+    const int r = allocate(ws, ws->max_grid_cells);
+    if (r != FT_OK) {
+        free(ws);
+        return r;
+    }
+    if (bytes) *bytes = ws->bytes;
+    *out = ws;
+    return FT_OK;
+}
+
+int ft_batch_set(ft_workspace* ws, int32_t nf, const ft_batch_front* fr, void* stream) {
+    if (!ws || !ws->batch || nf < 1 || !fr) return FT_ERR_ARG;
+    if (nf > ws->max_fronts) return FT_ERR_CAPACITY;
+    long long cells = 0, cols = 0, nt = 0, nv = 0;
+    for (int b = 0; b < nf; b++) {
+        const ft_batch_front& f = fr[b];
+        if (!grid_ok(&f.grid) || f.nt < 0 || f.nv < 0 || f.nt > 0x7fffffffLL || f.nv > 0x7fffffffLL) return FT_ERR_ARG;
+        if (f.nt > 0 && (!f.verts || !f.tris)) return FT_ERR_ARG;
+        cells += (long long)f.grid.n[0] * f.grid.n[1] * f.grid.n[2];
+        cols += (long long)f.grid.n[0] * f.grid.n[1];
+        nt += f.nt;
+        nv += f.nv;
+    }
+    if (cells > ws->max_grid_cells || nt > ws->max_nt) return FT_ERR_CAPACITY;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    cudaStream_t s = as_stream(stream);
+    // the staging buffers may still feed the previous table's copy
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FT_ERR_CUDA;
+    // plane tables of every front (grown here when the table needs more)
+    long long nplanes = 0, max_planes = 0;
+    for (int b = 0; b < nf; b++) {
+        const long long q = ft_plane_count(fr[b].grid);
+        nplanes += q;
+        if (q > max_planes) max_planes = q;
+    }
+    if (nplanes > ws->planes_cap) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return FT_ERR_CUDA;
+        if (ws->planes) cudaFree(ws->planes);
+        ws->planes = nullptr;
+        ws->planes_cap = 0;
+        if (cudaMalloc(reinterpret_cast<void**>(&ws->planes), sizeof(double) * (size_t)nplanes) != cudaSuccess) {
+            cudaGetLastError();
+            return FT_ERR_ALLOC;
+        }
+        ws->planes_cap = nplanes;
+        ws->bytes += sizeof(double) * (size_t)nplanes;
+    }
+    long long* kb = ws->h_fbase;
+    long long* cb = kb + (nf + 1);
+    long long* tb = cb + (nf + 1);
+    long long* vb = tb + (nf + 1);
+    kb[0] = cb[0] = tb[0] = vb[0] = 0;
+    long long pofs = 0;
+    for (int b = 0; b < nf; b++) {
+        const ft_batch_front& f = fr[b];
+        ft_fdesc& d = ws->h_fdesc[b];
+        d = ft_fdesc{};
+        d.g = f.grid;
+        d.verts = f.verts;
+        d.tris = f.tris;
+        d.alpha = f.alpha;
+        d.force = f.force;
+        d.U = f.U;
+        d.V = f.V;
+        d.W = f.W;
+        d.vel = f.vel;
+        d.verts_next = f.verts_next;
+        d.dt = f.dt;
+        d.nv = f.nv;
+        d.nt = f.nt;
+        d.planes = ws->planes + pofs;
+        d.inv_h = 1.0 / f.grid.h;
+        pofs += ft_plane_count(f.grid);
+        kb[b + 1] = kb[b] + (long long)f.grid.n[0] * f.grid.n[1] * f.grid.n[2];
+        cb[b + 1] = cb[b] + (long long)f.grid.n[0] * f.grid.n[1];
+        tb[b + 1] = tb[b] + f.nt;
+        vb[b + 1] = vb[b] + f.nv;
+    }
+    cudaError_t e = cudaMemcpyAsync(ws->fdesc, ws->h_fdesc, sizeof(ft_fdesc) * nf, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws->fbase, ws->h_fbase, sizeof(long long) * 4 * (nf + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws->fstatus, 0, sizeof(unsigned) * nf, s);
+    ws->nf = nf;
+    if (e == cudaSuccess) e = ft::launch_planes_batch(ws, (int)max_planes, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ws->nf = 0;
+        return FT_ERR_CUDA;
+    }
+    ws->ncells = cells;
+    ws->ncols = cols;
+    ws->nt_total = nt;
+    ws->nv_total = nv;
+    ws->key_bits = key_bits_for(cells);
+    ws->binned = false;
     return FT_OK;
 }
 
@@ -180,7 +332,7 @@ int ft_bin_pairs(ft_workspace* ws, int64_t cap, uint32_t* keys, int32_t* tris, v
 }
 
 int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* stream) {
-    if (!ws || !f || !params_ok(p) || f->nt < 0 || f->nv < 0 || f->nt > ws->max_nt) return FT_ERR_ARG;
+    if (!ws || ws->batch || !f || !params_ok(p) || f->nt < 0 || f->nv < 0 || f->nt > ws->max_nt) return FT_ERR_ARG;
     if (f->nt > 0 && (!f->verts || !f->tris)) return FT_ERR_ARG;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     cudaStream_t s = as_stream(stream);
@@ -194,7 +346,7 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
 }
 
 int front_volume_fraction(ft_workspace* ws, double* alpha, void* stream) {
-    if (!ws || !alpha) return FT_ERR_ARG;
+    if (!ws || ws->batch || !alpha) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     return cuda_err(ft::launch_alpha(ws, alpha, as_stream(stream)));
@@ -210,7 +362,7 @@ int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint
 
 int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                     const double* normal, double* force, void* stream) {
-    if (!ws || !params_ok(p) || !alpha || !kappa || !normal || !force) return FT_ERR_ARG;
+    if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || !force) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream)));
@@ -230,6 +382,125 @@ int front_interp_velocity(const ft_grid* g, const double* U, const double* V, co
         if (cudaSetDevice(at.device) != cudaSuccess) return FT_ERR_CUDA;
     }
     return cuda_err(ft::launch_interp(g, U, V, W, verts, nv, vel, as_stream(stream)));
+}
+
+int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream) {
+    if (!ws || !ws->batch || !params_ok(p)) return FT_ERR_ARG;
+    if (ws->nf < 1) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = ft::launch_clear_map(ws, s);
+    if (e == cudaSuccess) e = ft::launch_bin_batch(ws, p, s);
+    if (e == cudaSuccess) e = ft::launch_sort(ws, s);
+    if (e == cudaSuccess) e = ft::launch_rle(ws, s);
+    if (e == cudaSuccess) e = ft::launch_gather(ws, s);
+    ws->binned = (e == cudaSuccess);
+    return cuda_err(e);
+}
+
+int front_volume_fraction_batch(ft_workspace* ws, void* stream) {
+    if (!ws || !ws->batch) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++)
+        if (!ws->h_fdesc[b].alpha) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_alpha_batch(ws, as_stream(stream)));
+}
+
+int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                          void* stream) {
+    if (!ws || !ws->batch || !params_ok(p) || !kappa || !normal) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++)
+        if (!ws->h_fdesc[b].alpha || !ws->h_fdesc[b].force) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream)));
+}
+
+int front_interp_velocity_batch(ft_workspace* ws, void* stream) {
+    if (!ws || !ws->batch) return FT_ERR_ARG;
+    if (ws->nf < 1) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++) {
+        const ft_fdesc& d = ws->h_fdesc[b];
+        if (d.nv == 0) continue;
+        if (!d.U || !d.V || !d.W || !d.verts || !d.vel) return FT_ERR_ARG;
+        for (int k = 0; k < 3; k++)
+            if (d.g.n[k] < 2) return FT_ERR_ARG;
+    }
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_interp_batch(ws, as_stream(stream)));
+}
+
+int front_advect_rk4_batch(ft_workspace* ws, void* stream) {
+    if (!ws || !ws->batch) return FT_ERR_ARG;
+    if (ws->nf < 1) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++) {
+        const ft_fdesc& d = ws->h_fdesc[b];
+        if (d.nv == 0) continue;
+        if (!d.U || !d.V || !d.W || !d.verts || !d.verts_next || !isfinite(d.dt)) return FT_ERR_ARG;
+        for (int k = 0; k < 3; k++)
+            if (d.g.n[k] < 2) return FT_ERR_ARG;
+    }
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_advect_batch(ws, as_stream(stream)));
+}
+
+int ft_batch_cell_ranges(ft_workspace* ws, int64_t* off, void* stream) {
+    if (!ws || !ws->batch || !off) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_cell_ranges(ws, reinterpret_cast<long long*>(off), as_stream(stream)));
+}
+
+int ft_batch_status(ft_workspace* ws, void* stream, uint32_t* bits) {
+    if (!ws || !ws->batch || !bits) return FT_ERR_ARG;
+    if (ws->nf < 1) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    cudaStream_t s = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(bits, ws->fstatus, sizeof(unsigned) * ws->nf, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws->fstatus, 0, sizeof(unsigned) * ws->nf, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_err(e);
+}
+
+int ft_set_tuning(ft_workspace* ws, const ft_tuning* t) {
+    if (!ws || !t) return FT_ERR_ARG;
+    const int v[4] = {t->clip_blocks_per_sm, t->ppic_blocks_per_sm, t->csf_blocks_per_sm, t->fill_blocks_per_sm};
+    for (int x : v)
+        if (x < 1 || x > 32) return FT_ERR_ARG;
+    if (t->ppic_min_blocks != 4 && t->ppic_min_blocks != 6) return FT_ERR_ARG;
+    if (t->ppic_dynamic != 0 && t->ppic_dynamic != 1) return FT_ERR_ARG;
+    ws->tune = ft_tune{v[0], v[1], v[2], v[3], t->ppic_min_blocks, t->ppic_dynamic};
+    return FT_OK;
+}
+
+int ft_get_tuning(ft_workspace* ws, ft_tuning* t) {
+    if (!ws || !t) return FT_ERR_ARG;
+    memset(t, 0, sizeof(*t));
+    t->clip_blocks_per_sm = ws->tune.clip_bps;
+    t->ppic_blocks_per_sm = ws->tune.ppic_bps;
+    t->csf_blocks_per_sm = ws->tune.csf_bps;
+    t->fill_blocks_per_sm = ws->tune.fill_bps;
+    t->ppic_min_blocks = ws->tune.ppic_min_blocks;
+    t->ppic_dynamic = ws->tune.ppic_dynamic;
+    return FT_OK;
+}
+
+int front_advect_rk4(const ft_grid* g, const double* U, const double* V, const double* W, const double* verts,
+                     int64_t nv, double dt, double* verts_out, double* vel, void* stream) {
+    if (!grid_ok(g) || nv < 0 || !isfinite(dt) || (nv > 0 && (!U || !V || !W || !verts || !verts_out)))
+        return FT_ERR_ARG;
+    for (int d = 0; d < 3; d++)
+        if (g->n[d] < 2) return FT_ERR_ARG;
+    if (nv > 0) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, verts) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return FT_ERR_ARG;
+        }
+        if (cudaSetDevice(at.device) != cudaSuccess) return FT_ERR_CUDA;
+    }
+    return cuda_err(ft::launch_advect(g, U, V, W, verts, nv, dt, verts_out, vel, as_stream(stream)));
 }
 
 int64_t ft_launch_count(void) { return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }

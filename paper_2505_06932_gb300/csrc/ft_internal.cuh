@@ -9,7 +9,7 @@
 #define FT_WARP 32
 #define FT_SENTINEL 0xffffffffu
 
-// Device-side counters of one workspace (one cache line).
+// Device-side counters of one workspace.
 struct ft_counters {
     unsigned int status;   // FT_ST_* bits
     unsigned int pad;
@@ -19,7 +19,8 @@ struct ft_counters {
     long long P;           // binned pairs
     long long M;           // interfacial cells (also: entries set in the index map)
     long long fit_pairs;   // (cell, fragment) pairs inside the support, last PPIC
-    long long pad2;
+    long long work;        // next cell of the dynamically scheduled PPIC accumulation
+    long long scratch;     // sink for totals nobody reads (later sort passes)
 };
 
 // Fragment record (cell-local, lengths in units of h, relative to the centre of
@@ -46,6 +47,38 @@ struct __align__(16) ft_cellsys {
     double v[32];
 };
 
+// One front of a batch as the kernels see it: its grid and its caller-owned
+// device arrays (see ft_batch_front in front.h).  128 B.
+struct __align__(16) ft_fdesc {
+    ft_grid g;
+    const double* verts;
+    const int* tris;
+    double* alpha;
+    double* force;
+    const double* U;
+    const double* V;
+    const double* W;
+    double* vel;
+    double* verts_next;  // RK4 output positions (may equal verts)
+    double dt;           // RK4 time step
+    long long nv;
+    long long nt;
+    // grid plane coordinates X_i = origin + i h (i = 0..n0, then Y, then Z),
+    // computed once with the canonical operations; NULL: computed on the fly
+    const double* planes;
+    double inv_h;  // 1 / h (moments and interpolation weights; never in the predicate)
+};
+
+// Launch-shape parameters (see ft_tuning in front.h).
+struct ft_tune {
+    int clip_bps;   // k_clip blocks per SM
+    int ppic_bps;   // k_ppic_acc blocks per SM
+    int csf_bps;    // k_csf_dense blocks per SM
+    int fill_bps;   // k_alpha_fill blocks per SM
+    int ppic_min_blocks;  // FP32 k_ppic_acc compiled for 4 (more registers) or 6 resident blocks per SM
+    int ppic_dynamic;     // k_ppic_acc cells from a global work counter (1) or interleaved (0)
+};
+
 struct ft_workspace {
     int device;
     int sm_count;
@@ -62,7 +95,10 @@ struct ft_workspace {
     int* idx_map;          // ncells: interfacial index or -1
     int* tri_cnt;          // max_nt
     int* tri_off;          // max_nt
-    int* tri_box;          // max_nt * 6: lo[3], ext[3]
+    int* tri_box;          // max_nt * 8: lo[3], ext[3], front, 0
+    double* tri_nrm;       // max_nt * 4: normal direction of each triangle (x, y, z, 0)
+    double* planes;        // grid plane coordinates of every front (see ft_fdesc)
+    long long planes_cap;  // entries allocated in planes
     int* cand_tri;         // max_cand
     unsigned* keys[2];     // max_cand
     unsigned* vals[2];     // max_cand
@@ -82,6 +118,19 @@ struct ft_workspace {
     int* partials;         // grid_blocks + 1
     int* hist;             // 256 * grid_blocks
     int sorted_buf;        // which keys/vals buffer holds the sorted pairs
+    ft_tune tune;
+
+    // batched form (nf > 0 after ft_batch_set; 0 for a one-front workspace)
+    bool batch;
+    int nf, max_fronts;
+    long long max_grid_cells;   // index-map entries (sum of the fronts' cells)
+    long long ncols;            // sum of the fronts' (i, j) columns
+    long long nt_total, nv_total;
+    ft_fdesc* fdesc;            // max_fronts descriptors (device)
+    long long* fbase;           // 4 x (max_fronts + 1): key, column, triangle, vertex bases (device)
+    unsigned* fstatus;          // max_fronts per-front status words (device)
+    ft_fdesc* h_fdesc;          // host copies of the table (pinned staging)
+    long long* h_fbase;
 };
 
 // kernels / launchers (one translation unit each)
@@ -108,6 +157,20 @@ cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha
                        const double* kappa, const double* normal, double* force, cudaStream_t s);
 cudaError_t launch_interp(const ft_grid* g, const double* U, const double* V, const double* W,
                           const double* verts, long long nv, double* vel, cudaStream_t s);
+// batched form: the fronts of the workspace's table
+cudaError_t launch_bin_batch(ft_workspace* ws, const ft_params* p, cudaStream_t s);
+cudaError_t launch_alpha_batch(ft_workspace* ws, cudaStream_t s);
+cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                             cudaStream_t s);
+cudaError_t launch_interp_batch(ft_workspace* ws, cudaStream_t s);
+cudaError_t launch_advect(const ft_grid* g, const double* U, const double* V, const double* W,
+                          const double* verts, long long nv, double dt, double* verts_out, double* vel,
+                          cudaStream_t s);
+cudaError_t launch_advect_batch(ft_workspace* ws, cudaStream_t s);
+cudaError_t launch_cell_ranges(ft_workspace* ws, long long* off, cudaStream_t s);
+// plane tables: of the workspace's grid (one front), or of every front of the table
+cudaError_t launch_planes_one(ft_workspace* ws, cudaStream_t s);
+cudaError_t launch_planes_batch(ft_workspace* ws, int max_planes, cudaStream_t s);
 cudaError_t probe_fma(int kind, double* flops);
 
 }  // namespace ft
@@ -138,4 +201,91 @@ __device__ __forceinline__ int ft_warp_sum_i(int v) {
 // plane coordinate origin + idx*h, rounded once per operation (never fused)
 __device__ __forceinline__ double ft_plane(double o, double h, long long idx) {
     return __dadd_rn(o, __dmul_rn((double)idx, h));
+}
+
+// entries of a front's plane table: (n0 + 1) + (n1 + 1) + (n2 + 1)
+inline long long ft_plane_count(const ft_grid& g) { return (long long)g.n[0] + g.n[1] + g.n[2] + 3; }
+
+// ---------------------------------------------------------------------------
+// Front lookups.  Kernels are instantiated for one of two policies:
+//  * FrontsOne  -- a single front; its descriptor is a kernel argument and every
+//                  lookup is a constant (the one-front entry points);
+//  * FrontsMany -- a batch: the front owning a batch-global cell key, (i, j)
+//                  column, triangle or vertex is found by binary search of the
+//                  prefix bases (the batched entry points).
+// Batch-global numbering: front b's cells are keys key_base[b] + local key, its
+// columns col_base[b] + i n1 + j, its triangles tri_base[b] + t, its vertices
+// vert_base[b] + v; each base array ends with the total.
+// ---------------------------------------------------------------------------
+struct FrontsOne {
+    ft_fdesc d0;
+    long long ncells, ncols;
+    __device__ __forceinline__ int by_key(long long) const { return 0; }
+    __device__ __forceinline__ int by_col(long long) const { return 0; }
+    __device__ __forceinline__ int by_tri(long long) const { return 0; }
+    __device__ __forceinline__ int by_vert(long long) const { return 0; }
+    __device__ __forceinline__ const ft_fdesc& desc(int) const { return d0; }
+    __device__ __forceinline__ long long key_base(int) const { return 0; }
+    __device__ __forceinline__ long long col_base(int) const { return 0; }
+    __device__ __forceinline__ long long tri_base(int) const { return 0; }
+    __device__ __forceinline__ long long vert_base(int) const { return 0; }
+    __device__ __forceinline__ void flag(int, unsigned) const {}
+};
+
+struct FrontsMany {
+    const ft_fdesc* d;
+    const long long* base;  // key, column, triangle, vertex bases, (nf + 1) each
+    unsigned* fstatus;
+    int nf;
+    long long ncells, ncols;
+    // largest b with b-th base <= x (empty fronts share their successor's base)
+    __device__ __forceinline__ int search(int which, long long x) const {
+        const long long* b = base + (long long)which * (nf + 1);
+        int lo = 0, hi = nf - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(b + mid) <= x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ int by_key(long long x) const { return search(0, x); }
+    __device__ __forceinline__ int by_col(long long x) const { return search(1, x); }
+    __device__ __forceinline__ int by_tri(long long x) const { return search(2, x); }
+    __device__ __forceinline__ int by_vert(long long x) const { return search(3, x); }
+    __device__ __forceinline__ const ft_fdesc& desc(int b) const { return d[b]; }
+    __device__ __forceinline__ long long key_base(int b) const { return __ldg(base + b); }
+    __device__ __forceinline__ long long col_base(int b) const { return __ldg(base + (nf + 1) + b); }
+    __device__ __forceinline__ long long tri_base(int b) const { return __ldg(base + 2 * (nf + 1) + b); }
+    __device__ __forceinline__ long long vert_base(int b) const { return __ldg(base + 3 * (nf + 1) + b); }
+    __device__ __forceinline__ void flag(int b, unsigned bits) const { atomicOr(fstatus + b, bits); }
+};
+
+// host-side construction of the policies
+inline FrontsOne ft_one(const ft_workspace* ws, const double* verts, const int* tris, long long nv, long long nt) {
+    FrontsOne f;
+    f.d0 = ft_fdesc{};
+    f.d0.g = ws->g;
+    f.d0.planes = ws->planes;
+    f.d0.inv_h = 1.0 / ws->g.h;
+    f.d0.verts = verts;
+    f.d0.tris = tris;
+    f.d0.nv = nv;
+    f.d0.nt = nt;
+    f.ncells = ws->ncells;
+    f.ncols = (long long)ws->g.n[0] * ws->g.n[1];
+    return f;
+}
+
+inline FrontsMany ft_many(const ft_workspace* ws) {
+    FrontsMany f;
+    f.d = ws->fdesc;
+    f.base = ws->fbase;
+    f.fstatus = ws->fstatus;
+    f.nf = ws->nf;
+    f.ncells = ws->ncells;
+    f.ncols = ws->ncols;
+    return f;
 }

@@ -24,7 +24,8 @@ constexpr size_t kOffMap = kOffCtr + up256(sizeof(ft_counters));
 constexpr size_t kOffTriCnt = kOffMap + up256(sizeof(int) * kMaxCells);
 constexpr size_t kOffTriOff = kOffTriCnt + up256(sizeof(int) * kMaxNt);
 constexpr size_t kOffTriBox = kOffTriOff + up256(sizeof(int) * kMaxNt);
-constexpr size_t kOffCandTri = kOffTriBox + up256(sizeof(int) * 6 * kMaxNt);
+constexpr size_t kOffTriNrm = kOffTriBox + up256(sizeof(int) * 8 * kMaxNt);
+constexpr size_t kOffCandTri = kOffTriNrm + up256(sizeof(double) * 4 * kMaxNt);
 constexpr size_t kOffKeys0 = kOffCandTri + up256(sizeof(int) * kMaxCand);
 constexpr size_t kOffKeys1 = kOffKeys0 + up256(sizeof(unsigned) * kMaxCand);
 constexpr size_t kOffVals0 = kOffKeys1 + up256(sizeof(unsigned) * kMaxCand);
@@ -88,6 +89,7 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
     ws.device = dev;
     cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev);
     ws.grid_blocks = kBlocks;
+    ws.tune = ft_tune{4, 4, 16, 8, 4, 0};
     int bits = 1;
     while (bits < 32 && ((ncells - 1) >> bits) > 0) bits++;
     ws.key_bits = bits < 8 ? 8 : bits;
@@ -101,6 +103,8 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
     ws.tri_cnt = reinterpret_cast<int*>(base + kOffTriCnt);
     ws.tri_off = reinterpret_cast<int*>(base + kOffTriOff);
     ws.tri_box = reinterpret_cast<int*>(base + kOffTriBox);
+    ws.tri_nrm = reinterpret_cast<double*>(base + kOffTriNrm);
+    ws.planes = nullptr;  // plane coordinates are computed on the fly here
     ws.cand_tri = reinterpret_cast<int*>(base + kOffCandTri);
     ws.keys[0] = reinterpret_cast<unsigned*>(base + kOffKeys0);
     ws.keys[1] = reinterpret_cast<unsigned*>(base + kOffKeys1);

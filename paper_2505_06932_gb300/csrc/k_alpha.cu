@@ -90,22 +90,32 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells32(const int* __restric
 }
 
 // one warp per (i, j) column, walking k downwards in chunks of 32 cells
-__global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* __restrict__ idx_map,
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_alpha_fill(F fr, const int* __restrict__ idx_map,
                                                          const double* __restrict__ cell_L,
-                                                         const double* __restrict__ cell_P, double* __restrict__ alpha,
-                                                         double closure_tol, ft_counters* ctr) {
+                                                         const double* __restrict__ cell_P, double closure_tol,
+                                                         ft_counters* ctr) {
     const int lane = threadIdx.x & 31;
-    const long long ncol = (long long)g.n[0] * g.n[1];
-    const int n2 = g.n[2];
+    const long long ncol = fr.ncols;
     const long long nw = (long long)gridDim.x * kWarps;
-    unsigned err = 0;
-    for (long long col = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); col < ncol; col += nw) {
-        const long long base = col * n2;
+    for (long long gcol = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); gcol < ncol; gcol += nw) {
+        const int b = fr.by_col(gcol);
+        const ft_fdesc& D = fr.desc(b);
+        const int n2 = D.g.n[2];
+        const long long col = gcol - fr.col_base(b);
+        const long long base = col * n2;            // front-local key of the column's first cell
+        const long long gbase = fr.key_base(b) + base;  // the same, batch-global (index map)
+        double* __restrict__ alpha = D.alpha;
+        unsigned err = 0;
         double carry = 0.0;
-        for (int k0 = ((n2 - 1) / 32) * 32; k0 >= 0; k0 -= 32) {
+        // the index map of the chunk below is loaded while this chunk is processed
+        int k0 = ((n2 - 1) / 32) * 32;
+        int m_next = (k0 + lane < n2) ? idx_map[gbase + k0 + lane] : -1;
+        for (; k0 >= 0; k0 -= 32) {
             const int k = k0 + lane;
             const bool valid = k < n2;
-            const int m = valid ? idx_map[base + k] : -1;
+            const int m = m_next;
+            if (k0 >= 32) m_next = idx_map[gbase + k0 - 32 + lane];
             if (__ballot_sync(0xffffffffu, m >= 0) == 0u) {
                 // no interfacial cell in this chunk: every cell takes the parity above it
                 const long long cb = __double_as_longlong(carry);
@@ -148,16 +158,20 @@ __global__ void __launch_bounds__(kThreads) k_alpha_fill(ft_grid g, const int* _
                 alpha[base + k] = fmin(fmax(a, 0.0), 1.0);
             }
         }
+        err = __reduce_or_sync(0xffffffffu, err);
+        if (err && lane == 0) {
+            ft_flag(ctr, err);
+            fr.flag(b, err);
+        }
     }
-    err = __reduce_or_sync(0xffffffffu, err);
-    if (err && lane == 0) ft_flag(ctr, err);
 }
 
 }  // namespace
 
 namespace ft {
 
-cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s) {
+template <class F>
+cudaError_t alpha_with(ft_workspace* ws, const F& fr, cudaStream_t s) {
     const bool fp32 = ws->last_precision == FT_FP32C;
     // records in sorted pair order when front_bin gathered them, else through the slot index
     const bool sorted = fp32 ? ws->srec32 != nullptr : ws->srec != nullptr;
@@ -171,9 +185,17 @@ cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s) {
                                                             ws->cell_L, ws->cell_P, ws->ctr);
     // the column parity of a closed front is an integer up to rounding of the fragment terms
     const double closure_tol = fp32 ? 1e-5 : 1e-9;
-    k_alpha_fill<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->g, ws->idx_map, ws->cell_L, ws->cell_P, alpha,
-                                                       closure_tol, ws->ctr);
+    k_alpha_fill<F><<<ws->sm_count * ws->tune.fill_bps, kThreads, 0, s>>>(fr, ws->idx_map, ws->cell_L, ws->cell_P,
+                                                                          closure_tol, ws->ctr);
     return cudaGetLastError();
 }
+
+cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s) {
+    FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
+    fr.d0.alpha = alpha;
+    return alpha_with(ws, fr, s);
+}
+
+cudaError_t launch_alpha_batch(ft_workspace* ws, cudaStream_t s) { return alpha_with(ws, ft_many(ws), s); }
 
 }  // namespace ft

@@ -21,37 +21,76 @@ __device__ __forceinline__ long long okey(double x) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
+// Plane coordinates of one front: the table entry when the front has a table
+// (identical values: the table is filled with the same canonical operations),
+// else origin + i h computed here.
+struct Planes {
+    const double* t;
+    int off1, off2;  // first Y and Z entries
+    double o[3], h;
+    __device__ __forceinline__ explicit Planes(const ft_fdesc& D)
+        : t(D.planes), off1(D.g.n[0] + 1), off2(D.g.n[0] + D.g.n[1] + 2),
+          o{D.g.origin[0], D.g.origin[1], D.g.origin[2]}, h(D.g.h) {}
+    __device__ __forceinline__ double at(int ax, long long i) const {
+        if (t) return __ldg(t + (ax == 0 ? 0 : (ax == 1 ? off1 : off2)) + i);
+        return ft_plane(o[ax], h, i);
+    }
+};
+
 // Candidate range along one axis: cells whose closed extent [X_i, X_i+1] meets
 // [lo, hi]: i0 = min{i : X_i+1 >= lo}, i1 = max{i : X_i <= hi}.  The product
 // with 1/h is only a starting guess; the exact comparisons make the result exact.
-__device__ void cand_range(double o, double h, double inv_h, int n, double lo, double hi, int& i0, int& i1) {
+__device__ void cand_range(const Planes& P, int ax, double inv_h, int n, double lo, double hi, int& i0, int& i1) {
+    const double o = P.o[ax];
     const long long klo = okey(lo), khi = okey(hi);
     double f = floor((lo - o) * inv_h);
     int e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
-    while (e > 0 && okey(ft_plane(o, h, e)) >= klo) e--;
-    while (e < n - 1 && okey(ft_plane(o, h, e + 1)) < klo) e++;
+    while (e > 0 && okey(P.at(ax, e)) >= klo) e--;
+    while (e < n - 1 && okey(P.at(ax, e + 1)) < klo) e++;
     i0 = e;
     f = floor((hi - o) * inv_h);
     e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
-    while (e < n - 1 && okey(ft_plane(o, h, e + 1)) <= khi) e++;
-    while (e > 0 && okey(ft_plane(o, h, e)) > khi) e--;
+    while (e < n - 1 && okey(P.at(ax, e + 1)) <= khi) e++;
+    while (e > 0 && okey(P.at(ax, e)) > khi) e--;
     i1 = e;
 }
 
-__global__ void __launch_bounds__(kThreads) k_tri_setup(const double* __restrict__ verts, long long nv,
-                                                        const int* __restrict__ tris, long long T,
-                                                        ft_grid g, int margin, long long max_cand,
+// The plane table of front blockIdx.y (grid-stride over its entries).
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_planes(F fr) {
+    const ft_fdesc& D = fr.desc((int)blockIdx.y);
+    double* out = const_cast<double*>(D.planes);
+    const ft_grid g = D.g;
+    const int n0 = g.n[0] + 1, n1 = g.n[1] + 1, n2 = g.n[2] + 1;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < n0 + n1 + n2; e += gridDim.x * kThreads) {
+        const int ax = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+        const int i = e - (ax == 0 ? 0 : (ax == 1 ? n0 : n0 + n1));
+        out[e] = ft_plane(g.origin[ax], g.h, i);
+    }
+}
+
+// Per triangle: the candidate box (cells whose closed extent meets the
+// triangle's closed bounding box) and its size.  tri_box holds lo[3], ext[3]
+// and the owning front per triangle (8 ints).
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int margin, long long max_cand,
                                                         int* __restrict__ tri_cnt, int* __restrict__ tri_box,
-                                                        ft_counters* ctr) {
+                                                        double* __restrict__ tri_nrm, ft_counters* ctr) {
     const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
     if (t == 0) ctr->T = T;
     if (t >= T) return;
+    const int b = fr.by_tri(t);
+    const ft_fdesc& D = fr.desc(b);
+    const ft_grid g = D.g;
+    const long long tl = t - fr.tri_base(b);
+    const long long nv = D.nv;
+    const double* __restrict__ verts = D.verts;
     int cnt = 0;
     int box[6] = {0, 0, 0, 1, 1, 1};
     unsigned err = 0;
     int vi[3];
     for (int c = 0; c < 3; c++) {
-        vi[c] = tris[3 * t + c];
+        vi[c] = D.tris[3 * tl + c];
         if (vi[c] < 0 || vi[c] >= nv) err |= FT_ST_BAD_INDEX;
     }
     if (!err) {
@@ -63,8 +102,8 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(const double* __restrict
             long long klo = 0, khi = 0;
             for (int c = 0; c < 3; c++) {
                 const double x = verts[3 * (long long)vi[c] + ax];
-                const long long b = __double_as_longlong(x);
-                finite = finite && ((b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
+                const long long bits = __double_as_longlong(x);
+                finite = finite && ((bits & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
                 const long long kx = okey(x);
                 if (c == 0 || kx < klo) { klo = kx; lo = x; }
                 if (c == 0 || kx > khi) { khi = kx; hi = x; }
@@ -74,10 +113,10 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(const double* __restrict
         }
         if (!finite) err |= FT_ST_OUTSIDE_GRID;
         long long total = 1;
-        const double inv_h = 1.0 / g.h;
+        const Planes P(D);
         for (int ax = 0; ax < 3 && !err; ax++) {
             int i0, i1;
-            cand_range(g.origin[ax], g.h, inv_h, g.n[ax], mn[ax], mx[ax], i0, i1);
+            cand_range(P, ax, D.inv_h, g.n[ax], mn[ax], mx[ax], i0, i1);
             if (i0 < margin || i1 > g.n[ax] - 1 - margin) err |= FT_ST_OUTSIDE_GRID;
             box[ax] = i0;
             box[3 + ax] = i1 - i0 + 1;
@@ -91,9 +130,31 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(const double* __restrict
             cnt = (int)total;
         }
     }
-    if (err) ft_flag(ctr, err);
+    if (err) {
+        ft_flag(ctr, err);
+        fr.flag(b, err);
+    }
     tri_cnt[t] = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
-    for (int d = 0; d < 6; d++) tri_box[6 * t + d] = box[d];
+    // normal direction (orientation of every fragment of the triangle; zero if
+    // degenerate): twice the area vector in units of h^2.  Only its direction
+    // matters -- the moments use ratios of areas signed along it.
+    double nrm[3] = {0.0, 0.0, 0.0};
+    if (!err) {
+        double e1[3], e2[3];
+        for (int d = 0; d < 3; d++) {
+            e1[d] = (verts[3 * (long long)vi[1] + d] - verts[3 * (long long)vi[0] + d]) * D.inv_h;
+            e2[d] = (verts[3 * (long long)vi[2] + d] - verts[3 * (long long)vi[0] + d]) * D.inv_h;
+        }
+        nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    double2* nb = reinterpret_cast<double2*>(tri_nrm + 4 * t);
+    nb[0] = make_double2(nrm[0], nrm[1]);
+    nb[1] = make_double2(nrm[2], 0.0);
+    int4* bx = reinterpret_cast<int4*>(tri_box + 8 * t);
+    bx[0] = make_int4(box[0], box[1], box[2], box[3]);
+    bx[1] = make_int4(box[4], box[5], b, 0);
 }
 
 __global__ void __launch_bounds__(kThreads) k_expand(const int* __restrict__ tri_cnt, const int* __restrict__ tri_off,
@@ -205,49 +266,42 @@ __device__ __noinline__ int canon_stages_wide(const double (*v)[3], const ft_gri
     return canon_stages<32>(v, g, idx, res);
 }
 
-// Fragment moments in units of h relative to the fragment cell's centre, from
-// the fan triangles (p0, p_m, p_m+1) of the convex fragment polygon.
-__device__ void frag_moments(const double (*p)[3], int n, const double xc[3], double inv_h, ft_frag& f) {
-    double an[3] = {0.0, 0.0, 0.0};
+// Fragment moments in units of h relative to the fragment cell's centre, in one
+// pass over the fan triangles (p0, p_m, p_m+1) of the convex fragment polygon.
+// Fan areas are signed along the triangle's normal direction tn (a fragment
+// lies in its triangle's plane, with the triangle's orientation), so the
+// centroid and second moment need no second pass; they are ratios of such
+// areas, so the length of tn cancels.  q0 = (p0 - cell centre) / h.
+__device__ void frag_moments(const double (*p)[3], int n, const double q0[3], const double tn[3], double inv_h,
+                             ft_frag& f) {
+    double an[3] = {0.0, 0.0, 0.0}, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0}, As = 0.0;
+    double e1[3], e2[3];
+    for (int d = 0; d < 3; d++) e1[d] = (p[1][d] - p[0][d]) * inv_h;
     for (int m = 1; m + 1 < n; m++) {
-        double e1[3], e2[3];
-        for (int d = 0; d < 3; d++) {
-            e1[d] = (p[m][d] - p[0][d]) * inv_h;
-            e2[d] = (p[m + 1][d] - p[0][d]) * inv_h;
-        }
-        an[0] += 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
-        an[1] += 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
-        an[2] += 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+        for (int d = 0; d < 3; d++) e2[d] = (p[m + 1][d] - p[0][d]) * inv_h;
+        const double cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+        const double cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+        const double cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+        an[0] += 0.5 * cr0;
+        an[1] += 0.5 * cr1;
+        an[2] += 0.5 * cr2;
+        const double a = 0.5 * (cr0 * tn[0] + cr1 * tn[1] + cr2 * tn[2]);
+        As += a;
+        const double s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+        const double a3 = a * (1.0 / 3.0), a12 = a * (1.0 / 12.0);
+        for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
+        // int x_i x_j over a triangle with one vertex at the origin:
+        // (A/12) (s_i s_j + e1_i e1_j + e2_i e2_j)
+        m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+        m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+        m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+        m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+        m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+        m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
+        for (int d = 0; d < 3; d++) e1[d] = e2[d];
     }
-    const double A = sqrt(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
-    double q0[3];
-    for (int d = 0; d < 3; d++) q0[d] = (p[0][d] - xc[d]) * inv_h;
-    double m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
-    if (A > 0.0) {
-        const double nh[3] = {an[0] / A, an[1] / A, an[2] / A};
-        for (int m = 1; m + 1 < n; m++) {
-            double e1[3], e2[3];
-            for (int d = 0; d < 3; d++) {
-                e1[d] = (p[m][d] - p[0][d]) * inv_h;
-                e2[d] = (p[m + 1][d] - p[0][d]) * inv_h;
-            }
-            const double cr0 = e1[1] * e2[2] - e1[2] * e2[1];
-            const double cr1 = e1[2] * e2[0] - e1[0] * e2[2];
-            const double cr2 = e1[0] * e2[1] - e1[1] * e2[0];
-            const double a = 0.5 * (cr0 * nh[0] + cr1 * nh[1] + cr2 * nh[2]);
-            const double s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
-            const double a3 = a * (1.0 / 3.0), a12 = a * (1.0 / 12.0);
-            for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
-            // int x_i x_j over a triangle with one vertex at the origin:
-            // (A/12) (s_i s_j + e1_i e1_j + e2_i e2_j)
-            m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
-            m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
-            m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
-            m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
-            m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
-            m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
-        }
-        const double ia = 1.0 / A;
+    if (As > 0.0) {
+        const double ia = 1.0 / As;
         const double c[3] = {m1[0] * ia, m1[1] * ia, m1[2] * ia};
         f.k[0] = m2[0] * ia - c[0] * c[0];
         f.k[1] = m2[1] * ia - c[1] * c[1];
@@ -263,45 +317,36 @@ __device__ void frag_moments(const double (*p)[3], int n, const double xc[3], do
     for (int d = 0; d < 3; d++) f.an[d] = an[d];
 }
 
-// The same moments in float32 (the FP32 form): vertex offsets from p0 and the
-// offset of p0 from the cell centre are formed in float64 and rounded once; all
-// products and sums are float32.
-__device__ void frag_moments32(const double (*p)[3], int n, const double xc[3], double inv_h, ft_frag32& f) {
-    float q0[3];
-    for (int d = 0; d < 3; d++) q0[d] = (float)((p[0][d] - xc[d]) * inv_h);
-    float an[3] = {0.f, 0.f, 0.f};
+// The same moments in float32 (the FP32 form): each vertex offset from p0 is
+// formed in float64 and rounded once; all products and sums are float32.
+__device__ void frag_moments32(const double (*p)[3], int n, const float q0[3], const float tn[3], float inv_h,
+                               ft_frag32& f) {
+    float an[3] = {0.f, 0.f, 0.f}, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0}, As = 0.f;
     float e1[3], e2[3];
-    for (int d = 0; d < 3; d++) e1[d] = (float)((p[1][d] - p[0][d]) * inv_h);
+    for (int d = 0; d < 3; d++) e1[d] = (float)(p[1][d] - p[0][d]) * inv_h;
     for (int m = 1; m + 1 < n; m++) {
-        for (int d = 0; d < 3; d++) e2[d] = (float)((p[m + 1][d] - p[0][d]) * inv_h);
-        an[0] += 0.5f * (e1[1] * e2[2] - e1[2] * e2[1]);
-        an[1] += 0.5f * (e1[2] * e2[0] - e1[0] * e2[2]);
-        an[2] += 0.5f * (e1[0] * e2[1] - e1[1] * e2[0]);
+        for (int d = 0; d < 3; d++) e2[d] = (float)(p[m + 1][d] - p[0][d]) * inv_h;
+        const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+        const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+        const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+        an[0] += 0.5f * cr0;
+        an[1] += 0.5f * cr1;
+        an[2] += 0.5f * cr2;
+        const float a = 0.5f * (cr0 * tn[0] + cr1 * tn[1] + cr2 * tn[2]);
+        As += a;
+        const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+        const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
+        for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
+        m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+        m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+        m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+        m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+        m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+        m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
         for (int d = 0; d < 3; d++) e1[d] = e2[d];
     }
-    const float A = sqrtf(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
-    float m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
-    if (A > 0.f) {
-        const float nh[3] = {an[0] / A, an[1] / A, an[2] / A};
-        for (int d = 0; d < 3; d++) e1[d] = (float)((p[1][d] - p[0][d]) * inv_h);
-        for (int m = 1; m + 1 < n; m++) {
-            for (int d = 0; d < 3; d++) e2[d] = (float)((p[m + 1][d] - p[0][d]) * inv_h);
-            const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
-            const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
-            const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
-            const float a = 0.5f * (cr0 * nh[0] + cr1 * nh[1] + cr2 * nh[2]);
-            const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
-            const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
-            for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
-            m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
-            m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
-            m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
-            m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
-            m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
-            m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
-            for (int d = 0; d < 3; d++) e1[d] = e2[d];
-        }
-        const float ia = 1.f / A;
+    if (As > 0.f) {
+        const float ia = 1.f / As;
         const float c[3] = {m1[0] * ia, m1[1] * ia, m1[2] * ia};
         f.k[0] = m2[0] * ia - c[0] * c[0];
         f.k[1] = m2[1] * ia - c[1] * c[1];
@@ -334,10 +379,12 @@ constexpr int kClipJobs = 64;  // <= 2 crossings per lane and stage
 // than two crossings in some lane (degenerate) is done lane by lane with
 // clip_half, and a polygon that outgrows kClipV is redone with the wide serial
 // clip: both give the same result as this path would.
-__device__ int clip_warp(const double (*v)[3], const ft_grid& g, const int idx[3], bool active, ClipJob* jobs,
-                         double (*res)[3]) {
+// The surviving polygon is left in A or B (or, after the wide fallback, in
+// wide_res); *out points to it.
+__device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g, const int idx[3], bool active,
+                         ClipJob* jobs, double (*A)[3], double (*B)[3], double (*wide_res)[3],
+                         const double (**out)[3]) {
     const int lane = threadIdx.x & 31;
-    double A[kClipV][3], B[kClipV][3];
     double(*src)[3] = A;
     double(*dst)[3] = B;
     int n = 3;
@@ -347,7 +394,7 @@ __device__ int clip_warp(const double (*v)[3], const ft_grid& g, const int idx[3
     for (int st = 0; st < 6; st++) {
         const int ax = st >> 1;
         const bool ge = (st & 1) == 0;
-        const double pv = ft_plane(g.origin[ax], g.h, idx[ax] + (st & 1));
+        const double pv = P.at(ax, idx[ax] + (st & 1));
         unsigned flags = 0, cross = 0;
         int ncross = 0;
         if (alive) {
@@ -445,56 +492,68 @@ __device__ int clip_warp(const double (*v)[3], const ft_grid& g, const int idx[3
         }
         __syncwarp();
     }
-    if (wide) return canon_stages_wide(v, g, idx, res);
+    if (wide) {
+        *out = wide_res;
+        return canon_stages_wide(v, g, idx, wide_res);
+    }
+    *out = src;
     if (!alive) return 0;
     for (int ax = 0; ax < 3; ax++) {
-        const long long ku = okey(ft_plane(g.origin[ax], g.h, idx[ax] + 1));
+        const long long ku = okey(P.at(ax, idx[ax] + 1));
         bool all = true;
         for (int m = 0; m < n && all; m++) all = (okey(src[m][ax]) == ku);
         if (all) return 0;
     }
-    for (int m = 0; m < n; m++)
-        for (int d = 0; d < 3; d++) res[m][d] = src[m][d];
     return n;
 }
 
-__global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ verts, const int* __restrict__ tris,
-                                                   ft_grid g, const int* __restrict__ cand_tri,
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_clip(F fr, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
+                                                   const double* __restrict__ tri_nrm,
                                                    unsigned* __restrict__ keys, unsigned* __restrict__ vals,
                                                    ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
                                                    float4* __restrict__ cen32, int fp32, const ft_counters* ctr) {
     __shared__ ClipJob s_jobs[kThreads / 32][kClipJobs];
     ClipJob* jobs = s_jobs[threadIdx.x >> 5];
     const long long C = ctr->C;
-    const double inv_h = 1.0 / g.h;
     const int lane = threadIdx.x & 31;
     const long long nwarps = (long long)gridDim.x * (kThreads / 32);
     for (long long cb = ((long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; cb < C; cb += nwarps * 32) {
         const long long c = cb + lane;
         const bool active = c < C;
         int idx[3] = {0, 0, 0};
+        int b = 0;
         double v[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         if (active) {
             const int t = cand_tri[c];
             const int l = (int)(c - tri_off[t]);
-            const int* bx = tri_box + 6 * (long long)t;
-            const int e1 = bx[4], e2 = bx[5];
-            idx[0] = bx[0] + l / (e1 * e2);
-            idx[1] = bx[1] + (l / e2) % e1;
-            idx[2] = bx[2] + l % e2;
+            const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
+            const int4 b0 = bx[0], b1 = bx[1];
+            const int e1 = b1.x, e2 = b1.y;
+            b = b1.z;
+            idx[0] = b0.x + l / (e1 * e2);
+            idx[1] = b0.y + (l / e2) % e1;
+            idx[2] = b0.z + l % e2;
+            const ft_fdesc& D = fr.desc(b);
+            const long long tl = t - fr.tri_base(b);
             for (int a = 0; a < 3; a++) {
-                const long long vi = tris[3 * (long long)t + a];
-                for (int d = 0; d < 3; d++) v[a][d] = verts[3 * vi + d];
+                const long long vi = D.tris[3 * tl + a];
+                for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
             }
         }
-        double poly[32][3];
-        const int n = clip_warp(v, g, idx, active, jobs, poly);
+        const ft_fdesc& D = fr.desc(b);
+        const ft_grid g = D.g;
+        const Planes P(D);
+        double bufA[kClipV][3], bufB[kClipV][3], wide[32][3];
+        const double(*poly)[3] = bufA;
+        const int n = clip_warp(v, P, g, idx, active, jobs, bufA, bufB, wide, &poly);
         if (!active) continue;
         unsigned key = FT_SENTINEL;
         if (n >= 3) {
-            double xc[3];
-            for (int d = 0; d < 3; d++) xc[d] = ft_plane(g.origin[d], g.h, idx[d]) + 0.5 * g.h;
+            const double inv_h = D.inv_h;
+            const double2* tnp = reinterpret_cast<const double2*>(tri_nrm + 4 * (long long)cand_tri[c]);
+            const double2 tn01 = tnp[0], tn2 = tnp[1];
             // The moments' own area vector certifies the canonical "area vector
             // is not zero" condition whenever it exceeds its rounding bound by
             // far (float32: 1e-4 h^2, float64: 1e-9 h^2); only smaller fragments
@@ -502,13 +561,20 @@ __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ ve
             bool accept;
             if (fp32) {
                 ft_frag32 f;
-                frag_moments32(poly, n, xc, inv_h, f);
+                const float tn[3] = {(float)tn01.x, (float)tn01.y, (float)tn2.x};
+                const float ih = (float)inv_h;
+                float q0[3];
+                for (int d = 0; d < 3; d++) q0[d] = (float)(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
+                frag_moments32(poly, n, q0, tn, ih, f);
                 const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
                 accept = (a > 1e-4f) || canon_area_nonzero(poly, n);
                 if (accept) rec32[c] = f;
             } else {
                 ft_frag f;
-                frag_moments(poly, n, xc, inv_h, f);
+                const double tn[3] = {tn01.x, tn01.y, tn2.x};
+                double q0[3];
+                for (int d = 0; d < 3; d++) q0[d] = (poly[0][d] - P.at(d, idx[d])) * inv_h - 0.5;
+                frag_moments(poly, n, q0, tn, inv_h, f);
                 const double a = fmax(fabs(f.an[0]), fmax(fabs(f.an[1]), fabs(f.an[2])));
                 accept = (a > 1e-9) || canon_area_nonzero(poly, n);
                 if (accept) {
@@ -516,7 +582,8 @@ __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ ve
                     if (cen32) cen32[c] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
                 }
             }
-            if (accept) key = (unsigned)(((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
+            if (accept)
+                key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
         }
         keys[c] = key;
         vals[c] = (unsigned)c;
@@ -527,13 +594,13 @@ __global__ void __launch_bounds__(kThreads) k_clip(const double* __restrict__ ve
 
 namespace ft {
 
-cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s) {
-    const long long T = f->nt;
+template <class F>
+cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params* p, cudaStream_t s) {
     const int margin = 2 + (int)ceil(p->delta_max_h);
     const unsigned nb = (unsigned)((T + kThreads - 1) / kThreads);
     if (T > 0) {
-        k_tri_setup<<<nb, kThreads, 0, s>>>(f->verts, f->nv, f->tris, T, ws->g, margin, ws->max_cand, ws->tri_cnt,
-                                            ws->tri_box, ws->ctr);
+        k_tri_setup<F><<<nb, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_box, ws->tri_nrm,
+                                               ws->ctr);
     } else {
         cudaMemsetAsync(&ws->ctr->T, 0, sizeof(long long), s);
     }
@@ -544,10 +611,33 @@ cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, 
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     ws->last_precision = fp32 ? FT_FP32C : FT_FP64;
-    k_clip<<<ws->sm_count * 4, kThreads, 0, s>>>(f->verts, f->tris, ws->g, ws->cand_tri, ws->tri_off, ws->tri_box,
-                                                ws->keys[0], ws->vals[0], ws->rec, ws->rec32, ws->cen32, fp32 ? 1 : 0,
-                                                ws->ctr);
+    k_clip<F><<<ws->sm_count * ws->tune.clip_bps, kThreads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
+                                                                    ws->tri_nrm, ws->keys[0], ws->vals[0], ws->rec, ws->rec32,
+                                                                    ws->cen32, fp32 ? 1 : 0, ws->ctr);
     return cudaGetLastError();
+}
+
+cudaError_t launch_planes_one(ft_workspace* ws, cudaStream_t s) {
+    const long long n = ft_plane_count(ws->g);
+    count_launches(1);
+    k_planes<FrontsOne><<<dim3((unsigned)((n + kThreads - 1) / kThreads), 1), kThreads, 0, s>>>(
+        ft_one(ws, nullptr, nullptr, 0, 0));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planes_batch(ft_workspace* ws, int max_planes, cudaStream_t s) {
+    count_launches(1);
+    k_planes<FrontsMany><<<dim3((unsigned)((max_planes + kThreads - 1) / kThreads), (unsigned)ws->nf), kThreads, 0, s>>>(
+        ft_many(ws));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s) {
+    return bin_with(ws, ft_one(ws, f->verts, f->tris, f->nv, f->nt), f->nt, p, s);
+}
+
+cudaError_t launch_bin_batch(ft_workspace* ws, const ft_params* p, cudaStream_t s) {
+    return bin_with(ws, ft_many(ws), ws->nt_total, p, s);
 }
 
 }  // namespace ft

@@ -10,8 +10,8 @@
 //    exactly 1 and 0) write zero force, interfacial cells write sigma kappa grad
 //    alpha, and the remaining cells (the ring around the interface) are appended
 //    to a compact list.
-//  * k_csf_ring -- one thread per listed cell: the smoothed curvature and the
-//    force.  Keeping the float64 smoothing out of the dense pass keeps that pass
+//  * k_csf_ring -- one warp per listed cell (a lane per neighbour): the
+//    smoothed curvature and the force.  Keeping the float64 smoothing out of the dense pass keeps that pass
 //    bound by memory instead of by divergent float64 issue.
 #include "ft_internal.cuh"
 
@@ -19,18 +19,23 @@ namespace {
 
 constexpr int kThreads = 128;  // one block per column; 128 and 256 cell columns fill it
 
-__global__ void __launch_bounds__(kThreads) k_csf_dense(ft_grid g, double sigma, const double* __restrict__ alpha,
-                                                        const int* __restrict__ idx_map,
-                                                        const double* __restrict__ kappa, double* __restrict__ force,
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_csf_dense(F fr, double sigma, const int* __restrict__ idx_map,
+                                                        const double* __restrict__ kappa,
                                                         unsigned* __restrict__ ring, unsigned* __restrict__ nring,
                                                         long long ring_cap, ft_counters* ctr) {
-    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    const long long NC = (long long)n0 * n1 * n2;
-    const long long s1 = n2, s0 = (long long)n1 * n2;
-    const double ih2 = 0.5 / g.h;
-    const long long ncol = (long long)n0 * n1;
     const int lane = threadIdx.x & 31;
-    for (long long col = blockIdx.x; col < ncol; col += gridDim.x) {
+    for (long long gcol = blockIdx.x; gcol < fr.ncols; gcol += gridDim.x) {
+        const int b = fr.by_col(gcol);
+        const ft_fdesc& D = fr.desc(b);
+        const int n0 = D.g.n[0], n1 = D.g.n[1], n2 = D.g.n[2];
+        const long long NC = (long long)n0 * n1 * n2;
+        const long long s1 = n2, s0 = (long long)n1 * n2;
+        const double ih2 = 0.5 * D.inv_h;
+        const double* __restrict__ alpha = D.alpha;
+        double* __restrict__ force = D.force;
+        const long long kb = fr.key_base(b);
+        const long long col = gcol - fr.col_base(b);
         const int i = (int)(col / n1), j = (int)(col - (long long)i * n1);
         for (int k0 = 0; k0 < n2; k0 += kThreads) {
             const int k = k0 + (int)threadIdx.x;
@@ -59,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) k_csf_dense(ft_grid g, double sigma,
                 const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
                 double kp = 0.0;
                 if (gx != 0.0 || gy != 0.0 || gz != 0.0) {
-                    const int m = idx_map[key];
+                    const int m = idx_map[kb + key];
                     if (m >= 0)
                         kp = kappa[m];
                     else
@@ -72,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_csf_dense(ft_grid g, double sigma,
                     force[2 * NC + key] = f * gz;
                 }
             }
-            // append this warp's ring cells with one atomic
+            // append this warp's ring cells (batch-global keys) with one atomic
             const unsigned bal = __ballot_sync(0xffffffffu, to_ring);
             if (bal) {
                 unsigned base = 0;
@@ -81,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_csf_dense(ft_grid g, double sigma,
                 if (to_ring) {
                     const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
                     if (pos < ring_cap)
-                        ring[pos] = (unsigned)key;
+                        ring[pos] = (unsigned)(kb + key);
                     else
                         ft_flag(ctr, FT_ST_CAPACITY);
                 }
@@ -90,59 +95,74 @@ __global__ void __launch_bounds__(kThreads) k_csf_dense(ft_grid g, double sigma,
     }
 }
 
-__global__ void __launch_bounds__(128) k_csf_ring(ft_grid g, double sigma, const double* __restrict__ alpha,
-                                                  const int* __restrict__ idx_map, const double* __restrict__ kappa,
-                                                  const double* __restrict__ normal, double* __restrict__ force,
+// One warp per ring cell: lanes 0..25 take the 26 neighbours (smoothing
+// weights), lanes 26..31 the six alpha values of the central-difference
+// gradient; the sums are reduced over the warp.
+template <class F>
+__global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int* __restrict__ idx_map,
+                                                  const double* __restrict__ kappa, const double* __restrict__ normal,
                                                   const unsigned* __restrict__ ring, const unsigned* __restrict__ nring,
                                                   long long ring_cap) {
-    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-    const long long NC = (long long)n0 * n1 * n2;
-    const long long s1 = n2, s0 = (long long)n1 * n2;
-    const double ih2 = 0.5 / g.h;
-    const double inv_len[4] = {0.0, 1.0, 0.70710678118654752440, 0.57735026918962576451};
+    const int lane = threadIdx.x & 31;
     const long long nr = min((long long)*nring, ring_cap);
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
-         r += (long long)gridDim.x * blockDim.x) {
-        const long long key = ring[r];
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    // neighbour offset of this lane (lanes 0..25: the 26 neighbours, centre skipped)
+    const int code = lane < 13 ? lane : lane + 1;
+    const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
+    const int nsq = di * di + dj * dj + dk * dk;
+    const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nr; r += nw) {
+        const long long gkey = ring[r];
+        const int b = fr.by_key(gkey);
+        const ft_fdesc& D = fr.desc(b);
+        const int n0 = D.g.n[0], n1 = D.g.n[1], n2 = D.g.n[2];
+        const long long NC = (long long)n0 * n1 * n2;
+        const long long s1 = n2, s0 = (long long)n1 * n2;
+        const double* __restrict__ alpha = D.alpha;
+        const long long kb = fr.key_base(b);
+        const long long key = gkey - kb;
         const int k = (int)(key % n2);
         const int j = (int)((key / n2) % n1);
         const int i = (int)(key / s0);
-        const double axp = (i + 1 < n0) ? alpha[key + s0] : 0.0;
-        const double axm = (i > 0) ? alpha[key - s0] : 0.0;
-        const double ayp = (j + 1 < n1) ? alpha[key + s1] : 0.0;
-        const double aym = (j > 0) ? alpha[key - s1] : 0.0;
-        const double azp = (k + 1 < n2) ? alpha[key + 1] : 0.0;
-        const double azm = (k > 0) ? alpha[key - 1] : 0.0;
-        const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
-        double num = 0.0, den = 0.0, ks = 0.0;
-        int cnt = 0;
-        for (int di = -1; di <= 1; di++) {
-            const int ii = i + di;
-            if (ii < 0 || ii >= n0) continue;
-            for (int dj = -1; dj <= 1; dj++) {
-                const int jj = j + dj;
-                if (jj < 0 || jj >= n1) continue;
-                for (int dk = -1; dk <= 1; dk++) {
-                    const int kk = k + dk;
-                    if (kk < 0 || kk >= n2 || (di == 0 && dj == 0 && dk == 0)) continue;
-                    const int q = idx_map[((long long)ii * n1 + jj) * n2 + kk];
-                    if (q < 0) continue;
+        double num = 0.0, den = 0.0, ks = 0.0, cnt = 0.0, av = 0.0;
+        if (lane < 26) {
+            const int ii = i + di, jj = j + dj, kk = k + dk;
+            if (ii >= 0 && ii < n0 && jj >= 0 && jj < n1 && kk >= 0 && kk < n2) {
+                const int q = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
+                if (q >= 0) {
                     const double* nq = normal + 3 * (long long)q;
-                    const double w =
-                        fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len[di * di + dj * dj + dk * dk];
+                    const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
                     const double kq = kappa[q];
-                    num += kq * w;
-                    den += w;
-                    ks += kq;
-                    cnt++;
+                    num = kq * w;
+                    den = w;
+                    ks = kq;
+                    cnt = 1.0;
                 }
             }
+        } else {
+            // lanes 26..31: alpha at +x, -x, +y, -y, +z, -z (0 outside the grid)
+            const int e = lane - 26, ax = e >> 1, sg = (e & 1) ? -1 : 1;
+            const int c = ax == 0 ? i : (ax == 1 ? j : k);
+            const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+            const long long st = ax == 0 ? s0 : (ax == 1 ? s1 : 1);
+            if (c + sg >= 0 && c + sg < n) av = alpha[key + sg * st];
         }
-        const double kp = (den > 0.0) ? num / den : (cnt ? ks / cnt : 0.0);
-        const double f = sigma * kp;
-        force[key] = f * gx;
-        force[NC + key] = f * gy;
-        force[2 * NC + key] = f * gz;
+        num = ft_warp_sum(num);
+        den = ft_warp_sum(den);
+        ks = ft_warp_sum(ks);
+        cnt = ft_warp_sum(cnt);
+        const double ih2 = 0.5 * D.inv_h;
+        double g3[3];
+        for (int ax = 0; ax < 3; ax++)
+            g3[ax] = (__shfl_sync(0xffffffffu, av, 26 + 2 * ax) - __shfl_sync(0xffffffffu, av, 27 + 2 * ax)) * ih2;
+        if (lane == 0) {
+            const double kp = (den > 0.0) ? num / den : (cnt > 0.0 ? ks / cnt : 0.0);
+            const double f = sigma * kp;
+            double* __restrict__ force = D.force;
+            force[key] = f * g3[0];
+            force[NC + key] = f * g3[1];
+            force[2 * NC + key] = f * g3[2];
+        }
     }
 }
 
@@ -150,18 +170,32 @@ __global__ void __launch_bounds__(128) k_csf_ring(ft_grid g, double sigma, const
 
 namespace ft {
 
-cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
-                       const double* normal, double* force, cudaStream_t s) {
+template <class F>
+cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const double* kappa, const double* normal,
+                     cudaStream_t s) {
     // the ring list lives in the sort's spare key buffer (max_cand entries)
     unsigned* ring = ws->keys[ws->sorted_buf ^ 1];
     unsigned* nring = &ws->ctr->pad;
     cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
     count_launches(2);
-    k_csf_dense<<<ws->sm_count * 16, kThreads, 0, s>>>(ws->g, p->sigma, alpha, ws->idx_map, kappa, force, ring, nring,
-                                                       ws->max_cand, ws->ctr);
-    k_csf_ring<<<ws->sm_count * 4, 128, 0, s>>>(ws->g, p->sigma, alpha, ws->idx_map, kappa, normal, force, ring,
-                                                nring, ws->max_cand);
+    k_csf_dense<F><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, ring, nring,
+                                                                        ws->max_cand, ws->ctr);
+    k_csf_ring<F><<<ws->sm_count * 16, 128, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, normal, ring, nring,
+                                                    ws->max_cand);
     return cudaGetLastError();
+}
+
+cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                       const double* normal, double* force, cudaStream_t s) {
+    FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
+    fr.d0.alpha = const_cast<double*>(alpha);  // read only here
+    fr.d0.force = force;
+    return csf_with(ws, fr, p, kappa, normal, s);
+}
+
+cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                             cudaStream_t s) {
+    return csf_with(ws, ft_many(ws), p, kappa, normal, s);
 }
 
 }  // namespace ft

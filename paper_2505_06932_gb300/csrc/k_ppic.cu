@@ -13,7 +13,9 @@
 //   sum_f u_f v_f v_f^T a = sum_f u_f z_f v_f.
 //
 // Two kernels:
-//  * k_ppic_acc<T> -- one warp per cell (fragment records in sorted pair
+//  * k_ppic_acc<T> -- one warp per cell (static interleaving or a global work
+//    counter; kMinBlocks sets the occupancy the registers are fitted to); fragment
+//    records are read in sorted pair
 //    order, so a cell's fragments are one contiguous range): frame, candidate
 //    fragments of the cells within ceil(delta - 1/2), a float32 support test
 //    on a compact centroid array that appends the
@@ -23,6 +25,8 @@
 //    warp reduction of the 27 sums (compensated hi/lo pairs for float).
 //  * k_ppic_solve -- one thread per cell: the 6x6 LDL^T solve in float64, the
 //    curvature of z = P(x, y) at the origin and the outputs.
+#include <stddef.h>
+
 #include "ft_internal.cuh"
 
 namespace {
@@ -32,9 +36,9 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kQueue = 64;
 
 struct PpicArgs {
-    ft_grid g;
     double delta_h, delta_growth, delta_max_h;
     int fit_min;
+    int dynamic;  // 1: cells from the global work counter, 0: static interleaving
 };
 
 // Tangents (t1, t2) completing the unit normal n: the branchless basis of Duff
@@ -46,13 +50,21 @@ struct PpicArgs {
 __constant__ double kFrameR[3][3] = {{0.890670841215793, -0.3614406733922875, -0.2758008198422935},
                                      {0.0, 0.6066239971779142, -0.7949888842291382},
                                      {0.4546487134128409, 0.7080734182735712, 0.5403023058681398}};
+// the same matrix rounded to float (the FP32 form reads it without conversions)
+__constant__ float kFrameRf[3][3] = {{0.890670841215793f, -0.3614406733922875f, -0.2758008198422935f},
+                                     {0.0f, 0.6066239971779142f, -0.7949888842291382f},
+                                     {0.4546487134128409f, 0.7080734182735712f, 0.5403023058681398f}};
+
+template <typename T> __device__ __forceinline__ T frame_r(int r, int c);
+template <> __device__ __forceinline__ double frame_r<double>(int r, int c) { return kFrameR[r][c]; }
+template <> __device__ __forceinline__ float frame_r<float>(int r, int c) { return kFrameRf[r][c]; }
 
 template <typename T>
 __device__ __forceinline__ void basis(const T n[3], T t1[3], T t2[3]) {
     T m[3], u1[3], u2[3];
 #pragma unroll
     for (int r = 0; r < 3; r++)
-        m[r] = (T)kFrameR[r][0] * n[0] + (T)kFrameR[r][1] * n[1] + (T)kFrameR[r][2] * n[2];
+        m[r] = frame_r<T>(r, 0) * n[0] + frame_r<T>(r, 1) * n[1] + frame_r<T>(r, 2) * n[2];
     const T sg = copysign((T)1, m[2]);
     const T a = (T)-1 / (sg + m[2]);
     const T b = m[0] * m[1] * a;
@@ -64,8 +76,8 @@ __device__ __forceinline__ void basis(const T n[3], T t1[3], T t2[3]) {
     u2[2] = -m[1];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        t1[c] = (T)kFrameR[0][c] * u1[0] + (T)kFrameR[1][c] * u1[1] + (T)kFrameR[2][c] * u1[2];
-        t2[c] = (T)kFrameR[0][c] * u2[0] + (T)kFrameR[1][c] * u2[1] + (T)kFrameR[2][c] * u2[2];
+        t1[c] = frame_r<T>(0, c) * u1[0] + frame_r<T>(1, c) * u1[1] + frame_r<T>(2, c) * u1[2];
+        t2[c] = frame_r<T>(0, c) * u2[0] + frame_r<T>(1, c) * u2[1] + frame_r<T>(2, c) * u2[2];
     }
 }
 
@@ -208,8 +220,8 @@ __device__ __forceinline__ void accumulate(const Rec<T>& rec, unsigned ri, int d
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(PpicArgs A, const unsigned* __restrict__ cells,
+template <typename T, class F, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F fr, const unsigned* __restrict__ cells,
                                                        const int* __restrict__ cell_off, Rec<T> rec,
                                                        const float4* __restrict__ cen,
                                                        const int* __restrict__ idx_map, ft_counters* ctr,
@@ -220,11 +232,29 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned* qr = s_qr[wid];
     int* qd = s_qd[wid];
-    const int n0 = A.g.n[0], n1 = A.g.n[1], n2 = A.g.n[2];
-    const long long nw = (long long)gridDim.x * kWarps;
     unsigned long long pairs_total = 0;
-    for (long long m = (long long)blockIdx.x * kWarps + wid; m < M; m += nw) {
-        const unsigned key = cells[m];
+    // Schedule: static interleaving (the warps of a block take consecutive
+    // cells, which share most of their candidate fragments in L1), or a global
+    // work counter (balances cells whose supports differ widely, as between the
+    // fronts of a batch); lane 0 fetches the next index while a cell runs.
+    const long long nw = (long long)gridDim.x * kWarps;
+    // support radii in T (the default radii 2.5, 3.125, 3.90625, 4 are exact in float)
+    const T d_start = (T)A.delta_h, d_growth = (T)A.delta_growth, d_max = (T)A.delta_max_h;
+    unsigned long long next = 0;
+    if (A.dynamic && lane == 0) next = atomicAdd((unsigned long long*)&ctr->work, 1ull);
+    for (long long m0 = (long long)blockIdx.x * kWarps + wid;; m0 += nw) {
+        long long m = m0;
+        if (A.dynamic) {
+            m = (long long)__shfl_sync(0xffffffffu, next, 0);
+            if (m < M && lane == 0) next = atomicAdd((unsigned long long*)&ctr->work, 1ull);
+        }
+        if (m >= M) break;
+        const unsigned gkey = cells[m];
+        const int fb = fr.by_key(gkey);
+        const ft_grid& G = fr.desc(fb).g;
+        const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+        const long long kb = fr.key_base(fb);
+        const unsigned key = (unsigned)(gkey - kb);
         const int ck = (int)(key % (unsigned)n2);
         const int cj = (int)((key / (unsigned)n2) % (unsigned)n1);
         const int ci = (int)(key / ((unsigned)n2 * (unsigned)n1));
@@ -289,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
         qform<T>(t2, t2, c22);
 
         // 2-4. normal equations; the support grows while too few fragments lie in it
-        T delta = (T)A.delta_h;
+        T delta = d_start;
         T S[21], B[6];
         int ctot;
         for (;;) {
@@ -301,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
             const T inv_delta = (T)1 / delta;
             // float pre-filter, slightly wider than the support; the exact test follows
             const float f_thr = (float)delta * (float)delta * 1.0001f;
-            const int R = (int)ceil((double)delta - 0.5);
+            const int R = (int)ceil(delta - (T)0.5);
             const int side = 2 * R + 1;
             const int nb = side * side * side;
             int qn = 0;
@@ -312,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
                     const int di = l / (side * side) - R, dj = (l / side) % side - R, dk = l % side - R;
                     const int ii = ci + di, jj = cj + dj, kk = ck + dk;
                     if (ii >= 0 && jj >= 0 && kk >= 0 && ii < n0 && jj < n1 && kk < n2) {
-                        const int m2 = idx_map[((long long)ii * n1 + jj) * n2 + kk];
+                        const int m2 = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
                         if (m2 >= 0) {
                             f0 = cell_off[m2];
                             cnt = cell_off[m2 + 1] - f0;
@@ -369,8 +399,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 3) k_ppic_acc(P
                 accumulate<T>(rec, qr[lane], qd[lane], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, S, B, count);
             __syncwarp();
             ctot = ft_warp_sum_i(count);
-            if (ctot >= A.fit_min || (double)delta >= A.delta_max_h) break;
-            delta = (T)fmin((double)delta * A.delta_growth, A.delta_max_h);
+            if (ctot >= A.fit_min || delta >= d_max) break;
+            delta = min(delta * d_growth, d_max);
             st |= FT_FIT_GROWN;
         }
         pairs_total += (unsigned long long)ctot;
@@ -440,17 +470,18 @@ __device__ double ldlt_solve(const double* S, const double* B, int n, double* a)
     };
     double tr = 0.0;
     for (int i = 0; i < n; i++) tr += at(i, i);
-    double minp = INFINITY;
+    double minp = INFINITY, inv_d[6];
     for (int j = 0; j < n; j++) {
         double dj = at(j, j);
         for (int k = 0; k < j; k++) dj -= Lm[j][k] * Lm[j][k] * d[k];
         d[j] = dj;
         minp = fmin(minp, dj);
         if (!(dj > 0.0)) return -1.0;
+        inv_d[j] = 1.0 / dj;  // one float64 division per pivot
         for (int i = j + 1; i < n; i++) {
             double v = at(i, j);
             for (int k = 0; k < j; k++) v -= Lm[i][k] * Lm[j][k] * d[k];
-            Lm[i][j] = v / dj;
+            Lm[i][j] = v * inv_d[j];
         }
     }
     double y[6];
@@ -460,16 +491,16 @@ __device__ double ldlt_solve(const double* S, const double* B, int n, double* a)
         y[i] = v;
     }
     for (int i = n - 1; i >= 0; i--) {
-        double v = y[i] / d[i];
+        double v = y[i] * inv_d[i];
         for (int k = i + 1; k < n; k++) v -= Lm[k][i] * a[k];
         a[i] = v;
     }
     return minp / tr;
 }
 
-__global__ void __launch_bounds__(128) k_ppic_solve(const ft_cellsys* __restrict__ sys, const int* __restrict__ fit_info,
-                                                    const unsigned* __restrict__ cells, int fp32, double h,
-                                                    long long cap, ft_counters* ctr, unsigned* __restrict__ out_keys,
+template <class F>
+__global__ void __launch_bounds__(128) k_ppic_solve(F fr, const ft_cellsys* __restrict__ sys, const int* __restrict__ fit_info,
+                                                    const unsigned* __restrict__ cells, int fp32, long long cap, ft_counters* ctr, unsigned* __restrict__ out_keys,
                                                     double* __restrict__ out_kappa, double* __restrict__ out_normal,
                                                     double* __restrict__ out_coeffs, int8_t* __restrict__ out_status) {
     const long long M = ctr->M;
@@ -485,8 +516,8 @@ __global__ void __launch_bounds__(128) k_ppic_solve(const ft_cellsys* __restrict
             for (int r = 0; r < 6; r++) B[r] = (double)v[42 + 2 * r] + (double)v[43 + 2 * r];
             for (int r = 0; r < 3; r++) n[r] = (double)v[54 + 2 * r];
             z0 = (double)v[60];
-            const double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-            for (int r = 0; r < 3; r++) n[r] /= nl;
+            const double il = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            for (int r = 0; r < 3; r++) n[r] *= il;
         } else {
             for (int r = 0; r < 21; r++) S[r] = sys[m].v[r];
             for (int r = 0; r < 6; r++) B[r] = sys[m].v[21 + r];
@@ -516,10 +547,11 @@ __global__ void __launch_bounds__(128) k_ppic_solve(const ft_cellsys* __restrict
                             2.0 * a[5] * (1.0 + a[1] * a[1])) / (g2 * sqrt(g2));
         double nv[3];
         for (int d = 0; d < 3; d++) nv[d] = n[d] - a[1] * t1[d] - a[2] * t2[d];
-        const double nl = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-        out_keys[m] = cells[m];
-        out_kappa[m] = kl / h;
-        for (int d = 0; d < 3; d++) out_normal[3 * m + d] = nv[d] / nl;
+        const double il = 1.0 / sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        const unsigned key = cells[m];
+        out_keys[m] = key;
+        out_kappa[m] = kl * fr.desc(fr.by_key(key)).inv_h;
+        for (int d = 0; d < 3; d++) out_normal[3 * m + d] = nv[d] * il;
         if (out_coeffs)
             for (int r = 0; r < 6; r++) out_coeffs[6 * m + r] = a[r];
         out_status[m] = (int8_t)st;
@@ -530,30 +562,46 @@ __global__ void __launch_bounds__(128) k_ppic_solve(const ft_cellsys* __restrict
 
 namespace ft {
 
-cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, unsigned* cell_keys, double* kappa,
-                        double* normal, double* coeffs, int8_t* fit_status, cudaStream_t s) {
+template <class F>
+cudaError_t ppic_with(ft_workspace* ws, const F& fr, const ft_params* p, long long cap, unsigned* cell_keys,
+                      double* kappa, double* normal, double* coeffs, int8_t* fit_status, cudaStream_t s) {
     PpicArgs A;
-    A.g = ws->g;
     A.delta_h = p->delta_h;
     A.delta_growth = p->delta_growth;
     A.delta_max_h = p->delta_max_h;
     A.fit_min = p->fit_min;
-    cudaMemsetAsync(&ws->ctr->fit_pairs, 0, sizeof(long long), s);
+    A.dynamic = ws->tune.ppic_dynamic;
+    // fit_pairs and the work counter are adjacent: one reset
+    static_assert(offsetof(ft_counters, work) == offsetof(ft_counters, fit_pairs) + sizeof(long long), "layout");
+    cudaMemsetAsync(&ws->ctr->fit_pairs, 0, 2 * sizeof(long long), s);
     const bool fp32 = ws->last_precision == FT_FP32C;
     count_launches(2);
+    const unsigned nb = (unsigned)(ws->sm_count * ws->tune.ppic_bps);
     // fragments are read in sorted pair order (front_bin gathers them)
     if (fp32) {
         Rec<float> r{ws->srec32};
-        k_ppic_acc<float><<<ws->sm_count * 4, kThreads, 0, s>>>(A, ws->cells, ws->cell_off, r, ws->scen,
-                                                                ws->idx_map, ws->ctr, ws->sys, ws->fit_info);
+        if (ws->tune.ppic_min_blocks >= 6)
+            k_ppic_acc<float, F, 6><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
+                                                           ws->ctr, ws->sys, ws->fit_info);
+        else
+            k_ppic_acc<float, F, 4><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
+                                                           ws->ctr, ws->sys, ws->fit_info);
     } else {
         Rec<double> r{ws->srec};
-        k_ppic_acc<double><<<ws->sm_count * 4, kThreads, 0, s>>>(A, ws->cells, ws->cell_off, r, ws->scen,
-                                                                 ws->idx_map, ws->ctr, ws->sys, ws->fit_info);
+        k_ppic_acc<double, F, 3><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
+                                                        ws->ctr, ws->sys, ws->fit_info);
     }
-    k_ppic_solve<<<ws->sm_count * 4, 128, 0, s>>>(ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, ws->g.h, cap,
-                                                 ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
+    k_ppic_solve<F><<<ws->sm_count * 4, 128, 0, s>>>(fr, ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, cap,
+                                                    ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, unsigned* cell_keys, double* kappa,
+                        double* normal, double* coeffs, int8_t* fit_status, cudaStream_t s) {
+    if (ws->batch)
+        return ppic_with(ws, ft_many(ws), p, cap, cell_keys, kappa, normal, coeffs, fit_status, s);
+    return ppic_with(ws, ft_one(ws, nullptr, nullptr, 0, 0), p, cap, cell_keys, kappa, normal, coeffs, fit_status,
+                     s);
 }
 
 }  // namespace ft

@@ -300,6 +300,27 @@ __global__ void __launch_bounds__(kB) k_gather(const unsigned* __restrict__ sval
     }
 }
 
+// Batched form: off[f] = first interfacial cell of front f in the sorted cell
+// list (the cells of front f are the keys in [key_base[f], key_base[f+1])),
+// off[nf] = M.
+__global__ void __launch_bounds__(kB) k_cell_ranges(const unsigned* __restrict__ cells,
+                                                    const long long* __restrict__ key_base, int nf,
+                                                    long long* __restrict__ off, const ft_counters* ctr) {
+    const int f = blockIdx.x * kB + threadIdx.x;
+    if (f > nf) return;
+    const long long M = ctr->M;
+    const long long kf = key_base[f];
+    long long lo = 0, hi = M;  // first index with cells[i] >= kf
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if ((long long)cells[mid] < kf)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[f] = lo;
+}
+
 }  // namespace
 
 namespace ft {
@@ -358,7 +379,7 @@ cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
     for (int p = 0; p < passes; p++) {
         // pass 0 reads the candidates (sentinels dropped) and counts the pairs
         const long long* n = (p == 0) ? &ws->ctr->C : &ws->ctr->P;
-        long long* tot = (p == 0) ? &ws->ctr->P : &ws->ctr->pad2;
+        long long* tot = (p == 0) ? &ws->ctr->P : &ws->ctr->scratch;
         count_launches(3);
         k_radix_hist<<<G, kB, 0, s>>>(ws->keys[src], n, 8 * p, ws->hist);
         k_radix_scan<<<1, kScanThreads, 256 * G * sizeof(int), s>>>(ws->hist, G, tot);
@@ -378,6 +399,12 @@ cudaError_t launch_rle(ft_workspace* ws, cudaStream_t s) {
     k_rle<<<ws->sm_count * 2, kB, 0, s>>>(keys, ws->heads, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
                                           ws->ctr);
     k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_ranges(ft_workspace* ws, long long* off, cudaStream_t s) {
+    count_launches(1);
+    k_cell_ranges<<<(ws->nf + 1 + kB - 1) / kB, kB, 0, s>>>(ws->cells, ws->fbase, ws->nf, off, ws->ctr);
     return cudaGetLastError();
 }
 

@@ -358,3 +358,45 @@ def solid_body_faces_exact(g: Grid, centre, omega):
         r = np.stack([X - c[0], Y - c[1], Z - c[2]], -1)
         out.append(np.ascontiguousarray(np.cross(np.broadcast_to(w, r.shape), r)[..., axis]))
     return tuple(out)
+
+
+# ----------------------------------------------------------------------------
+# served form: a stream of requests
+# ----------------------------------------------------------------------------
+
+def served_requests(seed: int = 11, count: int = 48, rate: float = 100.0, s_choices=(4, 5, 6, 7),
+                    n_choices=(32, 64, 128, 256, 512), max_steps: int = 50, pool_per_s: int = 2,
+                    delta_max_h: float = 4.0):
+    """A request stream: Poisson arrivals of the given rate (requests/s); each
+    request a spherical-harmonic-deformed icosphere (l = 2..8, c ~ N(0, (0.05R)^2),
+    the oscillating-droplet shape) with s ~ U(s_choices), on a unit grid with
+    N ~ U(n_choices), taking steps ~ U{1..max_steps} time steps of dt = 0.25 h,
+    advected by a solid-body rotation about its centre (speed 1 at 1.5 R, a
+    seeded axis).  The deformed shapes come from a pool of pool_per_s shapes per
+    subdivision (unit radius), scaled to R = 0.2 or less, so that the front keeps
+    the grid margin 2 + ceil(delta_max/h) plus two cells.  Returns dicts with
+    grid, verts, tris, steps, arrival, dt, centre, omega, s, R."""
+    gen = rng(seed)
+    pool = {}
+    for s in s_choices:
+        for k in range(pool_per_s):
+            v, t = sh_deformed_front(s, 1.0, np.zeros(3), rng(1000 * s + k))
+            pool[(s, k)] = (v, t, float(np.linalg.norm(v, axis=1).max()))
+    margin = 2 + math.ceil(delta_max_h)
+    out = []
+    t = 0.0
+    for i in range(count):
+        t += gen.exponential(1.0 / rate)
+        s = int(gen.choice(s_choices))
+        k = int(gen.integers(pool_per_s))
+        N = int(gen.choice(n_choices))
+        g = unit_grid(N)
+        v, tri, rmax = pool[(s, k)]
+        R = min(0.2, (N / 2 - margin - 2) * g.h / rmax)
+        centre = 0.5 + gen.uniform(0.0, g.h, size=3)
+        a = gen.normal(size=3)
+        a *= 1.0 / (1.5 * R * np.linalg.norm(a))
+        out.append(dict(rid=i, grid=g, verts=np.ascontiguousarray(centre + R * v), tris=tri,
+                        steps=int(gen.integers(1, max_steps + 1)), arrival=t, dt=0.25 * g.h,
+                        centre=centre, omega=a, s=s, R=R))
+    return out
