@@ -398,10 +398,14 @@ def run_ours(a):
     for fc in fcs:
         fc.ws.close()
     if a.batch_steps > 0:
+        t_leg = time.perf_counter()
         line["batched"] = run_batched(a, dev, local, flush)
+        line["batched"]["leg_wall_s"] = round(time.perf_counter() - t_leg, 1)
         torch.cuda.empty_cache()
     if a.serve_requests > 0:
+        t_leg = time.perf_counter()
         line["served"] = run_served(a, local)
+        line["served"]["leg_wall_s"] = round(time.perf_counter() - t_leg, 1)
         torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cb, _ = cpu_baseline(fronts)
@@ -546,19 +550,22 @@ def run_served(a, local):
     from paper_2505_06932_gb300 import inputs as I
     from paper_2505_06932_gb300 import serve as S
 
-    def requests(rate):
-        rq = I.served_requests(11, a.serve_requests, rate)
-        return [S.Request(r["rid"], r["grid"], r["verts"], r["tris"], r["steps"], r["arrival"], r["dt"],
-                          tuple(r["centre"]), tuple(r["omega"])) for r in rq]
-
     rates = [float(x) for x in a.serve_rates.split(",") if x]
+    # one stream; other rates rescale its Poisson arrival times (the same draws)
+    base = I.served_requests(11, a.serve_requests, rates[0], pool_per_s=1)
+
+    def requests(rate):
+        f = rates[0] / rate
+        return [S.Request(r["rid"], r["grid"], r["verts"], r["tris"], r["steps"], r["arrival"] * f, r["dt"],
+                          tuple(r["centre"]), tuple(r["omega"])) for r in base]
+
     budget = int(a.serve_budget_gb * 2 ** 30)
     probe = requests(rates[0])
     cap = S.Capacity(budget_bytes=budget, max_fronts=256,
                      max_grid_cells=min(2 ** 32 - 2, budget // 56),
                      max_nt=sum(r.tris.shape[0] for r in probe),
                      max_cand=sum(S.candidate_estimate(r) for r in probe))
-    out = {"workload": f"{a.serve_requests} requests per rate: icosphere s4-7 with real SH deformation "
+    out = {"workload": f"{a.serve_requests} requests per rate: icosphere s4-8 with real SH deformation "
                        f"(l 2-8, c ~ N(0,(0.05R)^2)), grids 32^3-512^3, 1-50 steps of dt = 0.25h each "
                        f"(bin, alpha, PPIC, CSF, RK4 advection), solid-body rotation about the front centre",
            "budget_bytes": budget, "admission": "FIFO by device footprint and batch capacities",

@@ -317,15 +317,34 @@ __device__ void frag_moments(const double (*p)[3], int n, const double q0[3], co
     for (int d = 0; d < 3; d++) f.an[d] = an[d];
 }
 
+// double -> float with round to nearest even, in integer operations: on this
+// GPU the conversion instruction runs on the float64 pipe at the float64 rate,
+// which the canonical clip already saturates.  Identical to the hardware
+// conversion for zero and for results in the normal float range; anything
+// else (float subnormals, overflow) takes the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const unsigned sign = hi & 0x80000000u;
+    if (((hi << 1) | lo) == 0u) return __uint_as_float(sign);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e < 1023 - 126 || e > 1023 + 127) return (float)x;
+    const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rb = lo & 0x1fffffffu, half = 0x10000000u;
+    unsigned r = sign | ((unsigned)(e - 1023 + 127) << 23) | m23;
+    if (rb > half || (rb == half && (m23 & 1u))) r += 1u;  // a carry moves into the exponent, as it should
+    return __uint_as_float(r);
+}
+
 // The same moments in float32 (the FP32 form): each vertex offset from p0 is
 // formed in float64 and rounded once; all products and sums are float32.
 __device__ void frag_moments32(const double (*p)[3], int n, const float q0[3], const float tn[3], float inv_h,
                                ft_frag32& f) {
     float an[3] = {0.f, 0.f, 0.f}, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0}, As = 0.f;
     float e1[3], e2[3];
-    for (int d = 0; d < 3; d++) e1[d] = (float)(p[1][d] - p[0][d]) * inv_h;
+    for (int d = 0; d < 3; d++) e1[d] = d2f_rn(p[1][d] - p[0][d]) * inv_h;
     for (int m = 1; m + 1 < n; m++) {
-        for (int d = 0; d < 3; d++) e2[d] = (float)(p[m + 1][d] - p[0][d]) * inv_h;
+        for (int d = 0; d < 3; d++) e2[d] = d2f_rn(p[m + 1][d] - p[0][d]) * inv_h;
         const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
         const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
         const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
@@ -561,10 +580,10 @@ __global__ void __launch_bounds__(kThreads) k_clip(F fr, const int* __restrict__
             bool accept;
             if (fp32) {
                 ft_frag32 f;
-                const float tn[3] = {(float)tn01.x, (float)tn01.y, (float)tn2.x};
-                const float ih = (float)inv_h;
+                const float tn[3] = {d2f_rn(tn01.x), d2f_rn(tn01.y), d2f_rn(tn2.x)};
+                const float ih = d2f_rn(inv_h);
                 float q0[3];
-                for (int d = 0; d < 3; d++) q0[d] = (float)(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
+                for (int d = 0; d < 3; d++) q0[d] = d2f_rn(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
                 frag_moments32(poly, n, q0, tn, ih, f);
                 const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
                 accept = (a > 1e-4f) || canon_area_nonzero(poly, n);
@@ -579,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) k_clip(F fr, const int* __restrict__
                 accept = (a > 1e-9) || canon_area_nonzero(poly, n);
                 if (accept) {
                     rec[c] = f;
-                    if (cen32) cen32[c] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
+                    if (cen32) cen32[c] = make_float4(d2f_rn(f.c[0]), d2f_rn(f.c[1]), d2f_rn(f.c[2]), 0.f);
                 }
             }
             if (accept)

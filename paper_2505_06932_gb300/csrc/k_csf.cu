@@ -10,8 +10,8 @@
 //    exactly 1 and 0) write zero force, interfacial cells write sigma kappa grad
 //    alpha, and the remaining cells (the ring around the interface) are appended
 //    to a compact list.
-//  * k_csf_ring -- one warp per listed cell (a lane per neighbour): the
-//    smoothed curvature and the force.  Keeping the float64 smoothing out of the dense pass keeps that pass
+//  * k_csf_ring -- one thread per listed cell: the smoothed curvature and the
+//    force.  Keeping the float64 smoothing out of the dense pass keeps that pass
 //    bound by memory instead of by divergent float64 issue.
 #include "ft_internal.cuh"
 
@@ -95,23 +95,17 @@ __global__ void __launch_bounds__(kThreads) k_csf_dense(F fr, double sigma, cons
     }
 }
 
-// One warp per ring cell: lanes 0..25 take the 26 neighbours (smoothing
-// weights), lanes 26..31 the six alpha values of the central-difference
-// gradient; the sums are reduced over the warp.
+// One thread per ring cell.  The 26 index-map lookups are issued together
+// (independent loads) before the float64 smoothing sums, which then run once
+// per cell instead of once per lane of a warp-wide reduction.
 template <class F>
 __global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int* __restrict__ idx_map,
                                                   const double* __restrict__ kappa, const double* __restrict__ normal,
                                                   const unsigned* __restrict__ ring, const unsigned* __restrict__ nring,
                                                   long long ring_cap) {
-    const int lane = threadIdx.x & 31;
     const long long nr = min((long long)*nring, ring_cap);
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    // neighbour offset of this lane (lanes 0..25: the 26 neighbours, centre skipped)
-    const int code = lane < 13 ? lane : lane + 1;
-    const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
-    const int nsq = di * di + dj * dj + dk * dk;
-    const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
-    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nr; r += nw) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+         r += (long long)gridDim.x * blockDim.x) {
         const long long gkey = ring[r];
         const int b = fr.by_key(gkey);
         const ft_fdesc& D = fr.desc(b);
@@ -124,45 +118,46 @@ __global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int*
         const int k = (int)(key % n2);
         const int j = (int)((key / n2) % n1);
         const int i = (int)(key / s0);
-        double num = 0.0, den = 0.0, ks = 0.0, cnt = 0.0, av = 0.0;
-        if (lane < 26) {
+        int q[26];
+#pragma unroll
+        for (int c = 0; c < 26; c++) {
+            const int code = c < 13 ? c : c + 1;  // the 27 offsets without the centre
+            const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
             const int ii = i + di, jj = j + dj, kk = k + dk;
-            if (ii >= 0 && ii < n0 && jj >= 0 && jj < n1 && kk >= 0 && kk < n2) {
-                const int q = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
-                if (q >= 0) {
-                    const double* nq = normal + 3 * (long long)q;
-                    const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
-                    const double kq = kappa[q];
-                    num = kq * w;
-                    den = w;
-                    ks = kq;
-                    cnt = 1.0;
-                }
-            }
-        } else {
-            // lanes 26..31: alpha at +x, -x, +y, -y, +z, -z (0 outside the grid)
-            const int e = lane - 26, ax = e >> 1, sg = (e & 1) ? -1 : 1;
-            const int c = ax == 0 ? i : (ax == 1 ? j : k);
-            const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
-            const long long st = ax == 0 ? s0 : (ax == 1 ? s1 : 1);
-            if (c + sg >= 0 && c + sg < n) av = alpha[key + sg * st];
+            const bool in = ii >= 0 && ii < n0 && jj >= 0 && jj < n1 && kk >= 0 && kk < n2;
+            q[c] = in ? idx_map[kb + key + (long long)di * s0 + (long long)dj * s1 + dk] : -1;
         }
-        num = ft_warp_sum(num);
-        den = ft_warp_sum(den);
-        ks = ft_warp_sum(ks);
-        cnt = ft_warp_sum(cnt);
+        const double axp = (i + 1 < n0) ? alpha[key + s0] : 0.0;
+        const double axm = (i > 0) ? alpha[key - s0] : 0.0;
+        const double ayp = (j + 1 < n1) ? alpha[key + s1] : 0.0;
+        const double aym = (j > 0) ? alpha[key - s1] : 0.0;
+        const double azp = (k + 1 < n2) ? alpha[key + 1] : 0.0;
+        const double azm = (k > 0) ? alpha[key - 1] : 0.0;
+        double num = 0.0, den = 0.0, ks = 0.0;
+        int cnt = 0;
+#pragma unroll
+        for (int c = 0; c < 26; c++) {
+            if (q[c] < 0) continue;
+            const int code = c < 13 ? c : c + 1;
+            const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
+            const int nsq = di * di + dj * dj + dk * dk;
+            const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
+            const double* nq = normal + 3 * (long long)q[c];
+            const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
+            const double kq = kappa[q[c]];
+            num += kq * w;
+            den += w;
+            ks += kq;
+            cnt++;
+        }
         const double ih2 = 0.5 * D.inv_h;
-        double g3[3];
-        for (int ax = 0; ax < 3; ax++)
-            g3[ax] = (__shfl_sync(0xffffffffu, av, 26 + 2 * ax) - __shfl_sync(0xffffffffu, av, 27 + 2 * ax)) * ih2;
-        if (lane == 0) {
-            const double kp = (den > 0.0) ? num / den : (cnt > 0.0 ? ks / cnt : 0.0);
-            const double f = sigma * kp;
-            double* __restrict__ force = D.force;
-            force[key] = f * g3[0];
-            force[NC + key] = f * g3[1];
-            force[2 * NC + key] = f * g3[2];
-        }
+        const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
+        const double kp = (den > 0.0) ? num / den : (cnt ? ks / cnt : 0.0);
+        const double f = sigma * kp;
+        double* __restrict__ force = D.force;
+        force[key] = f * gx;
+        force[NC + key] = f * gy;
+        force[2 * NC + key] = f * gz;
     }
 }
 
@@ -180,8 +175,8 @@ cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const do
     count_launches(2);
     k_csf_dense<F><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, ring, nring,
                                                                         ws->max_cand, ws->ctr);
-    k_csf_ring<F><<<ws->sm_count * 16, 128, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, normal, ring, nring,
-                                                    ws->max_cand);
+    k_csf_ring<F><<<ws->sm_count * 4, 128, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, normal, ring, nring,
+                                                   ws->max_cand);
     return cudaGetLastError();
 }
 

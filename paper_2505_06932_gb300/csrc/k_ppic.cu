@@ -334,12 +334,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
             const int R = (int)ceil(delta - (T)0.5);
             const int side = 2 * R + 1;
             const int nb = side * side * side;
+            // neighbour offsets decoded with float reciprocals: (l + 1/2)/side^k
+            // stays at least 1/(2 side^2) away from an integer for l < side^3,
+            // far beyond the float rounding, so the truncation is exact
+            const float inv_s = 1.0f / (float)side, inv_ss = inv_s * inv_s;
             int qn = 0;
             for (int cb = 0; cb < nb; cb += 32) {
                 const int l = cb + lane;
                 int f0 = 0, cnt = 0, dcode = 0;
                 if (l < nb) {
-                    const int di = l / (side * side) - R, dj = (l / side) % side - R, dk = l % side - R;
+                    const int a = (int)(((float)l + 0.5f) * inv_ss);
+                    const int rem = l - a * side * side;
+                    const int b = (int)(((float)rem + 0.5f) * inv_s);
+                    const int di = a - R, dj = b - R, dk = rem - b * side - R;
                     const int ii = ci + di, jj = cj + dj, kk = ck + dk;
                     if (ii >= 0 && jj >= 0 && kk >= 0 && ii < n0 && jj < n1 && kk < n2) {
                         const int m2 = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];

@@ -364,7 +364,7 @@ def solid_body_faces_exact(g: Grid, centre, omega):
 # served form: a stream of requests
 # ----------------------------------------------------------------------------
 
-def served_requests(seed: int = 11, count: int = 48, rate: float = 100.0, s_choices=(4, 5, 6, 7),
+def served_requests(seed: int = 11, count: int = 48, rate: float = 100.0, s_choices=(4, 5, 6, 7, 8),
                     n_choices=(32, 64, 128, 256, 512), max_steps: int = 50, pool_per_s: int = 2,
                     delta_max_h: float = 4.0):
     """A request stream: Poisson arrivals of the given rate (requests/s); each
