@@ -74,6 +74,8 @@ def lib():
             L.og_ppic.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64, P, P, P, P, P]
             L.og_csf.restype = C.c_int
             L.og_csf.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P]
+            L.og_face_force.restype = C.c_int
+            L.og_face_force.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P, P, P]
             L.og_interp.restype = None
             L.og_interp.argtypes = [P, P, P, P, P, C.c_int64, P]
             L.og_advect_rk4.restype = None
@@ -211,6 +213,20 @@ def csf(g, alpha_dense, cells, kappa, normal, sigma=1.0):
     gs = _grid(g)
     lib().og_csf(C.byref(gs), _ptr(a), cells.shape[0], _ptr(cells), _ptr(k), _ptr(n), float(sigma), _ptr(out))
     return out
+
+
+def face_force(g, alpha_dense, cells, kappa, normal, sigma=1.0):
+    """Balanced-force face term on the three staggered face arrays (Fx, Fy, Fz)."""
+    a = np.ascontiguousarray(alpha_dense, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    nrm = np.ascontiguousarray(normal, dtype=np.float64)
+    n = [int(x) for x in g.n]
+    out = [np.empty(tuple(n[e] + (1 if e == d else 0) for e in range(3)), np.float64) for d in range(3)]
+    gs = _grid(g)
+    lib().og_face_force(C.byref(gs), _ptr(a), cells.shape[0], _ptr(cells), _ptr(k), _ptr(nrm), float(sigma),
+                        _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+    return tuple(out)
 
 
 def interp(g, faces, pts):

@@ -14,6 +14,8 @@
  *                  (Sec. 3.2), curvature of the paraboloid at the local origin
  *   og_csf      -- S = sigma kappa grad alpha (Eq. csf) + curvature smoothing
  *                  (Sec. 3.3)
+ *   og_face_force -- balanced-force face term sigma kbar_f (alpha_Q - alpha_P)/h
+ *                  (Sec. 3.3, Eq. mwi_disc)
  *   og_interp   -- divergence-preserving velocity interpolation (Sec. 3.1)
  *   og_advect_rk4 -- one fourth-order Runge-Kutta step of the front vertices
  *                  in the interpolated velocity (Sec. 3.1)
@@ -709,12 +711,49 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
 /* CSF force                                                                 */
 /* ------------------------------------------------------------------------ */
 
-int og_csf(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t* cells,
-           const double* kappa, const double* normal, double sigma, double* force) {
-    const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2], NC = n0 * n1 * n2;
+/* The curvature of cell (i,j,k) used by the surface-tension terms (Sec. 3.3):
+ * its own kappa if it is interfacial, else the weighted mean
+ * kbar = sum_Q kappa_Q w_Q / sum_Q w_Q, w_Q = |s_Q . n_Q| / |s_Q|, over the
+ * interfacial cells Q among its 26 neighbours (the plain mean if every w_Q is 0,
+ * 0 if there is none). */
+static double og_cell_kappa(const og_grid* g, const int32_t* map, const double* kappa, const double* normal,
+                            int64_t i, int64_t j, int64_t k) {
+    const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2];
+    const int64_t key = (i * n1 + j) * n2 + k;
+    if (map[key] >= 0) return kappa[map[key]];
+    double num = 0.0, den = 0.0, ksum = 0.0;
+    int cnt = 0;
+    for (int di = -1; di <= 1; di++)
+        for (int dj = -1; dj <= 1; dj++)
+            for (int dk = -1; dk <= 1; dk++) {
+                if (!di && !dj && !dk) continue;
+                const int64_t ii = i + di, jj = j + dj, kk = k + dk;
+                if (ii < 0 || jj < 0 || kk < 0 || ii >= n0 || jj >= n1 || kk >= n2) continue;
+                const int32_t q = map[(ii * n1 + jj) * n2 + kk];
+                if (q < 0) continue;
+                const double* nq = normal + 3 * (int64_t)q;
+                const double sl = sqrt((double)(di * di + dj * dj + dk * dk));
+                const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) / sl;
+                num += kappa[q] * w;
+                den += w;
+                ksum += kappa[q];
+                cnt++;
+            }
+    return den > 0.0 ? num / den : (cnt ? ksum / cnt : 0.0);
+}
+
+static int32_t* og_index_map(const og_grid* g, int64_t ncells, const uint32_t* cells) {
+    const int64_t NC = (int64_t)g->n[0] * g->n[1] * g->n[2];
     int32_t* map = (int32_t*)malloc(sizeof(int32_t) * (size_t)NC);
     for (int64_t c = 0; c < NC; c++) map[c] = -1;
     for (int64_t m = 0; m < ncells; m++) map[cells[m]] = (int32_t)m;
+    return map;
+}
+
+int og_csf(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t* cells,
+           const double* kappa, const double* normal, double sigma, double* force) {
+    const int64_t n0 = g->n[0], n1 = g->n[1], n2 = g->n[2], NC = n0 * n1 * n2;
+    int32_t* map = og_index_map(g, ncells, cells);
     const double h = g->h;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n0; i++)
@@ -733,33 +772,49 @@ int og_csf(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t
                     force[key] = force[NC + key] = force[2 * NC + key] = 0.0;
                     continue;
                 }
-                double kp;
-                if (map[key] >= 0) {
-                    kp = kappa[map[key]];
-                } else {
-                    /* Sec. 3.3: kbar_P = sum_Q kappa_Q w_Q / sum_Q w_Q, w_Q = |s_Q . n_Q| / |s_Q| */
-                    double num = 0.0, den = 0.0, ksum = 0.0;
-                    int cnt = 0;
-                    for (int di = -1; di <= 1; di++)
-                        for (int dj = -1; dj <= 1; dj++)
-                            for (int dk = -1; dk <= 1; dk++) {
-                                if (!di && !dj && !dk) continue;
-                                const int64_t ii = i + di, jj = j + dj, kk = k + dk;
-                                if (ii < 0 || jj < 0 || kk < 0 || ii >= n0 || jj >= n1 || kk >= n2) continue;
-                                const int32_t q = map[(ii * n1 + jj) * n2 + kk];
-                                if (q < 0) continue;
-                                const double* nq = normal + 3 * (int64_t)q;
-                                const double sl = sqrt((double)(di * di + dj * dj + dk * dk));
-                                const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) / sl;
-                                num += kappa[q] * w;
-                                den += w;
-                                ksum += kappa[q];
-                                cnt++;
-                            }
-                    kp = den > 0.0 ? num / den : (cnt ? ksum / cnt : 0.0);
-                }
+                const double kp = og_cell_kappa(g, map, kappa, normal, i, j, k);
                 for (int d = 0; d < 3; d++) force[d * NC + key] = sigma * kp * gr[d];
             }
+    free(map);
+    return 0;
+}
+
+/* Face term of the balanced-force treatment of surface tension (Sec. 3.3,
+ * Eq. mwi_disc): on the face f between cells P and Q = P + e_d,
+ *   S_f = sigma kbar_f (alpha_Q - alpha_P) / h,  kbar_f = (kappa_P + kappa_Q) / 2,
+ * with kappa_P the cell curvature of og_cell_kappa; outside the grid alpha and
+ * kappa are 0.  F[d] has the staggered layout of the face velocities:
+ * (n0+1, n1, n2), (n0, n1+1, n2), (n0, n1, n2+1); face index i along d is the
+ * face between cells i-1 and i. */
+int og_face_force(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t* cells,
+                  const double* kappa, const double* normal, double sigma, double* Fx, double* Fy, double* Fz) {
+    const int64_t n[3] = {g->n[0], g->n[1], g->n[2]};
+    int32_t* map = og_index_map(g, ncells, cells);
+    double* F[3] = {Fx, Fy, Fz};
+    const double h = g->h;
+    for (int d = 0; d < 3; d++) {
+        int64_t e[3] = {n[0], n[1], n[2]};
+        e[d] += 1;
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < e[0]; a++)
+            for (int64_t b = 0; b < e[1]; b++)
+                for (int64_t c = 0; c < e[2]; c++) {
+                    const int64_t f = (a * e[1] + b) * e[2] + c;
+                    int64_t q[3] = {a, b, c}; /* cell Q (upper side) */
+                    int64_t p[3] = {a, b, c};
+                    p[d] -= 1;                 /* cell P (lower side) */
+                    const int pin = p[d] >= 0, qin = q[d] < n[d];
+                    const double ap = pin ? alpha[(p[0] * n[1] + p[1]) * n[2] + p[2]] : 0.0;
+                    const double aq = qin ? alpha[(q[0] * n[1] + q[1]) * n[2] + q[2]] : 0.0;
+                    if (ap == aq) {
+                        F[d][f] = 0.0;
+                        continue;
+                    }
+                    const double kp = pin ? og_cell_kappa(g, map, kappa, normal, p[0], p[1], p[2]) : 0.0;
+                    const double kq = qin ? og_cell_kappa(g, map, kappa, normal, q[0], q[1], q[2]) : 0.0;
+                    F[d][f] = sigma * 0.5 * (kp + kq) * (aq - ap) / h;
+                }
+    }
     free(map);
     return 0;
 }

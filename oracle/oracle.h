@@ -87,6 +87,13 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
 int og_csf(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t* cells,
            const double* kappa, const double* normal, double sigma, double* force);
 
+/* Balanced-force face term (Sec. 3.3, Eq. mwi_disc): F_d on the faces normal to
+ * axis d (staggered layout of U, V, W), sigma kbar_f (alpha_Q - alpha_P)/h with
+ * kbar_f the mean of the two cells' curvatures (own kappa in interfacial cells,
+ * the smoothed kbar elsewhere; 0 outside the grid). */
+int og_face_force(const og_grid* g, const double* alpha, int64_t ncells, const uint32_t* cells,
+                  const double* kappa, const double* normal, double sigma, double* Fx, double* Fy, double* Fz);
+
 /* Divergence-preserving interpolation of staggered face velocities to points
  * (Sec. 3.1).  U (n0+1,n1,n2), V (n0,n1+1,n2), W (n0,n1,n2+1); vel (np,3). */
 void og_interp(const og_grid* g, const double* U, const double* V, const double* W,
