@@ -76,6 +76,12 @@ def lib():
             L.og_csf.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P]
             L.og_face_force.restype = C.c_int
             L.og_face_force.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P, P, P]
+            L.og_roughness.restype = C.c_int
+            L.og_roughness.argtypes = [P, C.c_int64, P, C.c_int64, P, P, P, P, P, P, P]
+            L.og_roughness_smooth.restype = C.c_int
+            L.og_roughness_smooth.argtypes = [P, C.c_int64, P, C.c_int64, C.c_double, C.c_double, C.c_int, P]
+            L.og_edge_priority.restype = C.c_uint64
+            L.og_edge_priority.argtypes = [C.c_uint64]
             L.og_interp.restype = None
             L.og_interp.argtypes = [P, P, P, P, P, C.c_int64, P]
             L.og_advect_rk4.restype = None
@@ -250,6 +256,33 @@ def advect_rk4(g, faces, pts, dt):
     lib().og_advect_rk4(C.byref(gs), _ptr(U), _ptr(V), _ptr(W), _ptr(p), p.shape[0], C.c_double(dt), _ptr(out),
                         _ptr(vel))
     return out, vel
+
+
+def roughness(verts, tris):
+    """Local roughness metrics (Sec. 3.4): dict of gl (nv, 3), rough, r1, r2,
+    G, V (nv) and rt (nt)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    nv, nt = v.shape[0], t.shape[0]
+    out = dict(gl=np.empty((nv, 3)), rough=np.empty(nv), r1=np.empty(nv), r2=np.empty(nv), rt=np.empty(nt),
+               G=np.empty(nv), V=np.empty(nv))
+    lib().og_roughness(_ptr(v), nv, _ptr(t), nt, _ptr(out["gl"]), _ptr(out["rough"]), _ptr(out["r1"]),
+                       _ptr(out["r2"]), _ptr(out["rt"]), _ptr(out["G"]), _ptr(out["V"]))
+    return out
+
+
+def roughness_smooth(verts, tris, gl_thr, r_thr, max_rounds=64):
+    """Local roughness smoothing; returns (new verts, rounds, edges moved)."""
+    v = np.array(verts, dtype=np.float64, order="C", copy=True)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    moved = C.c_int64(0)
+    rounds = lib().og_roughness_smooth(_ptr(v), v.shape[0], _ptr(t), t.shape[0], float(gl_thr), float(r_thr),
+                                       int(max_rounds), C.byref(moved))
+    return v, rounds, moved.value
+
+
+def edge_priority(e):
+    return int(lib().og_edge_priority(int(e)))
 
 
 def green_moments(x, y):

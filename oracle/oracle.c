@@ -943,3 +943,338 @@ int og_get_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* local roughness detection and smoothing (Sec. 3.4)                        */
+/* ------------------------------------------------------------------------ */
+
+/* vertex -> incident triangles, each list in ascending triangle order */
+typedef struct {
+    int64_t* off; /* nv + 1 */
+    int32_t* tri; /* 3 nt   */
+} og_inc;
+
+static og_inc og_incidence(int64_t nv, const int32_t* tris, int64_t nt) {
+    og_inc I;
+    I.off = (int64_t*)calloc((size_t)nv + 1, sizeof(int64_t));
+    I.tri = (int32_t*)malloc(sizeof(int32_t) * (size_t)(3 * nt + 1));
+    for (int64_t t = 0; t < nt; t++)
+        for (int c = 0; c < 3; c++) I.off[tris[3 * t + c] + 1]++;
+    for (int64_t v = 0; v < nv; v++) I.off[v + 1] += I.off[v];
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nv + 1));
+    memcpy(cur, I.off, sizeof(int64_t) * (size_t)(nv + 1));
+    for (int64_t t = 0; t < nt; t++) /* ascending t: lists come out sorted */
+        for (int c = 0; c < 3; c++) I.tri[cur[tris[3 * t + c]]++] = (int32_t)t;
+    free(cur);
+    return I;
+}
+
+static void og_inc_free(og_inc* I) {
+    free(I->off);
+    free(I->tri);
+}
+
+/* position of vertex v in triangle t (0..2), -1 if absent */
+static int og_slot(const int32_t* tris, int64_t t, int64_t v) {
+    for (int c = 0; c < 3; c++)
+        if (tris[3 * t + c] == v) return c;
+    return -1;
+}
+
+/* the triangle (other than t) that holds the directed edge b -> a, found among
+ * the triangles incident to a; -1 if the mesh is open there */
+static int64_t og_twin(const og_inc* I, const int32_t* tris, int64_t a, int64_t b) {
+    for (int64_t q = I->off[a]; q < I->off[a + 1]; q++) {
+        const int64_t t = I->tri[q];
+        const int sb = og_slot(tris, t, b);
+        if (sb >= 0 && tris[3 * t + (sb + 1) % 3] == a) return t;
+    }
+    return -1;
+}
+
+int og_roughness(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double* gl, double* rough,
+                 double* r1, double* r2, double* rt, double* G, double* V) {
+    og_inc I = og_incidence(nv, tris, nt);
+    double* nrm = (double*)malloc(sizeof(double) * 3 * (size_t)(nt + 1));
+    double* area = (double*)malloc(sizeof(double) * (size_t)(nt + 1));
+    for (int64_t t = 0; t < nt; t++) {
+        const double* a = verts + 3 * (int64_t)tris[3 * t];
+        const double* b = verts + 3 * (int64_t)tris[3 * t + 1];
+        const double* c = verts + 3 * (int64_t)tris[3 * t + 2];
+        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const double x[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        const double l = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        area[t] = 0.5 * l;
+        for (int d = 0; d < 3; d++) nrm[3 * t + d] = l > 0.0 ? x[d] / l : 0.0;
+    }
+    for (int64_t i = 0; i < nv; i++) {
+        const double* xi = verts + 3 * i;
+        /* geometric Laplacian (Karni and Gotsman 2000): x_i minus the inverse-
+         * distance weighted mean of the one-ring; every neighbour of a closed
+         * mesh lies in exactly two incident triangles, so summing over the
+         * incident triangles' other vertices weights each neighbour twice */
+        double sw = 0.0, sx[3] = {0.0, 0.0, 0.0};
+        /* edge roughness over the edges i -> next(i) of the incident triangles
+         * (each undirected edge at i exactly once on a closed oriented mesh) */
+        double sum = 0.0, sum2 = 0.0;
+        int ne = 0;
+        for (int64_t q = I.off[i]; q < I.off[i + 1]; q++) {
+            const int64_t t = I.tri[q];
+            const int s = og_slot(tris, t, i);
+            for (int o = 1; o <= 2; o++) {
+                const double* xj = verts + 3 * (int64_t)tris[3 * t + (s + o) % 3];
+                const double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+                const double w = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+                sw += w;
+                for (int d = 0; d < 3; d++) sx[d] += w * xj[d];
+            }
+            const int64_t j = tris[3 * t + (s + 1) % 3];
+            const int64_t u = og_twin(&I, tris, i, j);
+            if (u < 0) continue;
+            const double re = 1.0 - (nrm[3 * t] * nrm[3 * u] + nrm[3 * t + 1] * nrm[3 * u + 1] +
+                                     nrm[3 * t + 2] * nrm[3 * u + 2]);
+            sum += re;
+            sum2 += re * re;
+            ne++;
+        }
+        for (int d = 0; d < 3; d++) gl[3 * i + d] = sw > 0.0 ? xi[d] - sx[d] / sw : 0.0;
+        G[i] = ne ? sum / ne : 0.0;
+        /* variance of the edge roughness at i (population variance) */
+        V[i] = ne ? sum2 / ne - G[i] * G[i] : 0.0;
+        if (V[i] < 0.0) V[i] = 0.0;
+    }
+    for (int64_t t = 0; t < nt; t++) {
+        /* R_t = sum G_i V_i / sum V_i over its vertices (Corsini et al. 2007);
+         * equal weights when every V_i is zero */
+        double num = 0.0, den = 0.0, gm = 0.0;
+        for (int c = 0; c < 3; c++) {
+            const int64_t v = tris[3 * t + c];
+            num += G[v] * V[v];
+            den += V[v];
+            gm += G[v];
+        }
+        rt[t] = den > 0.0 ? num / den : gm / 3.0;
+    }
+    int32_t* mark = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nt + 1));
+    for (int64_t t = 0; t < nt; t++) mark[t] = -1;
+    for (int64_t i = 0; i < nv; i++) {
+        /* one ring: the incident triangles; two rings: the triangles incident to
+         * i or to one of its neighbours (each counted once) */
+        double s1 = 0.0, s2 = 0.0;
+        int64_t c1 = 0, c2 = 0;
+        for (int64_t q = I.off[i]; q < I.off[i + 1]; q++) {
+            const int64_t t = I.tri[q];
+            s1 += area[t] * rt[t];
+            c1++;
+            for (int c = 0; c < 3; c++) {
+                const int64_t v = tris[3 * t + c];
+                for (int64_t q2 = I.off[v]; q2 < I.off[v + 1]; q2++) {
+                    const int64_t t2 = I.tri[q2];
+                    if (mark[t2] == (int32_t)i) continue;
+                    mark[t2] = (int32_t)i;
+                    s2 += area[t2] * rt[t2];
+                    c2++;
+                }
+            }
+        }
+        r1[i] = c1 ? s1 / c1 : 0.0;
+        r2[i] = c2 ? s2 / c2 : 0.0;
+        rough[i] = r1[i] > r2[i] ? r1[i] : r2[i];
+    }
+    free(mark);
+    free(nrm);
+    free(area);
+    og_inc_free(&I);
+    return 0;
+}
+
+/* Edge priority of the parallel smoothing schedule: the 64-bit finalizer of
+ * SplitMix64 (Steele, Lea and Flood 2014) applied to the edge id. */
+uint64_t og_edge_priority(uint64_t e) {
+    uint64_t z = e + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* The volume-conserving move of edge (a, b) (Kuprat et al. 2001, Algorithm 4,
+ * as stated in Sec. 3.4): simultaneous Laplacian smoothing of both vertices,
+ * then a common shift h n along the direction that keeps the enclosed volume,
+ * with |h n| minimal.  Moving a by da and b by db changes six times the
+ * enclosed volume by da.A_a + db.A_b + da.(db x y), A_i = sum over the
+ * triangles (i, j, k) at i of x_j x x_k, y = x_p - x_q for the triangles
+ * (a, b, p) and (b, a, q) holding the edge; with da = d_a + h n, db = d_b + h n
+ * this is linear in h. */
+static void og_kuprat_move(const double* verts, const og_inc* I, const int32_t* tris, int64_t a, int64_t b,
+                           int64_t p, int64_t q, double* xa_new, double* xb_new) {
+    const double* xa = verts + 3 * a;
+    const double* xb = verts + 3 * b;
+    double Sa[3] = {0, 0, 0}, Sb[3] = {0, 0, 0}, Aa[3] = {0, 0, 0}, Ab[3] = {0, 0, 0};
+    int64_t na = 0, nb = 0;
+    for (int side = 0; side < 2; side++) {
+        const int64_t v = side ? b : a;
+        const int64_t other = side ? a : b;
+        double* S = side ? Sb : Sa;
+        double* A = side ? Ab : Aa;
+        int64_t cnt = 0;
+        for (int64_t r = I->off[v]; r < I->off[v + 1]; r++) {
+            const int64_t t = I->tri[r];
+            const int s = og_slot(tris, t, v);
+            const double* xj = verts + 3 * (int64_t)tris[3 * t + (s + 1) % 3];
+            const double* xk = verts + 3 * (int64_t)tris[3 * t + (s + 2) % 3];
+            A[0] += xj[1] * xk[2] - xj[2] * xk[1];
+            A[1] += xj[2] * xk[0] - xj[0] * xk[2];
+            A[2] += xj[0] * xk[1] - xj[1] * xk[0];
+            /* neighbours other than the edge partner: next(v) of every triangle */
+            const int64_t jn = tris[3 * t + (s + 1) % 3];
+            cnt++;
+            if (jn != other)
+                for (int d = 0; d < 3; d++) S[d] += verts[3 * jn + d];
+        }
+        if (side)
+            nb = cnt;
+        else
+            na = cnt;
+    }
+    /* x_a^s = (x_b^s + S_a)/n_a, x_b^s = (x_a^s + S_b)/n_b solved together */
+    double xsa[3], xsb[3], da[3], db[3], y[3], m[3];
+    const double den = (double)na * (double)nb - 1.0;
+    for (int d = 0; d < 3; d++) {
+        xsa[d] = (Sb[d] + (double)nb * Sa[d]) / den;
+        xsb[d] = (xsa[d] + Sb[d]) / (double)nb;
+        da[d] = xsa[d] - xa[d];
+        db[d] = xsb[d] - xb[d];
+        y[d] = verts[3 * p + d] - verts[3 * q + d];
+    }
+    const double ydd[3] = {y[1] * (da[2] - db[2]) - y[2] * (da[1] - db[1]), y[2] * (da[0] - db[0]) - y[0] * (da[2] - db[2]),
+                           y[0] * (da[1] - db[1]) - y[1] * (da[0] - db[0])};
+    for (int d = 0; d < 3; d++) m[d] = Aa[d] + Ab[d] + ydd[d];
+    const double ml = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    const double dbxy[3] = {db[1] * y[2] - db[2] * y[1], db[2] * y[0] - db[0] * y[2], db[0] * y[1] - db[1] * y[0]};
+    const double c0 = da[0] * Aa[0] + da[1] * Aa[1] + da[2] * Aa[2] + db[0] * Ab[0] + db[1] * Ab[1] + db[2] * Ab[2] +
+                      da[0] * dbxy[0] + da[1] * dbxy[1] + da[2] * dbxy[2];
+    double h = 0.0, n[3] = {0.0, 0.0, 0.0};
+    if (ml > 0.0) {
+        for (int d = 0; d < 3; d++) n[d] = m[d] / ml;
+        h = -c0 / ml; /* n . m = |m| */
+    }
+    for (int d = 0; d < 3; d++) {
+        xa_new[d] = xsa[d] + h * n[d];
+        xb_new[d] = xsb[d] + h * n[d];
+    }
+}
+
+/* Local roughness smoothing (Sec. 3.4): a vertex is rough when |GL| > gl_thr
+ * and its roughness R > r_thr; every edge with a rough endpoint is smoothed by
+ * og_kuprat_move.  Edges are taken in rounds: an edge moves in a round when its
+ * priority (og_edge_priority of its id 3t + s, the triangle t and slot s where
+ * it runs a -> b with a < b) is the smallest among the pending edges that touch
+ * the closed one-rings of a and b; the moves of a round read the positions at
+ * its start and touch disjoint vertex stars.  verts is updated in place;
+ * returns the number of rounds (at most max_rounds), *moved the edges moved. */
+int og_roughness_smooth(double* verts, int64_t nv, const int32_t* tris, int64_t nt, double gl_thr, double r_thr,
+                        int max_rounds, int64_t* moved) {
+    double* gl = (double*)malloc(sizeof(double) * 3 * (size_t)(nv + 1));
+    double* rough = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    double* r1 = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    double* r2 = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    double* rtt = (double*)malloc(sizeof(double) * (size_t)(nt + 1));
+    double* G = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    double* V = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    og_roughness(verts, nv, tris, nt, gl, rough, r1, r2, rtt, G, V);
+    og_inc I = og_incidence(nv, tris, nt);
+    uint8_t* pend = (uint8_t*)calloc((size_t)(3 * nt + 1), 1);
+    int64_t npend = 0;
+    for (int64_t t = 0; t < nt; t++)
+        for (int s = 0; s < 3; s++) {
+            const int64_t a = tris[3 * t + s], b = tris[3 * t + (s + 1) % 3];
+            if (a >= b) continue;
+            const int ra = sqrt(gl[3 * a] * gl[3 * a] + gl[3 * a + 1] * gl[3 * a + 1] + gl[3 * a + 2] * gl[3 * a + 2]) > gl_thr &&
+                           rough[a] > r_thr;
+            const int rb = sqrt(gl[3 * b] * gl[3 * b] + gl[3 * b + 1] * gl[3 * b + 1] + gl[3 * b + 2] * gl[3 * b + 2]) > gl_thr &&
+                           rough[b] > r_thr;
+            if (ra || rb) {
+                pend[3 * t + s] = 1;
+                npend++;
+            }
+        }
+    int64_t total = 0;
+    int rounds = 0;
+    double* newpos = (double*)malloc(sizeof(double) * 6 * (size_t)(3 * nt + 1));
+    uint8_t* sel = (uint8_t*)calloc((size_t)(3 * nt + 1), 1);
+    while (npend > 0 && rounds < max_rounds) {
+        /* selection against the pending set at the start of the round */
+        for (int64_t e = 0; e < 3 * nt; e++) {
+            sel[e] = 0;
+            if (!pend[e]) continue;
+            const int64_t t = e / 3;
+            const int s = (int)(e % 3);
+            const int64_t a = tris[3 * t + s], b = tris[3 * t + (s + 1) % 3];
+            const uint64_t pe = og_edge_priority((uint64_t)e);
+            int best = 1;
+            /* pending edges with an endpoint in the closed one-ring of a or b:
+             * every such edge has an endpoint w in a triangle incident to a or b,
+             * and is listed in a triangle incident to w */
+            for (int side = 0; side < 2 && best; side++) {
+                const int64_t v = side ? b : a;
+                for (int64_t r = I.off[v]; r < I.off[v + 1] && best; r++) {
+                    const int64_t t1 = I.tri[r];
+                    for (int c = 0; c < 3 && best; c++) {
+                        const int64_t w = tris[3 * t1 + c];
+                        for (int64_t r2 = I.off[w]; r2 < I.off[w + 1] && best; r2++) {
+                            const int64_t t2 = I.tri[r2];
+                            for (int s2 = 0; s2 < 3; s2++) {
+                                const int64_t f = 3 * t2 + s2;
+                                if (f == e || !pend[f]) continue;
+                                const uint64_t pf = og_edge_priority((uint64_t)f);
+                                if (pf < pe || (pf == pe && f < e)) {
+                                    best = 0;
+                                    break;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            sel[e] = (uint8_t)best;
+        }
+        for (int64_t e = 0; e < 3 * nt; e++) {
+            if (!sel[e]) continue;
+            const int64_t t = e / 3;
+            const int s = (int)(e % 3);
+            const int64_t a = tris[3 * t + s], b = tris[3 * t + (s + 1) % 3];
+            const int64_t p = tris[3 * t + (s + 2) % 3];
+            const int64_t u = og_twin(&I, tris, a, b);
+            const int64_t q = u >= 0 ? tris[3 * u + (og_slot(tris, u, b) + 2) % 3] : p;
+            og_kuprat_move(verts, &I, tris, a, b, p, q, newpos + 6 * e, newpos + 6 * e + 3);
+        }
+        for (int64_t e = 0; e < 3 * nt; e++) {
+            if (!sel[e]) continue;
+            const int64_t t = e / 3;
+            const int s = (int)(e % 3);
+            const int64_t a = tris[3 * t + s], b = tris[3 * t + (s + 1) % 3];
+            for (int d = 0; d < 3; d++) {
+                verts[3 * a + d] = newpos[6 * e + d];
+                verts[3 * b + d] = newpos[6 * e + 3 + d];
+            }
+            pend[e] = 0;
+            npend--;
+            total++;
+        }
+        rounds++;
+    }
+    free(sel);
+    free(newpos);
+    free(pend);
+    og_inc_free(&I);
+    free(gl);
+    free(rough);
+    free(r1);
+    free(r2);
+    free(rtt);
+    free(G);
+    free(V);
+    if (moved) *moved = total;
+    return rounds;
+}

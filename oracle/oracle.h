@@ -105,6 +105,18 @@ void og_interp(const og_grid* g, const double* U, const double* V, const double*
 void og_advect_rk4(const og_grid* g, const double* U, const double* V, const double* W,
                    const double* pts, int64_t np, double dt, double* out, double* vel);
 
+/* Local roughness (Sec. 3.4): per vertex the geometric Laplacian gl (nv, 3),
+ * R^1, R^2, R = max(R^1, R^2) and the mean G and variance V of the edge
+ * roughness 1 - n1.n2 of its edges; per triangle R_t (nt). */
+int og_roughness(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double* gl, double* rough,
+                 double* r1, double* r2, double* rt, double* G, double* V);
+
+/* Local roughness smoothing (Sec. 3.4; Kuprat et al. 2001, Algorithm 4) in
+ * rounds of independent edges; verts updated in place; returns the rounds. */
+int og_roughness_smooth(double* verts, int64_t nv, const int32_t* tris, int64_t nt, double gl_thr, double r_thr,
+                        int max_rounds, int64_t* moved);
+uint64_t og_edge_priority(uint64_t e);
+
 /* Helpers exposed for pin tests. */
 void og_green_moments(const double* x, const double* y, int n, double* m6);
 double og_signed_volume(const double* verts, const int32_t* tris, int64_t nt);
