@@ -284,6 +284,41 @@ def run_ours(a):
         return dict(prm=prm, fcs=fcs, counts=counts, total_ms=total_ms, phase_ms=phase_ms,
                     ppic_ms=ppic_ms_eager, launches=launches, clocks=clk, graph=graph)
 
+    def measure_batch_of_fronts(precision, steps):
+        """The same fronts as one batch (one launch sequence for both), one CUDA
+        graph per step, launch shapes from ft_autotune."""
+        prm = F.make_params(precision=precision)
+        dl = [dict(grid=w["grid"], verts=v, tris=t, U=fa[0], V=fa[1], W=fa[2]) for w, (v, t, fa) in zip(fronts, dfr)]
+        bc = F.BatchCoupling(dl, params=prm, device=local)
+        tune = F.ft_autotune(bc.ws, prm, reps=3)
+        for _ in range(3):
+            bc.step()
+        torch.cuda.synchronize()
+        if bc.ws.status() or any(bc.ws.front_status()):
+            raise RuntimeError("batch of the bench fronts: device status")
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bc.step()
+        g.replay()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        M = bc.ws.counts()["M"]
+        del g
+        bc.ws.close()
+        return dict(value=round(M * steps / (tot * 1e-3), 1), ms_per_step=round(tot / steps, 4), steps=steps,
+                    tuning={k: tune[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm", "csf_blocks_per_sm",
+                                                 "fill_blocks_per_sm", "ppic_min_blocks", "ppic_dynamic",
+                                                 "sort_blocks")},
+                    launch="the two fronts as one batch (front_*_batch), one CUDA graph per step")
+
     r = measure(prec, a.steps, a.warmup, clocks=True)
     counts = r["counts"]
     cells_per_step = sum(c["M"] for c in counts)
@@ -301,8 +336,13 @@ def run_ours(a):
         probe = F.probe_fma_rate(0 if prec == F.FT_FP64 else 1, local) / 1e12
     except Exception:
         probe = None
+    # DRAM bytes of one call (k_ppic_acc<float> + k_ppic_solve) from one ncu capture on the ellipsoid front
+    traffic = (13.444864e6 + 3.780096e6) if prec == F.FT_FP32C else None
     roof = {"kernel": "k_ppic_acc + k_ppic_solve", "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of each kernel on the "
+                              "ellipsoid front (profiles/k_ppic_acc_fp32c_ellipsoid_128.md, "
+                              "profiles/k_ppic_solve_fp32c_ellipsoid_128.md)" if traffic else None,
             "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if prec == F.FT_FP64
             else "152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz (recipe unit counts and clock)",
             "probe_measured_peak": round(probe, 4) if probe else None,
@@ -322,6 +362,8 @@ def run_ours(a):
                "phases_ms": {n: round(v, 4) for n, v in ra["phase_ms"].items()}}
         for fc in ra["fcs"]:
             fc.ws.close()
+
+    one_batch = measure_batch_of_fronts(prec, a.steps) if a.alt_steps > 0 else None
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     prm, fcs = r["prm"], r["fcs"]
@@ -390,6 +432,7 @@ def run_ours(a):
         "phases_note": "eager per-call CUDA-event times per step (sum over fronts), not the graph replay",
         "roofline": roof,
         "alt_precision": alt,
+        "same_workload_as_one_batch": one_batch,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps},
         "gpu_launches": int(r["launches"]),
@@ -465,11 +508,12 @@ def run_batched(a, dev, local, flush):
             tuning = F.ft_autotune(bc.ws, prm, reps=2)
             out["tuning"] = {k: tuning[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm",
                                                     "csf_blocks_per_sm", "fill_blocks_per_sm", "ppic_min_blocks",
-                                                    "ppic_dynamic")}
+                                                    "ppic_dynamic", "sort_blocks")}
         else:
             F.ft_set_tuning(bc.ws, clip=tuning["clip_blocks_per_sm"], ppic=tuning["ppic_blocks_per_sm"],
                             csf=tuning["csf_blocks_per_sm"], fill=tuning["fill_blocks_per_sm"],
-                            ppic_min_blocks=tuning["ppic_min_blocks"], ppic_dynamic=tuning["ppic_dynamic"])
+                            ppic_min_blocks=tuning["ppic_min_blocks"], ppic_dynamic=tuning["ppic_dynamic"],
+                            sort_blocks=tuning["sort_blocks"])
         for _ in range(3):
             bc.step()
         torch.cuda.synchronize()

@@ -172,6 +172,18 @@ int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint
 int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                     const double* normal, double* force, void* stream);
 
+/* Balanced-force face term of the surface tension (Sec. 3.3, Eq. mwi_disc: the
+ * term that enters the face fluxes of the pressure-velocity coupling): on the
+ * face between cells P and Q = P + e_d, sigma kbar_f (alpha_Q - alpha_P) / h with
+ * kbar_f = (kappa_P + kappa_Q) / 2, each cell's curvature being its own kappa if
+ * it is interfacial and otherwise the smoothed kbar of front_csf_force (0 if it
+ * has no interfacial neighbour); alpha and kappa are 0 outside the grid.  Output
+ * fx (n0+1,n1,n2), fy (n0,n1+1,n2), fz (n0,n1,n2+1) float64, face index i along d
+ * being the face between cells i-1 and i.  kappa and normal as for
+ * front_csf_force. */
+int front_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                     const double* normal, double* fx, double* fy, double* fz, void* stream);
+
 /* (a5) Divergence-preserving velocity interpolation (Sec. 3.1) of the staggered
  * face velocities U (n0+1,n1,n2), V (n0,n1+1,n2), W (n0,n1,n2+1) to the nv
  * points verts (nv x 3) into vel (nv x 3).  The cell is floor((x - origin)/h)
@@ -258,6 +270,7 @@ typedef struct {
     double* vel;
     double* verts_next; /* front_advect_rk4_batch output positions (may equal verts) */
     double dt;          /* front_advect_rk4_batch time step of this front            */
+    double* face_force[3]; /* front_face_force_batch output, staggered like U, V, W  */
 } ft_batch_front;
 
 /* Capacities of a batch workspace; 0 selects the default of ft_capacity. */
@@ -295,6 +308,10 @@ int front_volume_fraction_batch(ft_workspace* ws, void* stream);
 int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
                           void* stream);
 
+/* front_face_force of every front, from its alpha into its face_force arrays. */
+int front_face_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                           void* stream);
+
 /* (a5) front_interp_velocity of every front (its U, V, W, verts -> vel). */
 int front_interp_velocity_batch(ft_workspace* ws, void* stream);
 
@@ -326,6 +343,9 @@ typedef struct {
                                    6 resident blocks per SM (fewer registers each)   */
     int32_t ppic_dynamic;       /* PPIC cells from a global work counter (1) or
                                    interleaved over the warps (0, default)           */
+    int32_t sort_blocks;        /* segments of the radix sort and the scans (1 to the
+                                   SM count; 0: the SM count, default)               */
+    int32_t pad;
     /* outputs of ft_autotune: what the tuned workload needed, for sizing a
      * workspace (ft_capacity / ft_batch_capacity) to it */
     int64_t cand_need;
@@ -346,6 +366,52 @@ int ft_get_tuning(ft_workspace* ws, ft_tuning* t);
  * not inside a capture. */
 int ft_autotune(ft_workspace* ws, const ft_front* f, const ft_params* p, int32_t reps, ft_tuning* best,
                 void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Local roughness detection and smoothing of the front mesh (Sec. 3.4).  The
+ * front is a closed, consistently oriented triangle mesh (as everywhere here).
+ * A roughness workspace holds the mesh adjacency built on the device.
+ * --------------------------------------------------------------------------- */
+typedef struct ft_rough ft_rough;
+
+int ft_rough_create(ft_rough** r, int64_t max_nv, int64_t max_nt, int device, size_t* bytes);
+int ft_rough_destroy(ft_rough* r);
+
+/* Synchronize `stream`, return the FT_ST_* bits of the last call (capacity:
+ * a two-ring neighbourhood of more than 512 triangles) and clear them. */
+int ft_rough_status(ft_rough* r, void* stream, uint32_t* bits);
+
+/* Roughness metrics of the front verts (nv x 3) / tris (nt x 3), device arrays:
+ * gl (nv x 3) the geometric Laplacian x_i - sum_j w_ij x_j / sum_j w_ij over the
+ * one-ring, w_ij = 1/|x_i - x_j| (Karni and Gotsman 2000); for every edge the
+ * roughness R_e = 1 - n_1 . n_2 of its two triangles; G, V (nv; may be NULL) the
+ * mean and variance of R_e over the edges of each vertex; rt (nt; may be NULL)
+ * the triangle roughness sum G_i V_i / sum V_i over its vertices (the mean G_i
+ * when every V_i is 0) (Corsini et al. 2007); r1, r2 (nv; may be NULL) the
+ * vertex roughness (1/|N|) sum A_t R_t over the triangles of its one- and
+ * two-ring neighbourhood; rough (nv) = max(r1, r2).  Synchronizes `stream` once
+ * (index check); FT_ERR_ARG for a vertex index out of range. */
+int front_roughness(ft_rough* r, const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double* gl,
+                    double* rough, double* r1, double* r2, double* rt, double* G, double* V, void* stream);
+
+/* Local roughness smoothing (Sec. 3.4): a vertex is rough when |gl| > gl_thr and
+ * rough > r_thr (the paper sets both at 1.2 to 1.5 times their maximum on the
+ * initial front); every edge with a rough endpoint gets the volume-conserving
+ * move of Kuprat et al. (2001, Algorithm 4): simultaneous Laplacian smoothing of
+ * both endpoints, then a common shift h n with 6 dV = d_a.A_a + d_b.A_b +
+ * d_a.(d_b x y) = 0 (A_i = sum of x_j x x_k over the triangles (i, j, k) at i,
+ * y = x_p - x_q for the triangles (a, b, p) and (b, a, q) of the edge), n along
+ * the gradient of that volume change so that |h n| is minimal.  Edges move in
+ * rounds; in a round, an edge moves when its priority (the SplitMix64 finalizer
+ * of its id 3 t + s, the triangle t and slot s where it runs a -> b with a < b)
+ * is the smallest among the pending edges touching the closed one-rings of its
+ * endpoints, so the moves of a round touch disjoint stars and each keeps the
+ * enclosed volume.  verts is updated in place; *rounds, *moved and *status
+ * (host; may be NULL) receive the rounds run (at most max_rounds), the edges
+ * moved and the FT_ST_* bits.  Synchronizes `stream` once per round. */
+int front_roughness_smooth(ft_rough* r, double* verts, int64_t nv, const int32_t* tris, int64_t nt, double gl_thr,
+                           double r_thr, int32_t max_rounds, int32_t* rounds, int64_t* moved, uint32_t* status,
+                           void* stream);
 
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all workspaces). */

@@ -42,7 +42,8 @@ class FtCapacity(C.Structure):
 class FtBatchFront(C.Structure):
     _fields_ = [("grid", FtGrid), ("verts", C.c_void_p), ("nv", C.c_int64), ("tris", C.c_void_p), ("nt", C.c_int64),
                 ("alpha", C.c_void_p), ("force", C.c_void_p), ("U", C.c_void_p), ("V", C.c_void_p),
-                ("W", C.c_void_p), ("vel", C.c_void_p), ("verts_next", C.c_void_p), ("dt", C.c_double)]
+                ("W", C.c_void_p), ("vel", C.c_void_p), ("verts_next", C.c_void_p), ("dt", C.c_double),
+                ("face_force", C.c_void_p * 3)]
 
 
 class FtBatchCapacity(C.Structure):
@@ -53,7 +54,8 @@ class FtBatchCapacity(C.Structure):
 class FtTuning(C.Structure):
     _fields_ = [("clip_blocks_per_sm", C.c_int32), ("ppic_blocks_per_sm", C.c_int32),
                 ("csf_blocks_per_sm", C.c_int32), ("fill_blocks_per_sm", C.c_int32),
-                ("ppic_min_blocks", C.c_int32), ("ppic_dynamic", C.c_int32), ("cand_need", C.c_int64), ("cells_need", C.c_int64), ("fit_pairs", C.c_int64),
+                ("ppic_min_blocks", C.c_int32), ("ppic_dynamic", C.c_int32), ("sort_blocks", C.c_int32),
+                ("pad", C.c_int32), ("cand_need", C.c_int64), ("cells_need", C.c_int64), ("fit_pairs", C.c_int64),
                 ("step_ms", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -100,6 +102,15 @@ def lib():
                 "ft_autotune": (I32, [P, P, P, I32, P, P]),
                 "front_advect_rk4": (I32, [P, P, P, P, P, I64, C.c_double, P, P, P]),
                 "front_advect_rk4_batch": (I32, [P, P]),
+                "front_face_force": (I32, [P, P, P, P, P, P, P, P, P]),
+                "front_face_force_batch": (I32, [P, P, P, P, P]),
+                "ft_rough_create": (I32, [C.POINTER(P), I64, I64, I32, C.POINTER(C.c_size_t)]),
+                "ft_rough_destroy": (I32, [P]),
+                "ft_rough_status": (I32, [P, P, C.POINTER(C.c_uint32)]),
+                "front_roughness": (I32, [P, P, I64, P, I64, P, P, P, P, P, P, P, P]),
+                "front_roughness_smooth": (I32, [P, P, I64, P, I64, C.c_double, C.c_double, I32,
+                                                 C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                                 C.POINTER(C.c_uint32), P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -227,6 +238,13 @@ class BatchWorkspace(Workspace):
                     raise FrontError(f"front {b}: {name} has the wrong shape")
                 setattr(e, name, _ptr(t, torch.float64, name) if t is not None else None)
             e.dt = float(f.get("dt", 0.0))
+            ff = f.get("face_force")
+            if ff is not None:
+                for d in range(3):
+                    shp = tuple(int(n[e2]) + (1 if e2 == d else 0) for e2 in range(3))
+                    if tuple(ff[d].shape) != shp:
+                        raise FrontError(f"front {b}: face_force[{d}] must have shape {shp}")
+                    e.face_force[d] = _ptr(ff[d], torch.float64, "face_force")
             keep.append(f)
         _check(lib().ft_batch_set(self.handle, len(fronts), arr, _stream(stream)), "ft_batch_set")
         self._keep = keep
@@ -281,6 +299,25 @@ def front_csf_force(ws: Workspace, params: FtParams, alpha, kappa, normal, force
     _check(lib().front_csf_force(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),
                                  _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
                                  _ptr(force, torch.float64, "force"), _stream(stream)), "front_csf_force")
+
+
+def front_face_force(ws: Workspace, params: FtParams, alpha, kappa, normal, fx, fy, fz, stream=None):
+    """Balanced-force face term into the staggered arrays fx, fy, fz."""
+    n = ws.grid.n
+    for d, f in enumerate((fx, fy, fz)):
+        shp = tuple(int(n[e]) + (1 if e == d else 0) for e in range(3))
+        if tuple(f.shape) != shp:
+            raise FrontError(f"face array {d} must have shape {shp}")
+    _check(lib().front_face_force(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),
+                                  _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
+                                  _ptr(fx, torch.float64, "fx"), _ptr(fy, torch.float64, "fy"),
+                                  _ptr(fz, torch.float64, "fz"), _stream(stream)), "front_face_force")
+
+
+def front_face_force_batch(ws: "BatchWorkspace", params: FtParams, kappa, normal, stream=None):
+    _check(lib().front_face_force_batch(ws.handle, C.byref(params), _ptr(kappa, torch.float64, "kappa"),
+                                        _ptr(normal, torch.float64, "normal"), _stream(stream)),
+           "front_face_force_batch")
 
 
 def front_interp_velocity(grid, U, V, W, verts, vel, stream=None):
@@ -353,8 +390,9 @@ def ft_batch_cell_ranges(ws: BatchWorkspace, off: torch.Tensor, stream=None):
            "ft_batch_cell_ranges")
 
 
-def ft_set_tuning(ws: Workspace, clip=4, ppic=4, csf=16, fill=8, ppic_min_blocks=4, ppic_dynamic=0):
-    t = FtTuning(int(clip), int(ppic), int(csf), int(fill), int(ppic_min_blocks), int(ppic_dynamic), 0, 0, 0, 0.0)
+def ft_set_tuning(ws: Workspace, clip=4, ppic=4, csf=16, fill=8, ppic_min_blocks=4, ppic_dynamic=0, sort_blocks=0):
+    t = FtTuning(int(clip), int(ppic), int(csf), int(fill), int(ppic_min_blocks), int(ppic_dynamic),
+                 int(sort_blocks), 0, 0, 0, 0, 0.0)
     _check(lib().ft_set_tuning(ws.handle, C.byref(t)), "ft_set_tuning")
 
 
@@ -376,6 +414,60 @@ def ft_autotune(ws: Workspace, params: FtParams, reps: int = 5, verts=None, tris
         fp = None
     _check(lib().ft_autotune(ws.handle, fp, C.byref(params), int(reps), C.byref(t), _stream(stream)), "ft_autotune")
     return t.as_dict()
+
+
+class Roughness:
+    """Roughness workspace (ft_rough_create): metrics and smoothing of a front."""
+
+    def __init__(self, max_nv: int, max_nt: int, device: int = 0):
+        h = C.c_void_p()
+        nbytes = C.c_size_t()
+        _check(lib().ft_rough_create(C.byref(h), int(max_nv), int(max_nt), int(device), C.byref(nbytes)),
+               "ft_rough_create")
+        self.handle = h
+        self.bytes = int(nbytes.value)
+
+    def close(self):
+        if self.handle:
+            lib().ft_rough_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None) -> int:
+        bits = C.c_uint32()
+        _check(lib().ft_rough_status(self.handle, _stream(stream), C.byref(bits)), "ft_rough_status")
+        return int(bits.value)
+
+    def metrics(self, verts, tris, stream=None) -> dict:
+        nv, nt = verts.shape[0], tris.shape[0]
+        dev = verts.device
+        out = dict(gl=torch.empty((nv, 3), dtype=torch.float64, device=dev),
+                   rough=torch.empty(nv, dtype=torch.float64, device=dev),
+                   r1=torch.empty(nv, dtype=torch.float64, device=dev),
+                   r2=torch.empty(nv, dtype=torch.float64, device=dev),
+                   rt=torch.empty(nt, dtype=torch.float64, device=dev),
+                   G=torch.empty(nv, dtype=torch.float64, device=dev),
+                   V=torch.empty(nv, dtype=torch.float64, device=dev))
+        _check(lib().front_roughness(self.handle, _ptr(verts, torch.float64, "verts"), nv,
+                                     _ptr(tris, torch.int32, "tris"), nt, *(C.c_void_p(out[k].data_ptr()) for k in
+                                                                             ("gl", "rough", "r1", "r2", "rt", "G",
+                                                                              "V")), _stream(stream)),
+               "front_roughness")
+        return out
+
+    def smooth(self, verts, tris, gl_thr, r_thr, max_rounds=64, stream=None) -> dict:
+        """In place on verts; returns rounds, moved, status."""
+        rounds, moved, st = C.c_int32(), C.c_int64(), C.c_uint32()
+        _check(lib().front_roughness_smooth(self.handle, _ptr(verts, torch.float64, "verts"), verts.shape[0],
+                                            _ptr(tris, torch.int32, "tris"), tris.shape[0], float(gl_thr),
+                                            float(r_thr), int(max_rounds), C.byref(rounds), C.byref(moved),
+                                            C.byref(st), _stream(stream)), "front_roughness_smooth")
+        return dict(rounds=int(rounds.value), moved=int(moved.value), status=int(st.value))
 
 
 def launch_count() -> int:

@@ -67,7 +67,7 @@ int allocate(ft_workspace* ws, long long map_cells) {
     cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, ws->device);
     // segments of the scan / sort kernels; the sort stages 256 x grid_blocks counts in shared memory
     ws->grid_blocks = ws->sm_count > 192 ? 192 : ws->sm_count;
-    ws->tune = ft_tune{4, 4, 16, 8, 4, 0};
+    ws->tune = ft_tune{4, 4, 16, 8, 4, 0, ws->grid_blocks};
     size_t tot = 0;
     cudaError_t e = cudaSuccess;
     const size_t C = (size_t)ws->max_cand, Mx = (size_t)ws->max_cells, T = (size_t)ws->max_nt;
@@ -260,6 +260,7 @@ int ft_batch_set(ft_workspace* ws, int32_t nf, const ft_batch_front* fr, void* s
         d.vel = f.vel;
         d.verts_next = f.verts_next;
         d.dt = f.dt;
+        for (int k = 0; k < 3; k++) d.fface[k] = f.face_force[k];
         d.nv = f.nv;
         d.nt = f.nt;
         d.planes = ws->planes + pofs;
@@ -417,6 +418,26 @@ int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* ka
     return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream)));
 }
 
+int front_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                     const double* normal, double* fx, double* fy, double* fz, void* stream) {
+    if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || !fx || !fy || !fz) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_face_force(ws, p, alpha, kappa, normal, fx, fy, fz, as_stream(stream)));
+}
+
+int front_face_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                           void* stream) {
+    if (!ws || !ws->batch || !params_ok(p) || !kappa || !normal) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++) {
+        const ft_fdesc& d = ws->h_fdesc[b];
+        if (!d.alpha || !d.fface[0] || !d.fface[1] || !d.fface[2]) return FT_ERR_ARG;
+    }
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_face_force_batch(ws, p, kappa, normal, as_stream(stream)));
+}
+
 int front_interp_velocity_batch(ft_workspace* ws, void* stream) {
     if (!ws || !ws->batch) return FT_ERR_ARG;
     if (ws->nf < 1) return FT_ERR_STATE;
@@ -470,7 +491,9 @@ int ft_set_tuning(ft_workspace* ws, const ft_tuning* t) {
         if (x < 1 || x > 32) return FT_ERR_ARG;
     if (t->ppic_min_blocks != 4 && t->ppic_min_blocks != 6) return FT_ERR_ARG;
     if (t->ppic_dynamic != 0 && t->ppic_dynamic != 1) return FT_ERR_ARG;
-    ws->tune = ft_tune{v[0], v[1], v[2], v[3], t->ppic_min_blocks, t->ppic_dynamic};
+    const int seg = t->sort_blocks == 0 ? ws->grid_blocks : t->sort_blocks;
+    if (seg < 1 || seg > ws->grid_blocks) return FT_ERR_ARG;
+    ws->tune = ft_tune{v[0], v[1], v[2], v[3], t->ppic_min_blocks, t->ppic_dynamic, seg};
     return FT_OK;
 }
 
@@ -483,6 +506,7 @@ int ft_get_tuning(ft_workspace* ws, ft_tuning* t) {
     t->fill_blocks_per_sm = ws->tune.fill_bps;
     t->ppic_min_blocks = ws->tune.ppic_min_blocks;
     t->ppic_dynamic = ws->tune.ppic_dynamic;
+    t->sort_blocks = ws->tune.seg_blocks;
     return FT_OK;
 }
 

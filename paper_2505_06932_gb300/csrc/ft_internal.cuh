@@ -60,6 +60,7 @@ struct __align__(16) ft_fdesc {
     const double* W;
     double* vel;
     double* verts_next;  // RK4 output positions (may equal verts)
+    double* fface[3];    // balanced-force face term, staggered like U, V, W
     double dt;           // RK4 time step
     long long nv;
     long long nt;
@@ -77,6 +78,7 @@ struct ft_tune {
     int fill_bps;   // k_alpha_fill blocks per SM
     int ppic_min_blocks;  // FP32 k_ppic_acc compiled for 4 (more registers) or 6 resident blocks per SM
     int ppic_dynamic;     // k_ppic_acc cells from a global work counter (1) or interleaved (0)
+    int seg_blocks;       // segments (blocks) of the radix sort and the scans, <= grid_blocks
 };
 
 struct ft_workspace {
@@ -168,6 +170,10 @@ cudaError_t launch_advect(const ft_grid* g, const double* U, const double* V, co
                           cudaStream_t s);
 cudaError_t launch_advect_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_cell_ranges(ft_workspace* ws, long long* off, cudaStream_t s);
+cudaError_t launch_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                              const double* normal, double* fx, double* fy, double* fz, cudaStream_t s);
+cudaError_t launch_face_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                                    cudaStream_t s);
 // plane tables: of the workspace's grid (one front), or of every front of the table
 cudaError_t launch_planes_one(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_planes_batch(ft_workspace* ws, int max_planes, cudaStream_t s);

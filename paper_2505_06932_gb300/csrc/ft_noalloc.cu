@@ -89,7 +89,7 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
     ws.device = dev;
     cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev);
     ws.grid_blocks = kBlocks;
-    ws.tune = ft_tune{4, 4, 16, 8, 4, 0};
+    ws.tune = ft_tune{4, 4, 16, 8, 4, 0, kBlocks};
     int bits = 1;
     while (bits < 32 && ((ncells - 1) >> bits) > 0) bits++;
     ws.key_bits = bits < 8 ? 8 : bits;

@@ -1,5 +1,6 @@
 // ft_tune.cu -- ft_autotune: picks the launch shapes of the grid-stride kernels
-// (canonical clip, column parity fill, PPIC accumulation, CSF dense pass) and
+// (canonical clip, column parity fill, PPIC accumulation, CSF dense pass), the
+// segment count of the radix sort and scans, and
 // the register/occupancy variant and cell schedule of the PPIC accumulation for the workload
 // on a workspace, by timing each step with CUDA events, one parameter at a
 // time, and installs the fastest.  The results of the steps do not depend on
@@ -106,13 +107,17 @@ extern "C" int ft_autotune(ft_workspace* ws, const ft_front* f, const ft_params*
         int step;
         std::vector<int> cand;
     };
-    Knob knobs[6] = {{&ws->tune.clip_bps, 0, {2, 4, 6, 8, 12, 16}},
+    std::vector<int> segs;
+    for (int g : {16, 32, 64, 96, 128, ws->grid_blocks})
+        if (g <= ws->grid_blocks && (segs.empty() || segs.back() != g)) segs.push_back(g);
+    Knob knobs[7] = {{&ws->tune.seg_blocks, 0, segs},
+                     {&ws->tune.clip_bps, 0, {2, 4, 6, 8, 12, 16}},
                      {&ws->tune.fill_bps, 1, {2, 4, 8, 16}},
                      {&ws->tune.ppic_dynamic, 2, {0, 1}},
                      {&ws->tune.ppic_min_blocks, 2, {4, 6}},
                      {&ws->tune.ppic_bps, 2, {2, 3, 4, 6, 8}},
                      {&ws->tune.csf_bps, 3, {4, 8, 16, 32}}};
-    for (int k = 0; k < 6 && r == FT_OK; k++) {
+    for (int k = 0; k < 7 && r == FT_OK; k++) {
         Knob& K = knobs[k];
         int bv = *K.v;
         double bt = 1e30;

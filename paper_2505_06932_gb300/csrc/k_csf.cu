@@ -161,6 +161,104 @@ __global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int*
     }
 }
 
+// Cell curvature of the surface-tension terms (Sec. 3.3): the cell's own kappa
+// if it is interfacial, else the weighted mean of its interfacial neighbours'
+// kappa (w_Q = |s_Q . n_Q| / |s_Q|; plain mean if every w_Q is 0; 0 if none).
+template <class F>
+__device__ double cell_kappa(const int* __restrict__ idx_map, const double* __restrict__ kappa,
+                             const double* __restrict__ normal, long long kb, int n0, int n1, int n2, int i, int j,
+                             int k) {
+    const long long key = ((long long)i * n1 + j) * n2 + k;
+    const int m = idx_map[kb + key];
+    if (m >= 0) return kappa[m];
+    double num = 0.0, den = 0.0, ks = 0.0;
+    int cnt = 0;
+    for (int c = 0; c < 27; c++) {
+        if (c == 13) continue;
+        const int di = c / 9 - 1, dj = (c / 3) % 3 - 1, dk = c % 3 - 1;
+        const int ii = i + di, jj = j + dj, kk = k + dk;
+        if (ii < 0 || jj < 0 || kk < 0 || ii >= n0 || jj >= n1 || kk >= n2) continue;
+        const int q = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
+        if (q < 0) continue;
+        const int nsq = di * di + dj * dj + dk * dk;
+        const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
+        const double* nq = normal + 3 * (long long)q;
+        const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
+        num += kappa[q] * w;
+        den += w;
+        ks += kappa[q];
+        cnt++;
+    }
+    return (den > 0.0) ? num / den : (cnt ? ks / cnt : 0.0);
+}
+
+// Balanced-force face term (Sec. 3.3, Eq. mwi_disc): S_f = sigma kbar_f
+// (alpha_Q - alpha_P)/h on the face between P and Q = P + e_d, kbar_f the mean
+// of the two cells' curvatures, alpha and kappa 0 outside the grid.  Block per
+// (i, j) column, threads along k; cell (i, j, k) writes its three lower faces,
+// the last cell of each direction also the upper boundary face.
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_face_force(F fr, double sigma, const int* __restrict__ idx_map,
+                                                         const double* __restrict__ kappa,
+                                                         const double* __restrict__ normal) {
+    for (long long gcol = blockIdx.x; gcol < fr.ncols; gcol += gridDim.x) {
+        const int b = fr.by_col(gcol);
+        const ft_fdesc& D = fr.desc(b);
+        const int n0 = D.g.n[0], n1 = D.g.n[1], n2 = D.g.n[2];
+        const long long kb = fr.key_base(b);
+        const long long col = gcol - fr.col_base(b);
+        const int i = (int)(col / n1), j = (int)(col - (long long)i * n1);
+        const double* __restrict__ alpha = D.alpha;
+        const double sh = 0.5 * sigma * D.inv_h;
+        for (int k0 = 0; k0 <= n2; k0 += kThreads) {
+            const int k = k0 + (int)threadIdx.x;
+            if (k > n2) continue;
+            const bool in = k < n2;
+            const long long key = ((long long)i * n1 + j) * n2 + k;
+            const double aq = in ? alpha[key] : 0.0;
+            auto kap = [&](int a, int bb, int c) { return cell_kappa<F>(idx_map, kappa, normal, kb, n0, n1, n2, a, bb, c); };
+            // z-face between (i, j, k-1) and (i, j, k): index (i, j, k) of (n0, n1, n2+1)
+            {
+                const double ap = (k > 0) ? alpha[key - 1] : 0.0;
+                double f = 0.0;
+                if (__double_as_longlong(ap) != __double_as_longlong(aq)) {
+                    const double kp = (k > 0) ? kap(i, j, k - 1) : 0.0;
+                    const double kq = in ? kap(i, j, k) : 0.0;
+                    f = sh * (kp + kq) * (aq - ap);
+                }
+                D.fface[2][((long long)i * n1 + j) * (n2 + 1) + k] = f;
+            }
+            if (!in) continue;
+            // x-faces (i, j, k) and, for the last i, (n0, j, k) of (n0+1, n1, n2)
+            for (int up = 0; up < ((i == n0 - 1) ? 2 : 1); up++) {
+                const int fi = i + up;  // face between cells fi-1 and fi
+                const double a_lo = (fi > 0) ? alpha[key - (long long)(1 - up) * n1 * n2] : 0.0;
+                const double a_hi = (fi < n0) ? alpha[key + (long long)up * n1 * n2] : 0.0;
+                double f = 0.0;
+                if (__double_as_longlong(a_lo) != __double_as_longlong(a_hi)) {
+                    const double klo = (fi > 0) ? kap(fi - 1, j, k) : 0.0;
+                    const double khi = (fi < n0) ? kap(fi, j, k) : 0.0;
+                    f = sh * (klo + khi) * (a_hi - a_lo);
+                }
+                D.fface[0][((long long)fi * n1 + j) * n2 + k] = f;
+            }
+            // y-faces (i, j, k) and, for the last j, (i, n1, k) of (n0, n1+1, n2)
+            for (int up = 0; up < ((j == n1 - 1) ? 2 : 1); up++) {
+                const int fj = j + up;
+                const double a_lo = (fj > 0) ? alpha[key - (long long)(1 - up) * n2] : 0.0;
+                const double a_hi = (fj < n1) ? alpha[key + (long long)up * n2] : 0.0;
+                double f = 0.0;
+                if (__double_as_longlong(a_lo) != __double_as_longlong(a_hi)) {
+                    const double klo = (fj > 0) ? kap(i, fj - 1, k) : 0.0;
+                    const double khi = (fj < n1) ? kap(i, fj, k) : 0.0;
+                    f = sh * (klo + khi) * (a_hi - a_lo);
+                }
+                D.fface[1][((long long)i * (n1 + 1) + fj) * n2 + k] = f;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 namespace ft {
@@ -191,6 +289,27 @@ cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha
 cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
                              cudaStream_t s) {
     return csf_with(ws, ft_many(ws), p, kappa, normal, s);
+}
+
+cudaError_t launch_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                              const double* normal, double* fx, double* fy, double* fz, cudaStream_t s) {
+    FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
+    fr.d0.alpha = const_cast<double*>(alpha);  // read only here
+    fr.d0.fface[0] = fx;
+    fr.d0.fface[1] = fy;
+    fr.d0.fface[2] = fz;
+    count_launches(1);
+    k_face_force<FrontsOne><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr, p->sigma, ws->idx_map, kappa,
+                                                                                 normal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                                    cudaStream_t s) {
+    count_launches(1);
+    k_face_force<FrontsMany><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(ft_many(ws), p->sigma,
+                                                                                  ws->idx_map, kappa, normal);
+    return cudaGetLastError();
 }
 
 }  // namespace ft

@@ -179,45 +179,174 @@ __device__ __forceinline__ void warp_transpose_sum2(float (&h)[32], float (&l)[3
     }
 }
 
-// the expensive part for one queued fragment: exact support test, weight,
-// projected moments and the 27 accumulations
+// The 27 sums of the normal equations: S (packed upper triangle of the 6x6
+// matrix, row by row) and B.
+template <typename T> struct Acc;
+
+template <> struct Acc<double> {
+    double S[21], B[6];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int r = 0; r < 21; r++) S[r] = 0.0;
+#pragma unroll
+        for (int r = 0; r < 6; r++) B[r] = 0.0;
+    }
+    __device__ __forceinline__ void get(double (&s)[21], double (&b)[6]) const {
+#pragma unroll
+        for (int r = 0; r < 21; r++) s[r] = S[r];
+#pragma unroll
+        for (int r = 0; r < 6; r++) b[r] = B[r];
+    }
+};
+
+// Float sums kept in pairs for the paired float instructions of this GPU
+// (two fused multiply-adds per instruction): the packed entries 0..9, 11..16
+// and 18..19 are nine adjacent pairs, entries 10 and 17 (rows 1 and 3, column
+// 5) form one more, entry 20 stays single; B in three pairs.
+template <> struct Acc<float> {
+    float2 P[9], Q, Bp[3];
+    float s20;
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int r = 0; r < 9; r++) P[r] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 3; r++) Bp[r] = make_float2(0.f, 0.f);
+        Q = make_float2(0.f, 0.f);
+        s20 = 0.f;
+    }
+    __device__ __forceinline__ void get(float (&s)[21], float (&b)[6]) const {
+        const int first[9] = {0, 2, 4, 6, 8, 11, 13, 15, 18};
+#pragma unroll
+        for (int r = 0; r < 9; r++) {
+            s[first[r]] = P[r].x;
+            s[first[r] + 1] = P[r].y;
+        }
+        s[10] = Q.x;
+        s[17] = Q.y;
+        s[20] = s20;
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            b[2 * r] = Bp[r].x;
+            b[2 * r + 1] = Bp[r].y;
+        }
+    }
+};
+
+// The expensive part for one queued fragment: exact support test, weight,
+// projected moments and the 27 accumulations.
+// A queue entry (float4): the float form holds the fragment centroid relative
+// to the fitted cell (x, y, z) and the record index (w); the float64 form the
+// neighbour offset code (x) and the record index (w), the centroid being
+// rebuilt exactly in float64.
 template <typename T>
-__device__ __forceinline__ void accumulate(const Rec<T>& rec, unsigned ri, int dcode, T delta, T inv_delta,
+__device__ __forceinline__ void accumulate(const Rec<T>& rec, const float4 qe, T delta, T inv_delta,
                                           const T n[3], const T t1[3], const T t2[3], const T c11[6],
-                                          const T c12[6], const T c22[6], T z0, T S[21], T B[6], int& count) {
-    T an[3], c[3], k[6];
+                                          const T c12[6], const T c22[6], T z0, Acc<T>& acc, int& count);
+
+template <>
+__device__ __forceinline__ void accumulate<double>(const Rec<double>& rec, const float4 qe, double delta,
+                                                   double inv_delta, const double n[3], const double t1[3],
+                                                   const double t2[3], const double c11[6], const double c12[6],
+                                                   const double c22[6], double z0, Acc<double>& acc, int& count) {
+    const unsigned ri = __float_as_uint(qe.w);
+    const int dcode = __float_as_int(qe.x);
+    double an[3], c[3], k[6];
     rec.load(ri, an, c, k);
-    const T p[3] = {c[0] + (T)(((dcode >> 8) & 15) - 8), c[1] + (T)(((dcode >> 4) & 15) - 8),
-                    c[2] + (T)((dcode & 15) - 8)};
-    const T d2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-    const T dist = sqrt(d2);
+    const double p[3] = {c[0] + (double)(((dcode >> 8) & 15) - 8), c[1] + (double)(((dcode >> 4) & 15) - 8),
+                         c[2] + (double)((dcode & 15) - 8)};
+    const double d2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    const double dist = sqrt(d2);
     if (!(dist < delta)) return;
     count++;
-    const T q = dist * inv_delta;
-    const T om = (T)1 - q;
-    const T om2 = om * om;
-    const T w = ((T)1 + (T)4 * q) * om2 * om2;
-    const T x = t1[0] * p[0] + t1[1] * p[1] + t1[2] * p[2];
-    const T y = t2[0] * p[0] + t2[1] * p[1] + t2[2] * p[2];
-    const T z = n[0] * p[0] + n[1] * p[1] + n[2] * p[2] - z0;
-    const T sA = n[0] * an[0] + n[1] * an[1] + n[2] * an[2];
-    T q11 = 0, q12 = 0, q22 = 0;
+    const double q = dist * inv_delta;
+    const double om = 1.0 - q;
+    const double om2 = om * om;
+    const double w = (1.0 + 4.0 * q) * om2 * om2;
+    const double x = t1[0] * p[0] + t1[1] * p[1] + t1[2] * p[2];
+    const double y = t2[0] * p[0] + t2[1] * p[1] + t2[2] * p[2];
+    const double z = n[0] * p[0] + n[1] * p[1] + n[2] * p[2] - z0;
+    const double sA = n[0] * an[0] + n[1] * an[1] + n[2] * an[2];
+    double q11 = 0, q12 = 0, q22 = 0;
 #pragma unroll
     for (int r = 0; r < 6; r++) {
         q11 += c11[r] * k[r];
         q12 += c12[r] * k[r];
         q22 += c22[r] * k[r];
     }
-    const T v[6] = {(T)1, x, y, x * x + q11, x * y + q12, y * y + q22};
-    const T u = w * sA * sA;
+    const double v[6] = {1.0, x, y, x * x + q11, x * y + q12, y * y + q22};
+    const double u = w * sA * sA;
     int r = 0;
 #pragma unroll
     for (int i = 0; i < 6; i++) {
-        const T uv = (i == 0) ? u : u * v[i];
+        const double uv = (i == 0) ? u : u * v[i];
 #pragma unroll
-        for (int j = i; j < 6; j++) S[r++] += uv * v[j];
-        B[i] += uv * z;
+        for (int j = i; j < 6; j++) acc.S[r++] += uv * v[j];
+        acc.B[i] += uv * z;
     }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <>
+__device__ __forceinline__ void accumulate<float>(const Rec<float>& rec, const float4 qe, float delta,
+                                                  float inv_delta, const float n[3], const float t1[3],
+                                                  const float t2[3], const float c11[6], const float c12[6],
+                                                  const float c22[6], float z0, Acc<float>& acc, int& count) {
+    float an[3], c[3], k[6];
+    rec.load(__float_as_uint(qe.w), an, c, k);
+    const float p[3] = {qe.x, qe.y, qe.z};
+    const float d2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+    const float dist = sqrtf(d2);
+    if (!(dist < delta)) return;
+    count++;
+    const float q = dist * inv_delta;
+    const float om = 1.f - q;
+    const float om2 = om * om;
+    const float w = (1.f + 4.f * q) * om2 * om2;
+    // (x, y) = (t1 . p, t2 . p) and (z + z0, sA) = (n . p, n . AN), two lanes per instruction
+    float2 xy = __fmul2_rn(f2(t1[0], t2[0]), f2(p[0], p[0]));
+    xy = __ffma2_rn(f2(t1[1], t2[1]), f2(p[1], p[1]), xy);
+    xy = __ffma2_rn(f2(t1[2], t2[2]), f2(p[2], p[2]), xy);
+    float2 zs = __fmul2_rn(f2(n[0], n[0]), f2(p[0], an[0]));
+    zs = __ffma2_rn(f2(n[1], n[1]), f2(p[1], an[1]), zs);
+    zs = __ffma2_rn(f2(n[2], n[2]), f2(p[2], an[2]), zs);
+    const float x = xy.x, y = xy.y, z = zs.x - z0, sA = zs.y;
+    // (q11, q12) = (t1.K.t1, t1.K.t2); q22 = t2.K.t2 as two half sums
+    float2 q1 = __fmul2_rn(f2(c11[0], c12[0]), f2(k[0], k[0]));
+#pragma unroll
+    for (int r = 1; r < 6; r++) q1 = __ffma2_rn(f2(c11[r], c12[r]), f2(k[r], k[r]), q1);
+    float2 q2 = __fmul2_rn(f2(c22[0], c22[1]), f2(k[0], k[1]));
+    q2 = __ffma2_rn(f2(c22[2], c22[3]), f2(k[2], k[3]), q2);
+    q2 = __ffma2_rn(f2(c22[4], c22[5]), f2(k[4], k[5]), q2);
+    const float q22 = q2.x + q2.y;
+    // v = [1, x, y, x^2 + q11, xy + q12, y^2 + q22]
+    const float2 v34 = __ffma2_rn(f2(x, x), f2(x, y), q1);
+    const float v5 = y * y + q22;
+    const float u = w * sA * sA;
+    // uv_i = u v_i
+    const float2 uv12 = __fmul2_rn(f2(u, u), f2(x, y));
+    const float2 uv34 = __fmul2_rn(f2(u, u), v34);
+    const float uv5 = u * v5;
+    // row 0 (uv0 = u): entries 0..5
+    acc.P[0] = __ffma2_rn(f2(u, u), f2(1.f, x), acc.P[0]);
+    acc.P[1] = __ffma2_rn(f2(u, u), f2(y, v34.x), acc.P[1]);
+    acc.P[2] = __ffma2_rn(f2(u, u), f2(v34.y, v5), acc.P[2]);
+    // row 1: entries 6..9 (columns 1..4), entry 10 (column 5) in Q.x
+    acc.P[3] = __ffma2_rn(f2(uv12.x, uv12.x), f2(x, y), acc.P[3]);
+    acc.P[4] = __ffma2_rn(f2(uv12.x, uv12.x), v34, acc.P[4]);
+    // row 2: entries 11..14 (columns 2..5)
+    acc.P[5] = __ffma2_rn(f2(uv12.y, uv12.y), f2(y, v34.x), acc.P[5]);
+    acc.P[6] = __ffma2_rn(f2(uv12.y, uv12.y), f2(v34.y, v5), acc.P[6]);
+    // row 3: entries 15..16 (columns 3..4), entry 17 (column 5) in Q.y
+    acc.P[7] = __ffma2_rn(f2(uv34.x, uv34.x), v34, acc.P[7]);
+    acc.Q = __ffma2_rn(f2(uv12.x, uv34.x), f2(v5, v5), acc.Q);
+    // row 4: entries 18..19 (columns 4..5); row 5: entry 20
+    acc.P[8] = __ffma2_rn(f2(uv34.y, uv34.y), f2(v34.y, v5), acc.P[8]);
+    acc.s20 += uv5 * v5;
+    // B_i += uv_i z
+    acc.Bp[0] = __ffma2_rn(f2(u, uv12.x), f2(z, z), acc.Bp[0]);
+    acc.Bp[1] = __ffma2_rn(f2(uv12.y, uv34.x), f2(z, z), acc.Bp[1]);
+    acc.Bp[2] = __ffma2_rn(f2(uv34.y, uv5), f2(z, z), acc.Bp[2]);
 }
 
 template <typename T, class F, int kMinBlocks>
@@ -226,12 +355,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                                                        const float4* __restrict__ cen,
                                                        const int* __restrict__ idx_map, ft_counters* ctr,
                                                        ft_cellsys* __restrict__ sys, int* __restrict__ fit_info) {
-    __shared__ unsigned s_qr[kWarps][kQueue];
-    __shared__ int s_qd[kWarps][kQueue];
+    __shared__ float4 s_q[kWarps][kQueue];
     const long long M = ctr->M;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned* qr = s_qr[wid];
-    int* qd = s_qd[wid];
+    float4* qq = s_q[wid];
     unsigned long long pairs_total = 0;
     // Schedule: static interleaving (the warps of a block take consecutive
     // cells, which share most of their candidate fragments in L1), or a global
@@ -320,13 +447,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
 
         // 2-4. normal equations; the support grows while too few fragments lie in it
         T delta = d_start;
-        T S[21], B[6];
+        Acc<T> acc;
         int ctot;
         for (;;) {
-#pragma unroll
-            for (int r = 0; r < 21; r++) S[r] = 0;
-#pragma unroll
-            for (int r = 0; r < 6; r++) B[r] = 0;
+            acc.zero();
             int count = 0;
             const T inv_delta = (T)1 / delta;
             // float pre-filter, slightly wider than the support; the exact test follows
@@ -342,6 +466,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
             for (int cb = 0; cb < nb; cb += 32) {
                 const int l = cb + lane;
                 int f0 = 0, cnt = 0, dcode = 0;
+                float ox = 0.f, oy = 0.f, oz = 0.f;
                 if (l < nb) {
                     const int a = (int)(((float)l + 0.5f) * inv_ss);
                     const int rem = l - a * side * side;
@@ -356,6 +481,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                         }
                     }
                     dcode = ((di + 8) << 8) | ((dj + 8) << 4) | (dk + 8);
+                    ox = (float)di;
+                    oy = (float)dj;
+                    oz = (float)dk;
                 }
                 int incl = cnt;
 #pragma unroll
@@ -365,7 +493,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                 }
                 const int excl = incl - cnt;
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
-                for (int fb = 0; fb < total; fb += 32) {
+                // candidate fi of this round -> owning neighbour lane o, record ri;
+                // the next batch's mapping and centroid load are issued before
+                // the current batch is tested (software pipelining of the loads)
+                auto map = [&](int fb, unsigned& ri, float& dx, float& dy, float& dz, int& dc, bool& valid) {
                     const int fi = fb + lane;
                     int o = 0;
 #pragma unroll
@@ -375,35 +506,70 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                     }
                     const int fo = __shfl_sync(0xffffffffu, f0, o);
                     const int eo = __shfl_sync(0xffffffffu, excl, o);
-                    const int dc = __shfl_sync(0xffffffffu, dcode, o);
+                    if constexpr (sizeof(T) == 4) {
+                        dx = __shfl_sync(0xffffffffu, ox, o);
+                        dy = __shfl_sync(0xffffffffu, oy, o);
+                        dz = __shfl_sync(0xffffffffu, oz, o);
+                        dc = 0;
+                    } else {
+                        // one shuffle of the offset code; the float64 form is issue-bound
+                        dc = __shfl_sync(0xffffffffu, dcode, o);
+                        dx = (float)(((dc >> 8) & 15) - 8);
+                        dy = (float)(((dc >> 4) & 15) - 8);
+                        dz = (float)((dc & 15) - 8);
+                    }
+                    valid = fi < total;
+                    ri = valid ? (unsigned)(fo + (fi - eo)) : 0u;
+                };
+                unsigned ri_n = 0;
+                float dx_n = 0.f, dy_n = 0.f, dz_n = 0.f;
+                int dc_n = 0;
+                bool v_n = false;
+                float4 c4_n = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (total > 0) {
+                    map(0, ri_n, dx_n, dy_n, dz_n, dc_n, v_n);
+                    if (v_n) c4_n = cen[ri_n];
+                }
+                // (the float64 form maps each batch in turn: its registers are full)
+                constexpr bool kPipe = sizeof(T) == 4;
+                for (int fb = 0; fb < total; fb += 32) {
+                    if (!kPipe && fb > 0) {
+                        map(fb, ri_n, dx_n, dy_n, dz_n, dc_n, v_n);
+                        if (v_n) c4_n = cen[ri_n];
+                    }
+                    const unsigned ri = ri_n;
+                    const float dx = dx_n, dy = dy_n, dz = dz_n;
+                    const int dc = dc_n;
+                    const bool valid = v_n;
+                    const float4 c4 = c4_n;
+                    if (kPipe && fb + 32 < total) {
+                        map(fb + 32, ri_n, dx_n, dy_n, dz_n, dc_n, v_n);
+                        if (v_n) c4_n = cen[ri_n];
+                    }
                     bool pass = false;
-                    unsigned ri = 0;
-                    if (fi < total) {
-                        ri = (unsigned)(fo + (fi - eo));
-                        const float4 c4 = cen[ri];
-                        const float px = c4.x + (float)(((dc >> 8) & 15) - 8);
-                        const float py = c4.y + (float)(((dc >> 4) & 15) - 8);
-                        const float pz = c4.z + (float)((dc & 15) - 8);
+                    float4 entry = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (valid) {
+                        const float px = c4.x + dx, py = c4.y + dy, pz = c4.z + dz;
                         pass = (px * px + py * py + pz * pz) < f_thr;
+                        if (sizeof(T) == 4)
+                            entry = make_float4(px, py, pz, __uint_as_float(ri));
+                        else
+                            entry = make_float4(__int_as_float(dc), 0.f, 0.f, __uint_as_float(ri));
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                    if (pass) {
-                        const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                        qr[pos] = ri;
-                        qd[pos] = dc;
-                    }
+                    if (pass) qq[qn + __popc(bal & ((1u << lane) - 1u))] = entry;
                     qn += __popc(bal);
                     __syncwarp();
                     if (qn >= 32) {
-                        const int e = qn - 32 + lane;
-                        accumulate<T>(rec, qr[e], qd[e], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, S, B, count);
+                        accumulate<T>(rec, qq[qn - 32 + lane], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, acc,
+                                      count);
                         qn -= 32;
                         __syncwarp();
                     }
                 }
             }
             if (lane < qn)
-                accumulate<T>(rec, qr[lane], qd[lane], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, S, B, count);
+                accumulate<T>(rec, qq[lane], delta, inv_delta, n, t1, t2, c11, c12, c22, z0, acc, count);
             __syncwarp();
             ctot = ft_warp_sum_i(count);
             if (ctot >= A.fit_min || delta >= d_max) break;
@@ -415,6 +581,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
         // 5. reduce the 27 sums over the warp (transposed: lane r ends with sum r)
         //    and leave them for the solve kernel
         ft_cellsys* out = sys + m;
+        T S[21], B[6];
+        acc.get(S, B);
         if (sizeof(T) == 8) {
             double v[32];
 #pragma unroll
@@ -463,43 +631,65 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
     if (lane == 0 && pairs_total) atomicAdd((unsigned long long*)&ctr->fit_pairs, pairs_total);
 }
 
-// LDL^T solve of the leading n x n block of the packed symmetric 6x6 system.
+// float -> double (exact) with integer operations: on this GPU the conversion
+// instruction runs on the float64 pipe at the float64 rate.  Zero and normal
+// floats are widened here; anything else takes the hardware conversion.
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if ((b << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (b & 0x80000000u) | ((e - 127u + 1023u) << 20) | ((b & 0x7fffffu) >> 3);
+    const unsigned lo = (b & 7u) << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// LDL^T solve of the leading N x N block of the packed symmetric 6x6 system
+// (N a compile-time size: every loop unrolls, the factors stay in registers).
 // Returns the smallest pivot relative to the trace (-1 if a pivot is not > 0).
-__device__ double ldlt_solve(const double* S, const double* B, int n, double* a) {
-    double Lm[6][6], d[6];
-    auto at = [&](int i, int j) {  // packed upper triangle of the 6x6 matrix
-        if (i > j) {
-            const int t = i;
-            i = j;
-            j = t;
-        }
-        return S[i * 6 - (i * (i - 1)) / 2 + (j - i)];
-    };
+__device__ __forceinline__ constexpr int packed(int i, int j) {  // i <= j
+    return i * 6 - (i * (i - 1)) / 2 + (j - i);
+}
+
+template <int N>
+__device__ __forceinline__ double ldlt_solve(const double (&S)[21], const double (&B)[6], double (&a)[6]) {
+    double Lm[N][N], d[N], inv_d[N];
     double tr = 0.0;
-    for (int i = 0; i < n; i++) tr += at(i, i);
-    double minp = INFINITY, inv_d[6];
-    for (int j = 0; j < n; j++) {
-        double dj = at(j, j);
+#pragma unroll
+    for (int i = 0; i < N; i++) tr += S[packed(i, i)];
+    double minp = INFINITY;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        double dj = S[packed(j, j)];
+#pragma unroll
         for (int k = 0; k < j; k++) dj -= Lm[j][k] * Lm[j][k] * d[k];
         d[j] = dj;
         minp = fmin(minp, dj);
-        if (!(dj > 0.0)) return -1.0;
+        ok = ok && (dj > 0.0);
         inv_d[j] = 1.0 / dj;  // one float64 division per pivot
-        for (int i = j + 1; i < n; i++) {
-            double v = at(i, j);
+#pragma unroll
+        for (int i = j + 1; i < N; i++) {
+            double v = S[packed(j, i)];
+#pragma unroll
             for (int k = 0; k < j; k++) v -= Lm[i][k] * Lm[j][k] * d[k];
             Lm[i][j] = v * inv_d[j];
         }
     }
-    double y[6];
-    for (int i = 0; i < n; i++) {
+    if (!ok) return -1.0;
+    double y[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
         double v = B[i];
+#pragma unroll
         for (int k = 0; k < i; k++) v -= Lm[i][k] * y[k];
         y[i] = v;
     }
-    for (int i = n - 1; i >= 0; i--) {
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
         double v = y[i] * inv_d[i];
-        for (int k = i + 1; k < n; k++) v -= Lm[k][i] * a[k];
+#pragma unroll
+        for (int k = i + 1; k < N; k++) v -= Lm[k][i] * a[k];
         a[i] = v;
     }
     return minp / tr;
@@ -519,15 +709,21 @@ __global__ void __launch_bounds__(128) k_ppic_solve(F fr, const ft_cellsys* __re
         double S[21], B[6], n[3], z0;
         if (fp32) {
             const float* v = reinterpret_cast<const float*>(sys[m].v);
-            for (int r = 0; r < 21; r++) S[r] = (double)v[2 * r] + (double)v[2 * r + 1];
-            for (int r = 0; r < 6; r++) B[r] = (double)v[42 + 2 * r] + (double)v[43 + 2 * r];
-            for (int r = 0; r < 3; r++) n[r] = (double)v[54 + 2 * r];
-            z0 = (double)v[60];
+#pragma unroll
+            for (int r = 0; r < 21; r++) S[r] = f2d(v[2 * r]) + f2d(v[2 * r + 1]);
+#pragma unroll
+            for (int r = 0; r < 6; r++) B[r] = f2d(v[42 + 2 * r]) + f2d(v[43 + 2 * r]);
+#pragma unroll
+            for (int r = 0; r < 3; r++) n[r] = f2d(v[54 + 2 * r]);
+            z0 = f2d(v[60]);
             const double il = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
             for (int r = 0; r < 3; r++) n[r] *= il;
         } else {
+#pragma unroll
             for (int r = 0; r < 21; r++) S[r] = sys[m].v[r];
+#pragma unroll
             for (int r = 0; r < 6; r++) B[r] = sys[m].v[21 + r];
+#pragma unroll
             for (int r = 0; r < 3; r++) n[r] = sys[m].v[27 + r];
             z0 = sys[m].v[30];
         }
@@ -535,12 +731,12 @@ __global__ void __launch_bounds__(128) k_ppic_solve(F fr, const ft_cellsys* __re
         double t1[3], t2[3];
         basis<double>(n, t1, t2);
         double a[6] = {0, 0, 0, 0, 0, 0};
-        const double rel = ldlt_solve(S, B, 6, a);
+        const double rel = ldlt_solve<6>(S, B, a);
         if (!(rel >= 1e-12)) {
             // singular: plane fit on the leading 3x3 block, kappa = 0
             for (int r = 0; r < 6; r++) a[r] = 0.0;
-            double a3[6];
-            if (ldlt_solve(S, B, 3, a3) > 0.0) {
+            double a3[6] = {0, 0, 0, 0, 0, 0};
+            if (ldlt_solve<3>(S, B, a3) > 0.0) {
                 a[0] = a3[0];
                 a[1] = a3[1];
                 a[2] = a3[2];

@@ -342,7 +342,7 @@ cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys,
 
 cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n, long long* total,
                                cudaStream_t s) {
-    const int G = ws->grid_blocks;
+    const int G = ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     LoadCounts ld{in};
     count_launches(3);
@@ -354,7 +354,7 @@ cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const 
 
 cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, const long long* n,
                               long long* total, cudaStream_t s) {
-    const int G = ws->grid_blocks;
+    const int G = ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     LoadHeads ld{keys};
     count_launches(3);
@@ -373,7 +373,7 @@ cudaError_t prepare_sort(int grid_blocks) {
 }
 
 cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
-    const int G = ws->grid_blocks;
+    const int G = ws->tune.seg_blocks;
     const int passes = (ws->key_bits + 7) / 8;
     int src = 0;
     for (int p = 0; p < passes; p++) {

@@ -164,7 +164,8 @@ def test_autotune_keeps_results():
             if f in after:
                 assert np.array_equal(after[f], before[b][f]), f
     # every shape gives the same results
-    F.ft_set_tuning(bc.ws, clip=1, ppic=1, csf=1, fill=1, ppic_min_blocks=6, ppic_dynamic=1 - t["ppic_dynamic"])
+    F.ft_set_tuning(bc.ws, clip=1, ppic=1, csf=1, fill=1, ppic_min_blocks=6, ppic_dynamic=1 - t["ppic_dynamic"],
+                    sort_blocks=7)
     bc.step()
     torch.cuda.synchronize()
     for b in range(len(wl)):
