@@ -38,15 +38,15 @@ class _Params(C.Structure):
 
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, OpenMP if available)."""
-    src = os.path.join(_HERE, "oracle.c")
+    srcs = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "paraboloid.c")]
     hdr = os.path.join(_HERE, "oracle.h")
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+            and os.path.getmtime(_LIB_PATH) >= max([os.path.getmtime(x) for x in srcs] + [os.path.getmtime(hdr)])):
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-            src, "-o", tmp, "-lm"]
+            *srcs, "-o", tmp, "-lm"]
     try:
         subprocess.run(base[:-3] + ["-fopenmp"] + base[-3:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -71,7 +71,7 @@ def lib():
             L.og_alpha.restype = C.c_int
             L.og_alpha.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int32, P, P]
             L.og_ppic.restype = C.c_int
-            L.og_ppic.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64, P, P, P, P, P]
+            L.og_ppic.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64, P, P, P, P, P, P]
             L.og_csf.restype = C.c_int
             L.og_csf.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P]
             L.og_face_force.restype = C.c_int
@@ -87,6 +87,8 @@ def lib():
             L.og_advect_rk4.restype = None
             L.og_advect_rk4.argtypes = [P, P, P, P, P, C.c_int64, C.c_double, P, P]
             L.og_green_moments.restype = None
+            L.og_paraboloid_cells.argtypes = [C.c_int64, P, P, P, P, P, P, P]
+            L.og_paraboloid_cells.restype = None
             L.og_green_moments.argtypes = [P, P, C.c_int, P]
             L.og_signed_volume.restype = C.c_double
             L.og_signed_volume.argtypes = [P, P, C.c_int64]
@@ -187,8 +189,9 @@ def alpha(verts, tris, g, margin=None):
     return out, int(st[0])
 
 
-def ppic(verts, tris, g, cells, params=None, frame_angle=0.0):
-    """PPIC curvature, paraboloid normal, coefficients and status in the given cells."""
+def ppic(verts, tris, g, cells, params=None, frame_angle=0.0, frame=False):
+    """PPIC curvature, paraboloid normal, coefficients and status in the given
+    cells (and, with ``frame=True``, each cell's frame (t1, t2, n) as (M, 9))."""
     p = dict(DEFAULT_PARAMS)
     if params:
         p.update(params)
@@ -202,10 +205,13 @@ def ppic(verts, tris, g, cells, params=None, frame_angle=0.0):
     normal = np.empty((M, 3), np.float64)
     coeffs = np.empty((M, 6), np.float64)
     status = np.empty(M, np.int8)
+    fr = np.empty((M, 9), np.float64)
     rc = lib().og_ppic(_ptr(v), v.shape[0], _ptr(t), t.shape[0], C.byref(gs), C.byref(ps), M, _ptr(cells),
-                       _ptr(kappa), _ptr(normal), _ptr(coeffs), _ptr(status))
+                       _ptr(kappa), _ptr(normal), _ptr(coeffs), _ptr(status), _ptr(fr))
     if rc != 0:
         raise ValueError("og_ppic: a listed cell is not interfacial")
+    if frame:
+        return kappa, normal, coeffs, status, fr
     return kappa, normal, coeffs, status
 
 
@@ -283,6 +289,22 @@ def roughness_smooth(verts, tris, gl_thr, r_thr, max_rounds=64):
 
 def edge_priority(e):
     return int(lib().og_edge_priority(int(e)))
+
+
+def paraboloid_cells(frame, coeffs):
+    """The paper's cut-cell quantities from fitted paraboloids (Sec. 3.2): per
+    cell alpha = V_P / V_C, the surface area inside the cell (cell units), the
+    area-averaged mean curvature (1 / cell width) and the normalised
+    area-integrated normal; status 1 where the surface misses the cell."""
+    fr = np.ascontiguousarray(np.asarray(frame, dtype=np.float64).reshape(-1, 9))
+    co = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64).reshape(-1, 6))
+    m = fr.shape[0]
+    assert co.shape[0] == m
+    out = dict(alpha=np.empty(m), area=np.empty(m), kbar=np.empty(m), nbar=np.empty((m, 3)),
+               status=np.empty(m, np.int8))
+    lib().og_paraboloid_cells(m, _ptr(fr), _ptr(co), _ptr(out["alpha"]), _ptr(out["area"]), _ptr(out["kbar"]),
+                              _ptr(out["nbar"]), _ptr(out["status"]))
+    return out
 
 
 def green_moments(x, y):

@@ -572,7 +572,7 @@ static int64_t og_find(const og_frags* F, uint64_t key) {
 
 int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, const og_grid* g,
             const og_params* p, int64_t ncells, const uint32_t* cells, double* kappa, double* normal,
-            double* coeffs, int8_t* fit_status) {
+            double* coeffs, int8_t* fit_status, double* frame) {
     const int32_t margin = 2 + (int32_t)ceil(p->delta_max_h);
     og_frags F = og_build_frags(verts, nv, tris, nt, g, margin);
     const double h = g->h;
@@ -588,6 +588,7 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
             kappa[c] = 0.0;
             normal[3 * c] = normal[3 * c + 1] = normal[3 * c + 2] = 0.0;
             if (coeffs) for (int r = 0; r < 6; r++) coeffs[6 * c + r] = 0.0;
+            if (frame) for (int r = 0; r < 9; r++) frame[9 * c + r] = 0.0;
             fit_status[c] = -1;
             continue;
         }
@@ -701,6 +702,12 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
         const double nl = sqrt(nv3[0] * nv3[0] + nv3[1] * nv3[1] + nv3[2] * nv3[2]);
         for (int d = 0; d < 3; d++) normal[3 * c + d] = nv3[d] / nl;
         if (coeffs) for (int r = 0; r < 6; r++) coeffs[6 * c + r] = a[r];
+        if (frame)
+            for (int d = 0; d < 3; d++) {
+                frame[9 * c + d] = t1[d];
+                frame[9 * c + 3 + d] = t2[d];
+                frame[9 * c + 6 + d] = n[d];
+            }
         fit_status[c] = stc;
     }
     free(F.keys); free(F.off); free(F.voff); free(F.pv);

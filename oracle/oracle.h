@@ -76,11 +76,12 @@ int og_alpha(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
  * listed interfacial cells: curvature kappa (= div n, 2/R on a sphere), the
  * paraboloid normal at the cell's local origin, the coefficients a1..a6 (local
  * frame, lengths in units of h; may be NULL) and a status per cell
- * (bit0 support grown, bit1 singular -> plane fit, bit2 normal fallback).
+ * (bit0 support grown, bit1 singular -> plane fit, bit2 normal fallback),
+ * and the frame (t1, t2, n) of each cell as 9 doubles (may be NULL).
  * Pinned by sphere convergence, planes, ellipsoids, frame invariance. */
 int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
             const og_grid* g, const og_params* p, int64_t ncells, const uint32_t* cells,
-            double* kappa, double* normal, double* coeffs, int8_t* fit_status);
+            double* kappa, double* normal, double* coeffs, int8_t* fit_status, double* frame);
 
 /* CSF source S = sigma kappa grad(alpha) (Eq. csf) with the weighted curvature
  * smoothing of Sec. 3.3 in non-interfacial cells.  force is (3, n0*n1*n2). */
@@ -118,6 +119,22 @@ int og_roughness_smooth(double* verts, int64_t nv, const int32_t* tris, int64_t 
 uint64_t og_edge_priority(uint64_t e);
 
 /* Helpers exposed for pin tests. */
+/* The paper's own cut-cell quantities from a fitted paraboloid (Sec. 3.2):
+ * frame = (t1, t2, n) as 9 doubles (rows, orthonormal), coeffs = a0..a5 of
+ * z = P(x, y) in that frame, cell units (the cell is [-1/2, 1/2]^3).  Writes
+ * alpha = V_P (volume below the paraboloid), area = surface area inside the
+ * cell, kbar = area-averaged mean curvature, nbar = normalised
+ * area-integrated normal; status 1 when the surface misses the cell (then kbar
+ * and nbar are the point values at the frame origin).  Nested adaptive
+ * quadrature of the definitions (paraboloid.c); pinned by plane and
+ * whole-cell closed forms, the complement identity, cube symmetries and the
+ * divergence identity. */
+void og_paraboloid_cell(const double* frame, const double* coeffs, double* alpha, double* area, double* kbar,
+                        double* nbar, int* status);
+/* the same for m cells (frame m x 9, coeffs m x 6), threads over cells */
+void og_paraboloid_cells(int64_t m, const double* frame, const double* coeffs, double* alpha, double* area,
+                         double* kbar, double* nbar, int8_t* status);
+
 void og_green_moments(const double* x, const double* y, int n, double* m6);
 double og_signed_volume(const double* verts, const int32_t* tris, int64_t nt);
 double og_wendland_weight(double q); /* Eq. Wendland with q = d/delta */

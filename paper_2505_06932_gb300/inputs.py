@@ -400,3 +400,41 @@ def served_requests(seed: int = 11, count: int = 48, rate: float = 100.0, s_choi
                         steps=int(gen.integers(1, max_steps + 1)), arrival=t, dt=0.25 * g.h,
                         centre=centre, omega=a, s=s, R=R))
     return out
+
+
+def random_frames(gen, m: int) -> np.ndarray:
+    """m random right-handed orthonormal frames, rows (t1, t2, n), as (m, 9)."""
+    out = np.empty((m, 9))
+    for c in range(m):
+        Q, R = np.linalg.qr(gen.normal(size=(3, 3)))
+        Q = Q * np.sign(np.diag(R))
+        if np.linalg.det(Q) < 0:
+            Q[:, 2] = -Q[:, 2]
+        out[c] = Q.T.reshape(9)
+    return out
+
+
+def paraboloid_cells(seed: int = 21, m: int = 512):
+    """Cut-cell paraboloids in cell units: random frames and coefficients of
+    z = a1 + a2 x + a3 y + a4 x^2 + a5 x y + a6 y^2 spanning planes, the
+    curvatures of fitted fronts (|a4..a6| up to 0.06 for R >= 8h), strongly
+    curved patches (up to 0.4), steep slopes and heights that cut the cell
+    anywhere from a corner to the middle; every fifth cell is axis-aligned
+    (a signed permutation frame), where degenerate cases (faces parallel to
+    the tangent plane) occur."""
+    gen = rng(seed)
+    fr = random_frames(gen, m)
+    perms = [(0, 1, 2), (1, 2, 0), (2, 0, 1)]
+    for c in range(0, m, 5):
+        p = perms[(c // 5) % 3]
+        s = gen.choice([-1.0, 1.0], 2)
+        E = np.eye(3)[list(p)]
+        E[0] *= s[0]
+        E[1] *= s[1]
+        E[2] = np.cross(E[0], E[1])
+        fr[c] = E.reshape(9)
+    co = np.zeros((m, 6))
+    co[:, 0] = gen.uniform(-0.6, 0.6, m)
+    co[:, 1:3] = gen.uniform(-0.5, 0.5, (m, 2)) * gen.choice([0.0, 0.1, 1.0], (m, 1))
+    co[:, 3:] = gen.uniform(-1.0, 1.0, (m, 3)) * gen.choice([0.0, 0.01, 0.06, 0.4], (m, 1))
+    return fr, co
