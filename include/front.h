@@ -105,6 +105,10 @@ enum {
 /* per-cell fit_status bits of front_curvature_ppic */
 #define FT_FIT_GROWN 0x1     /* support radius was grown beyond delta_h          */
 #define FT_FIT_SINGULAR 0x2  /* normal equations singular: plane fit, kappa = 0  */
+
+/* per-cell status of the paraboloid cut-cell calls */
+#define FT_PARAB_MISS 0x1    /* the surface misses the cell: kappa and normal are
+                                the point values at the frame origin, area 0    */
 #define FT_FIT_NORMAL 0x4    /* opposing sheets: normal of the largest fragment  */
 
 /* Create a workspace for grid *g on CUDA device `device`; *bytes (host, may be
@@ -183,6 +187,42 @@ int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, c
  * front_csf_force. */
 int front_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                      const double* normal, double* fx, double* fy, double* fz, void* stream);
+
+/* The paper's own indicator and interface properties from the fitted
+ * paraboloids (Sec. 3.2, the paragraph after Eq. volumefit2), for m cells
+ * given directly.  frame: m x 9 float64, the rows t1, t2, n of an orthonormal
+ * frame whose origin is the cell centre; coeffs: m x 6 float64, a1..a6 of
+ * z = P(x, y) = a1 + a2 x + a3 y + a4 x^2 + a5 x y + a6 y^2 in that frame,
+ * lengths in cell widths (the cell is [-1/2, 1/2]^3).  Outputs per cell:
+ * alpha (m float64) = V_P / V_C, the fraction of the cell below the surface
+ * (z < P, the side n points away from), clamped to [0, 1]; area (m float64,
+ * cell widths squared) of the surface inside the cell; kappa (m float64, per
+ * cell width) = the mean curvature (div n, > 0 on a sphere) averaged over that
+ * surface; normal (m x 3 float64) = the normalised integral of the upward
+ * surface normal over it; status (m int8, FT_PARAB_* bits).  area, kappa,
+ * normal and status may be NULL.  The integrals are evaluated to float64
+ * rounding by graded Gauss-Legendre quadrature (the paper uses the closed
+ * forms of Evrard et al. 2023). */
+int front_paraboloid_cells(const double* frame, const double* coeffs, int64_t m, double* alpha, double* area,
+                           double* kappa, double* normal, int8_t* status, void* stream);
+
+/* The frames (t1, t2, n) of the interfacial cells of the last
+ * front_curvature_ppic call on ws, as m x 9 float64 in its cell order (the
+ * frame in which its coeffs are given).  `cap` as for that call. */
+int front_ppic_frame(ft_workspace* ws, int64_t cap, double* frame, void* stream);
+
+/* The paper's indicator in the cut cells (Sec. 3.2): after front_volume_fraction
+ * and front_curvature_ppic (with coeffs) on ws, replaces alpha at every
+ * interfacial cell by V_P / V_C of that cell's fitted paraboloid (full and
+ * empty cells keep their column-parity value, the paper's flood fill), and
+ * writes per interfacial cell, in the order of front_curvature_ppic, the
+ * surface-averaged kappa (1/length), normal and area (length^2) and the status
+ * as for front_paraboloid_cells (each may be NULL).  coeffs is the array that
+ * front_curvature_ppic wrote; `cap` is the length of the per-cell arrays
+ * (M > cap sets FT_ST_CAPACITY and writes nothing).  FT_ERR_STATE unless a
+ * fit ran since the last front_bin. */
+int front_volume_fraction_ppic(ft_workspace* ws, const double* coeffs, int64_t cap, double* alpha, double* kappa,
+                               double* normal, double* area, int8_t* status, void* stream);
 
 /* (a5) Divergence-preserving velocity interpolation (Sec. 3.1) of the staggered
  * face velocities U (n0+1,n1,n2), V (n0,n1+1,n2), W (n0,n1,n2+1) to the nv
@@ -312,6 +352,11 @@ int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* ka
 int front_face_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
                            void* stream);
 
+/* front_volume_fraction_ppic of every front: alpha_P into each front's alpha
+ * at its interfacial cells; per-cell outputs in the batch's cell order. */
+int front_volume_fraction_ppic_batch(ft_workspace* ws, const double* coeffs, int64_t cap, double* kappa,
+                                     double* normal, double* area, int8_t* status, void* stream);
+
 /* (a5) front_interp_velocity of every front (its U, V, W, verts -> vel). */
 int front_interp_velocity_batch(ft_workspace* ws, void* stream);
 
@@ -337,7 +382,7 @@ int ft_batch_status(ft_workspace* ws, void* stream, uint32_t* bits);
 typedef struct {
     int32_t clip_blocks_per_sm; /* canonical clip (front_bin), default 4            */
     int32_t ppic_blocks_per_sm; /* PPIC accumulation, default 4                      */
-    int32_t csf_blocks_per_sm;  /* CSF dense pass, default 16                        */
+    int32_t csf_blocks_per_sm;  /* force clear (batch) and face force, default 16     */
     int32_t fill_blocks_per_sm; /* column parity fill, default 8                     */
     int32_t ppic_min_blocks;    /* FP32 PPIC accumulation compiled for 4 (default) or
                                    6 resident blocks per SM (fewer registers each)   */

@@ -74,7 +74,7 @@ struct __align__(16) ft_fdesc {
 struct ft_tune {
     int clip_bps;   // k_clip blocks per SM
     int ppic_bps;   // k_ppic_acc blocks per SM
-    int csf_bps;    // k_csf_dense blocks per SM
+    int csf_bps;    // k_zero_force / k_face_force blocks per SM
     int fill_bps;   // k_alpha_fill blocks per SM
     int ppic_min_blocks;  // FP32 k_ppic_acc compiled for 4 (more registers) or 6 resident blocks per SM
     int ppic_dynamic;     // k_ppic_acc cells from a global work counter (1) or interleaved (0)
@@ -91,6 +91,7 @@ struct ft_workspace {
     long long max_nt, max_cand, max_cells;
     size_t bytes;
     bool binned;
+    bool fitted;           // front_curvature_ppic ran since the last bin
     int last_precision;
 
     ft_counters* ctr;
@@ -137,6 +138,14 @@ struct ft_workspace {
 
 // kernels / launchers (one translation unit each)
 namespace ft {
+cudaError_t launch_parab_cells(const double* frame, const double* coeffs, long long m, double* alpha, double* area,
+                               double* kappa, double* normal, int8_t* status, int sm_count, cudaStream_t s);
+cudaError_t launch_parab_ppic(ft_workspace* ws, const double* coeffs, long long cap, double* alpha, double* area,
+                              double* kappa, double* normal, int8_t* status, cudaStream_t s);
+cudaError_t launch_parab_ppic_batch(ft_workspace* ws, const double* coeffs, long long cap, double* area,
+                                    double* kappa, double* normal, int8_t* status, cudaStream_t s);
+cudaError_t launch_ppic_frame(ft_workspace* ws, long long cap, double* frame, cudaStream_t s);
+
 
 void count_launches(int n);  // kernels launched by this library (ft_launch_count)
 

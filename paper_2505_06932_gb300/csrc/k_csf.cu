@@ -3,95 +3,114 @@
 // kbar_P = sum_Q kappa_Q w_Q / sum_Q w_Q, w_Q = |s_Q . n_Q| / |s_Q|, over the
 // interfacial cells Q among the 26 neighbours of P (plain mean if all w_Q = 0).
 //
-// Two passes:
-//  * k_csf_dense -- one block per (i, j) column, threads along k (coalesced):
-//    the central-difference gradient (alpha = 0 outside the grid); flat
-//    neighbourhoods (bitwise-equal neighbour pairs: full and empty cells hold
-//    exactly 1 and 0) write zero force, interfacial cells write sigma kappa grad
-//    alpha, and the remaining cells (the ring around the interface) are appended
-//    to a compact list.
-//  * k_csf_ring -- one thread per listed cell: the smoothed curvature and the
-//    force.  Keeping the float64 smoothing out of the dense pass keeps that pass
-//    bound by memory instead of by divergent float64 issue.
+// Only cells next to the interface carry a force: grad alpha_P != 0 needs
+// alpha_{P+e} != alpha_{P-e} along some axis, and two full/empty cells on
+// either side differ only if the front passes through P; so P is interfacial
+// or a face neighbour of an interfacial cell.  Hence:
+//  * the force arrays are zeroed (a memset, or k_zero_force for a batch);
+//  * k_csf_cells -- seven threads per interfacial cell: one writes its own
+//    force sigma kappa grad alpha (central differences, alpha = 0 outside the
+//    grid), each of the others looks at one face neighbour and lists it as a
+//    ring cell when it is not interfacial and this cell is the smallest-key
+//    interfacial face neighbour it has (so it is listed once);
+//  * k_csf_ring -- one thread per ring cell: the smoothed curvature and the
+//    force.
+#include <type_traits>
+
 #include "ft_internal.cuh"
 
 namespace {
 
 constexpr int kThreads = 128;  // one block per column; 128 and 256 cell columns fill it
 
+// zero the force arrays of every front (the batched form).  A block clears a
+// tile of 8 x 128 consecutive cells of the batch-wide cell index (one front
+// search per tile, then a step to the next front where the tile crosses one),
+// each warp storing 3 x 256 contiguous bytes per row of the tile.
 template <class F>
-__global__ void __launch_bounds__(kThreads) k_csf_dense(F fr, double sigma, const int* __restrict__ idx_map,
+__global__ void __launch_bounds__(kThreads) k_zero_force(F fr) {
+    constexpr int kTile = 8 * kThreads;
+    const long long total = fr.ncells;
+    for (long long t0 = (long long)blockIdx.x * kTile; t0 < total; t0 += (long long)gridDim.x * kTile) {
+        int b = fr.by_key(t0);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const long long g = t0 + i * kThreads + threadIdx.x;
+            if (g >= total) break;
+            while (g >= fr.key_base(b + 1)) b++;
+            const ft_fdesc& D = fr.desc(b);
+            const long long NC = (long long)D.g.n[0] * D.g.n[1] * D.g.n[2];
+            const long long c = g - fr.key_base(b);
+            double* __restrict__ force = D.force;
+            force[c] = 0.0;
+            force[NC + c] = 0.0;
+            force[2 * NC + c] = 0.0;
+        }
+    }
+}
+
+// Seven tasks per interfacial cell (one thread each): task 0 writes the cell's
+// own force; task 1 + e looks at the face neighbour e and lists it as a ring
+// cell when it is not interfacial and this cell is its smallest-key
+// interfacial face neighbour.
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_csf_cells(F fr, double sigma, const unsigned* __restrict__ cells,
+                                                        const int* __restrict__ idx_map,
                                                         const double* __restrict__ kappa,
                                                         unsigned* __restrict__ ring, unsigned* __restrict__ nring,
                                                         long long ring_cap, ft_counters* ctr) {
-    const int lane = threadIdx.x & 31;
-    for (long long gcol = blockIdx.x; gcol < fr.ncols; gcol += gridDim.x) {
-        const int b = fr.by_col(gcol);
+    const long long M = ctr->M;
+    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < 7 * M; w += (long long)gridDim.x * kThreads) {
+        const long long m = w / 7;
+        const int task = (int)(w - 7 * m);
+        const long long gkey = cells[m];
+        const int b = fr.by_key(gkey);
         const ft_fdesc& D = fr.desc(b);
-        const int n0 = D.g.n[0], n1 = D.g.n[1], n2 = D.g.n[2];
-        const long long NC = (long long)n0 * n1 * n2;
-        const long long s1 = n2, s0 = (long long)n1 * n2;
-        const double ih2 = 0.5 * D.inv_h;
-        const double* __restrict__ alpha = D.alpha;
-        double* __restrict__ force = D.force;
+        const unsigned n0 = (unsigned)D.g.n[0], n1 = (unsigned)D.g.n[1], n2 = (unsigned)D.g.n[2];
         const long long kb = fr.key_base(b);
-        const long long col = gcol - fr.col_base(b);
-        const int i = (int)(col / n1), j = (int)(col - (long long)i * n1);
-        for (int k0 = 0; k0 < n2; k0 += kThreads) {
-            const int k = k0 + (int)threadIdx.x;
-            const bool valid = k < n2;
-            const long long key = col * n2 + k;
-            double axp = 0.0, axm = 0.0, ayp = 0.0, aym = 0.0, azp = 0.0, azm = 0.0;
-            if (valid) {
-                if (i + 1 < n0) axp = alpha[key + s0];
-                if (i > 0) axm = alpha[key - s0];
-                if (j + 1 < n1) ayp = alpha[key + s1];
-                if (j > 0) aym = alpha[key - s1];
-                if (k + 1 < n2) azp = alpha[key + 1];
-                if (k > 0) azm = alpha[key - 1];
+        const unsigned key = (unsigned)(gkey - kb);  // a front's keys fit 32 bits
+        const unsigned col = key / n2, k = key - col * n2;
+        const unsigned i = col / n1, j = col - i * n1;
+        const long long s0 = (long long)n1 * n2, s1 = n2;
+        const int c[3] = {(int)i, (int)j, (int)k}, n[3] = {(int)n0, (int)n1, (int)n2};
+        const long long st[3] = {s0, s1, 1};
+        if (task == 0) {
+            const long long NC = (long long)n0 * n1 * n2;
+            const double* __restrict__ alpha = D.alpha;
+            double a[6];
+#pragma unroll
+            for (int e = 0; e < 6; e++) {
+                const int ax = e >> 1, sg = (e & 1) ? -1 : 1;
+                a[e] = (c[ax] + sg >= 0 && c[ax] + sg < n[ax]) ? alpha[key + sg * st[ax]] : 0.0;
             }
-            const bool flat = __double_as_longlong(axp) == __double_as_longlong(axm) &&
-                              __double_as_longlong(ayp) == __double_as_longlong(aym) &&
-                              __double_as_longlong(azp) == __double_as_longlong(azm);
-            bool to_ring = false;
-            if (__all_sync(0xffffffffu, flat)) {
-                if (valid) {
-                    force[key] = 0.0;
-                    force[NC + key] = 0.0;
-                    force[2 * NC + key] = 0.0;
-                }
-            } else if (valid) {
-                const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
-                double kp = 0.0;
-                if (gx != 0.0 || gy != 0.0 || gz != 0.0) {
-                    const int m = idx_map[kb + key];
-                    if (m >= 0)
-                        kp = kappa[m];
-                    else
-                        to_ring = true;
-                }
-                if (!to_ring) {
-                    const double f = sigma * kp;
-                    force[key] = f * gx;
-                    force[NC + key] = f * gy;
-                    force[2 * NC + key] = f * gz;
-                }
-            }
-            // append this warp's ring cells (batch-global keys) with one atomic
-            const unsigned bal = __ballot_sync(0xffffffffu, to_ring);
-            if (bal) {
-                unsigned base = 0;
-                if (lane == 0) base = atomicAdd(nring, (unsigned)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (to_ring) {
-                    const unsigned pos = base + __popc(bal & ((1u << lane) - 1u));
-                    if (pos < ring_cap)
-                        ring[pos] = (unsigned)(kb + key);
-                    else
-                        ft_flag(ctr, FT_ST_CAPACITY);
-                }
-            }
+            const double ih2 = 0.5 * D.inv_h;
+            const double f = sigma * kappa[m];
+            double* __restrict__ force = D.force;
+            force[key] = f * ((a[0] - a[1]) * ih2);
+            force[NC + key] = f * ((a[2] - a[3]) * ih2);
+            force[2 * NC + key] = f * ((a[4] - a[5]) * ih2);
+            continue;
         }
+        const int e = task - 1, ax = e >> 1, sg = (e & 1) ? -1 : 1;
+        if (c[ax] + sg < 0 || c[ax] + sg >= n[ax]) continue;
+        const long long q = (long long)key + sg * st[ax];
+        if (idx_map[kb + q] >= 0) continue;
+        // the interfacial face neighbours of q: is this cell the smallest key?
+        bool own = true;
+        int cq[3] = {c[0], c[1], c[2]};
+        cq[ax] += sg;
+        for (int e2 = 0; e2 < 6 && own; e2++) {
+            const int ax2 = e2 >> 1, sg2 = (e2 & 1) ? -1 : 1;
+            if (cq[ax2] + sg2 < 0 || cq[ax2] + sg2 >= n[ax2]) continue;
+            const long long r = q + sg2 * st[ax2];
+            if (r < (long long)key && idx_map[kb + r] >= 0) own = false;
+        }
+        if (!own) continue;
+        const unsigned pos = atomicAdd(nring, 1u);
+        if (pos < ring_cap)
+            ring[pos] = (unsigned)(kb + q);
+        else
+            ft_flag(ctr, FT_ST_CAPACITY);
     }
 }
 
@@ -115,9 +134,10 @@ __global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int*
         const double* __restrict__ alpha = D.alpha;
         const long long kb = fr.key_base(b);
         const long long key = gkey - kb;
-        const int k = (int)(key % n2);
-        const int j = (int)((key / n2) % n1);
-        const int i = (int)(key / s0);
+        const unsigned ukey = (unsigned)key, ucol = ukey / (unsigned)n2;
+        const int k = (int)(ukey - ucol * (unsigned)n2);
+        const int i = (int)(ucol / (unsigned)n1);
+        const int j = (int)(ucol - (unsigned)i * (unsigned)n1);
         int q[26];
 #pragma unroll
         for (int c = 0; c < 26; c++) {
@@ -270,9 +290,15 @@ cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const do
     unsigned* ring = ws->keys[ws->sorted_buf ^ 1];
     unsigned* nring = &ws->ctr->pad;
     cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
+    if constexpr (std::is_same<F, FrontsOne>::value) {
+        cudaMemsetAsync(fr.d0.force, 0, 3 * sizeof(double) * (size_t)fr.ncells, s);
+    } else {
+        count_launches(1);
+        k_zero_force<F><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr);
+    }
     count_launches(2);
-    k_csf_dense<F><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, ring, nring,
-                                                                        ws->max_cand, ws->ctr);
+    k_csf_cells<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, p->sigma, ws->cells, ws->idx_map, kappa, ring, nring,
+                                                         ws->max_cand, ws->ctr);
     k_csf_ring<F><<<ws->sm_count * 4, 128, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, normal, ring, nring,
                                                    ws->max_cand);
     return cudaGetLastError();
