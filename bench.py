@@ -34,6 +34,7 @@ FLOPS_PER_FIT_PAIR = 130.0   # per (cell, fragment-in-support) pair of the volum
 FLOPS_PER_FIT_SOLVE = 150.0  # per cell: the 6x6 solve
 FP64_PEAK_TFLOPS = 1.25      # GB300 nominal float64 (profiling recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz
+PARAB_FP64_FLOPS_PER_CELL = None  # FP64 operations per cell of k_parab_ppic on this workload (ncu count)
 
 
 def parse():
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager launches instead of one CUDA graph per step")
     ap.add_argument("--phase-steps", type=int, default=20, help="eager steps timed per phase")
+    ap.add_argument("--paraboloid-reps", type=int, default=5,
+                    help="timed calls of front_volume_fraction_ppic (the paper's own alpha) on the step's fits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the batched form (512 fronts); 0: skip")
@@ -413,6 +416,9 @@ def run_ours(a):
     e2e_max = allmax(ws, e2e_ms)
     e2e_value = allsum(ws, cells_per_step * a.e2e_steps) / (e2e_max * 1e-3)
 
+    # the paper's own indicator on the same fits: alpha_P, surface-averaged kappa and normal
+    parab = measure_paraboloid(fcs, counts, a.paraboloid_reps, flush, stream) if a.paraboloid_reps > 0 else None
+
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "interfacial cells/s", "n_gpus": ws,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(tmax / a.steps, 4),
@@ -433,6 +439,7 @@ def run_ours(a):
         "roofline": roof,
         "alt_precision": alt,
         "same_workload_as_one_batch": one_batch,
+        "paraboloid": parab,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps},
         "gpu_launches": int(r["launches"]),
@@ -455,6 +462,55 @@ def run_ours(a):
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_paraboloid(fcs, counts, reps, flush, stream):
+    """front_volume_fraction_ppic on the fits of the last step of every front:
+    per interfacial cell the cell-below-paraboloid volume, the surface area and
+    the surface-averaged curvature and normal (one FP64 thread per cell)."""
+    import torch
+    from paper_2505_06932_gb300 import _front as F
+
+    outs = []
+    for fc in fcs:
+        cap = fc.coeffs.shape[0]
+        dev = fc.coeffs.device
+        outs.append(dict(k=torch.empty(cap, dtype=torch.float64, device=dev),
+                         n=torch.empty((cap, 3), dtype=torch.float64, device=dev),
+                         a=torch.empty(cap, dtype=torch.float64, device=dev),
+                         s=torch.empty(cap, dtype=torch.int8, device=dev)))
+
+    def call():
+        for fc, o in zip(fcs, outs):
+            F.front_volume_fraction_ppic(fc.ws, fc.coeffs, fc.alpha, o["k"], o["n"], o["a"], o["s"])
+
+    call()
+    torch.cuda.synchronize()
+    if any(fc.ws.status() for fc in fcs):
+        raise RuntimeError("front_volume_fraction_ppic: device status")
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = sum(ms) / len(ms)
+    cells = sum(c["M"] for c in counts)
+    misses = sum(int((o["s"][:c["M"]] != 0).sum()) for o, c in zip(outs, counts))
+    roof = None
+    if PARAB_FP64_FLOPS_PER_CELL:
+        ach = PARAB_FP64_FLOPS_PER_CELL * cells / (t * 1e-3) / 1e12
+        roof = {"kernel": "k_parab_ppic", "bound": "alu", "achieved": round(ach, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "flops_source": "FP64 operations per cell counted by ncu on this workload "
+                                "(profiles/k_parab_ppic_two_fronts_128.md)",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)"}
+    return {"call": "front_volume_fraction_ppic", "cells_per_call": cells, "ms_per_call": round(t, 4),
+            "cells_per_s": round(cells / (t * 1e-3), 1), "surface_misses": misses, "reps": reps,
+            "timing": "CUDA events around both fronts' calls, L2 flushed before each", "roofline": roof}
 
 
 def device_faces(f, dev):

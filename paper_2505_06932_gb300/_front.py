@@ -104,6 +104,10 @@ def lib():
                 "front_advect_rk4_batch": (I32, [P, P]),
                 "front_face_force": (I32, [P, P, P, P, P, P, P, P, P]),
                 "front_face_force_batch": (I32, [P, P, P, P, P]),
+                "front_paraboloid_cells": (I32, [P, P, I64, P, P, P, P, P, P]),
+                "front_ppic_frame": (I32, [P, I64, P, P]),
+                "front_volume_fraction_ppic": (I32, [P, P, I64, P, P, P, P, P, P]),
+                "front_volume_fraction_ppic_batch": (I32, [P, P, I64, P, P, P, P, P]),
                 "ft_rough_create": (I32, [C.POINTER(P), I64, I64, I32, C.POINTER(C.c_size_t)]),
                 "ft_rough_destroy": (I32, [P]),
                 "ft_rough_status": (I32, [P, P, C.POINTER(C.c_uint32)]),
@@ -318,6 +322,49 @@ def front_face_force_batch(ws: "BatchWorkspace", params: FtParams, kappa, normal
     _check(lib().front_face_force_batch(ws.handle, C.byref(params), _ptr(kappa, torch.float64, "kappa"),
                                         _ptr(normal, torch.float64, "normal"), _stream(stream)),
            "front_face_force_batch")
+
+
+FT_PARAB_MISS = 0x1
+
+
+def front_paraboloid_cells(frame, coeffs, alpha, area=None, kappa=None, normal=None, status=None, stream=None):
+    """alpha = V_P / V_C, surface area, surface-averaged curvature and normal
+    of the paraboloids coeffs (m, 6) in the frames frame (m, 9) (cell units)."""
+    m = frame.shape[0]
+    if coeffs.shape[0] != m or alpha.shape[0] < m:
+        raise FrontError("frame, coeffs and alpha must describe the same cells")
+    _check(lib().front_paraboloid_cells(_ptr(frame, torch.float64, "frame"), _ptr(coeffs, torch.float64, "coeffs"), m,
+                                        _ptr(alpha, torch.float64, "alpha"), _ptr(area, torch.float64, "area"),
+                                        _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
+                                        _ptr(status, torch.int8, "status"), _stream(stream)),
+           "front_paraboloid_cells")
+
+
+def front_ppic_frame(ws, frame, stream=None):
+    """The (t1, t2, n) frame of every interfacial cell of the last PPIC fit."""
+    _check(lib().front_ppic_frame(ws.handle, frame.shape[0], _ptr(frame, torch.float64, "frame"), _stream(stream)),
+           "front_ppic_frame")
+
+
+def front_volume_fraction_ppic(ws, coeffs, alpha, kappa=None, normal=None, area=None, status=None, stream=None):
+    """alpha_P of the fitted paraboloids into alpha at the interfacial cells, and
+    the surface-averaged kappa, normal and area per interfacial cell."""
+    cap = coeffs.shape[0]
+    _check(lib().front_volume_fraction_ppic(ws.handle, _ptr(coeffs, torch.float64, "coeffs"), cap,
+                                            _ptr(alpha, torch.float64, "alpha"), _ptr(kappa, torch.float64, "kappa"),
+                                            _ptr(normal, torch.float64, "normal"), _ptr(area, torch.float64, "area"),
+                                            _ptr(status, torch.int8, "status"), _stream(stream)),
+           "front_volume_fraction_ppic")
+
+
+def front_volume_fraction_ppic_batch(ws, coeffs, kappa=None, normal=None, area=None, status=None, stream=None):
+    cap = coeffs.shape[0]
+    _check(lib().front_volume_fraction_ppic_batch(ws.handle, _ptr(coeffs, torch.float64, "coeffs"), cap,
+                                                  _ptr(kappa, torch.float64, "kappa"),
+                                                  _ptr(normal, torch.float64, "normal"),
+                                                  _ptr(area, torch.float64, "area"), _ptr(status, torch.int8, "status"),
+                                                  _stream(stream)),
+           "front_volume_fraction_ppic_batch")
 
 
 def front_interp_velocity(grid, U, V, W, verts, vel, stream=None):

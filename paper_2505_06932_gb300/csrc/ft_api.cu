@@ -284,6 +284,7 @@ int ft_batch_set(ft_workspace* ws, int32_t nf, const ft_batch_front* fr, void* s
     }
     ws->ncells = cells;
     ws->ncols = cols;
+    ws->fitted = false;
     ws->nt_total = nt;
     ws->nv_total = nv;
     ws->key_bits = key_bits_for(cells);
@@ -343,6 +344,7 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     if (e == cudaSuccess) e = ft::launch_rle(ws, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
+    ws->fitted = false;
     return cuda_err(e);
 }
 
@@ -358,7 +360,50 @@ int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint
     if (!ws || !params_ok(p) || cap < 0 || !cell_keys || !kappa || !normal || !fit_status) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_ppic(ws, p, cap, cell_keys, kappa, normal, coeffs, fit_status, as_stream(stream)));
+    const cudaError_t e = ft::launch_ppic(ws, p, cap, cell_keys, kappa, normal, coeffs, fit_status, as_stream(stream));
+    ws->fitted = (e == cudaSuccess);
+    return cuda_err(e);
+}
+
+int front_paraboloid_cells(const double* frame, const double* coeffs, int64_t m, double* alpha, double* area,
+                           double* kappa, double* normal, int8_t* status, void* stream) {
+    if (m < 0 || (m > 0 && (!frame || !coeffs || !alpha))) return FT_ERR_ARG;
+    if (m == 0) return FT_OK;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, frame) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return FT_ERR_ARG;
+    }
+    if (cudaSetDevice(at.device) != cudaSuccess) return FT_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, at.device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_parab_cells(frame, coeffs, m, alpha, area, kappa, normal, status, sms,
+                                           as_stream(stream)));
+}
+
+int front_ppic_frame(ft_workspace* ws, int64_t cap, double* frame, void* stream) {
+    if (!ws || cap < 0 || !frame) return FT_ERR_ARG;
+    if (!ws->binned || !ws->fitted) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_ppic_frame(ws, cap, frame, as_stream(stream)));
+}
+
+int front_volume_fraction_ppic(ft_workspace* ws, const double* coeffs, int64_t cap, double* alpha, double* kappa,
+                               double* normal, double* area, int8_t* status, void* stream) {
+    if (!ws || ws->batch || cap < 0 || !coeffs || !alpha) return FT_ERR_ARG;
+    if (!ws->binned || !ws->fitted) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_parab_ppic(ws, coeffs, cap, alpha, area, kappa, normal, status, as_stream(stream)));
+}
+
+int front_volume_fraction_ppic_batch(ft_workspace* ws, const double* coeffs, int64_t cap, double* kappa,
+                                     double* normal, double* area, int8_t* status, void* stream) {
+    if (!ws || !ws->batch || cap < 0 || !coeffs) return FT_ERR_ARG;
+    if (!ws->binned || !ws->fitted) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++)
+        if (!ws->h_fdesc[b].alpha) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_parab_ppic_batch(ws, coeffs, cap, area, kappa, normal, status, as_stream(stream)));
 }
 
 int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
@@ -396,6 +441,7 @@ int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream) {
     if (e == cudaSuccess) e = ft::launch_rle(ws, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
+    ws->fitted = false;
     return cuda_err(e);
 }
 

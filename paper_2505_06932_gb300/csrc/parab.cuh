@@ -1,0 +1,492 @@
+// parab.cuh -- the cut-cell quantities of a fitted paraboloid (Sec. 3.2):
+// with z = P(x, y) = a0 + a1 x + a2 y + a3 x^2 + a4 x y + a5 y^2 in the cell
+// frame [t1 t2 n] (origin at the cell centre, lengths in cell widths, so the
+// cell is [-1/2, 1/2]^3):
+//   V  = |{X in cell : n.X <= P(t1.X, t2.X)}|      (alpha = V_P / V_C = V)
+//   A  = int_{S in cell} dA,   K = int_{S in cell} kappa dA   (kappa = div n)
+//   N  = int_{S in cell} n dA                      (S the surface z = P)
+//
+// The paper takes these from closed forms obtained by repeated use of the
+// divergence theorem (Evrard et al. 2023, not reproduced); here:
+//  * V: with Fv = (0, 0, z - P) (div Fv = 1, Fv = 0 on S) the divergence
+//    theorem over the part of the cell below S leaves only the cell faces:
+//    V = -sum_faces (nu_f . n) int_face max(F, 0) dA, F = P - z a quadratic in
+//    the face's two coordinates.
+//  * A, K, N: integrals over the parameter domain D = {(x, y) : the surface
+//    point lies in the cell} with dA = W dx dy, W = sqrt(1 + Px^2 + Py^2) and
+//    n dA = (-Px t1 - Py t2 + n) dx dy.  (N integrated over the surface keeps
+//    its relative accuracy on small patches, which the equivalent face form,
+//    differences of face areas of order one, would not.)
+// Every 2D integral is iterated: the inner direction exactly (the set where a
+// quadratic is positive, from its roots, and a polynomial antiderivative) for
+// V, by Gauss-Legendre on exact intervals for A, K, N.  The outer direction is
+// cut where the inner set changes (roots crossing the square's edges, the
+// surface crossing cube edges) and at the branch points of the inner roots
+// (zeros of their discriminants; the real parts of complex pairs); each piece
+// is integrated by Gauss-Legendre under a map that is flat at ends holding a
+// branch point (turning a square-root end into an analytic function) and cut
+// geometrically towards nearby branch points (see graded()).
+//
+// Host and device code: one definition for the kernels; the host build only
+// serves offline checks of the quadrature.
+#pragma once
+
+#include <math.h>
+
+#ifdef __CUDACC__
+#define PB_HD __host__ __device__ __forceinline__
+#else
+#define PB_HD inline
+#endif
+#ifdef __CUDA_ARCH__
+#define PB_RSQRT(x) rsqrt(x)
+#else
+#define PB_RSQRT(x) (1.0 / sqrt(x))
+#endif
+
+namespace parab {
+
+constexpr int kNS = 16;  // nodes per outer piece
+constexpr int kNX = 12;  // nodes per inner interval of the surface integrals
+constexpr double kR = 0.86602540378443865;  // |x|, |y| <= sqrt(3)/2 on the cell
+
+// Gauss-Legendre rules on [0, 1] under four maps s(u) of the unit interval:
+// m = 0 linear, 1 s = u^2 (flat at 0), 2 s = 1 - (1 - u)^2 (flat at 1),
+// 3 s = 3u^2 - 2u^3 (flat at both ends); node s(u_k), weight w_k s'(u_k).
+struct Rule {
+    double os[4][kNS], ow[4][kNS];
+    double ix[kNX], iw[kNX];
+};
+
+struct Out {
+    double V, A, K, N[3];
+};
+
+// real roots of c2 t^2 + c1 t + c0 strictly inside (lo, hi), appended at r[n..]
+PB_HD int roots_in(double c2, double c1, double c0, double lo, double hi, double* r, int n) {
+    if (c2 == 0.0) {
+        if (c1 != 0.0) {
+            const double t = -c0 / c1;
+            if (t > lo && t < hi) r[n++] = t;
+        }
+        return n;
+    }
+    const double disc = c1 * c1 - 4.0 * c2 * c0;
+    if (disc < 0.0) return n;
+    const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
+    const double t1 = q / c2;
+    if (t1 > lo && t1 < hi) r[n++] = t1;
+    if (q != 0.0) {
+        const double t2 = c0 / q;
+        if (t2 > lo && t2 < hi) r[n++] = t2;
+    }
+    return n;
+}
+
+// roots of c2 t^2 + c1 t + c0 as (re, im >= 0) pairs appended at re/im[n..]
+PB_HD int croots(double c2, double c1, double c0, double* re, double* im, int n) {
+    if (c2 == 0.0) {
+        if (c1 != 0.0) {
+            re[n] = -c0 / c1;
+            im[n++] = 0.0;
+        }
+        return n;
+    }
+    const double disc = c1 * c1 - 4.0 * c2 * c0;
+    if (disc >= 0.0) {
+        const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
+        re[n] = q / c2;
+        im[n++] = 0.0;
+        if (q != 0.0) {
+            re[n] = c0 / q;
+            im[n++] = 0.0;
+        }
+    } else {
+        re[n] = -c1 / (2.0 * c2);
+        im[n++] = sqrt(-disc) / (2.0 * fabs(c2));
+    }
+    return n;
+}
+
+PB_HD void sort_small(double* v, int n) {
+    for (int i = 1; i < n; i++) {
+        const double x = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > x) {
+            v[j + 1] = v[j];
+            j--;
+        }
+        v[j + 1] = x;
+    }
+}
+
+// Integrate a function that is analytic inside [y0, y1] except for branch
+// points at (sre, sim).  A branch point at an end is taken by a map flat at
+// that end; towards an end that has other branch points at a distance d below
+// half the length, the piece is cut at d, 3d, 7d, ... from that end, so that
+// every sub-piece is at least as far from them as it is long (Gauss-Legendre
+// then converges like 5.8^-2n or faster).  f(y, w) accumulates w * integrand(y).
+template <class Fn>
+PB_HD void graded(double y0, double y1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
+    const double L = y1 - y0, eps = 1e-12 * L;
+    double d0 = 2.0 * L, d1 = 2.0 * L;
+    bool s0 = false, s1 = false;
+    for (int i = 0; i < ns; i++) {
+        const double e0 = hypot(sre[i] - y0, sim[i]), e1 = hypot(sre[i] - y1, sim[i]);
+        if (e0 <= eps)
+            s0 = true;
+        else if (e0 < d0)
+            d0 = e0;
+        if (e1 <= eps)
+            s1 = true;
+        else if (e1 < d1)
+            d1 = e1;
+    }
+    auto sub = [&](double a, double b, bool fa, bool fb) {
+        const int m = (fa ? 1 : 0) + (fb ? 2 : 0);
+        const double h = b - a;
+        for (int k = 0; k < kNS; k++) f(a + h * R.os[m][k], h * R.ow[m][k]);
+    };
+    double a = y0, b = y1;
+    bool fa = s0, fb = s1;
+    if (d0 < 0.5 * L)
+        for (double st = d0; a + st < y0 + 0.5 * L; st *= 2.0) {
+            sub(a, a + st, fa, false);
+            fa = false;
+            a += st;
+        }
+    if (d1 < 0.5 * L)
+        for (double st = d1; b - st > a && b - st > y1 - 0.5 * L; st *= 2.0) {
+            sub(b - st, b, false, fb);
+            fb = false;
+            b -= st;
+        }
+    sub(a, b, fa, fb);
+}
+
+// the same cutting for the inner x integrals (no branch point at the ends)
+template <class Fn>
+PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
+    const double L = x1 - x0;
+    double d0 = 2.0 * L, d1 = 2.0 * L;
+    for (int i = 0; i < ns; i++) {
+        d0 = fmin(d0, hypot(sre[i] - x0, sim[i]));
+        d1 = fmin(d1, hypot(sre[i] - x1, sim[i]));
+    }
+    auto sub = [&](double a, double b) {
+        const double h = b - a;
+        for (int k = 0; k < kNX; k++) f(a + h * R.ix[k], h * R.iw[k]);
+    };
+    double a = x0, b = x1;
+    if (d0 < 0.5 * L)
+        for (double st = d0; a + st < x0 + 0.5 * L; st *= 2.0) {
+            sub(a, a + st);
+            a += st;
+        }
+    if (d1 < 0.5 * L)
+        for (double st = d1; b - st > a && b - st > x1 - 0.5 * L; st *= 2.0) {
+            sub(b - st, b);
+            b -= st;
+        }
+    sub(a, b);
+}
+
+// int_{-1/2}^{1/2} max(f, 0) du for f(u) = al u^2 + be u + ga
+PB_HD double row_positive(double al, double be, double ga) {
+    double p[4];
+    p[0] = -0.5;
+    int np = roots_in(al, be, ga, -0.5, 0.5, p, 1);
+    if (np == 3 && p[1] > p[2]) {
+        const double t = p[1];
+        p[1] = p[2];
+        p[2] = t;
+    }
+    p[np++] = 0.5;
+    double I = 0.0;
+    for (int i = 0; i + 1 < np; i++) {
+        const double u0 = p[i], u1 = p[i + 1], m = 0.5 * (u0 + u1);
+        if ((al * m + be) * m + ga > 0.0) {
+            // antiderivative u (ga + u (be/2 + u al/3))
+            const double F1 = u1 * (ga + u1 * (0.5 * be + u1 * (al * (1.0 / 3.0))));
+            const double F0 = u0 * (ga + u0 * (0.5 * be + u0 * (al * (1.0 / 3.0))));
+            I += F1 - F0;
+        }
+    }
+    return I;
+}
+
+// int over the face [-1/2, 1/2]^2 of max(F, 0), with F(u, v) = Auu u^2 +
+// Auv u v + Avv v^2 + Bu u + Bv v + C.  The row integral is analytic in v
+// except where a root crosses u = +-1/2 (kinks: cut there) and at the branch
+// points of the roots, the zeros of the discriminant in u (cut at real ones
+// and at the real part of a complex pair; the pieces are graded towards them).
+PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double Bv, double C, const Rule& R) {
+    double sre[2], sim[2];
+    const int ns = croots(Auv * Auv - 4.0 * Auu * Avv, 2.0 * Auv * Bu - 4.0 * Auu * Bv, Bu * Bu - 4.0 * Auu * C, sre,
+                          sim, 0);
+    double p[8];
+    p[0] = -0.5;
+    int np = 1;
+    np = roots_in(Avv, Bv + 0.5 * Auv, C + 0.5 * Bu + 0.25 * Auu, -0.5, 0.5, p, np);
+    np = roots_in(Avv, Bv - 0.5 * Auv, C - 0.5 * Bu + 0.25 * Auu, -0.5, 0.5, p, np);
+    bool real_branch = false;
+    for (int i = 0; i < ns; i++) real_branch |= (sim[i] == 0.0 && sre[i] > -0.5 && sre[i] < 0.5);
+    if (np == 1 && !real_branch) {
+        // no root crosses an edge and the number of real roots per row never
+        // changes: every row has as many roots inside as the middle row; none
+        // there means that F keeps one sign on the whole face
+        double r[2];
+        if (roots_in(Auu, Bu, C, -0.5, 0.5, r, 0) == 0) return (C > 0.0) ? C + (Auu + Avv) * (1.0 / 12.0) : 0.0;
+    }
+    for (int i = 0; i < ns; i++)
+        if (sre[i] > -0.5 && sre[i] < 0.5) p[np++] = sre[i];
+    p[np++] = 0.5;
+    sort_small(p, np);
+    double I = 0.0;
+    for (int i = 0; i + 1 < np; i++) {
+        if (!(p[i + 1] > p[i])) continue;
+        graded(p[i], p[i + 1], sre, sim, ns, R,
+               [&](double v, double w) { I += w * row_positive(Auu, Auv * v + Bu, (Avv * v + Bv) * v + C); });
+    }
+    return I;
+}
+
+// The surface in world (cell) coordinates: X_d(x, y) = e2 x^2 + (e1c + e1y y) x
+// + (e0c + e0y y + e0yy y^2), one row per axis d.
+struct Surf {
+    double e2[3], e1c[3], e1y[3], e0c[3], e0y[3], e0yy[3];
+};
+
+PB_HD bool on_cell(const Surf& S, double x, double y) {
+    for (int d = 0; d < 3; d++) {
+        const double X = S.e2[d] * x * x + (S.e1c[d] + S.e1y[d] * y) * x + (S.e0c[d] + (S.e0y[d] + S.e0yy[d] * y) * y);
+        if (!(fabs(X) <= 0.5)) return false;
+    }
+    return true;
+}
+
+// Inside a strip of y between breakpoints the x-intervals of D keep their
+// structure: each end is the same root of the same curve.  A tag names it:
+// 4 d + 2 l + b for the smaller (b = 0) or larger (b = 1) root of X_d = -1/2
+// (l = 0) or +1/2 (l = 1) (the only root if the curve is linear in x), and
+// -1 / -2 for the range ends -kR / kR.
+PB_HD double tagged_root(const Surf& S, int tag, double y) {
+    if (tag == -1) return -kR;
+    if (tag == -2) return kR;
+    const int d = tag >> 2, l = (tag >> 1) & 1, b = tag & 1;
+    const double c2 = S.e2[d], c1 = S.e1c[d] + S.e1y[d] * y;
+    const double c0 = S.e0c[d] + (S.e0y[d] + S.e0yy[d] * y) * y - (l ? 0.5 : -0.5);
+    if (c2 == 0.0) return -c0 / c1;
+    const double q = -0.5 * (c1 + copysign(sqrt(fmax(c1 * c1 - 4.0 * c2 * c0, 0.0)), c1));
+    const double r1 = q / c2, r2 = (q != 0.0) ? c0 / q : r1;
+    return b ? fmax(r1, r2) : fmin(r1, r2);
+}
+
+// the x-intervals of D at y (at most 7) as the tags of their ends
+PB_HD int row_plan(const Surf& S, double y, int* tlo, int* thi) {
+    double p[14];
+    int tg[14];
+    p[0] = -kR;
+    tg[0] = -1;
+    int np = 1;
+    for (int d = 0; d < 3; d++) {
+        const double e1 = S.e1c[d] + S.e1y[d] * y, e0 = S.e0c[d] + (S.e0y[d] + S.e0yy[d] * y) * y;
+        for (int l = 0; l < 2; l++) {
+            const double c0 = e0 - (l ? 0.5 : -0.5);
+            double r[2];
+            const int nr = roots_in(S.e2[d], e1, c0, -kR, kR, r, 0);
+            if (nr == 1) {
+                // one root in range: which one of the pair (for a quadratic)
+                int b = 0;
+                if (S.e2[d] != 0.0) b = (r[0] == tagged_root(S, 4 * d + 2 * l + 1, y)) ? 1 : 0;
+                p[np] = r[0];
+                tg[np++] = 4 * d + 2 * l + b;
+            } else if (nr == 2) {
+                const bool sw = r[0] > r[1];
+                p[np] = sw ? r[1] : r[0];
+                tg[np++] = 4 * d + 2 * l;
+                p[np] = sw ? r[0] : r[1];
+                tg[np++] = 4 * d + 2 * l + 1;
+            }
+        }
+    }
+    p[np] = kR;
+    tg[np++] = -2;
+    for (int i = 1; i < np; i++) {  // insertion sort carrying the tags
+        const double x = p[i];
+        const int t = tg[i];
+        int j = i - 1;
+        while (j >= 0 && p[j] > x) {
+            p[j + 1] = p[j];
+            tg[j + 1] = tg[j];
+            j--;
+        }
+        p[j + 1] = x;
+        tg[j + 1] = t;
+    }
+    int ni = 0;
+    for (int i = 0; i + 1 < np; i++) {
+        if (!(p[i + 1] > p[i])) continue;
+        if (!on_cell(S, 0.5 * (p[i] + p[i + 1]), y)) continue;
+        if (ni > 0 && thi[ni - 1] == tg[i]) {
+            thi[ni - 1] = tg[i + 1];  // a split by a root that does not bound D
+        } else {
+            tlo[ni] = tg[i];
+            thi[ni] = tg[i + 1];
+            ni++;
+        }
+    }
+    return ni;
+}
+
+PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3], const double a[6], const Rule& R,
+                      Out& o) {
+    // F(X) = P(t1.X, t2.X) - n.X = a0 + g.X + X^T H X
+    double g[3], H[3][3];
+    for (int i = 0; i < 3; i++) {
+        g[i] = a[1] * t1[i] + a[2] * t2[i] - n[i];
+        for (int j = 0; j < 3; j++)
+            H[i][j] = a[3] * t1[i] * t1[j] + 0.5 * a[4] * (t1[i] * t2[j] + t2[i] * t1[j]) + a[5] * t2[i] * t2[j];
+    }
+    o.V = 0.0;
+    for (int d = 0; d < 3; d++) {
+        const int p = (d + 1) % 3, q = (d + 2) % 3;
+        for (int s = -1; s <= 1; s += 2) {
+            const double I = face_positive(H[p][p], 2.0 * H[p][q], H[q][q], g[p] + s * H[p][d], g[q] + s * H[q][d],
+                                           a[0] + 0.5 * s * g[d] + 0.25 * H[d][d], R);
+            o.V -= s * n[d] * I;
+        }
+    }
+
+    // surface integrals over D
+    Surf S;
+    for (int d = 0; d < 3; d++) {
+        S.e2[d] = n[d] * a[3];
+        S.e1c[d] = t1[d] + n[d] * a[1];
+        S.e1y[d] = n[d] * a[4];
+        S.e0c[d] = n[d] * a[0];
+        S.e0y[d] = t2[d] + n[d] * a[2];
+        S.e0yy[d] = n[d] * a[5];
+    }
+    double yb[40], sre[12], sim[12];
+    yb[0] = -kR;
+    int nb = 1, ns = 0;
+    // branch points of the x-roots: zeros of each curve's discriminant in x
+    // (X_d = +-1/2 has a double root); real ones and the real parts of complex
+    // pairs cut the y range
+    for (int d = 0; d < 3; d++)
+        for (int s = -1; s <= 1; s += 2) {
+            const int n0 = ns;
+            ns = croots(S.e1y[d] * S.e1y[d] - 4.0 * S.e2[d] * S.e0yy[d],
+                        2.0 * S.e1c[d] * S.e1y[d] - 4.0 * S.e2[d] * S.e0y[d],
+                        S.e1c[d] * S.e1c[d] - 4.0 * S.e2[d] * (S.e0c[d] - 0.5 * s), sre, sim, ns);
+            for (int i = n0; i < ns; i++)
+                if (sre[i] > -kR && sre[i] < kR) yb[nb++] = sre[i];
+        }
+    // y where the surface crosses one of the twelve cube edges
+    for (int f = 0; f < 3; f++) {
+        const int d = (f + 1) % 3, e = (f + 2) % 3;
+        for (int s1 = -1; s1 <= 1; s1 += 2)
+            for (int s2 = -1; s2 <= 1; s2 += 2) {
+                const double Xd = 0.5 * s1, Xe = 0.5 * s2;
+                double r[2];
+                const int nr = roots_in(H[f][f], g[f] + 2.0 * (H[f][d] * Xd + H[f][e] * Xe),
+                                        a[0] + g[d] * Xd + g[e] * Xe + H[d][d] * Xd * Xd + 2.0 * H[d][e] * Xd * Xe +
+                                            H[e][e] * Xe * Xe,
+                                        -0.5, 0.5, r, 0);
+                for (int i = 0; i < nr; i++) {
+                    double X[3];
+                    X[f] = r[i];
+                    X[d] = Xd;
+                    X[e] = Xe;
+                    yb[nb++] = t2[0] * X[0] + t2[1] * X[1] + t2[2] * X[2];
+                }
+            }
+    }
+    yb[nb++] = kR;
+    sort_small(yb, nb);
+    double A = 0.0, K = 0.0, Nx = 0.0, Ny = 0.0, Nz = 0.0;
+    const double pxx = 2.0 * a[3], pxy = a[4], pyy = 2.0 * a[5];
+    for (int i = 0; i + 1 < nb; i++) {
+        const double y0 = yb[i], y1 = yb[i + 1];
+        if (!(y1 > y0)) continue;
+        int tlo[7], thi[7];
+        const int ni = row_plan(S, 0.5 * (y0 + y1), tlo, thi);
+        if (ni == 0) continue;  // D does not meet this strip
+        graded(y0, y1, sre, sim, ns, R, [&](double y, double wy) {
+            // W^2 = 1 + px^2 + py^2 is a quadratic in x; its complex zeros are
+            // the branch points (W) and poles (kappa W) of the row integrand
+            const double b1 = a[1] + pxy * y, b2 = a[2] + pyy * y;
+            double xre[2], xim[2];
+            const int nx = croots(pxx * pxx + pxy * pxy, 2.0 * (pxx * b1 + pxy * b2), 1.0 + b1 * b1 + b2 * b2, xre,
+                                  xim, 0);
+            for (int j = 0; j < ni; j++) {
+                const double lo = tagged_root(S, tlo[j], y), hi = tagged_root(S, thi[j], y);
+                if (!(hi > lo)) continue;
+                graded_x(lo, hi, xre, xim, nx, R, [&](double x, double wx) {
+                    const double px = b1 + pxx * x, py = b2 + pxy * x;
+                    const double W2 = 1.0 + px * px + py * py, rW = PB_RSQRT(W2);
+                    const double w = wy * wx;
+                    A += w * (W2 * rW);
+                    // kappa W = -((1 + py^2) pxx - 2 px py pxy + (1 + px^2) pyy) / W^2
+                    K -= w * ((1.0 + py * py) * pxx - 2.0 * px * py * pxy + (1.0 + px * px) * pyy) * (rW * rW);
+                    Nx -= w * px;
+                    Ny -= w * py;
+                    Nz += w;
+                });
+            }
+        });
+    }
+    o.A = A;
+    o.K = K;
+    for (int d = 0; d < 3; d++) o.N[d] = Nx * t1[d] + Ny * t2[d] + Nz * n[d];
+}
+
+// Gauss-Legendre rule of order n on [0, 1] by Newton's iteration on P_n
+inline void gauss_legendre01(int n, double* x, double* w) {
+    for (int i = 0; i < n; i++) {
+        double t = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; k++) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= n; k++) {
+            const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double dp = n * (t * p1 - p0) / (t * t - 1.0);
+        x[i] = 0.5 * (1.0 - t);
+        w[i] = 1.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+inline Rule make_rule() {
+    Rule R;
+    double u[kNS], w[kNS];
+    gauss_legendre01(kNS, u, w);
+    for (int k = 0; k < kNS; k++) {
+        const double v = 1.0 - u[k];
+        R.os[0][k] = u[k];
+        R.ow[0][k] = w[k];
+        R.os[1][k] = u[k] * u[k];
+        R.ow[1][k] = w[k] * 2.0 * u[k];
+        R.os[2][k] = 1.0 - v * v;
+        R.ow[2][k] = w[k] * 2.0 * v;
+        R.os[3][k] = u[k] * u[k] * (3.0 - 2.0 * u[k]);
+        R.ow[3][k] = w[k] * 6.0 * u[k] * v;
+    }
+    gauss_legendre01(kNX, R.ix, R.iw);
+    return R;
+}
+
+}  // namespace parab
