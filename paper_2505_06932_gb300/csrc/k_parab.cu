@@ -1,9 +1,12 @@
 // k_parab.cu -- the paper's own cut-cell quantities from the fitted
 // paraboloids (Sec. 3.2): alpha = V_P / V_C of the cell below its paraboloid,
 // and the curvature and normal averaged over the paraboloid surface inside
-// the cell (parab.cuh has the integration).  One thread per cell: the work
-// per cell is thousands of float64 operations with data-dependent control
-// flow, and float64 work is never repeated across the lanes of a warp.
+// the cell (parab.cuh has the integration).  A group of kG = 8 lanes per cell
+// (four cells per warp): every lane walks the cell's breakpoints and pieces,
+// evaluates every kG-th quadrature node, and the group adds its shares with
+// shuffles.  One thread per cell would leave the GPU nearly empty (a front has
+// tens of thousands of interfacial cells, a few warps per SM) with each thread
+// running a long serial float64 chain.
 //  * k_parab_cells -- from caller-given frames and coefficients (cell units);
 //  * k_parab_ppic<F> -- from the last PPIC fit of a workspace (frame normal
 //    from the stored normal equations, the tangents as the fit built them),
@@ -16,6 +19,8 @@
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kG = 8;                   // lanes per cell
+constexpr int kCellsPerWarp = 32 / kG;  // cells per warp and pass
 
 struct ParabOut {
     double* alpha;  // per cell (k_parab_cells) or nullptr
@@ -36,11 +41,20 @@ __device__ void point_values(const double t1[3], const double t2[3], const doubl
     for (int d = 0; d < 3; d++) nv[d] *= il;
 }
 
-// one cell (cell units): returns alpha; writes area, kbar, nbar and status
-__device__ double parab_one(const double t1[3], const double t2[3], const double n[3], const double a[6],
-                            const parab::Rule& R, double& area, double& kbar, double nb[3], int& st) {
-    parab::Out o;
-    parab::parab_cell(t1, t2, n, a, R, o);
+// this lane's share of a cell, added over the group (all 32 lanes call it)
+__device__ void group_sum(parab::Out& o) {
+#pragma unroll
+    for (int off = kG / 2; off >= 1; off >>= 1) {
+        o.V += __shfl_xor_sync(0xffffffffu, o.V, off);
+        o.A += __shfl_xor_sync(0xffffffffu, o.A, off);
+        o.K += __shfl_xor_sync(0xffffffffu, o.K, off);
+        for (int d = 0; d < 3; d++) o.N[d] += __shfl_xor_sync(0xffffffffu, o.N[d], off);
+    }
+}
+
+// from the cell totals (cell units): returns alpha; writes area, kbar, nbar and status
+__device__ double finish(const double t1[3], const double t2[3], const double n[3], const double a[6],
+                         const parab::Out& o, double& area, double& kbar, double nb[3], int& st) {
     area = o.A;
     const double nl = sqrt(o.N[0] * o.N[0] + o.N[1] * o.N[1] + o.N[2] * o.N[2]);
     if (o.A > 0.0 && nl > 0.0) {
@@ -58,23 +72,35 @@ __device__ double parab_one(const double t1[3], const double t2[3], const double
 __global__ void __launch_bounds__(kThreads) k_parab_cells(const double* __restrict__ frame,
                                                           const double* __restrict__ coeffs, long long m,
                                                           parab::Rule R, ParabOut out) {
-    for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < m; c += (long long)gridDim.x * kThreads) {
+    const int lane = threadIdx.x & 31, g = lane % kG;
+    const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
+    // warp-uniform loop: all 32 lanes reach the shuffles of every pass
+    for (long long base = warp * kCellsPerWarp; base < m; base += nwarps * kCellsPerWarp) {
+        const long long c = base + lane / kG;
         double t1[3], t2[3], n[3], a[6];
-        for (int d = 0; d < 3; d++) {
-            t1[d] = frame[9 * c + d];
-            t2[d] = frame[9 * c + 3 + d];
-            n[d] = frame[9 * c + 6 + d];
+        parab::Out o{0.0, 0.0, 0.0, {0.0, 0.0, 0.0}};
+        if (c < m) {
+            for (int d = 0; d < 3; d++) {
+                t1[d] = frame[9 * c + d];
+                t2[d] = frame[9 * c + 3 + d];
+                n[d] = frame[9 * c + 6 + d];
+            }
+            for (int r = 0; r < 6; r++) a[r] = coeffs[6 * c + r];
+            parab::Split sp{g, kG, 0};
+            parab::parab_cell(t1, t2, n, a, R, sp, o);
         }
-        for (int r = 0; r < 6; r++) a[r] = coeffs[6 * c + r];
-        double area, kbar, nb[3];
-        int st;
-        const double al = parab_one(t1, t2, n, a, R, area, kbar, nb, st);
-        out.alpha[c] = al;
-        if (out.area) out.area[c] = area;
-        if (out.kappa) out.kappa[c] = kbar;
-        if (out.normal)
-            for (int d = 0; d < 3; d++) out.normal[3 * c + d] = nb[d];
-        if (out.status) out.status[c] = (int8_t)st;
+        group_sum(o);
+        if (c < m && g == 0) {
+            double area, kbar, nb[3];
+            int st;
+            out.alpha[c] = finish(t1, t2, n, a, o, area, kbar, nb, st);
+            if (out.area) out.area[c] = area;
+            if (out.kappa) out.kappa[c] = kbar;
+            if (out.normal)
+                for (int d = 0; d < 3; d++) out.normal[3 * c + d] = nb[d];
+            if (out.status) out.status[c] = (int8_t)st;
+        }
     }
 }
 
@@ -88,24 +114,36 @@ __global__ void __launch_bounds__(kThreads) k_parab_ppic(F fr, const ft_cellsys*
         if (blockIdx.x == 0 && threadIdx.x == 0) ft_flag(ctr, FT_ST_CAPACITY);
         return;
     }
-    for (long long m = (long long)blockIdx.x * kThreads + threadIdx.x; m < M; m += (long long)gridDim.x * kThreads) {
+    const int lane = threadIdx.x & 31, g = lane % kG;
+    const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
+    for (long long base = warp * kCellsPerWarp; base < M; base += nwarps * kCellsPerWarp) {
+        const long long m = base + lane / kG;
         double n[3], t1[3], t2[3], a[6];
-        sys_normal(sys[m], fp32 != 0, n);
-        basis<double>(n, t1, t2);
-        for (int r = 0; r < 6; r++) a[r] = coeffs[6 * m + r];
-        double area, kbar, nb[3];
-        int st;
-        const double al = parab_one(t1, t2, n, a, R, area, kbar, nb, st);
-        const long long gkey = cells[m];
-        const int b = fr.by_key(gkey);
-        const ft_fdesc& D = fr.desc(b);
-        const double h = D.g.h;
-        D.alpha[gkey - fr.key_base(b)] = al;
-        if (out.area) out.area[m] = area * h * h;
-        if (out.kappa) out.kappa[m] = kbar * D.inv_h;
-        if (out.normal)
-            for (int d = 0; d < 3; d++) out.normal[3 * m + d] = nb[d];
-        if (out.status) out.status[m] = (int8_t)st;
+        parab::Out o{0.0, 0.0, 0.0, {0.0, 0.0, 0.0}};
+        if (m < M) {
+            sys_normal(sys[m], fp32 != 0, n);
+            basis<double>(n, t1, t2);
+            for (int r = 0; r < 6; r++) a[r] = coeffs[6 * m + r];
+            parab::Split sp{g, kG, 0};
+            parab::parab_cell(t1, t2, n, a, R, sp, o);
+        }
+        group_sum(o);
+        if (m < M && g == 0) {
+            double area, kbar, nb[3];
+            int st;
+            const double al = finish(t1, t2, n, a, o, area, kbar, nb, st);
+            const long long gkey = cells[m];
+            const int b = fr.by_key(gkey);
+            const ft_fdesc& D = fr.desc(b);
+            const double h = D.g.h;
+            D.alpha[gkey - fr.key_base(b)] = al;
+            if (out.area) out.area[m] = area * h * h;
+            if (out.kappa) out.kappa[m] = kbar * D.inv_h;
+            if (out.normal)
+                for (int d = 0; d < 3; d++) out.normal[3 * m + d] = nb[d];
+            if (out.status) out.status[m] = (int8_t)st;
+        }
     }
 }
 
@@ -141,9 +179,9 @@ cudaError_t launch_parab_cells(const double* frame, const double* coeffs, long l
                                double* kappa, double* normal, int8_t* status, int sm_count, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     ParabOut out{alpha, area, kappa, normal, status};
-    const long long blocks = (m + kThreads - 1) / kThreads;
+    const long long blocks = (m * kG + kThreads - 1) / kThreads;
     count_launches(1);
-    k_parab_cells<<<(unsigned)(blocks < 8LL * sm_count ? blocks : 8LL * sm_count), kThreads, 0, s>>>(
+    k_parab_cells<<<(unsigned)(blocks < 16LL * sm_count ? blocks : 16LL * sm_count), kThreads, 0, s>>>(
         frame, coeffs, m, rule(), out);
     return cudaGetLastError();
 }
@@ -153,7 +191,7 @@ static cudaError_t parab_with(ft_workspace* ws, const F& fr, const double* coeff
                               double* kappa, double* normal, int8_t* status, cudaStream_t s) {
     ParabOut out{nullptr, area, kappa, normal, status};
     count_launches(1);
-    k_parab_ppic<F><<<ws->sm_count * 8, kThreads, 0, s>>>(fr, ws->sys, ws->last_precision == FT_FP32C ? 1 : 0,
+    k_parab_ppic<F><<<ws->sm_count * 16, kThreads, 0, s>>>(fr, ws->sys, ws->last_precision == FT_FP32C ? 1 : 0,
                                                           ws->cells, coeffs, cap, ws->ctr, rule(), out);
     return cudaGetLastError();
 }

@@ -62,6 +62,15 @@ struct Out {
     double V, A, K, N[3];
 };
 
+// A cell's quadrature can be shared by G threads: every thread walks the same
+// breakpoints and pieces, numbers the nodes in the same order, and evaluates
+// only the nodes whose number is g modulo G; the G partial results add up to
+// the cell's (G = 1: one thread does everything).
+struct Split {
+    int g, G, next;
+    PB_HD bool mine() { return (next++ % G) == g; }
+};
+
 // real roots of c2 t^2 + c1 t + c0 strictly inside (lo, hi), appended at r[n..]
 PB_HD int roots_in(double c2, double c1, double c0, double lo, double hi, double* r, int n) {
     if (c2 == 0.0) {
@@ -220,7 +229,8 @@ PB_HD double row_positive(double al, double be, double ga) {
 // except where a root crosses u = +-1/2 (kinks: cut there) and at the branch
 // points of the roots, the zeros of the discriminant in u (cut at real ones
 // and at the real part of a complex pair; the pieces are graded towards them).
-PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double Bv, double C, const Rule& R) {
+PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double Bv, double C, const Rule& R,
+                           Split& sp) {
     double sre[2], sim[2];
     const int ns = croots(Auv * Auv - 4.0 * Auu * Avv, 2.0 * Auv * Bu - 4.0 * Auu * Bv, Bu * Bu - 4.0 * Auu * C, sre,
                           sim, 0);
@@ -236,7 +246,8 @@ PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double
         // changes: every row has as many roots inside as the middle row; none
         // there means that F keeps one sign on the whole face
         double r[2];
-        if (roots_in(Auu, Bu, C, -0.5, 0.5, r, 0) == 0) return (C > 0.0) ? C + (Auu + Avv) * (1.0 / 12.0) : 0.0;
+        if (roots_in(Auu, Bu, C, -0.5, 0.5, r, 0) == 0)
+            return (sp.mine() && C > 0.0) ? C + (Auu + Avv) * (1.0 / 12.0) : 0.0;
     }
     for (int i = 0; i < ns; i++)
         if (sre[i] > -0.5 && sre[i] < 0.5) p[np++] = sre[i];
@@ -245,8 +256,9 @@ PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double
     double I = 0.0;
     for (int i = 0; i + 1 < np; i++) {
         if (!(p[i + 1] > p[i])) continue;
-        graded(p[i], p[i + 1], sre, sim, ns, R,
-               [&](double v, double w) { I += w * row_positive(Auu, Auv * v + Bu, (Avv * v + Bv) * v + C); });
+        graded(p[i], p[i + 1], sre, sim, ns, R, [&](double v, double w) {
+            if (sp.mine()) I += w * row_positive(Auu, Auv * v + Bu, (Avv * v + Bv) * v + C);
+        });
     }
     return I;
 }
@@ -265,21 +277,48 @@ PB_HD bool on_cell(const Surf& S, double x, double y) {
     return true;
 }
 
+// The roots of c2 x^2 + c1 x + c0 as an ordered pair (lo <= hi): 2 for a
+// quadratic with a real pair (a negative discriminant that rounding produced
+// next to a double root counts as zero), 1 for a linear equation (lo = hi), 0
+// otherwise.  Tagging and evaluating the ends of D's rows both go through it,
+// so a tag always names the same root whatever the rounding.
+PB_HD int root_pair(double c2, double c1, double c0, bool clamp, double& lo, double& hi) {
+    if (c2 == 0.0) {
+        if (c1 == 0.0) return 0;
+        lo = hi = -c0 / c1;
+        return 1;
+    }
+    double disc = c1 * c1 - 4.0 * c2 * c0;
+    if (disc < 0.0) {
+        if (!clamp) return 0;
+        disc = 0.0;
+    }
+    const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
+    const double r1 = q / c2, r2 = (q != 0.0) ? c0 / q : r1;
+    lo = fmin(r1, r2);
+    hi = fmax(r1, r2);
+    return 2;
+}
+
 // Inside a strip of y between breakpoints the x-intervals of D keep their
 // structure: each end is the same root of the same curve.  A tag names it:
 // 4 d + 2 l + b for the smaller (b = 0) or larger (b = 1) root of X_d = -1/2
 // (l = 0) or +1/2 (l = 1) (the only root if the curve is linear in x), and
 // -1 / -2 for the range ends -kR / kR.
+PB_HD void curve_coeffs(const Surf& S, int d, int l, double y, double& c2, double& c1, double& c0) {
+    c2 = S.e2[d];
+    c1 = S.e1c[d] + S.e1y[d] * y;
+    c0 = S.e0c[d] + (S.e0y[d] + S.e0yy[d] * y) * y - (l ? 0.5 : -0.5);
+}
+
 PB_HD double tagged_root(const Surf& S, int tag, double y) {
     if (tag == -1) return -kR;
     if (tag == -2) return kR;
     const int d = tag >> 2, l = (tag >> 1) & 1, b = tag & 1;
-    const double c2 = S.e2[d], c1 = S.e1c[d] + S.e1y[d] * y;
-    const double c0 = S.e0c[d] + (S.e0y[d] + S.e0yy[d] * y) * y - (l ? 0.5 : -0.5);
-    if (c2 == 0.0) return -c0 / c1;
-    const double q = -0.5 * (c1 + copysign(sqrt(fmax(c1 * c1 - 4.0 * c2 * c0, 0.0)), c1));
-    const double r1 = q / c2, r2 = (q != 0.0) ? c0 / q : r1;
-    return b ? fmax(r1, r2) : fmin(r1, r2);
+    double c2, c1, c0, lo = 0.0, hi = 0.0;
+    curve_coeffs(S, d, l, y, c2, c1, c0);
+    root_pair(c2, c1, c0, true, lo, hi);
+    return b ? hi : lo;
 }
 
 // the x-intervals of D at y (at most 7) as the tags of their ends
@@ -289,27 +328,20 @@ PB_HD int row_plan(const Surf& S, double y, int* tlo, int* thi) {
     p[0] = -kR;
     tg[0] = -1;
     int np = 1;
-    for (int d = 0; d < 3; d++) {
-        const double e1 = S.e1c[d] + S.e1y[d] * y, e0 = S.e0c[d] + (S.e0y[d] + S.e0yy[d] * y) * y;
+    for (int d = 0; d < 3; d++)
         for (int l = 0; l < 2; l++) {
-            const double c0 = e0 - (l ? 0.5 : -0.5);
-            double r[2];
-            const int nr = roots_in(S.e2[d], e1, c0, -kR, kR, r, 0);
-            if (nr == 1) {
-                // one root in range: which one of the pair (for a quadratic)
-                int b = 0;
-                if (S.e2[d] != 0.0) b = (r[0] == tagged_root(S, 4 * d + 2 * l + 1, y)) ? 1 : 0;
-                p[np] = r[0];
-                tg[np++] = 4 * d + 2 * l + b;
-            } else if (nr == 2) {
-                const bool sw = r[0] > r[1];
-                p[np] = sw ? r[1] : r[0];
+            double c2, c1, c0, lo, hi;
+            curve_coeffs(S, d, l, y, c2, c1, c0);
+            const int nr = root_pair(c2, c1, c0, false, lo, hi);
+            if (nr >= 1 && lo > -kR && lo < kR) {
+                p[np] = lo;
                 tg[np++] = 4 * d + 2 * l;
-                p[np] = sw ? r[0] : r[1];
+            }
+            if (nr == 2 && hi > -kR && hi < kR) {
+                p[np] = hi;
                 tg[np++] = 4 * d + 2 * l + 1;
             }
         }
-    }
     p[np] = kR;
     tg[np++] = -2;
     for (int i = 1; i < np; i++) {  // insertion sort carrying the tags
@@ -339,8 +371,9 @@ PB_HD int row_plan(const Surf& S, double y, int* tlo, int* thi) {
     return ni;
 }
 
+// this thread's share (sp) of the cell's V, A, K and N
 PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3], const double a[6], const Rule& R,
-                      Out& o) {
+                      Split& sp, Out& o) {
     // F(X) = P(t1.X, t2.X) - n.X = a0 + g.X + X^T H X
     double g[3], H[3][3];
     for (int i = 0; i < 3; i++) {
@@ -353,7 +386,7 @@ PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3],
         const int p = (d + 1) % 3, q = (d + 2) % 3;
         for (int s = -1; s <= 1; s += 2) {
             const double I = face_positive(H[p][p], 2.0 * H[p][q], H[q][q], g[p] + s * H[p][d], g[q] + s * H[q][d],
-                                           a[0] + 0.5 * s * g[d] + 0.25 * H[d][d], R);
+                                           a[0] + 0.5 * s * g[d] + 0.25 * H[d][d], R, sp);
             o.V -= s * n[d] * I;
         }
     }
@@ -368,7 +401,7 @@ PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3],
         S.e0y[d] = t2[d] + n[d] * a[2];
         S.e0yy[d] = n[d] * a[5];
     }
-    double yb[40], sre[12], sim[12];
+    double yb[46], sre[12], sim[12];
     yb[0] = -kR;
     int nb = 1, ns = 0;
     // branch points of the x-roots: zeros of each curve's discriminant in x
@@ -383,6 +416,12 @@ PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3],
             for (int i = n0; i < ns; i++)
                 if (sre[i] > -kR && sre[i] < kR) yb[nb++] = sre[i];
         }
+    // a coordinate that does not depend on x (the surface is a cylinder along
+    // x in that direction, e.g. a plane lying in a cube face) bounds D at the
+    // y where it equals +-1/2
+    for (int d = 0; d < 3; d++)
+        if (S.e2[d] == 0.0 && S.e1c[d] == 0.0 && S.e1y[d] == 0.0)
+            for (int s = -1; s <= 1; s += 2) nb = roots_in(S.e0yy[d], S.e0y[d], S.e0c[d] - 0.5 * s, -kR, kR, yb, nb);
     // y where the surface crosses one of the twelve cube edges
     for (int f = 0; f < 3; f++) {
         const int d = (f + 1) % 3, e = (f + 2) % 3;
@@ -414,6 +453,7 @@ PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3],
         const int ni = row_plan(S, 0.5 * (y0 + y1), tlo, thi);
         if (ni == 0) continue;  // D does not meet this strip
         graded(y0, y1, sre, sim, ns, R, [&](double y, double wy) {
+            if (!sp.mine()) return;
             // W^2 = 1 + px^2 + py^2 is a quadratic in x; its complex zeros are
             // the branch points (W) and poles (kappa W) of the row integrand
             const double b1 = a[1] + pxy * y, b2 = a[2] + pyy * y;
