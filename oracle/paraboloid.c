@@ -362,6 +362,15 @@ static void pb_surface(const pb_cell* q, double tol, double* I) {
             np += pb_roots(c2, c1, c0, -PB_R, PB_R, pts + np);
         }
     }
+    /* a world coordinate that does not depend on x (the surface is a cylinder
+     * along x in that direction, as a plane lying in a cube face is) bounds the
+     * domain at the y where it equals +-1/2 */
+    for (int d = 0; d < 3; d++) {
+        if (q->n[d] * a[3] != 0.0 || q->t1[d] + q->n[d] * a[1] != 0.0 || q->n[d] * a[4] != 0.0) continue;
+        for (int sg = -1; sg <= 1; sg += 2)
+            np += pb_roots(q->n[d] * a[5], q->t2[d] + q->n[d] * a[2], q->n[d] * a[0] - 0.5 * sg, -PB_R, PB_R,
+                           pts + np);
+    }
     /* the twelve cube edges: X_d = +-1/2, X_e = +-1/2, the third coordinate free */
     for (int f = 0; f < 3; f++)
         for (int s1 = -1; s1 <= 1; s1 += 2)

@@ -220,3 +220,15 @@ def test_paraboloid_alpha_of_a_fitted_droplet_is_close_to_the_exact_alpha():
     hit = o["status"] == 0
     kb = o["kbar"][hit] / g.h
     assert abs(np.median(kb) * w["R"] / 2.0 - 1.0) < 0.02
+
+
+def test_surfaces_lying_in_cube_faces_and_diagonal_planes():
+    """Planes in the cube's faces (area 1, alpha 1 or 0 up to the face itself)
+    and through two opposite edges (area sqrt 2, alpha 1/2): the domain of the
+    surface integral is bounded there by a coordinate that does not depend on
+    x, a degenerate case of its breakpoints."""
+    E = np.eye(3).reshape(9)
+    co = np.array([[0.5, 0, 0, 0, 0, 0], [-0.5, 0, 0, 0, 0, 0], [0.0, 1.0, 0, 0, 0, 0], [0.0, 0, 1.0, 0, 0, 0]])
+    o = oracle.paraboloid_cells(np.tile(E, (4, 1)), co)
+    assert np.max(np.abs(o["area"] - [1.0, 1.0, np.sqrt(2.0), np.sqrt(2.0)])) <= 1e-14
+    assert np.max(np.abs(o["alpha"] - [1.0, 0.0, 0.5, 0.5])) <= 1e-15
