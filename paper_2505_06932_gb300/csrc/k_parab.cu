@@ -3,8 +3,8 @@
 // and the curvature and normal averaged over the paraboloid surface inside
 // the cell (parab.cuh has the integration).  A group of kG = 8 lanes per cell
 // (four cells per warp): every lane walks the cell's breakpoints and pieces,
-// evaluates every kG-th quadrature node, and the group adds its shares with
-// shuffles.  One thread per cell would leave the GPU nearly empty (a front has
+// the lanes take different outer quadrature nodes of each piece side by side
+// (lane g the nodes g, g + kG), and the group adds its shares with shuffles.  One thread per cell would leave the GPU nearly empty (a front has
 // tens of thousands of interfacial cells, a few warps per SM) with each thread
 // running a long serial float64 chain.
 //  * k_parab_cells -- from caller-given frames and coefficients (cell units);
@@ -19,7 +19,7 @@
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kG = 8;                   // lanes per cell
+constexpr int kG = 8;                   // lanes per cell (divides parab::kNS)
 constexpr int kCellsPerWarp = 32 / kG;  // cells per warp and pass
 
 struct ParabOut {
@@ -61,10 +61,12 @@ __device__ double finish(const double t1[3], const double t2[3], const double n[
         kbar = o.K / o.A;
         for (int d = 0; d < 3; d++) nb[d] = o.N[d] / nl;
         st = 0;
-    } else {  // the surface misses the cell: the point values at the origin
+    } else {  // the surface misses the cell: the point values at the origin, and
+              // the cell lies on one side of it (alpha exactly 0 or 1)
         area = 0.0;
         point_values(t1, t2, n, a, kbar, nb);
         st = FT_PARAB_MISS;
+        return o.V > 0.5 ? 1.0 : 0.0;
     }
     return fmin(fmax(o.V, 0.0), 1.0);
 }
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_parab_cells(const double* __restri
                 n[d] = frame[9 * c + 6 + d];
             }
             for (int r = 0; r < 6; r++) a[r] = coeffs[6 * c + r];
-            parab::Split sp{g, kG, 0};
+            const parab::Split sp{g, kG};
             parab::parab_cell(t1, t2, n, a, R, sp, o);
         }
         group_sum(o);
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_parab_ppic(F fr, const ft_cellsys*
             sys_normal(sys[m], fp32 != 0, n);
             basis<double>(n, t1, t2);
             for (int r = 0; r < 6; r++) a[r] = coeffs[6 * m + r];
-            parab::Split sp{g, kG, 0};
+            const parab::Split sp{g, kG};
             parab::parab_cell(t1, t2, n, a, R, sp, o);
         }
         group_sum(o);

@@ -62,13 +62,13 @@ struct Out {
     double V, A, K, N[3];
 };
 
-// A cell's quadrature can be shared by G threads: every thread walks the same
-// breakpoints and pieces, numbers the nodes in the same order, and evaluates
-// only the nodes whose number is g modulo G; the G partial results add up to
-// the cell's (G = 1: one thread does everything).
+// A cell's quadrature can be shared by G threads (G divides kNS): every
+// thread walks the same breakpoints and pieces, and of each piece's kNS outer
+// nodes thread g takes nodes g, g + G, ..., so that the G threads evaluate
+// different nodes at the same time; the G partial results add up to the
+// cell's (G = 1: one thread does everything).
 struct Split {
-    int g, G, next;
-    PB_HD bool mine() { return (next++ % G) == g; }
+    int g, G;
 };
 
 // real roots of c2 t^2 + c1 t + c0 strictly inside (lo, hi), appended at r[n..]
@@ -136,7 +136,8 @@ PB_HD void sort_small(double* v, int n) {
 // every sub-piece is at least as far from them as it is long (Gauss-Legendre
 // then converges like 5.8^-2n or faster).  f(y, w) accumulates w * integrand(y).
 template <class Fn>
-PB_HD void graded(double y0, double y1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
+PB_HD void graded(double y0, double y1, const double* sre, const double* sim, int ns, const Rule& R, const Split& sp,
+                  Fn&& f) {
     const double L = y1 - y0, eps = 1e-12 * L;
     double d0 = 2.0 * L, d1 = 2.0 * L;
     bool s0 = false, s1 = false;
@@ -154,7 +155,7 @@ PB_HD void graded(double y0, double y1, const double* sre, const double* sim, in
     auto sub = [&](double a, double b, bool fa, bool fb) {
         const int m = (fa ? 1 : 0) + (fb ? 2 : 0);
         const double h = b - a;
-        for (int k = 0; k < kNS; k++) f(a + h * R.os[m][k], h * R.ow[m][k]);
+        for (int k = sp.g; k < kNS; k += sp.G) f(a + h * R.os[m][k], h * R.ow[m][k]);
     };
     double a = y0, b = y1;
     bool fa = s0, fb = s1;
@@ -230,7 +231,7 @@ PB_HD double row_positive(double al, double be, double ga) {
 // points of the roots, the zeros of the discriminant in u (cut at real ones
 // and at the real part of a complex pair; the pieces are graded towards them).
 PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double Bv, double C, const Rule& R,
-                           Split& sp) {
+                           const Split& sp) {
     double sre[2], sim[2];
     const int ns = croots(Auv * Auv - 4.0 * Auu * Avv, 2.0 * Auv * Bu - 4.0 * Auu * Bv, Bu * Bu - 4.0 * Auu * C, sre,
                           sim, 0);
@@ -247,7 +248,7 @@ PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double
         // there means that F keeps one sign on the whole face
         double r[2];
         if (roots_in(Auu, Bu, C, -0.5, 0.5, r, 0) == 0)
-            return (sp.mine() && C > 0.0) ? C + (Auu + Avv) * (1.0 / 12.0) : 0.0;
+            return (sp.g == 0 && C > 0.0) ? C + (Auu + Avv) * (1.0 / 12.0) : 0.0;
     }
     for (int i = 0; i < ns; i++)
         if (sre[i] > -0.5 && sre[i] < 0.5) p[np++] = sre[i];
@@ -256,9 +257,8 @@ PB_HD double face_positive(double Auu, double Auv, double Avv, double Bu, double
     double I = 0.0;
     for (int i = 0; i + 1 < np; i++) {
         if (!(p[i + 1] > p[i])) continue;
-        graded(p[i], p[i + 1], sre, sim, ns, R, [&](double v, double w) {
-            if (sp.mine()) I += w * row_positive(Auu, Auv * v + Bu, (Avv * v + Bv) * v + C);
-        });
+        graded(p[i], p[i + 1], sre, sim, ns, R, sp,
+               [&](double v, double w) { I += w * row_positive(Auu, Auv * v + Bu, (Avv * v + Bv) * v + C); });
     }
     return I;
 }
@@ -373,7 +373,7 @@ PB_HD int row_plan(const Surf& S, double y, int* tlo, int* thi) {
 
 // this thread's share (sp) of the cell's V, A, K and N
 PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3], const double a[6], const Rule& R,
-                      Split& sp, Out& o) {
+                      const Split& sp, Out& o) {
     // F(X) = P(t1.X, t2.X) - n.X = a0 + g.X + X^T H X
     double g[3], H[3][3];
     for (int i = 0; i < 3; i++) {
@@ -452,8 +452,7 @@ PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3],
         int tlo[7], thi[7];
         const int ni = row_plan(S, 0.5 * (y0 + y1), tlo, thi);
         if (ni == 0) continue;  // D does not meet this strip
-        graded(y0, y1, sre, sim, ns, R, [&](double y, double wy) {
-            if (!sp.mine()) return;
+        graded(y0, y1, sre, sim, ns, R, sp, [&](double y, double wy) {
             // W^2 = 1 + px^2 + py^2 is a quadratic in x; its complex zeros are
             // the branch points (W) and poles (kappa W) of the row integrand
             const double b1 = a[1] + pxy * y, b2 = a[2] + pyy * y;
