@@ -189,9 +189,11 @@ PB_HD void graded(double y0, double y1, const double* sre, const double* sim, in
     sub(a, b, fa, fb);
 }
 
-// the same cutting for the inner x integrals (no branch point at the ends)
+// the same cutting for the inner x integrals (no branch point at the ends);
+// a complex singular point over the interval's interior first cuts it at its
+// real part, so that its distance to the interval is measured from an end
 template <class Fn>
-PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
+PB_HD void graded_x_piece(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn& f) {
     const double L = x1 - x0;
     double d0 = 4.0 * L * L, d1 = 4.0 * L * L;  // squared distances
     for (int i = 0; i < ns; i++) {
@@ -217,6 +219,25 @@ PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, 
             b -= st;
         }
     sub(a, b);
+}
+
+template <class Fn>
+PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
+    // the real part of the closest singular point over the interior, if it is
+    // within 1.25 lengths (beyond that 12 nodes already converge to rounding)
+    double xs = x0;
+    double best = 1.25 * (x1 - x0);
+    for (int i = 0; i < ns; i++)
+        if (sre[i] > x0 && sre[i] < x1 && sim[i] < best) {
+            best = sim[i];
+            xs = sre[i];
+        }
+    if (xs > x0) {
+        graded_x_piece(x0, xs, sre, sim, ns, R, f);
+        graded_x_piece(xs, x1, sre, sim, ns, R, f);
+    } else {
+        graded_x_piece(x0, x1, sre, sim, ns, R, f);
+    }
 }
 
 // int_{-1/2}^{1/2} max(f, 0) du for f(u) = al u^2 + be u + ga
