@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager launches instead of one CUDA graph per step")
     ap.add_argument("--phase-steps", type=int, default=20, help="eager steps timed per phase")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="only run this many eager steps of the 512-front batch (for a profiler's launch list)")
     ap.add_argument("--paraboloid-reps", type=int, default=5,
                     help="timed calls of front_volume_fraction_ppic (the paper's own alpha) on the step's fits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -513,6 +515,27 @@ def measure_paraboloid(fcs, counts, reps, flush, stream):
             "timing": "CUDA events around both fronts' calls, L2 flushed before each", "roofline": roof}
 
 
+def profile_batch(a):
+    """Eager steps of the 512-front batched workload with the autotuner's usual
+    choice fixed (clip 16, PPIC 4, CSF 4, fill 16 blocks per SM, dynamic PPIC
+    schedule): a short, deterministic launch sequence for a profiler."""
+    import torch
+    from paper_2505_06932_gb300 import _front as F, inputs as I
+
+    dev = torch.device("cuda", 0)
+    dl = []
+    for f in I.batch_fronts(5, a.batch_fronts):
+        U, V, W = device_faces(f, dev)
+        dl.append(dict(grid=f["grid"], verts=torch.from_numpy(f["verts"]).to(dev),
+                       tris=torch.from_numpy(f["tris"]).to(dev), U=U, V=V, W=W))
+    bc = F.BatchCoupling(dl, params=F.make_params(precision=F.FT_FP32C), headroom=1.02)
+    F.ft_set_tuning(bc.ws, clip=16, ppic=4, csf=4, fill=16, ppic_min_blocks=4, ppic_dynamic=1)
+    for _ in range(a.profile_batch):
+        bc.step()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batch_steps": a.profile_batch, "status": bc.ws.status(), "counts": bc.ws.counts()}))
+
+
 def device_faces(f, dev):
     """Noise-free solid-body rotation u = omega x (x - c) at the face centres of
     front f's grid, built on the device (the batched workload's face velocities)."""
@@ -732,6 +755,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.profile_batch > 0:
+        profile_batch(a)
     else:
         run_ours(a)
 
