@@ -40,16 +40,26 @@ struct Planes {
 // Candidate range along one axis: cells whose closed extent [X_i, X_i+1] meets
 // [lo, hi]: i0 = min{i : X_i+1 >= lo}, i1 = max{i : X_i <= hi}.  The product
 // with 1/h is only a starting guess; the exact comparisons make the result exact.
+__device__ __forceinline__ float d2f_rn(double x);
+
+// first guess of the cell index of coordinate x along an axis: the offset
+// from the origin in float64, the rest in float32 (the exact answer comes from
+// the integer plane-key comparisons after it; a guess off by one cell costs
+// one more comparison)
+__device__ __forceinline__ int cell_guess(double x, double o, float inv_h, int n) {
+    const float f = floorf(d2f_rn(x - o) * inv_h);
+    return (f >= 0.0f) ? ((f <= (float)(n - 1)) ? (int)f : n - 1) : 0;
+}
+
 __device__ void cand_range(const Planes& P, int ax, double inv_h, int n, double lo, double hi, int& i0, int& i1) {
     const double o = P.o[ax];
+    const float ihf = d2f_rn(inv_h);
     const long long klo = okey(lo), khi = okey(hi);
-    double f = floor((lo - o) * inv_h);
-    int e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
+    int e = cell_guess(lo, o, ihf, n);
     while (e > 0 && okey(P.at(ax, e)) >= klo) e--;
     while (e < n - 1 && okey(P.at(ax, e + 1)) < klo) e++;
     i0 = e;
-    f = floor((hi - o) * inv_h);
-    e = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
+    e = cell_guess(hi, o, ihf, n);
     while (e < n - 1 && okey(P.at(ax, e + 1)) <= khi) e++;
     while (e > 0 && okey(P.at(ax, e)) > khi) e--;
     i1 = e;

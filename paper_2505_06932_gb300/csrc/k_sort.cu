@@ -134,21 +134,27 @@ __global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ 
 }
 
 // Exclusive scan of the 256 x G digit-major histogram in one block: the whole
-// histogram is staged in shared memory with coalesced loads (all in flight at
-// once), each thread scans a contiguous chunk, and a block scan of the chunk
-// totals supplies the offsets.
+// histogram is staged in shared memory with 16-byte coalesced loads (unrolled,
+// so that a thread's loads are in flight together), each thread scans a
+// contiguous chunk of a multiple of 4 entries read as int4, and a block scan
+// of the chunk totals supplies the offsets.
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) k_radix_scan(int* hist, int G, long long* total) {
-    extern __shared__ int sh[];
+    extern __shared__ int4 sh4[];
     __shared__ long long wsum[32];
-    const int N = 256 * G;
-    for (int i = threadIdx.x; i < N; i += kScanThreads) sh[i] = hist[i];
+    const int N4 = 64 * G;  // 256 G entries as int4
+    const int4* __restrict__ h4 = reinterpret_cast<const int4*>(hist);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < N4; i += kScanThreads) sh4[i] = h4[i];
     __syncthreads();
-    const int per = (N + kScanThreads - 1) / kScanThreads;
-    const int b0 = threadIdx.x * per, b1 = min(N, b0 + per);
+    const int per4 = (N4 + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * per4, b1 = min(N4, b0 + per4);
     long long acc = 0;
-    for (int i = b0; i < b1; i++) acc += sh[i];
+    for (int i = b0; i < b1; i++) {
+        const int4 v = sh4[i];
+        acc += (long long)v.x + v.y + v.z + v.w;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     long long x = acc;
 #pragma unroll
@@ -170,18 +176,29 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scan(int* hist, int G, l
     __syncthreads();
     long long run = ((w > 0) ? wsum[w - 1] : 0) + x - acc;
     for (int i = b0; i < b1; i++) {
-        const int v = sh[i];
-        sh[i] = (int)run;
-        run += v;
+        const int4 v = sh4[i];
+        int4 o;
+        o.x = (int)run;
+        run += v.x;
+        o.y = (int)run;
+        run += v.y;
+        o.z = (int)run;
+        run += v.z;
+        o.w = (int)run;
+        run += v.w;
+        sh4[i] = o;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < N; i += kScanThreads) hist[i] = sh[i];
+    int4* __restrict__ o4 = reinterpret_cast<int4*>(hist);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < N4; i += kScanThreads) o4[i] = sh4[i];
     if (threadIdx.x == 0) *total = wsum[31];
 }
 
-// Stable scatter: each block walks its segment in tiles of 256 keys in order;
-// a key's destination is the digit's offset for this block + the count of the
-// same digit earlier in the segment (earlier tiles, earlier warps, lower lanes).
+// Stable scatter: each block walks its segment in tiles of 256 keys in order
+// (the next tile's keys loaded while this one is ranked); a key's destination
+// is the digit's offset for this block + the count of the same digit earlier
+// in the segment (earlier tiles, earlier warps, lower lanes).
 __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
                                                       unsigned* __restrict__ kout, unsigned* __restrict__ vout,
                                                       const long long* n_ptr, int shift,
@@ -193,15 +210,23 @@ __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict
     const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     base[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+    // the next tile's key and value are loaded while this tile is ranked
+    unsigned kn = FT_SENTINEL, vn = 0;
+    if (b0 + threadIdx.x < b1) {
+        kn = kin[b0 + threadIdx.x];
+        vn = vin[b0 + threadIdx.x];
+    }
     for (long long t0 = b0; t0 < b1; t0 += kB) {
+        const unsigned k = kn, v = vn;
+        const long long in = t0 + kB + threadIdx.x;
+        kn = FT_SENTINEL;
+        vn = 0;
+        if (in < b1) {
+            kn = kin[in];
+            vn = vin[in];
+        }
         for (int d = 0; d < kB / 32; d++) wcnt[d][threadIdx.x] = 0;
         __syncthreads();
-        const long long i = t0 + threadIdx.x;
-        unsigned k = FT_SENTINEL, v = 0;
-        if (i < b1) {
-            k = kin[i];
-            v = vin[i];
-        }
         const bool valid = (k != FT_SENTINEL);
         const unsigned dig = valid ? ((k >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, dig);
