@@ -108,64 +108,54 @@ __global__ void __launch_bounds__(kThreads) k_alpha_fill(F fr, const int* __rest
         double* __restrict__ alpha = D.alpha;
         unsigned err = 0;
         double carry = 0.0;
-        // the index map of four chunks at a time (a 128-cell column at once) is
-        // loaded together, so that the loads are in flight at the same time;
-        // then the chunks are walked downwards
-        for (int g0 = (n2 - 1) / 32; g0 >= 0; g0 -= 4) {
-            int mm[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int kq = (g0 - q) * 32 + lane;
-                mm[q] = (g0 - q >= 0 && kq < n2) ? idx_map[gbase + kq] : -1;
+        // the index map of the chunk below is loaded while this chunk is processed
+        int k0 = ((n2 - 1) / 32) * 32;
+        int m_next = (k0 + lane < n2) ? idx_map[gbase + k0 + lane] : -1;
+        for (; k0 >= 0; k0 -= 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n2;
+            const int m = m_next;
+            if (k0 >= 32) m_next = idx_map[gbase + k0 - 32 + lane];
+            if (__ballot_sync(0xffffffffu, m >= 0) == 0u) {
+                // no interfacial cell in this chunk: every cell takes the parity above it
+                const long long cb = __double_as_longlong(carry);
+                double r;
+                if (cb == __double_as_longlong(0.0) || cb == __double_as_longlong(1.0)) {
+                    r = carry;  // already exact: no float64 arithmetic needed
+                } else {
+                    r = rint(carry);
+                    if (fabs(carry - r) > closure_tol) err |= FT_ST_NOT_CLOSED;
+                    if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
+                    r = fmin(fmax(r, 0.0), 1.0);
+                    // below a closed stretch of front the parity is exact again
+                    if (fabs(carry - rint(carry)) <= closure_tol) carry = rint(carry);
+                }
+                if (valid) alpha[base + k] = r;
+                continue;
             }
+            const double Pz = (m >= 0) ? cell_P[m] : 0.0;
+            const double L = (m >= 0) ? cell_L[m] : 0.0;
+            double x = Pz;  // inclusive suffix sum within the chunk
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                if (g0 - q < 0) break;
-                const int k0 = (g0 - q) * 32;
-                const int k = k0 + lane;
-                const bool valid = k < n2;
-                const int m = mm[q];
-                if (__ballot_sync(0xffffffffu, m >= 0) == 0u) {
-                    // no interfacial cell in this chunk: every cell takes the parity above it
-                    const long long cb = __double_as_longlong(carry);
-                    double r;
-                    if (cb == __double_as_longlong(0.0) || cb == __double_as_longlong(1.0)) {
-                        r = carry;  // already exact: no float64 arithmetic needed
-                    } else {
-                        r = rint(carry);
-                        if (fabs(carry - r) > closure_tol) err |= FT_ST_NOT_CLOSED;
-                        if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
-                        r = fmin(fmax(r, 0.0), 1.0);
-                        // below a closed stretch of front the parity is exact again
-                        if (fabs(carry - rint(carry)) <= closure_tol) carry = rint(carry);
-                    }
-                    if (valid) alpha[base + k] = r;
-                    continue;
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_down_sync(0xffffffffu, x, o);
+                if (lane + o < 32) x += y;
+            }
+            double ex = __shfl_down_sync(0xffffffffu, x, 1);
+            if (lane == 31) ex = 0.0;
+            const double S = carry + ex;
+            carry += __shfl_sync(0xffffffffu, x, 0);
+            if (valid) {
+                double a;
+                if (m >= 0) {
+                    a = L + S;
+                } else {
+                    const double r = rint(S);
+                    if (fabs(S - r) > closure_tol) err |= FT_ST_NOT_CLOSED;
+                    if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
+                    a = r;
                 }
-                const double Pz = (m >= 0) ? cell_P[m] : 0.0;
-                const double L = (m >= 0) ? cell_L[m] : 0.0;
-                double x = Pz;  // inclusive suffix sum within the chunk
-    #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const double y = __shfl_down_sync(0xffffffffu, x, o);
-                    if (lane + o < 32) x += y;
-                }
-                double ex = __shfl_down_sync(0xffffffffu, x, 1);
-                if (lane == 31) ex = 0.0;
-                const double S = carry + ex;
-                carry += __shfl_sync(0xffffffffu, x, 0);
-                if (valid) {
-                    double a;
-                    if (m >= 0) {
-                        a = L + S;
-                    } else {
-                        const double r = rint(S);
-                        if (fabs(S - r) > closure_tol) err |= FT_ST_NOT_CLOSED;
-                        if (r != 0.0 && r != 1.0) err |= FT_ST_ORIENTATION;
-                        a = r;
-                    }
-                    alpha[base + k] = fmin(fmax(a, 0.0), 1.0);
-                }
+                alpha[base + k] = fmin(fmax(a, 0.0), 1.0);
             }
         }
         err = __reduce_or_sync(0xffffffffu, err);

@@ -130,69 +130,7 @@ __global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ 
         if (k != FT_SENTINEL) atomicAdd(&h[(k >> shift) & 255u], 1);
     }
     __syncthreads();
-    hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];  // digit-major
-}
-
-// Exclusive scan of the 256 x G digit-major histogram in one block: the whole
-// histogram is staged in shared memory with 16-byte coalesced loads (unrolled,
-// so that a thread's loads are in flight together), each thread scans a
-// contiguous chunk of a multiple of 4 entries read as int4, and a block scan
-// of the chunk totals supplies the offsets.
-constexpr int kScanThreads = 1024;
-
-__global__ void __launch_bounds__(kScanThreads) k_radix_scan(int* hist, int G, long long* total) {
-    extern __shared__ int4 sh4[];
-    __shared__ long long wsum[32];
-    const int N4 = 64 * G;  // 256 G entries as int4
-    const int4* __restrict__ h4 = reinterpret_cast<const int4*>(hist);
-#pragma unroll 4
-    for (int i = threadIdx.x; i < N4; i += kScanThreads) sh4[i] = h4[i];
-    __syncthreads();
-    const int per4 = (N4 + kScanThreads - 1) / kScanThreads;
-    const int b0 = threadIdx.x * per4, b1 = min(N4, b0 + per4);
-    long long acc = 0;
-    for (int i = b0; i < b1; i++) {
-        const int4 v = sh4[i];
-        acc += (long long)v.x + v.y + v.z + v.w;
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    long long x = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        long long t = wsum[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        wsum[lane] = t;
-    }
-    __syncthreads();
-    long long run = ((w > 0) ? wsum[w - 1] : 0) + x - acc;
-    for (int i = b0; i < b1; i++) {
-        const int4 v = sh4[i];
-        int4 o;
-        o.x = (int)run;
-        run += v.x;
-        o.y = (int)run;
-        run += v.y;
-        o.z = (int)run;
-        run += v.z;
-        o.w = (int)run;
-        run += v.w;
-        sh4[i] = o;
-    }
-    __syncthreads();
-    int4* __restrict__ o4 = reinterpret_cast<int4*>(hist);
-#pragma unroll 4
-    for (int i = threadIdx.x; i < N4; i += kScanThreads) o4[i] = sh4[i];
-    if (threadIdx.x == 0) *total = wsum[31];
+    hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];  // block-major (coalesced)
 }
 
 // Stable scatter: each block walks its segment in tiles of 256 keys in order
@@ -202,14 +140,40 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scan(int* hist, int G, l
 __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
                                                       unsigned* __restrict__ kout, unsigned* __restrict__ vout,
                                                       const long long* n_ptr, int shift,
-                                                      const int* __restrict__ hist) {
+                                                      const int* __restrict__ hist, long long* total) {
     __shared__ int base[256];
     __shared__ int wcnt[kB / 32][256];
     const long long n = *n_ptr;
     const long long s = seg_len(n, gridDim.x);
     const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    base[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+    {
+        // this block's offset for digit d = threadIdx.x: the keys of all smaller
+        // digits plus the keys of digit d in earlier segments, from the
+        // block-major histogram (one coalesced row per segment) and a block scan
+        // of the digit totals
+        int tot = 0, before = 0;
+#pragma unroll 8
+        for (int j = 0; j < (int)gridDim.x; j++) {
+            const int c = hist[j * 256 + threadIdx.x];
+            tot += c;
+            before += (j < (int)blockIdx.x) ? c : 0;
+        }
+        int x = tot;  // inclusive scan over the digits
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wcnt[0][w] = x;
+        __syncthreads();
+        int wbase = 0;
+        for (int q = 0; q < w; q++) wbase += wcnt[0][q];
+        const int excl = wbase + x - tot;
+        base[threadIdx.x] = excl + before;
+        if (blockIdx.x == 0 && threadIdx.x == kB - 1) *total = excl + tot;
+        __syncthreads();
+    }
     // the next tile's key and value are loaded while this tile is ranked
     unsigned kn = FT_SENTINEL, vn = 0;
     if (b0 + threadIdx.x < b1) {
@@ -390,11 +354,8 @@ cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, 
 }
 
 cudaError_t prepare_sort(int grid_blocks) {
-    // once per workspace, outside any stream capture: the histogram scan stages
-    // 256 x grid_blocks counts in dynamic shared memory
-    const size_t bytes = 256 * (size_t)grid_blocks * sizeof(int);
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_radix_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    (void)grid_blocks;  // no kernel of the sort needs more than the default shared memory
+    return cudaSuccess;
 }
 
 cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
@@ -405,11 +366,10 @@ cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
         // pass 0 reads the candidates (sentinels dropped) and counts the pairs
         const long long* n = (p == 0) ? &ws->ctr->C : &ws->ctr->P;
         long long* tot = (p == 0) ? &ws->ctr->P : &ws->ctr->scratch;
-        count_launches(3);
+        count_launches(2);
         k_radix_hist<<<G, kB, 0, s>>>(ws->keys[src], n, 8 * p, ws->hist);
-        k_radix_scan<<<1, kScanThreads, 256 * G * sizeof(int), s>>>(ws->hist, G, tot);
         k_radix_scatter<<<G, kB, 0, s>>>(ws->keys[src], ws->vals[src], ws->keys[src ^ 1], ws->vals[src ^ 1], n,
-                                         8 * p, ws->hist);
+                                         8 * p, ws->hist, tot);
         src ^= 1;
     }
     ws->sorted_buf = src;
