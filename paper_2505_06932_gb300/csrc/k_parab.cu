@@ -19,7 +19,7 @@
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kG = 8;                   // lanes per cell (divides parab::kNS)
+constexpr int kG = 8;                   // lanes per cell (divides parab::kNS and parab::kN8)
 constexpr int kCellsPerWarp = 32 / kG;  // cells per warp and pass
 
 struct ParabOut {
@@ -71,7 +71,7 @@ __device__ double finish(const double t1[3], const double t2[3], const double n[
     return fmin(fmax(o.V, 0.0), 1.0);
 }
 
-__global__ void __launch_bounds__(kThreads) k_parab_cells(const double* __restrict__ frame,
+__global__ void __launch_bounds__(kThreads, 4) k_parab_cells(const double* __restrict__ frame,
                                                           const double* __restrict__ coeffs, long long m,
                                                           parab::Rule R, ParabOut out) {
     const int lane = threadIdx.x & 31, g = lane % kG;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_parab_cells(const double* __restri
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) k_parab_ppic(F fr, const ft_cellsys* __restrict__ sys, int fp32,
+__global__ void __launch_bounds__(kThreads, 4) k_parab_ppic(F fr, const ft_cellsys* __restrict__ sys, int fp32,
                                                          const unsigned* __restrict__ cells,
                                                          const double* __restrict__ coeffs, long long cap,
                                                          ft_counters* ctr, parab::Rule R, ParabOut out) {

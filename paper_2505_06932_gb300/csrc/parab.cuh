@@ -48,6 +48,7 @@ namespace parab {
 
 constexpr int kNS = 16;  // nodes per outer piece
 constexpr int kNX = 12;  // nodes per inner interval of the surface integrals
+constexpr int kN8 = 8;   // nodes of either when every singular point is >= 2 lengths away
 constexpr double kR = 0.86602540378443865;  // |x|, |y| <= sqrt(3)/2 on the cell
 
 // Gauss-Legendre rules on [0, 1] under four maps s(u) of the unit interval:
@@ -56,7 +57,18 @@ constexpr double kR = 0.86602540378443865;  // |x|, |y| <= sqrt(3)/2 on the cell
 struct Rule {
     double os[4][kNS], ow[4][kNS];
     double ix[kNX], iw[kNX];
+    double x8[kN8], w8[kN8];  // linear map
 };
+
+// squared distance from the singular points to the segment [a, b]
+PB_HD double seg_dist2(double a, double b, const double* sre, const double* sim, int ns) {
+    double best = 1e300;
+    for (int i = 0; i < ns; i++) {
+        const double dx = (sre[i] < a) ? a - sre[i] : ((sre[i] > b) ? sre[i] - b : 0.0);
+        best = fmin(best, dx * dx + sim[i] * sim[i]);
+    }
+    return best;
+}
 
 struct Out {
     double V, A, K, N[3];
@@ -141,90 +153,114 @@ PB_HD void sort_small(double* v, int n) {
     }
 }
 
-// Integrate a function that is analytic inside [y0, y1] except for branch
-// points at (sre, sim).  A branch point at an end is taken by a map flat at
-// that end; towards an end that has other branch points at a distance d below
-// half the length, the piece is cut at d, 3d, 7d, ... from that end, so that
-// every sub-piece is at least as far from them as it is long (Gauss-Legendre
-// then converges like 5.8^-2n or faster).  f(y, w) accumulates w * integrand(y).
-template <class Fn>
-PB_HD void graded(double y0, double y1, const double* sre, const double* sim, int ns, const Rule& R, const Split& sp,
-                  Fn&& f) {
-    const double L = y1 - y0, eps2 = 1e-24 * L * L;
+// Cutting [y0, y1] for a function analytic inside except for branch points at
+// (sre, sim): a branch point at an end is taken by a map flat at that end;
+// towards an end with other branch points at a distance d below half the
+// length, the piece is cut at d, 3d, 7d, ... from that end (d (2^k - 1)), so
+// that every sub-piece is at least as far from them as it is long
+// (Gauss-Legendre then converges like 5.8^-2n or faster).  The sub-pieces are
+// generated one by one from their index (no list), and the integrand is
+// expanded at one call site.  `inner`: the x integrals, no branch points at
+// the ends, the kNX-node rule.
+struct Cut {
+    double y0, y1, d0, d1;
+    bool s0, s1, inner;
+    int nl, nr;  // pieces cut from the lower / upper end
+};
+
+PB_HD Cut make_cut(double y0, double y1, const double* sre, const double* sim, int ns, bool inner) {
+    Cut c;
+    c.y0 = y0;
+    c.y1 = y1;
+    c.inner = inner;
+    const double L = y1 - y0, eps2 = inner ? -1.0 : 1e-24 * L * L;
     double d0 = 4.0 * L * L, d1 = 4.0 * L * L;  // squared distances
-    bool s0 = false, s1 = false;
+    c.s0 = c.s1 = false;
     for (int i = 0; i < ns; i++) {
         const double u0 = sre[i] - y0, u1 = sre[i] - y1, v2 = sim[i] * sim[i];
         const double e0 = u0 * u0 + v2, e1 = u1 * u1 + v2;
         if (e0 <= eps2)
-            s0 = true;
+            c.s0 = true;
         else if (e0 < d0)
             d0 = e0;
         if (e1 <= eps2)
-            s1 = true;
+            c.s1 = true;
         else if (e1 < d1)
             d1 = e1;
     }
-    d0 = sqrt(d0);
-    d1 = sqrt(d1);
-    auto sub = [&](double a, double b, bool fa, bool fb) {
-        const int m = (fa ? 1 : 0) + (fb ? 2 : 0);
-        const double h = b - a;
-        for (int k = sp.g; k < kNS; k += sp.G) f(a + h * R.os[m][k], h * R.ow[m][k]);
-    };
-    double a = y0, b = y1;
-    bool fa = s0, fb = s1;
-    if (d0 < 0.5 * L)
-        for (double st = d0; a + st < y0 + 0.5 * L; st *= 2.0) {
-            sub(a, a + st, fa, false);
-            fa = false;
+    c.d0 = sqrt(d0);
+    c.d1 = sqrt(d1);
+    c.nl = c.nr = 0;
+    double a = y0;
+    if (c.d0 < 0.5 * L)
+        for (double st = c.d0; a + st < y0 + 0.5 * L; st *= 2.0) {
             a += st;
+            c.nl++;
         }
-    if (d1 < 0.5 * L)
-        for (double st = d1; b - st > a && b - st > y1 - 0.5 * L; st *= 2.0) {
-            sub(b - st, b, false, fb);
-            fb = false;
+    double b = y1;
+    if (c.d1 < 0.5 * L)
+        for (double st = c.d1; b - st > a && b - st > y1 - 0.5 * L; st *= 2.0) {
             b -= st;
+            c.nr++;
         }
-    sub(a, b, fa, fb);
+    return c;
 }
 
-// the same cutting for the inner x integrals (no branch point at the ends);
-// a complex singular point over the interval's interior first cuts it at its
-// real part, so that its distance to the interval is measured from an end
-template <class Fn>
-PB_HD void graded_x_piece(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn& f) {
-    const double L = x1 - x0;
-    double d0 = 4.0 * L * L, d1 = 4.0 * L * L;  // squared distances
-    for (int i = 0; i < ns; i++) {
-        const double u0 = sre[i] - x0, u1 = sre[i] - x1, v2 = sim[i] * sim[i];
-        d0 = fmin(d0, u0 * u0 + v2);
-        d1 = fmin(d1, u1 * u1 + v2);
+// sub-piece i of nl + nr + 1 (lower-end pieces, the middle, upper-end pieces)
+// and its rule: 0..3 map with kNS nodes (see Rule), 4 linear with kN8 nodes
+// (every singular point at least two lengths away, where 8 nodes converge to
+// rounding), 5 the inner kNX-node rule
+PB_HD void cut_seg(const Cut& c, int i, const double* sre, const double* sim, int ns, double& a, double& b, int& m) {
+    bool fa = false, fb = false;
+    if (i < c.nl) {
+        a = c.y0 + c.d0 * (ldexp(1.0, i) - 1.0);
+        b = c.y0 + c.d0 * (ldexp(1.0, i + 1) - 1.0);
+        fa = c.s0 && i == 0;
+    } else if (i == c.nl) {
+        a = c.y0 + c.d0 * (ldexp(1.0, c.nl) - 1.0);
+        b = c.y1 - c.d1 * (ldexp(1.0, c.nr) - 1.0);
+        fa = c.s0 && c.nl == 0;
+        fb = c.s1 && c.nr == 0;
+    } else {
+        const int j = c.nl + c.nr - i;  // 0: the piece next to y1
+        a = c.y1 - c.d1 * (ldexp(1.0, j + 1) - 1.0);
+        b = c.y1 - c.d1 * (ldexp(1.0, j) - 1.0);
+        fb = c.s1 && j == 0;
     }
-    d0 = sqrt(d0);
-    d1 = sqrt(d1);
-    auto sub = [&](double a, double b) {
-        const double h = b - a;
-        for (int k = 0; k < kNX; k++) f(a + h * R.ix[k], h * R.iw[k]);
-    };
-    double a = x0, b = x1;
-    if (d0 < 0.5 * L)
-        for (double st = d0; a + st < x0 + 0.5 * L; st *= 2.0) {
-            sub(a, a + st);
-            a += st;
-        }
-    if (d1 < 0.5 * L)
-        for (double st = d1; b - st > a && b - st > x1 - 0.5 * L; st *= 2.0) {
-            sub(b - st, b);
-            b -= st;
-        }
-    sub(a, b);
+    m = c.inner ? 5 : (fa ? 1 : 0) + (fb ? 2 : 0);
+    if ((m == 0 || m == 5) && seg_dist2(a, b, sre, sim, ns) >= 4.0 * (b - a) * (b - a)) m = 4;
 }
 
+template <class Fn>
+PB_HD void run_cut(const Cut& c, const double* sre, const double* sim, int ns, const Rule& R, int g, int G, Fn& f) {
+    const int nseg = c.nl + c.nr + 1;
+    for (int i = 0; i < nseg; i++) {
+        double a, b;
+        int m;
+        cut_seg(c, i, sre, sim, ns, a, b, m);
+        const double h = b - a;
+        const double* xs = (m == 4) ? R.x8 : ((m == 5) ? R.ix : R.os[m]);
+        const double* ws = (m == 4) ? R.w8 : ((m == 5) ? R.iw : R.ow[m]);
+        const int nn = (m == 4) ? kN8 : ((m == 5) ? kNX : kNS);
+        for (int k = g; k < nn; k += G) f(a + h * xs[k], h * ws[k]);
+    }
+}
+
+// outer integral over [y0, y1]: thread sp.g of sp.G takes the nodes g, g + G, ...
+// of each sub-piece.  f(y, w) accumulates w * integrand(y).
+template <class Fn>
+PB_HD void graded(double y0, double y1, const double* sre, const double* sim, int ns, const Rule& R, const Split& sp,
+                  Fn&& f) {
+    const Cut c = make_cut(y0, y1, sre, sim, ns, false);
+    run_cut(c, sre, sim, ns, R, sp.g, sp.G, f);
+}
+
+// the inner x integrals: a complex singular point over the interval's
+// interior within 1.25 lengths first cuts it at its real part (beyond that
+// 12 nodes already converge to rounding), so that its distance is measured
+// from an end
 template <class Fn>
 PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, int ns, const Rule& R, Fn&& f) {
-    // the real part of the closest singular point over the interior, if it is
-    // within 1.25 lengths (beyond that 12 nodes already converge to rounding)
     double xs = x0;
     double best = 1.25 * (x1 - x0);
     for (int i = 0; i < ns; i++)
@@ -232,11 +268,11 @@ PB_HD void graded_x(double x0, double x1, const double* sre, const double* sim, 
             best = sim[i];
             xs = sre[i];
         }
-    if (xs > x0) {
-        graded_x_piece(x0, xs, sre, sim, ns, R, f);
-        graded_x_piece(xs, x1, sre, sim, ns, R, f);
-    } else {
-        graded_x_piece(x0, x1, sre, sim, ns, R, f);
+    const int nh = (xs > x0) ? 2 : 1;
+    for (int hh = 0; hh < nh; hh++) {
+        const double lo = (hh == 0) ? x0 : xs, hi = (nh == 1 || hh == 1) ? x1 : xs;
+        const Cut c = make_cut(lo, hi, sre, sim, ns, true);
+        run_cut(c, sre, sim, ns, R, 0, 1, f);
     }
 }
 
@@ -583,6 +619,7 @@ inline Rule make_rule() {
         R.ow[3][k] = w[k] * 6.0 * u[k] * v;
     }
     gauss_legendre01(kNX, R.ix, R.iw);
+    gauss_legendre01(kN8, R.x8, R.w8);
     return R;
 }
 
