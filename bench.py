@@ -34,7 +34,7 @@ FLOPS_PER_FIT_PAIR = 130.0   # per (cell, fragment-in-support) pair of the volum
 FLOPS_PER_FIT_SOLVE = 150.0  # per cell: the 6x6 solve
 FP64_PEAK_TFLOPS = 1.25      # GB300 nominal float64 (profiling recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz
-PARAB_FP64_FLOPS_PER_CELL = 83695.0  # FP64 flops (add + mul + 2 fma) executed per cell by k_parab_ppic on this workload (ncu)
+PARAB_FP64_FLOPS_PER_CELL = 72252.0  # FP64 flops (add + mul + 2 fma) executed per cell by k_parab_ppic on this workload (ncu)
 
 
 def parse():
