@@ -4,9 +4,10 @@
 // the cell (parab.cuh has the integration).  A group of kG = 8 lanes per cell
 // (four cells per warp): every lane walks the cell's breakpoints and pieces,
 // the lanes take different outer quadrature nodes of each piece side by side
-// (lane g the nodes g, g + kG), and the group adds its shares with shuffles.  One thread per cell would leave the GPU nearly empty (a front has
-// tens of thousands of interfacial cells, a few warps per SM) with each thread
-// running a long serial float64 chain.
+// (lane g the nodes g, g + kG), and the group adds its shares with shuffles.
+// One thread per cell would leave the GPU nearly empty (a front has tens of
+// thousands of interfacial cells, a few warps per SM) with each thread running
+// a long serial float64 chain.
 //  * k_parab_cells -- from caller-given frames and coefficients (cell units);
 //  * k_parab_ppic<F> -- from the last PPIC fit of a workspace (frame normal
 //    from the stored normal equations, the tangents as the fit built them),
