@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -112,7 +113,7 @@ class Clocks:
 
     def __init__(self, device):
         self.p = None
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.out = os.path.join(tempfile.gettempdir(), f"ft_bench_clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.out), exist_ok=True)
             self.f = open(self.out, "w")
