@@ -434,7 +434,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                     const int b = (int)(((float)rem + 0.5f) * inv_s);
                     const int di = a - R, dj = b - R, dk = rem - b * side - R;
                     const int ii = ci + di, jj = cj + dj, kk = ck + dk;
-                    if (ii >= 0 && jj >= 0 && kk >= 0 && ii < n0 && jj < n1 && kk < n2) {
+                    // a fragment's centroid lies in its own cell: a cell whose box is
+                    // farther than delta from this cell's centre holds none in the support
+                    const float bx = fmaxf(fabsf((float)di) - 0.5f, 0.0f), by = fmaxf(fabsf((float)dj) - 0.5f, 0.0f),
+                                bz = fmaxf(fabsf((float)dk) - 0.5f, 0.0f);
+                    const bool near = bx * bx + by * by + bz * bz <= f_thr;
+                    if (near && ii >= 0 && jj >= 0 && kk >= 0 && ii < n0 && jj < n1 && kk < n2) {
                         const int m2 = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
                         if (m2 >= 0) {
                             f0 = cell_off[m2];
