@@ -157,20 +157,29 @@ __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict
         {
             const int ph = threadIdx.x >> 6, d4 = threadIdx.x & 63;
             int4 t4 = make_int4(0, 0, 0, 0), b4 = make_int4(0, 0, 0, 0);
-#pragma unroll 4
-            for (int j = ph; j < (int)gridDim.x; j += 4) {
-                const int4 c = reinterpret_cast<const int4*>(hist + j * 256)[d4];
+            const int G = (int)gridDim.x, bid = (int)blockIdx.x;
+            const int4* __restrict__ h4 = reinterpret_cast<const int4*>(hist) + d4;
+            auto add = [&](const int4 c, int j) {
                 t4.x += c.x;
                 t4.y += c.y;
                 t4.z += c.z;
                 t4.w += c.w;
-                if (j < (int)blockIdx.x) {
+                if (j < bid) {
                     b4.x += c.x;
                     b4.y += c.y;
                     b4.z += c.z;
                     b4.w += c.w;
                 }
+            };
+            int j = ph;
+            for (; j + 28 < G; j += 32) {  // eight rows of this phase in flight together
+                int4 c[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) c[u] = h4[(j + 4 * u) * 64];
+#pragma unroll
+                for (int u = 0; u < 8; u++) add(c[u], j + 4 * u);
             }
+            for (; j < G; j += 4) add(h4[j * 64], j);
             reinterpret_cast<int4*>(&wcnt[ph][0])[d4] = t4;
             reinterpret_cast<int4*>(&wcnt[4 + ph][0])[d4] = b4;
         }
