@@ -172,7 +172,14 @@ __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict
                 }
             };
             int j = ph;
-            for (; j + 28 < G; j += 32) {  // eight rows of this phase in flight together
+            for (; j + 60 < G; j += 64) {  // sixteen rows of this phase in flight together
+                int4 c[16];
+#pragma unroll
+                for (int u = 0; u < 16; u++) c[u] = h4[(j + 4 * u) * 64];
+#pragma unroll
+                for (int u = 0; u < 16; u++) add(c[u], j + 4 * u);
+            }
+            for (; j + 28 < G; j += 32) {  // then eight
                 int4 c[8];
 #pragma unroll
                 for (int u = 0; u < 8; u++) c[u] = h4[(j + 4 * u) * 64];
