@@ -67,42 +67,24 @@ __global__ void __launch_bounds__(kB) k_scan_reduce(L ld, const long long* n_ptr
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-// exclusive scan of the gridDim-of-the-reduce partials (<= 1024) in one block
-__global__ void __launch_bounds__(1024) k_scan_partials(long long* partials, int G, long long* total) {
-    __shared__ long long sm[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long v = (threadIdx.x < G) ? partials[threadIdx.x] : 0;
-    long long x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sm[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        long long t = sm[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        sm[lane] = t;
-    }
-    __syncthreads();
-    const long long before = (w > 0) ? sm[w - 1] : 0;
-    if (threadIdx.x < G) partials[threadIdx.x] = before + x - v;
-    if (threadIdx.x == 0) *total = sm[31];
-}
-
+// The down-sweep: each block sums the reduce partials of the blocks before it
+// (gridDim <= kB, one per thread) for its carry, block 0 also writes the total;
+// then its segment is scanned tile by tile.
 template <class L>
 __global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, const long long* partials,
-                                                  int* out) {
+                                                  int* out, long long* total) {
     __shared__ long long sm[kB / 32];
     const long long n = *n_ptr;
     const long long s = seg_len(n, gridDim.x);
     const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
-    long long carry = partials[blockIdx.x];
+    long long carry;
+    {
+        const long long p = (threadIdx.x < gridDim.x) ? partials[threadIdx.x] : 0;
+        long long excl;
+        carry = block_excl_scan((threadIdx.x < blockIdx.x) ? p : 0, excl, sm);
+        const long long all = block_excl_scan(p, excl, sm);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *total = all;
+    }
     for (long long base = b0; base < b1; base += kB) {
         const long long i = base + threadIdx.x;
         const long long v = (i < b1) ? ld(i) : 0;
@@ -373,10 +355,9 @@ cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const 
     const int G = ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     LoadCounts ld{in};
-    count_launches(3);
+    count_launches(2);
     k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
-    k_scan_partials<<<1, 1024, 0, s>>>(part, G, total);
-    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out);
+    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out, total);
     return cudaGetLastError();
 }
 
@@ -385,10 +366,9 @@ cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, 
     const int G = ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     LoadHeads ld{keys};
-    count_launches(3);
+    count_launches(2);
     k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
-    k_scan_partials<<<1, 1024, 0, s>>>(part, G, total);
-    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out);
+    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out, total);
     return cudaGetLastError();
 }
 
