@@ -399,6 +399,7 @@ struct ClipJob {
 
 constexpr int kClipV = 12;     // polygon capacity of the warp-cooperative path
 constexpr int kClipJobs = 64;  // <= 2 crossings per lane and stage
+constexpr int kClipThreads = 256;
 
 // Warp-cooperative canonical clip: lane l holds candidate cb + l.  Each stage
 // computes the inside flags per lane, queues every crossing of the warp in
@@ -537,18 +538,18 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) k_clip(F fr, const int* __restrict__ cand_tri,
+__global__ void __launch_bounds__(kClipThreads) k_clip(F fr, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
                                                    const double* __restrict__ tri_nrm,
                                                    unsigned* __restrict__ keys, unsigned* __restrict__ vals,
                                                    ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
                                                    float4* __restrict__ cen32, int fp32, const ft_counters* ctr) {
-    __shared__ ClipJob s_jobs[kThreads / 32][kClipJobs];
+    __shared__ ClipJob s_jobs[kClipThreads / 32][kClipJobs];
     ClipJob* jobs = s_jobs[threadIdx.x >> 5];
     const long long C = ctr->C;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = (long long)gridDim.x * (kThreads / 32);
-    for (long long cb = ((long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32; cb < C; cb += nwarps * 32) {
+    const long long nwarps = (long long)gridDim.x * (kClipThreads / 32);
+    for (long long cb = ((long long)blockIdx.x * (kClipThreads / 32) + (threadIdx.x >> 5)) * 32; cb < C; cb += nwarps * 32) {
         const long long c = cb + lane;
         const bool active = c < C;
         int idx[3] = {0, 0, 0};
@@ -640,7 +641,7 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     ws->last_precision = fp32 ? FT_FP32C : FT_FP64;
-    k_clip<F><<<ws->sm_count * ws->tune.clip_bps, kThreads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
+    k_clip<F><<<ws->sm_count * ws->tune.clip_bps, kClipThreads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
                                                                     ws->tri_nrm, ws->keys[0], ws->vals[0], ws->rec, ws->rec32,
                                                                     ws->cen32, fp32 ? 1 : 0, ws->ctr);
     return cudaGetLastError();

@@ -4,8 +4,9 @@
 //
 // Element counts live in device memory (no host round trip), so every kernel
 // here splits its range into gridDim.x contiguous segments computed on the
-// device.  No kernel waits on another block: each pass is reduce -> scan ->
-// scatter in separate launches.
+// device.  No kernel waits on another block: a scan is a reduce launch and a
+// down-sweep launch, a radix pass a histogram launch and a scatter launch (the
+// down-sweep and the scatter each combine the per-block partials themselves).
 #include "ft_internal.cuh"
 
 namespace {
