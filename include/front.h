@@ -380,7 +380,7 @@ int ft_batch_status(ft_workspace* ws, void* stream, uint32_t* bits);
  * them by timing.
  * --------------------------------------------------------------------------- */
 typedef struct {
-    int32_t clip_blocks_per_sm; /* canonical clip (front_bin), default 4            */
+    int32_t clip_blocks_per_sm; /* canonical clip (front_bin), default 3            */
     int32_t ppic_blocks_per_sm; /* PPIC accumulation, default 4                      */
     int32_t csf_blocks_per_sm;  /* force clear (batch) and face force, default 16     */
     int32_t fill_blocks_per_sm; /* column parity fill, default 8                     */

@@ -67,7 +67,7 @@ int allocate(ft_workspace* ws, long long map_cells) {
     cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, ws->device);
     // segments of the scan / sort kernels; the sort stages 256 x grid_blocks counts in shared memory
     ws->grid_blocks = ws->sm_count > 192 ? 192 : ws->sm_count;
-    ws->tune = ft_tune{4, 4, 16, 8, 4, 0, ws->grid_blocks};
+    ws->tune = ft_tune{3, 4, 16, 8, 4, 0, ws->grid_blocks};
     size_t tot = 0;
     cudaError_t e = cudaSuccess;
     const size_t C = (size_t)ws->max_cand, Mx = (size_t)ws->max_cells, T = (size_t)ws->max_nt;

@@ -111,7 +111,7 @@ extern "C" int ft_autotune(ft_workspace* ws, const ft_front* f, const ft_params*
     for (int g : {16, 32, 64, 96, 128, ws->grid_blocks})
         if (g <= ws->grid_blocks && (segs.empty() || segs.back() != g)) segs.push_back(g);
     Knob knobs[7] = {{&ws->tune.seg_blocks, 0, segs},
-                     {&ws->tune.clip_bps, 0, {2, 4, 6, 8, 12, 16}},
+                     {&ws->tune.clip_bps, 0, {2, 3, 4, 6, 9, 12}},
                      {&ws->tune.fill_bps, 1, {2, 4, 8, 16}},
                      {&ws->tune.ppic_dynamic, 2, {0, 1}},
                      {&ws->tune.ppic_min_blocks, 2, {4, 6}},

@@ -537,8 +537,11 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
     return n;
 }
 
+// 80 registers (a few bytes of spills) let three blocks of 256 threads share
+// an SM instead of two: 24 resident warps hide more of the float64 and local
+// memory latency of the clip.
 template <class F>
-__global__ void __launch_bounds__(kClipThreads) k_clip(F fr, const int* __restrict__ cand_tri,
+__global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
                                                    const double* __restrict__ tri_nrm,
                                                    unsigned* __restrict__ keys, unsigned* __restrict__ vals,
