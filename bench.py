@@ -393,27 +393,24 @@ def run_ours(a):
         d2h += sum(o.numel() * o.element_size() for o in outs.values())
     torch.cuda.synchronize()
     e2e_ms = 0.0
-    # each front on its own compute stream plus an upload and a download stream:
-    # the face velocities (needed only by the last step) go up while the front
-    # is binned and fitted, alpha comes down during the fit and the force during
-    # the interpolation, and the two fronts overlap each other
+    # each front on its own compute stream plus a copy stream: the face
+    # velocities (needed only by the last step) go up and alpha comes down while
+    # the front is binned and fitted, and the two fronts overlap each other
     sides = [torch.cuda.Stream(device=dev) for _ in fcs]
-    ups = [torch.cuda.Stream(device=dev) for _ in fcs]
-    downs = [torch.cuda.Stream(device=dev) for _ in fcs]
+    copies = [torch.cuda.Stream(device=dev) for _ in fcs]
     for _ in range(a.e2e_steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for sd, up, dn in zip(sides, ups, downs):
+        for sd, cp in zip(sides, copies):
             sd.wait_stream(stream)
-            up.wait_stream(stream)
-            dn.wait_stream(stream)
-        for (hv, ht, hf), (v, t, fa), fc, o, c, sd, up, dn in zip(hin, dfr, fcs, hout, counts, sides, ups, downs):
-            faces_in, alpha_ready, force_ready = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
-            with torch.cuda.stream(up):
+            cp.wait_stream(stream)
+        for (hv, ht, hf), (v, t, fa), fc, o, c, sd, cp in zip(hin, dfr, fcs, hout, counts, sides, copies):
+            faces_in, alpha_ready = torch.cuda.Event(), torch.cuda.Event()
+            with torch.cuda.stream(cp):
                 for dst, src in zip(fa, hf):
                     dst.copy_(src, non_blocking=True)
-                faces_in.record(up)
+                faces_in.record(cp)
             with torch.cuda.stream(sd):
                 v.copy_(hv, non_blocking=True)
                 t.copy_(ht, non_blocking=True)
@@ -422,22 +419,19 @@ def run_ours(a):
                 alpha_ready.record(sd)
                 F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
                 F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
-                force_ready.record(sd)
-                M = c["M"]
-                o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
-                o["normal"].copy_(fc.normal[:M], non_blocking=True)
                 sd.wait_event(faces_in)
                 F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
-                o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
-            with torch.cuda.stream(dn):
-                dn.wait_event(alpha_ready)
-                o["alpha"].copy_(fc.alpha, non_blocking=True)
-                dn.wait_event(force_ready)
+                M = c["M"]
                 o["force"].copy_(fc.force, non_blocking=True)
-        for sd, up, dn in zip(sides, ups, downs):
+                o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
+                o["normal"].copy_(fc.normal[:M], non_blocking=True)
+                o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
+            with torch.cuda.stream(cp):
+                cp.wait_event(alpha_ready)
+                o["alpha"].copy_(fc.alpha, non_blocking=True)
+        for sd, cp in zip(sides, copies):
             stream.wait_stream(sd)
-            stream.wait_stream(up)
-            stream.wait_stream(dn)
+            stream.wait_stream(cp)
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
@@ -470,9 +464,8 @@ def run_ours(a):
         "paraboloid": parab,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
-                "launch": "eager calls; per front a compute stream, an upload stream (faces up during the "
-                          "binning and the fit) and a download stream (alpha down during the fit, the force during "
-                          "the interpolation), the two fronts concurrently"},
+                "launch": "eager calls; per front a compute stream and a copy stream (faces up and alpha down "
+                          "overlap the binning and the fit), the two fronts concurrently"},
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }
