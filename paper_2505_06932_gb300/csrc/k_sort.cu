@@ -12,6 +12,9 @@
 namespace {
 
 constexpr int kB = 256;             // threads per block
+constexpr int kKPT = 4;             // keys per thread and tile of the radix scatter
+constexpr int kTile = kKPT * kB;    // keys per tile
+constexpr int kRows = kKPT * (kB / 32);  // (row, warp) pairs of a tile
 
 __device__ __forceinline__ long long seg_len(long long n, int G) {
     long long s = (n + G - 1) / G;
@@ -116,16 +119,16 @@ __global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ 
     hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];  // block-major (coalesced)
 }
 
-// Stable scatter: each block walks its segment in tiles of 256 keys in order
-// (the next tile's keys loaded while this one is ranked); a key's destination
-// is the digit's offset for this block + the count of the same digit earlier
-// in the segment (earlier tiles, earlier warps, lower lanes).
+// Stable scatter: each block walks its segment in tiles of kTile keys in
+// order; a key's destination is the digit's offset for this block + the count
+// of the same digit earlier in the segment (earlier tiles, then earlier places
+// in its own tile).
 __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
                                                       unsigned* __restrict__ kout, unsigned* __restrict__ vout,
                                                       const long long* n_ptr, int shift,
                                                       const int* __restrict__ hist, long long* total) {
     __shared__ int base[256];
-    __shared__ __align__(16) int wcnt[kB / 32][256];
+    __shared__ __align__(16) int wcnt[kRows][256];
     const long long n = *n_ptr;
     const long long s = seg_len(n, gridDim.x);
     const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
@@ -196,48 +199,62 @@ __global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict
         if (blockIdx.x == 0 && threadIdx.x == kB - 1) *total = excl + tot;
         __syncthreads();
     }
-    // the next tile's key and value are loaded while this tile is ranked
-    unsigned kn = FT_SENTINEL, vn = 0;
-    if (b0 + threadIdx.x < b1) {
-        kn = kin[b0 + threadIdx.x];
-        vn = vin[b0 + threadIdx.x];
+    // Tiles of kTile = kKPT x 256 keys.  Row j of a tile is the 256 keys
+    // t0 + 256 j + threadIdx.x (coalesced); a key's place in the tile is
+    // (row, warp, lane), and its rank among the tile's keys of its digit counts
+    // the earlier (row, warp) pairs and the lower lanes of its own.  Four rows
+    // per tile cut the barriers per key fourfold.  The next tile's keys and
+    // values are loaded while this one is ranked.
+    unsigned kn[kKPT], vn[kKPT];
+#pragma unroll
+    for (int j = 0; j < kKPT; j++) {
+        const long long i = b0 + j * kB + threadIdx.x;
+        kn[j] = (i < b1) ? kin[i] : FT_SENTINEL;
+        vn[j] = (i < b1) ? vin[i] : 0u;
     }
-    for (long long t0 = b0; t0 < b1; t0 += kB) {
-        const unsigned k = kn, v = vn;
-        const long long in = t0 + kB + threadIdx.x;
-        kn = FT_SENTINEL;
-        vn = 0;
-        if (in < b1) {
-            kn = kin[in];
-            vn = vin[in];
+    for (long long t0 = b0; t0 < b1; t0 += kTile) {
+        unsigned k[kKPT], v[kKPT];
+#pragma unroll
+        for (int j = 0; j < kKPT; j++) {
+            k[j] = kn[j];
+            v[j] = vn[j];
+            const long long i = t0 + kTile + j * kB + threadIdx.x;
+            kn[j] = (i < b1) ? kin[i] : FT_SENTINEL;
+            vn[j] = (i < b1) ? vin[i] : 0u;
         }
-        for (int d = 0; d < kB / 32; d++) wcnt[d][threadIdx.x] = 0;
+#pragma unroll
+        for (int r = 0; r < kRows; r++) wcnt[r][threadIdx.x] = 0;
         __syncthreads();
-        const bool valid = (k != FT_SENTINEL);
-        const unsigned dig = valid ? ((k >> shift) & 255u) : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, dig);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0) wcnt[w][dig] = __popc(peers);
-        __syncthreads();
-        // per digit: exclusive prefix over warps (thread = digit)
-        {
-            int run = 0;
-            for (int d = 0; d < kB / 32; d++) {
-                const int c = wcnt[d][threadIdx.x];
-                wcnt[d][threadIdx.x] = run;
-                run += c;
-            }
-            // the total of this tile for the digit is `run`
-            __syncthreads();
-            if (valid) {
-                const int dst = base[dig] + wcnt[w][dig] + rank;
-                kout[dst] = k;
-                vout[dst] = v;
-            }
-            __syncthreads();
-            base[threadIdx.x] += run;
+        unsigned dig[kKPT];
+        int rank[kKPT];
+#pragma unroll
+        for (int j = 0; j < kKPT; j++) {
+            const bool valid = (k[j] != FT_SENTINEL);
+            dig[j] = valid ? ((k[j] >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+            rank[j] = __popc(peers & ((1u << lane) - 1u));
+            if (valid && rank[j] == 0) wcnt[j * (kB / 32) + w][dig[j]] = __popc(peers);
         }
         __syncthreads();
+        // per digit (thread = digit): exclusive prefix over the (row, warp) pairs
+        int run = 0;
+#pragma unroll 8
+        for (int r = 0; r < kRows; r++) {
+            const int c = wcnt[r][threadIdx.x];
+            wcnt[r][threadIdx.x] = run;
+            run += c;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kKPT; j++) {
+            if (dig[j] < 256u) {
+                const int dst = base[dig[j]] + wcnt[j * (kB / 32) + w][dig[j]] + rank[j];
+                kout[dst] = k[j];
+                vout[dst] = v[j];
+            }
+        }
+        __syncthreads();
+        base[threadIdx.x] += run;  // the tile's keys of this digit; read after the next tile's first barrier
     }
 }
 
