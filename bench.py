@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--paraboloid-reps", type=int, default=5,
                     help="timed calls of front_volume_fraction_ppic (the paper's own alpha) on the step's fits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="install ft_autotune's launch shapes on each front's workspace before timing")
     ap.add_argument("--batch-steps", type=int, default=5,
                     help="timed steps of the batched form (512 fronts); 0: skip")
     ap.add_argument("--batch-fronts", type=int, default=512)
@@ -247,6 +249,12 @@ def run_ours(a):
         for _ in range(max(3, warmup)):
             step(prm, fcs)
         torch.cuda.synchronize()
+        tunings = None
+        if a.autotune:
+            tunings = [F.ft_autotune(fc.ws, prm, reps=3, verts=v, tris=t) for (v, t, fa), fc in zip(dfr, fcs)]
+            for _ in range(max(3, warmup)):
+                step(prm, fcs)
+            torch.cuda.synchronize()
         counts = [fc.ws.counts() for fc in fcs]
         status = [fc.ws.status() for fc in fcs]
         if any(status):
@@ -288,7 +296,7 @@ def run_ours(a):
         clk = clk.stop() if clk else None
         total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         return dict(prm=prm, fcs=fcs, counts=counts, total_ms=total_ms, phase_ms=phase_ms,
-                    ppic_ms=ppic_ms_eager, launches=launches, clocks=clk, graph=graph)
+                    ppic_ms=ppic_ms_eager, launches=launches, clocks=clk, graph=graph, tunings=tunings)
 
     def measure_batch_of_fronts(precision, steps):
         """The same fronts as one batch (one launch sequence for both), one CUDA
@@ -455,7 +463,11 @@ def run_ours(a):
                                    "FP64 path: 1e-12 / 1e-9 (checked by tests/test_gpu_parity.py)",
                    "l2": "flushed (512 MB write) before every timed step",
                    "launch": "eager" if a.no_graph else "one CUDA graph per step, the two fronts on two streams",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}",
+                   "launch_shapes": ([{k: t[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm",
+                                                          "csf_blocks_per_sm", "fill_blocks_per_sm",
+                                                          "ppic_min_blocks", "ppic_dynamic", "sort_blocks")}
+                                      for t in r["tunings"]] if r["tunings"] else "library defaults")},
         "phases_ms": phases,
         "phases_note": "eager per-call CUDA-event times per step (sum over fronts), not the graph replay",
         "roofline": roof,

@@ -111,7 +111,16 @@ __global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ 
     const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
     h[threadIdx.x] = 0;
     __syncthreads();
-    for (long long i = b0 + threadIdx.x; i < b1; i += kB) {
+    long long i = b0 + threadIdx.x;
+    for (; i + 3 * kB < b1; i += 4 * kB) {  // four loads in flight
+        unsigned k[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) k[u] = keys[i + u * kB];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (k[u] != FT_SENTINEL) atomicAdd(&h[(k[u] >> shift) & 255u], 1);
+    }
+    for (; i < b1; i += kB) {
         const unsigned k = keys[i];
         if (k != FT_SENTINEL) atomicAdd(&h[(k >> shift) & 255u], 1);
     }
