@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--paraboloid-reps", type=int, default=5,
                     help="timed calls of front_volume_fraction_ppic (the paper's own alpha) on the step's fits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-mode", choices=("concurrent", "staggered"), default="concurrent",
+                    help="e2e leg: the fronts on concurrent compute streams, or one after the other so that "
+                         "the first front's outputs go down while the second is computed")
     ap.add_argument("--autotune", action="store_true",
                     help="install ft_autotune's launch shapes on each front's workspace before timing")
     ap.add_argument("--batch-steps", type=int, default=5,
@@ -351,7 +354,7 @@ def run_ours(a):
     except Exception:
         probe = None
     # DRAM bytes of one call (k_ppic_acc<float> + k_ppic_solve) from one ncu capture on the ellipsoid front
-    traffic = (13.444864e6 + 3.780096e6) if prec == F.FT_FP32C else None
+    traffic = (13.446400e6 + 0.000256e6 + 3.779328e6) if prec == F.FT_FP32C else None
     roof = {"kernel": "k_ppic_acc + k_ppic_solve", "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of each kernel on the "
@@ -401,48 +404,102 @@ def run_ours(a):
         d2h += sum(o.numel() * o.element_size() for o in outs.values())
     torch.cuda.synchronize()
     e2e_ms = 0.0
-    # each front on its own compute stream plus a copy stream: the face
-    # velocities (needed only by the last step) go up and alpha comes down while
-    # the front is binned and fitted, and the two fronts overlap each other
-    sides = [torch.cuda.Stream(device=dev) for _ in fcs]
-    copies = [torch.cuda.Stream(device=dev) for _ in fcs]
-    for _ in range(a.e2e_steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for sd, cp in zip(sides, copies):
-            sd.wait_stream(stream)
-            cp.wait_stream(stream)
-        for (hv, ht, hf), (v, t, fa), fc, o, c, sd, cp in zip(hin, dfr, fcs, hout, counts, sides, copies):
-            faces_in, alpha_ready = torch.cuda.Event(), torch.cuda.Event()
-            with torch.cuda.stream(cp):
-                for dst, src in zip(fa, hf):
-                    dst.copy_(src, non_blocking=True)
-                faces_in.record(cp)
-            with torch.cuda.stream(sd):
-                v.copy_(hv, non_blocking=True)
-                t.copy_(ht, non_blocking=True)
-                F.front_bin(fc.ws, v, t, prm)
-                F.front_volume_fraction(fc.ws, fc.alpha)
-                alpha_ready.record(sd)
-                F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
-                F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
-                sd.wait_event(faces_in)
-                F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
-                M = c["M"]
-                o["force"].copy_(fc.force, non_blocking=True)
-                o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
-                o["normal"].copy_(fc.normal[:M], non_blocking=True)
-                o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
-            with torch.cuda.stream(cp):
-                cp.wait_event(alpha_ready)
-                o["alpha"].copy_(fc.alpha, non_blocking=True)
-        for sd, cp in zip(sides, copies):
-            stream.wait_stream(sd)
-            stream.wait_stream(cp)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
+    if a.e2e_mode == "staggered":
+        # the fronts one after the other on one compute stream, so the first
+        # front's outputs go down while the second is computed; one upload stream
+        # (vertices and triangles of every front first, then the face velocities
+        # in front order) and a download stream per front
+        sd = torch.cuda.Stream(device=dev)
+        up = torch.cuda.Stream(device=dev)
+        dns = [torch.cuda.Stream(device=dev) for _ in fcs]
+        for _ in range(a.e2e_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for x in [sd, up] + dns:
+                x.wait_stream(stream)
+            vt_in = [torch.cuda.Event() for _ in fcs]
+            faces_in = [torch.cuda.Event() for _ in fcs]
+            with torch.cuda.stream(up):
+                for (hv, ht, hf), (v, t, fa), ev in zip(hin, dfr, vt_in):
+                    v.copy_(hv, non_blocking=True)
+                    t.copy_(ht, non_blocking=True)
+                    ev.record(up)
+                for (hv, ht, hf), (v, t, fa), ev in zip(hin, dfr, faces_in):
+                    for dst, src in zip(fa, hf):
+                        dst.copy_(src, non_blocking=True)
+                    ev.record(up)
+            for f, ((v, t, fa), fc, o, c, dn) in enumerate(zip(dfr, fcs, hout, counts, dns)):
+                alpha_ready, force_ready, vel_ready = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+                with torch.cuda.stream(sd):
+                    sd.wait_event(vt_in[f])
+                    F.front_bin(fc.ws, v, t, prm)
+                    F.front_volume_fraction(fc.ws, fc.alpha)
+                    alpha_ready.record(sd)
+                    F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
+                    F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+                    force_ready.record(sd)
+                    sd.wait_event(faces_in[f])
+                    F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+                    vel_ready.record(sd)
+                with torch.cuda.stream(dn):
+                    M = c["M"]
+                    dn.wait_event(alpha_ready)
+                    o["alpha"].copy_(fc.alpha, non_blocking=True)
+                    dn.wait_event(force_ready)
+                    o["force"].copy_(fc.force, non_blocking=True)
+                    o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
+                    o["normal"].copy_(fc.normal[:M], non_blocking=True)
+                    dn.wait_event(vel_ready)
+                    o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
+            for x in [sd, up] + dns:
+                stream.wait_stream(x)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+    else:
+        # each front on its own compute stream plus a copy stream: the face
+        # velocities (needed only by the last step) go up and alpha comes down while
+        # the front is binned and fitted, and the two fronts overlap each other
+        sides = [torch.cuda.Stream(device=dev) for _ in fcs]
+        copies = [torch.cuda.Stream(device=dev) for _ in fcs]
+        for _ in range(a.e2e_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for sd, cp in zip(sides, copies):
+                sd.wait_stream(stream)
+                cp.wait_stream(stream)
+            for (hv, ht, hf), (v, t, fa), fc, o, c, sd, cp in zip(hin, dfr, fcs, hout, counts, sides, copies):
+                faces_in, alpha_ready = torch.cuda.Event(), torch.cuda.Event()
+                with torch.cuda.stream(cp):
+                    for dst, src in zip(fa, hf):
+                        dst.copy_(src, non_blocking=True)
+                    faces_in.record(cp)
+                with torch.cuda.stream(sd):
+                    v.copy_(hv, non_blocking=True)
+                    t.copy_(ht, non_blocking=True)
+                    F.front_bin(fc.ws, v, t, prm)
+                    F.front_volume_fraction(fc.ws, fc.alpha)
+                    alpha_ready.record(sd)
+                    F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
+                    F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+                    sd.wait_event(faces_in)
+                    F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+                    M = c["M"]
+                    o["force"].copy_(fc.force, non_blocking=True)
+                    o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
+                    o["normal"].copy_(fc.normal[:M], non_blocking=True)
+                    o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
+                with torch.cuda.stream(cp):
+                    cp.wait_event(alpha_ready)
+                    o["alpha"].copy_(fc.alpha, non_blocking=True)
+            for sd, cp in zip(sides, copies):
+                stream.wait_stream(sd)
+                stream.wait_stream(cp)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
     e2e_max = allmax(ws, e2e_ms)
     e2e_value = allsum(ws, cells_per_step * a.e2e_steps) / (e2e_max * 1e-3)
 
@@ -476,8 +533,12 @@ def run_ours(a):
         "paraboloid": parab,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
-                "launch": "eager calls; per front a compute stream and a copy stream (faces up and alpha down "
-                          "overlap the binning and the fit), the two fronts concurrently"},
+                "mode": a.e2e_mode,
+                "launch": ("eager calls; the fronts one after the other on one compute stream (the first "
+                           "front's outputs go down while the second is computed), one upload stream, a download "
+                           "stream per front" if a.e2e_mode == "staggered" else
+                           "eager calls; per front a compute stream and a copy stream (faces up and alpha down "
+                           "overlap the binning and the fit), the two fronts concurrently")},
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }

@@ -424,27 +424,46 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
             // far beyond the float rounding, so the truncation is exact
             const float inv_s = 1.0f / (float)side, inv_ss = inv_s * inv_s;
             int qn = 0;
+            // neighbour l -> offsets (di, dj, dk) and its interfacial index m2 (-1: none,
+            // outside the grid, or a box beyond the support: a fragment's centroid
+            // lies in its own cell, so such a cell holds none in the support)
+            auto neighbour = [&](int l, int& di, int& dj, int& dk) -> int {
+                const int a = (int)(((float)l + 0.5f) * inv_ss);
+                const int rem = l - a * side * side;
+                const int b = (int)(((float)rem + 0.5f) * inv_s);
+                di = a - R;
+                dj = b - R;
+                dk = rem - b * side - R;
+                const int ii = ci + di, jj = cj + dj, kk = ck + dk;
+                const float bx = fmaxf(fabsf((float)di) - 0.5f, 0.0f), by = fmaxf(fabsf((float)dj) - 0.5f, 0.0f),
+                            bz = fmaxf(fabsf((float)dk) - 0.5f, 0.0f);
+                const bool near = bx * bx + by * by + bz * bz <= f_thr;
+                if (!near || ii < 0 || jj < 0 || kk < 0 || ii >= n0 || jj >= n1 || kk >= n2) return -1;
+                return idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
+            };
+            // the index map of the next round is read while this round runs
+            int m2_next = -1;
+            {
+                int di, dj, dk;
+                if (lane < nb) m2_next = neighbour(lane, di, dj, dk);
+            }
             for (int cb = 0; cb < nb; cb += 32) {
                 const int l = cb + lane;
                 int f0 = 0, cnt = 0, dcode = 0;
                 float ox = 0.f, oy = 0.f, oz = 0.f;
+                const int m2 = m2_next;
+                if (l + 32 < nb) {
+                    int di, dj, dk;
+                    m2_next = neighbour(l + 32, di, dj, dk);
+                }
                 if (l < nb) {
                     const int a = (int)(((float)l + 0.5f) * inv_ss);
                     const int rem = l - a * side * side;
                     const int b = (int)(((float)rem + 0.5f) * inv_s);
                     const int di = a - R, dj = b - R, dk = rem - b * side - R;
-                    const int ii = ci + di, jj = cj + dj, kk = ck + dk;
-                    // a fragment's centroid lies in its own cell: a cell whose box is
-                    // farther than delta from this cell's centre holds none in the support
-                    const float bx = fmaxf(fabsf((float)di) - 0.5f, 0.0f), by = fmaxf(fabsf((float)dj) - 0.5f, 0.0f),
-                                bz = fmaxf(fabsf((float)dk) - 0.5f, 0.0f);
-                    const bool near = bx * bx + by * by + bz * bz <= f_thr;
-                    if (near && ii >= 0 && jj >= 0 && kk >= 0 && ii < n0 && jj < n1 && kk < n2) {
-                        const int m2 = idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
-                        if (m2 >= 0) {
-                            f0 = cell_off[m2];
-                            cnt = cell_off[m2 + 1] - f0;
-                        }
+                    if (m2 >= 0) {
+                        f0 = cell_off[m2];
+                        cnt = cell_off[m2 + 1] - f0;
                     }
                     dcode = ((di + 8) << 8) | ((dj + 8) << 4) | (dk + 8);
                     ox = (float)di;
