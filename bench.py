@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--paraboloid-reps", type=int, default=5,
                     help="timed calls of front_volume_fraction_ppic (the paper's own alpha) on the step's fits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-mode", choices=("concurrent", "staggered"), default="concurrent",
+    ap.add_argument("--e2e-mode", choices=("concurrent", "staggered", "graph"), default="graph",
                     help="e2e leg: the fronts on concurrent compute streams, or one after the other so that "
-                         "the first front's outputs go down while the second is computed")
+                         "the first front's outputs go down while the second is computed (eager, or that step "
+                         "captured in one CUDA graph)")
     ap.add_argument("--autotune", action="store_true",
                     help="install ft_autotune's launch shapes on each front's workspace before timing")
     ap.add_argument("--batch-steps", type=int, default=5,
@@ -403,21 +404,26 @@ def run_ours(a):
         h2d += hv.numel() * 8 + ht.numel() * 4 + sum(f.numel() * 8 for f in hf)
         d2h += sum(o.numel() * o.element_size() for o in outs.values())
     torch.cuda.synchronize()
-    e2e_ms = 0.0
-    if a.e2e_mode == "staggered":
-        # the fronts one after the other on one compute stream, so the first
-        # front's outputs go down while the second is computed; one upload stream
-        # (vertices and triangles of every front first, then the face velocities
-        # in front order) and a download stream per front
-        sd = torch.cuda.Stream(device=dev)
-        up = torch.cuda.Stream(device=dev)
-        dns = [torch.cuda.Stream(device=dev) for _ in fcs]
-        for _ in range(a.e2e_steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+    # One step's transfers and calls, enqueued on streams forked from `cs` and
+    # joined back to it.  "staggered": the fronts one after the other on one
+    # compute stream, so the first front's outputs go down while the second is
+    # computed; one upload stream (vertices and triangles of every front first,
+    # then the face velocities in front order) and a download stream per front.
+    # "concurrent": each front on its own compute stream with a copy stream (face
+    # velocities up and alpha down during the binning and the fit).
+    stag = a.e2e_mode in ("staggered", "graph")
+    if stag:
+        e2e_streams = dict(sd=torch.cuda.Stream(device=dev), up=torch.cuda.Stream(device=dev),
+                           dns=[torch.cuda.Stream(device=dev) for _ in fcs])
+    else:
+        e2e_streams = dict(sides=[torch.cuda.Stream(device=dev) for _ in fcs],
+                           copies=[torch.cuda.Stream(device=dev) for _ in fcs])
+
+    def e2e_enqueue(cs):
+        if stag:
+            sd, up, dns = e2e_streams["sd"], e2e_streams["up"], e2e_streams["dns"]
             for x in [sd, up] + dns:
-                x.wait_stream(stream)
+                x.wait_stream(cs)
             vt_in = [torch.cuda.Event() for _ in fcs]
             faces_in = [torch.cuda.Event() for _ in fcs]
             with torch.cuda.stream(up):
@@ -453,23 +459,12 @@ def run_ours(a):
                     dn.wait_event(vel_ready)
                     o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
             for x in [sd, up] + dns:
-                stream.wait_stream(x)
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
-    else:
-        # each front on its own compute stream plus a copy stream: the face
-        # velocities (needed only by the last step) go up and alpha comes down while
-        # the front is binned and fitted, and the two fronts overlap each other
-        sides = [torch.cuda.Stream(device=dev) for _ in fcs]
-        copies = [torch.cuda.Stream(device=dev) for _ in fcs]
-        for _ in range(a.e2e_steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+                cs.wait_stream(x)
+        else:
+            sides, copies = e2e_streams["sides"], e2e_streams["copies"]
             for sd, cp in zip(sides, copies):
-                sd.wait_stream(stream)
-                cp.wait_stream(stream)
+                sd.wait_stream(cs)
+                cp.wait_stream(cs)
             for (hv, ht, hf), (v, t, fa), fc, o, c, sd, cp in zip(hin, dfr, fcs, hout, counts, sides, copies):
                 faces_in, alpha_ready = torch.cuda.Event(), torch.cuda.Event()
                 with torch.cuda.stream(cp):
@@ -495,11 +490,29 @@ def run_ours(a):
                     cp.wait_event(alpha_ready)
                     o["alpha"].copy_(fc.alpha, non_blocking=True)
             for sd, cp in zip(sides, copies):
-                stream.wait_stream(sd)
-                stream.wait_stream(cp)
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
+                cs.wait_stream(sd)
+                cs.wait_stream(cp)
+
+    e2e_graph = None
+    if a.e2e_mode == "graph":
+        # the step above captured once (copies from and to the same pinned host
+        # buffers, which a caller refills between steps) and replayed every step
+        e2e_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(e2e_graph):
+            e2e_enqueue(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(a.e2e_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if e2e_graph is not None:
+            e2e_graph.replay()
+        else:
+            e2e_enqueue(stream)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
     e2e_max = allmax(ws, e2e_ms)
     e2e_value = allsum(ws, cells_per_step * a.e2e_steps) / (e2e_max * 1e-3)
 
@@ -534,11 +547,12 @@ def run_ours(a):
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
                 "mode": a.e2e_mode,
-                "launch": ("eager calls; the fronts one after the other on one compute stream (the first "
-                           "front's outputs go down while the second is computed), one upload stream, a download "
-                           "stream per front" if a.e2e_mode == "staggered" else
-                           "eager calls; per front a compute stream and a copy stream (faces up and alpha down "
-                           "overlap the binning and the fit), the two fronts concurrently")},
+                "launch": (("one CUDA graph per step: " if a.e2e_mode == "graph" else "eager calls; ") +
+                           ("the fronts one after the other on one compute stream (the first front's outputs go "
+                            "down while the second is computed), one upload stream, a download stream per front"
+                            if stag else
+                            "per front a compute stream and a copy stream (faces up and alpha down overlap the "
+                            "binning and the fit), the two fronts concurrently"))},
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }
