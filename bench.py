@@ -59,6 +59,9 @@ def parse():
                     help="e2e leg: the fronts on concurrent compute streams, or one after the other so that "
                          "the first front's outputs go down while the second is computed (eager, or that step "
                          "captured in one CUDA graph)")
+    ap.add_argument("--no-fork", dest="fork", action="store_false",
+                    help="graph steps with each front's five calls in order on one stream, instead of the DAG "
+                         "per front (volume fraction beside the PPIC fit, the interpolation beside everything)")
     ap.add_argument("--autotune", action="store_true",
                     help="install ft_autotune's launch shapes on each front's workspace before timing")
     ap.add_argument("--batch-steps", type=int, default=5,
@@ -232,20 +235,43 @@ def run_ours(a):
         for (v, t, fa), fc in zip(dfr, fcs):
             step_one(prm, fc, v, t, fa, ev)
 
+    def step_forked(prm, fc, v, t, fa, sd, sa, si):
+        """One front's step as a small DAG: the volume fraction and the PPIC fit
+        both need only the binning (they may share a workspace on two streams),
+        the CSF force needs both, the interpolation only the face velocities."""
+        with torch.cuda.stream(si):
+            F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+        with torch.cuda.stream(sd):
+            F.front_bin(fc.ws, v, t, prm)
+        sa.wait_stream(sd)
+        with torch.cuda.stream(sa):
+            F.front_volume_fraction(fc.ws, fc.alpha)
+        with torch.cuda.stream(sd):
+            F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
+            sd.wait_stream(sa)
+            F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+
     def capture(prm, fcs):
         """One CUDA graph for a whole step; the fronts are independent, so each
-        runs on its own stream forked from (and joined back to) the capture stream."""
+        runs on its own streams forked from (and joined back to) the capture
+        stream: as the DAG of step_forked, or (--no-fork) in order on one stream."""
         g = torch.cuda.CUDAGraph()
-        sides = [torch.cuda.Stream(device=dev) for _ in fcs]
+        per = 3 if a.fork else 1
+        sides = [[torch.cuda.Stream(device=dev) for _ in range(per)] for _ in fcs]
         with torch.cuda.graph(g):
             cs = torch.cuda.current_stream()
-            for sd in sides:
-                sd.wait_stream(cs)
-            for (v, t, fa), fc, sd in zip(dfr, fcs, sides):
-                with torch.cuda.stream(sd):
-                    step_one(prm, fc, v, t, fa)
-            for sd in sides:
-                cs.wait_stream(sd)
+            for ss in sides:
+                for x in ss:
+                    x.wait_stream(cs)
+            for (v, t, fa), fc, ss in zip(dfr, fcs, sides):
+                if a.fork:
+                    step_forked(prm, fc, v, t, fa, *ss)
+                else:
+                    with torch.cuda.stream(ss[0]):
+                        step_one(prm, fc, v, t, fa)
+            for ss in sides:
+                for x in ss:
+                    cs.wait_stream(x)
         return g
 
     def measure(precision, steps, warmup, clocks=False):
@@ -532,7 +558,10 @@ def run_ours(a):
                    "stated_error": "FP32 form: |d alpha| <= 1e-6, |d kappa| <= 1e-4 rel. vs the FP64 oracle; "
                                    "FP64 path: 1e-12 / 1e-9 (checked by tests/test_gpu_parity.py)",
                    "l2": "flushed (512 MB write) before every timed step",
-                   "launch": "eager" if a.no_graph else "one CUDA graph per step, the two fronts on two streams",
+                   "launch": "eager" if a.no_graph else (
+                       "one CUDA graph per step, per front a DAG on three streams (alpha beside the PPIC fit, "
+                       "the interpolation beside both)" if a.fork else
+                       "one CUDA graph per step, the two fronts on two streams"),
                    "parallelism": f"replicas x{ws}",
                    "launch_shapes": ([{k: t[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm",
                                                           "csf_blocks_per_sm", "fill_blocks_per_sm",

@@ -29,7 +29,12 @@
  *     by key.  Fronts are closed 2-manifold triangle meshes whose triangles are
  *     counter-clockwise seen from outside the region with indicator 1.
  *   - A workspace is tied to one grid shape and one device, and is not safe to
- *     use from two streams at once.
+ *     use from two streams at once, with one exception: once front_bin (or
+ *     front_bin_batch) has completed, front_volume_fraction(_batch) and
+ *     front_curvature_ppic may run on two streams at the same time (they read
+ *     the binned fragments and write disjoint state; the calls themselves come
+ *     from one host thread); front_csf_force(_batch) must then wait for both.
+ *     front_interp_velocity takes no workspace.
  */
 #ifndef FRONT_H
 #define FRONT_H
