@@ -273,7 +273,7 @@ int front_advect_rk4(const ft_grid* g, const double* U, const double* V, const d
  * the one array and resets the parts that must start cleared, so calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialized by the caller. */
-#define FT_NOALLOC_SCRATCH_BYTES 7340032
+#define FT_NOALLOC_SCRATCH_BYTES 8388608
 #define FT_NOALLOC_MAX_GRID_CELLS 262144
 #define FT_NOALLOC_MAX_TRIANGLES 16384
 #define FT_NOALLOC_MAX_CANDIDATES 32768

@@ -46,7 +46,7 @@ cudaError_t alloc(T** p, size_t n, size_t* total) {
 void release(ft_workspace* ws) {
     void* ptrs[] = {ws->ctr,     ws->idx_map, ws->tri_cnt,  ws->tri_off,  ws->tri_box, ws->cand_tri,
                     ws->keys[0], ws->keys[1], ws->vals[0],  ws->vals[1],  ws->rec,     ws->cells,
-                    ws->cell_off, ws->heads,  ws->cell_L,   ws->cell_P,   ws->partials, ws->hist,
+                    ws->cell_off, ws->cell_cnt, ws->cell_L,   ws->cell_P,   ws->partials,
                     ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info, ws->srec, ws->srec32, ws->scen,
                     ws->fdesc,   ws->fbase,   ws->fstatus, ws->tri_nrm, ws->planes};
     for (void* p : ptrs)
@@ -55,17 +55,11 @@ void release(ft_workspace* ws) {
     if (ws->h_fbase) cudaFreeHost(ws->h_fbase);
 }
 
-int key_bits_for(long long ncells) {
-    int bits = 1;
-    while (bits < 32 && ((ncells - 1) >> bits) > 0) bits++;
-    return bits < 8 ? 8 : bits;
-}
-
 // Device memory of a workspace for `map_cells` index-map entries, once the
 // capacities are set; frees everything and returns FT_ERR_ALLOC on failure.
 int allocate(ft_workspace* ws, long long map_cells) {
     cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, ws->device);
-    // segments of the scan / sort kernels; the sort stages 256 x grid_blocks counts in shared memory
+    // segments (blocks) of the scan kernels; the down-sweeps take one partial per thread
     ws->grid_blocks = ws->sm_count > 192 ? 192 : ws->sm_count;
     ws->tune = ft_tune{3, 4, 16, 8, 4, 0, ws->grid_blocks};
     size_t tot = 0;
@@ -97,11 +91,10 @@ int allocate(ft_workspace* ws, long long map_cells) {
     e = e ? e : alloc(&ws->fit_info, 2 * Mx, &tot);
     e = e ? e : alloc(&ws->cells, Mx + 1, &tot);
     e = e ? e : alloc(&ws->cell_off, Mx + 1, &tot);
-    e = e ? e : alloc(&ws->heads, C, &tot);
+    e = e ? e : alloc(&ws->cell_cnt, (size_t)map_cells, &tot);
     e = e ? e : alloc(&ws->cell_L, Mx, &tot);
     e = e ? e : alloc(&ws->cell_P, Mx, &tot);
     e = e ? e : alloc(&ws->partials, 2 * (size_t)(ws->grid_blocks + 1), &tot);
-    e = e ? e : alloc(&ws->hist, 256 * (size_t)ws->grid_blocks, &tot);
     if (ws->batch) {
         const size_t F = (size_t)ws->max_fronts;
         e = e ? e : alloc(&ws->fdesc, F, &tot);
@@ -112,9 +105,9 @@ int allocate(ft_workspace* ws, long long map_cells) {
             e = cudaMallocHost(reinterpret_cast<void**>(&ws->h_fbase), 4 * (F + 1) * sizeof(long long));
         if (e == cudaSuccess) e = cudaMemset(ws->fstatus, 0, F * sizeof(unsigned));
     }
-    if (e == cudaSuccess) e = ft::prepare_sort(ws->grid_blocks);
     if (e == cudaSuccess) e = cudaMemset(ws->ctr, 0, sizeof(ft_counters));
     if (e == cudaSuccess) e = cudaMemset(ws->idx_map, 0xff, sizeof(int) * (size_t)map_cells);
+    if (e == cudaSuccess) e = cudaMemset(ws->cell_cnt, 0, sizeof(int) * (size_t)map_cells);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         release(ws);
@@ -161,7 +154,6 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
         free(ws);
         return FT_ERR_ARG;
     }
-    ws->key_bits = key_bits_for(ws->ncells);
     const int r = allocate(ws, ws->ncells);
     if (r != FT_OK) {
         free(ws);
@@ -191,7 +183,6 @@ int ft_batch_workspace_create(ft_workspace** out, const ft_batch_capacity* cap, 
         free(ws);
         return FT_ERR_ARG;
     }
-    ws->key_bits = 8;
     const int r = allocate(ws, ws->max_grid_cells);
     if (r != FT_OK) {
         free(ws);
@@ -287,7 +278,6 @@ int ft_batch_set(ft_workspace* ws, int32_t nf, const ft_batch_front* fr, void* s
     ws->fitted = false;
     ws->nt_total = nt;
     ws->nv_total = nv;
-    ws->key_bits = key_bits_for(cells);
     ws->binned = false;
     return FT_OK;
 }
@@ -340,8 +330,7 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     cudaStream_t s = as_stream(stream);
     cudaError_t e = ft::launch_clear_map(ws, s);
     if (e == cudaSuccess) e = ft::launch_bin(ws, f, p, s);
-    if (e == cudaSuccess) e = ft::launch_sort(ws, s);
-    if (e == cudaSuccess) e = ft::launch_rle(ws, s);
+    if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
     ws->fitted = false;
@@ -437,8 +426,7 @@ int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream) {
     cudaStream_t s = as_stream(stream);
     cudaError_t e = ft::launch_clear_map(ws, s);
     if (e == cudaSuccess) e = ft::launch_bin_batch(ws, p, s);
-    if (e == cudaSuccess) e = ft::launch_sort(ws, s);
-    if (e == cudaSuccess) e = ft::launch_rle(ws, s);
+    if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
     ws->fitted = false;

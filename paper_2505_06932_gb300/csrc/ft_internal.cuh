@@ -85,7 +85,6 @@ struct ft_workspace {
     int device;
     int sm_count;
     int grid_blocks;       // blocks of the segmented scan/sort kernels
-    int key_bits;          // bits of the largest cell key
     ft_grid g;
     long long ncells;
     long long max_nt, max_cand, max_cells;
@@ -115,12 +114,11 @@ struct ft_workspace {
     int* fit_info;         // max_cells x 2: fragments in support, status bits
     unsigned* cells;       // max_cells + 1
     int* cell_off;         // max_cells + 1
-    int* heads;            // max_cand: cell index of each sorted pair (scan output)
+    int* cell_cnt;         // index-map entries: kept pairs per cell key while binning, else all zero
     double* cell_L;        // max_cells
     double* cell_P;        // max_cells
-    int* partials;         // grid_blocks + 1
-    int* hist;             // 256 * grid_blocks
-    int sorted_buf;        // which keys/vals buffer holds the sorted pairs
+    int* partials;         // 2 (grid_blocks + 1): per-block sums of the segmented scans
+    int sorted_buf;        // which keys/vals buffer holds the pairs in cell order
     ft_tune tune;
 
     // batched form (nf > 0 after ft_batch_set; 0 for a one-front workspace)
@@ -152,11 +150,9 @@ void count_launches(int n);  // kernels launched by this library (ft_launch_coun
 cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s);
 cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n,
                                long long* total, cudaStream_t s);
-cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, const long long* n,
-                              long long* total, cudaStream_t s);
-cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s);
-cudaError_t prepare_sort(int grid_blocks);
-cudaError_t launch_rle(ft_workspace* ws, cudaStream_t s);
+// the kept pairs into cell order: interfacial cell list, offsets, index map
+// (the counts k_clip left in cell_cnt over keys [0, nkeys)); resets cell_cnt
+cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s);
 cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_clear_map(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s);

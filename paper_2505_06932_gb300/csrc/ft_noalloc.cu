@@ -14,7 +14,7 @@ constexpr long long kMaxCells = FT_NOALLOC_MAX_GRID_CELLS;
 constexpr long long kMaxNt = FT_NOALLOC_MAX_TRIANGLES;
 constexpr long long kMaxCand = FT_NOALLOC_MAX_CANDIDATES;
 constexpr long long kMaxIcells = FT_NOALLOC_MAX_CANDIDATES;
-constexpr int kBlocks = 32;  // segments of the scan / sort kernels (histogram scan fits 48 KB of shared memory)
+constexpr int kBlocks = 32;  // segments (blocks) of the scan kernels
 
 constexpr size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -33,12 +33,11 @@ constexpr size_t kOffVals1 = kOffVals0 + up256(sizeof(unsigned) * kMaxCand);
 constexpr size_t kOffRec = kOffVals1 + up256(sizeof(unsigned) * kMaxCand);
 constexpr size_t kOffCells = kOffRec + up256(sizeof(ft_frag) * kMaxCand);
 constexpr size_t kOffCellOff = kOffCells + up256(sizeof(unsigned) * (kMaxIcells + 1));
-constexpr size_t kOffHeads = kOffCellOff + up256(sizeof(int) * (kMaxIcells + 1));
-constexpr size_t kOffCellL = kOffHeads + up256(sizeof(int) * kMaxCand);
+constexpr size_t kOffCnt = kOffCellOff + up256(sizeof(int) * (kMaxIcells + 1));
+constexpr size_t kOffCellL = kOffCnt + up256(sizeof(int) * kMaxCells);
 constexpr size_t kOffCellP = kOffCellL + up256(sizeof(double) * kMaxIcells);
 constexpr size_t kOffPartials = kOffCellP + up256(sizeof(double) * kMaxIcells);
-constexpr size_t kOffHist = kOffPartials + up256(sizeof(long long) * (kBlocks + 1));
-constexpr size_t kEnd = kOffHist + up256(sizeof(int) * 256 * kBlocks);
+constexpr size_t kEnd = kOffPartials + up256(sizeof(long long) * 2 * (kBlocks + 1));
 static_assert(kEnd <= FT_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the static array");
 
 // The scratch itself.  Every device that loads the library holds one copy
@@ -90,9 +89,6 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
     cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev);
     ws.grid_blocks = kBlocks;
     ws.tune = ft_tune{4, 4, 16, 8, 4, 0, kBlocks};
-    int bits = 1;
-    while (bits < 32 && ((ncells - 1) >> bits) > 0) bits++;
-    ws.key_bits = bits < 8 ? 8 : bits;
     ws.g = *g;
     ws.ncells = ncells;
     ws.max_nt = kMaxNt;
@@ -113,19 +109,18 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
     ws.rec = reinterpret_cast<ft_frag*>(base + kOffRec);
     ws.cells = reinterpret_cast<unsigned*>(base + kOffCells);
     ws.cell_off = reinterpret_cast<int*>(base + kOffCellOff);
-    ws.heads = reinterpret_cast<int*>(base + kOffHeads);
+    ws.cell_cnt = reinterpret_cast<int*>(base + kOffCnt);
     ws.cell_L = reinterpret_cast<double*>(base + kOffCellL);
     ws.cell_P = reinterpret_cast<double*>(base + kOffCellP);
     ws.partials = reinterpret_cast<int*>(base + kOffPartials);
-    ws.hist = reinterpret_cast<int*>(base + kOffHist);
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // the array keeps the previous call's contents: reset counters and index map
+    // the array keeps the previous call's contents: reset counters, index map and cell counts
     cudaError_t e = cudaMemsetAsync(ws.ctr, 0, sizeof(ft_counters), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.idx_map, 0xff, sizeof(int) * (size_t)ncells, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.cell_cnt, 0, sizeof(int) * (size_t)ncells, s);
     if (e == cudaSuccess) e = ft::launch_bin(&ws, f, p, s);
-    if (e == cudaSuccess) e = ft::launch_sort(&ws, s);
-    if (e == cudaSuccess) e = ft::launch_rle(&ws, s);
+    if (e == cudaSuccess) e = ft::launch_place_pairs(&ws, ncells, s);
     if (e == cudaSuccess) e = ft::launch_alpha(&ws, alpha, s);
     if (e == cudaSuccess) {
         ft::count_launches(1);

@@ -544,9 +544,10 @@ template <class F>
 __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
                                                    const double* __restrict__ tri_nrm,
-                                                   unsigned* __restrict__ keys, unsigned* __restrict__ vals,
-                                                   ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
-                                                   float4* __restrict__ cen32, int fp32, const ft_counters* ctr) {
+                                                   unsigned* __restrict__ keys, unsigned* __restrict__ ranks,
+                                                   int* __restrict__ cell_cnt, ft_frag* __restrict__ rec,
+                                                   ft_frag32* __restrict__ rec32, float4* __restrict__ cen32, int fp32,
+                                                   const ft_counters* ctr) {
     __shared__ ClipJob s_jobs[kClipThreads / 32][kClipJobs];
     ClipJob* jobs = s_jobs[threadIdx.x >> 5];
     const long long C = ctr->C;
@@ -619,7 +620,9 @@ __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
                 key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
         }
         keys[c] = key;
-        vals[c] = (unsigned)c;
+        // the pair's rank among its cell's pairs, in arrival order (k_cell_order
+        // puts each cell's pairs back into slot order)
+        if (key != FT_SENTINEL) ranks[c] = (unsigned)atomicAdd(&cell_cnt[key], 1);
     }
 }
 
@@ -645,7 +648,7 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     ws->last_precision = fp32 ? FT_FP32C : FT_FP64;
     k_clip<F><<<ws->sm_count * ws->tune.clip_bps, kClipThreads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
-                                                                    ws->tri_nrm, ws->keys[0], ws->vals[0], ws->rec, ws->rec32,
+                                                                    ws->tri_nrm, ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec, ws->rec32,
                                                                     ws->cen32, fp32 ? 1 : 0, ws->ctr);
     return cudaGetLastError();
 }

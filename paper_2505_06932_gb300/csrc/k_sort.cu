@@ -1,20 +1,16 @@
-// k_sort.cu -- front_bin, part 2: device-wide exclusive scans, the stable LSD
-// radix sort of the (cell key, candidate slot) pairs and the run-length
-// encoding into the interfacial-cell list.
+// k_sort.cu -- front_bin, part 2: device-wide exclusive scans, and the
+// (cell key, candidate slot) pairs put into cell order by counting, with the
+// interfacial-cell list, its pair offsets and the index map.
 //
 // Element counts live in device memory (no host round trip), so every kernel
 // here splits its range into gridDim.x contiguous segments computed on the
 // device.  No kernel waits on another block: a scan is a reduce launch and a
-// down-sweep launch, a radix pass a histogram launch and a scatter launch (the
-// down-sweep and the scatter each combine the per-block partials themselves).
+// down-sweep launch (the down-sweep combines the per-block partials itself).
 #include "ft_internal.cuh"
 
 namespace {
 
 constexpr int kB = 256;             // threads per block
-constexpr int kKPT = 4;             // keys per thread and tile of the radix scatter
-constexpr int kTile = kKPT * kB;    // keys per tile
-constexpr int kRows = kKPT * (kB / 32);  // (row, warp) pairs of a tile
 
 __device__ __forceinline__ long long seg_len(long long n, int G) {
     long long s = (n + G - 1) / G;
@@ -52,10 +48,6 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long& exc
 struct LoadCounts {
     const int* in;
     __device__ long long operator()(long long i) const { return in[i]; }
-};
-struct LoadHeads {
-    const unsigned* keys;
-    __device__ long long operator()(long long i) const { return (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0; }
 };
 
 template <class L>
@@ -100,189 +92,137 @@ __global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, 
 }
 
 // ---------------------------------------------------------------------------
-// radix sort: 8-bit digits, stable, segment per block
+// Pairs into cell order by counting.  k_clip counted every kept pair into
+// cell_cnt[key]; the atomic's return value, the pair's rank among its cell's
+// pairs in arrival order, sits in ranks[slot].  Then:
+//  k_cnt_reduce, k_cnt_down -- one exclusive scan over the whole key range of
+//    the packed counts (pairs << 32 | has pairs): a key with pairs becomes
+//    interfacial cell m with pair offset cell_off[m] (cells, cell_off,
+//    idx_map), and its count goes back to zero, so that cell_cnt is all zero
+//    again for the next binning;
+//  k_place -- every kept pair to cell_off[m] + rank;
+//  k_cell_order -- each cell's pairs into ascending slot order, the order of a
+//    stable sort by key (pairs are generated in slot order).
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kB) k_radix_hist(const unsigned* __restrict__ keys, const long long* n_ptr,
-                                                   int shift, int* __restrict__ hist) {
-    __shared__ int h[256];
-    const long long n = *n_ptr;
-    const long long s = seg_len(n, gridDim.x);
-    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    long long i = b0 + threadIdx.x;
-    for (; i + 3 * kB < b1; i += 4 * kB) {  // four loads in flight
-        unsigned k[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) k[u] = keys[i + u * kB];
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-            if (k[u] != FT_SENTINEL) atomicAdd(&h[(k[u] >> shift) & 255u], 1);
-    }
-    for (; i < b1; i += kB) {
-        const unsigned k = keys[i];
-        if (k != FT_SENTINEL) atomicAdd(&h[(k >> shift) & 255u], 1);
-    }
-    __syncthreads();
-    hist[blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];  // block-major (coalesced)
+__device__ __forceinline__ long long pack_cnt(int c) { return ((long long)c << 32) | (c > 0 ? 1 : 0); }
+
+// segment of the key range per block: whole tiles of 4 keys per thread
+__device__ __forceinline__ long long key_seg(long long n, int G) {
+    const long long s = (n + G - 1) / G;
+    return (s + 4 * kB - 1) / (4 * kB) * (4 * kB);
 }
 
-// Stable scatter: each block walks its segment in tiles of kTile keys in
-// order; a key's destination is the digit's offset for this block + the count
-// of the same digit earlier in the segment (earlier tiles, then earlier places
-// in its own tile).
-__global__ void __launch_bounds__(kB) k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
-                                                      unsigned* __restrict__ kout, unsigned* __restrict__ vout,
-                                                      const long long* n_ptr, int shift,
-                                                      const int* __restrict__ hist, long long* total) {
-    __shared__ int base[256];
-    __shared__ __align__(16) int wcnt[kRows][256];
-    const long long n = *n_ptr;
-    const long long s = seg_len(n, gridDim.x);
-    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// four counts from i (a multiple of 4; the array is 16-byte aligned), zeros past b1
+__device__ __forceinline__ int4 load_cnt4(const int* __restrict__ cnt, long long i, long long b1) {
+    if (i + 3 < b1) return *reinterpret_cast<const int4*>(cnt + i);
+    int4 c = make_int4(0, 0, 0, 0);
+    if (i < b1) c.x = cnt[i];
+    if (i + 1 < b1) c.y = cnt[i + 1];
+    if (i + 2 < b1) c.z = cnt[i + 2];
+    return c;
+}
+
+__global__ void __launch_bounds__(kB) k_cnt_reduce(const int* __restrict__ cnt, long long nkeys,
+                                                   long long* __restrict__ partials) {
+    __shared__ long long sm[kB / 32];
+    const long long s = key_seg(nkeys, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(nkeys, b0 + s);
+    long long acc = 0;
+    for (long long i = b0 + 4 * threadIdx.x; i < b1; i += 4 * kB) {
+        const int4 c = load_cnt4(cnt, i, b1);
+        acc += pack_cnt(c.x) + pack_cnt(c.y) + pack_cnt(c.z) + pack_cnt(c.w);
+    }
+    long long excl;
+    const long long tot = block_excl_scan(acc, excl, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// Writes nothing but the totals and the count reset when M exceeds the
+// capacity (k_cap_cells then flags it and resets M and P).
+__global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long long nkeys,
+                                                 const long long* __restrict__ partials, unsigned* __restrict__ cells,
+                                                 int* __restrict__ cell_off, int* __restrict__ idx_map,
+                                                 long long max_cells, ft_counters* ctr) {
+    __shared__ long long sm[kB / 32];
+    const long long s = key_seg(nkeys, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(nkeys, b0 + s);
+    long long carry, all;
     {
-        // this block's offset for digit d = threadIdx.x: the keys of all smaller
-        // digits plus the keys of digit d in earlier segments, from the
-        // block-major histogram (one coalesced row per segment) and a block scan
-        // of the digit totals
-        // thread t adds four digits (4 (t % 64) ...) over the rows j = t / 64 mod 4
-        // with 16-byte loads; the four row phases are then combined
-        {
-            const int ph = threadIdx.x >> 6, d4 = threadIdx.x & 63;
-            int4 t4 = make_int4(0, 0, 0, 0), b4 = make_int4(0, 0, 0, 0);
-            const int G = (int)gridDim.x, bid = (int)blockIdx.x;
-            const int4* __restrict__ h4 = reinterpret_cast<const int4*>(hist) + d4;
-            auto add = [&](const int4 c, int j) {
-                t4.x += c.x;
-                t4.y += c.y;
-                t4.z += c.z;
-                t4.w += c.w;
-                if (j < bid) {
-                    b4.x += c.x;
-                    b4.y += c.y;
-                    b4.z += c.z;
-                    b4.w += c.w;
+        const long long p = (threadIdx.x < gridDim.x) ? partials[threadIdx.x] : 0;
+        long long excl;
+        carry = block_excl_scan((threadIdx.x < blockIdx.x) ? p : 0, excl, sm);
+        all = block_excl_scan(p, excl, sm);
+    }
+    const long long P = all >> 32, M = all & 0xffffffffLL;
+    const bool fits = M <= max_cells;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->P = P;
+        ctr->M = M;
+        if (fits) cell_off[M] = (int)P;
+    }
+    for (long long base = b0; base < b1; base += 4 * kB) {
+        const long long i = base + 4 * threadIdx.x;
+        const int4 c4 = load_cnt4(cnt, i, b1);
+        const int c[4] = {c4.x, c4.y, c4.z, c4.w};
+        long long excl;
+        const long long tot =
+            block_excl_scan(pack_cnt(c[0]) + pack_cnt(c[1]) + pack_cnt(c[2]) + pack_cnt(c[3]), excl, sm);
+        long long run = carry + excl;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (c[j] > 0) {
+                const long long key = i + j;
+                if (fits) {
+                    const int m = (int)(run & 0xffffffffLL);
+                    cells[m] = (unsigned)key;
+                    cell_off[m] = (int)(run >> 32);
+                    idx_map[key] = m;
                 }
-            };
-            int j = ph;
-            for (; j + 60 < G; j += 64) {  // sixteen rows of this phase in flight together
-                int4 c[16];
-#pragma unroll
-                for (int u = 0; u < 16; u++) c[u] = h4[(j + 4 * u) * 64];
-#pragma unroll
-                for (int u = 0; u < 16; u++) add(c[u], j + 4 * u);
+                cnt[key] = 0;
             }
-            for (; j + 28 < G; j += 32) {  // then eight
-                int4 c[8];
-#pragma unroll
-                for (int u = 0; u < 8; u++) c[u] = h4[(j + 4 * u) * 64];
-#pragma unroll
-                for (int u = 0; u < 8; u++) add(c[u], j + 4 * u);
-            }
-            for (; j < G; j += 4) add(h4[j * 64], j);
-            reinterpret_cast<int4*>(&wcnt[ph][0])[d4] = t4;
-            reinterpret_cast<int4*>(&wcnt[4 + ph][0])[d4] = b4;
+            run += pack_cnt(c[j]);
         }
-        __syncthreads();
-        int tot = 0, before = 0;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            tot += wcnt[q][threadIdx.x];
-            before += wcnt[4 + q][threadIdx.x];
-        }
-        __syncthreads();
-        int x = tot;  // inclusive scan over the digits
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wcnt[0][w] = x;
-        __syncthreads();
-        int wbase = 0;
-        for (int q = 0; q < w; q++) wbase += wcnt[0][q];
-        const int excl = wbase + x - tot;
-        base[threadIdx.x] = excl + before;
-        if (blockIdx.x == 0 && threadIdx.x == kB - 1) *total = excl + tot;
-        __syncthreads();
-    }
-    // Tiles of kTile = kKPT x 256 keys.  Row j of a tile is the 256 keys
-    // t0 + 256 j + threadIdx.x (coalesced); a key's place in the tile is
-    // (row, warp, lane), and its rank among the tile's keys of its digit counts
-    // the earlier (row, warp) pairs and the lower lanes of its own.  Four rows
-    // per tile cut the barriers per key fourfold.  The next tile's keys and
-    // values are loaded while this one is ranked.
-    unsigned kn[kKPT], vn[kKPT];
-#pragma unroll
-    for (int j = 0; j < kKPT; j++) {
-        const long long i = b0 + j * kB + threadIdx.x;
-        kn[j] = (i < b1) ? kin[i] : FT_SENTINEL;
-        vn[j] = (i < b1) ? vin[i] : 0u;
-    }
-    for (long long t0 = b0; t0 < b1; t0 += kTile) {
-        unsigned k[kKPT], v[kKPT];
-#pragma unroll
-        for (int j = 0; j < kKPT; j++) {
-            k[j] = kn[j];
-            v[j] = vn[j];
-            const long long i = t0 + kTile + j * kB + threadIdx.x;
-            kn[j] = (i < b1) ? kin[i] : FT_SENTINEL;
-            vn[j] = (i < b1) ? vin[i] : 0u;
-        }
-#pragma unroll
-        for (int r = 0; r < kRows; r++) wcnt[r][threadIdx.x] = 0;
-        __syncthreads();
-        unsigned dig[kKPT];
-        int rank[kKPT];
-#pragma unroll
-        for (int j = 0; j < kKPT; j++) {
-            const bool valid = (k[j] != FT_SENTINEL);
-            dig[j] = valid ? ((k[j] >> shift) & 255u) : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
-            rank[j] = __popc(peers & ((1u << lane) - 1u));
-            if (valid && rank[j] == 0) wcnt[j * (kB / 32) + w][dig[j]] = __popc(peers);
-        }
-        __syncthreads();
-        // per digit (thread = digit): exclusive prefix over the (row, warp) pairs
-        int run = 0;
-#pragma unroll 8
-        for (int r = 0; r < kRows; r++) {
-            const int c = wcnt[r][threadIdx.x];
-            wcnt[r][threadIdx.x] = run;
-            run += c;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kKPT; j++) {
-            if (dig[j] < 256u) {
-                const int dst = base[dig[j]] + wcnt[j * (kB / 32) + w][dig[j]] + rank[j];
-                kout[dst] = k[j];
-                vout[dst] = v[j];
-            }
-        }
-        __syncthreads();
-        base[threadIdx.x] += run;  // the tile's keys of this digit; read after the next tile's first barrier
+        carry += tot;
     }
 }
 
-// run-length encoding of the sorted keys: cells[m], cell_off[m], idx_map.
-// Writes nothing when M exceeds the capacity (k_cap_cells then resets M).
-__global__ void __launch_bounds__(kB) k_rle(const unsigned* __restrict__ keys, const int* __restrict__ head_idx,
-                                            unsigned* __restrict__ cells, int* __restrict__ cell_off,
-                                            int* __restrict__ idx_map, long long max_cells, const ft_counters* ctr) {
-    const long long P = ctr->P;
-    const long long M = ctr->M;  // computed by the head scan
+__global__ void __launch_bounds__(kB) k_place(const unsigned* __restrict__ keys, const unsigned* __restrict__ ranks,
+                                              const int* __restrict__ idx_map, const int* __restrict__ cell_off,
+                                              unsigned* __restrict__ skeys, unsigned* __restrict__ svals,
+                                              long long max_cells, const ft_counters* ctr) {
+    const long long C = ctr->C;
+    if (ctr->M > max_cells) return;
+    for (long long c = (long long)blockIdx.x * kB + threadIdx.x; c < C; c += (long long)gridDim.x * kB) {
+        const unsigned k = keys[c];
+        if (k == FT_SENTINEL) continue;
+        const long long dst = (long long)cell_off[idx_map[k]] + ranks[c];
+        skeys[dst] = k;
+        svals[dst] = (unsigned)c;
+    }
+}
+
+// Shell sort (gaps 57, 23, 10, 4, 1) of one cell's slots; cells rarely hold
+// more than a dozen pairs, and those arrive nearly in order.
+__global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
+                                                   long long max_cells, const ft_counters* ctr) {
+    const long long M = ctr->M;
     if (M > max_cells) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) cell_off[M] = (int)P;
-    for (long long q = (long long)blockIdx.x * kB + threadIdx.x; q < P; q += (long long)gridDim.x * kB) {
-        const unsigned k = keys[q];
-        if (q == 0 || keys[q - 1] != k) {
-            const int m = head_idx[q];
-            cells[m] = k;
-            cell_off[m] = (int)q;
-            idx_map[k] = m;
+    for (long long m = (long long)blockIdx.x * kB + threadIdx.x; m < M; m += (long long)gridDim.x * kB) {
+        unsigned* v = svals + cell_off[m];
+        const int n = cell_off[m + 1] - cell_off[m];
+        const int gaps[5] = {57, 23, 10, 4, 1};
+        for (int gi = 0; gi < 5; gi++) {
+            const int gap = gaps[gi];
+            for (int a = gap; a < n; a++) {
+                const unsigned x = v[a];
+                int b = a;
+                while (b >= gap && v[b - gap] > x) {
+                    v[b] = v[b - gap];
+                    b -= gap;
+                }
+                v[b] = x;
+            }
         }
     }
 }
@@ -388,48 +328,18 @@ cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_heads(ft_workspace* ws, const unsigned* keys, int* out, const long long* n,
-                              long long* total, cudaStream_t s) {
+cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s) {
     const int G = ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
-    LoadHeads ld{keys};
-    count_launches(2);
-    k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
-    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out, total);
-    return cudaGetLastError();
-}
-
-cudaError_t prepare_sort(int grid_blocks) {
-    (void)grid_blocks;  // no kernel of the sort needs more than the default shared memory
-    return cudaSuccess;
-}
-
-cudaError_t launch_sort(ft_workspace* ws, cudaStream_t s) {
-    const int G = ws->tune.seg_blocks;
-    const int passes = (ws->key_bits + 7) / 8;
-    int src = 0;
-    for (int p = 0; p < passes; p++) {
-        // pass 0 reads the candidates (sentinels dropped) and counts the pairs
-        const long long* n = (p == 0) ? &ws->ctr->C : &ws->ctr->P;
-        long long* tot = (p == 0) ? &ws->ctr->P : &ws->ctr->scratch;
-        count_launches(2);
-        k_radix_hist<<<G, kB, 0, s>>>(ws->keys[src], n, 8 * p, ws->hist);
-        k_radix_scatter<<<G, kB, 0, s>>>(ws->keys[src], ws->vals[src], ws->keys[src ^ 1], ws->vals[src ^ 1], n,
-                                         8 * p, ws->hist, tot);
-        src ^= 1;
-    }
-    ws->sorted_buf = src;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rle(ft_workspace* ws, cudaStream_t s) {
-    const unsigned* keys = ws->keys[ws->sorted_buf];
-    cudaError_t e = launch_scan_heads(ws, keys, ws->heads, &ws->ctr->P, &ws->ctr->M, s);
-    if (e != cudaSuccess) return e;
-    count_launches(2);
-    k_rle<<<ws->sm_count * 2, kB, 0, s>>>(keys, ws->heads, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
-                                          ws->ctr);
+    count_launches(5);
+    k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
+    k_cnt_down<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
+                                ws->ctr);
+    k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->idx_map, ws->cell_off, ws->keys[1],
+                                            ws->vals[1], ws->max_cells, ws->ctr);
+    k_cell_order<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->max_cells, ws->ctr);
     k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
+    ws->sorted_buf = 1;
     return cudaGetLastError();
 }
 
