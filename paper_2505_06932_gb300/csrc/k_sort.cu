@@ -107,20 +107,34 @@ __global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, 
 
 __device__ __forceinline__ long long pack_cnt(int c) { return ((long long)c << 32) | (c > 0 ? 1 : 0); }
 
-// segment of the key range per block: whole tiles of 4 keys per thread
+constexpr int kKeysPT = 16;  // keys per thread and tile of the key-range scan (four 16-byte loads in flight)
+
+// segment of the key range per block: whole tiles of kKeysPT keys per thread
 __device__ __forceinline__ long long key_seg(long long n, int G) {
     const long long s = (n + G - 1) / G;
-    return (s + 4 * kB - 1) / (4 * kB) * (4 * kB);
+    return (s + kKeysPT * kB - 1) / (kKeysPT * kB) * (kKeysPT * kB);
 }
 
-// four counts from i (a multiple of 4; the array is 16-byte aligned), zeros past b1
-__device__ __forceinline__ int4 load_cnt4(const int* __restrict__ cnt, long long i, long long b1) {
-    if (i + 3 < b1) return *reinterpret_cast<const int4*>(cnt + i);
-    int4 c = make_int4(0, 0, 0, 0);
-    if (i < b1) c.x = cnt[i];
-    if (i + 1 < b1) c.y = cnt[i + 1];
-    if (i + 2 < b1) c.z = cnt[i + 2];
-    return c;
+// this thread's counts of a tile: keys i .. i + kKeysPT - 1 (i a multiple of 4;
+// the array is 16-byte aligned), zeros past b1
+__device__ __forceinline__ void load_cnt_tile(const int* __restrict__ cnt, long long i, long long b1,
+                                              int (&c)[kKeysPT]) {
+#pragma unroll
+    for (int u = 0; u < kKeysPT / 4; u++) {
+        const long long k = i + 4 * u;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (k + 3 < b1) {
+            v = *reinterpret_cast<const int4*>(cnt + k);
+        } else {
+            if (k < b1) v.x = cnt[k];
+            if (k + 1 < b1) v.y = cnt[k + 1];
+            if (k + 2 < b1) v.z = cnt[k + 2];
+        }
+        c[4 * u] = v.x;
+        c[4 * u + 1] = v.y;
+        c[4 * u + 2] = v.z;
+        c[4 * u + 3] = v.w;
+    }
 }
 
 __global__ void __launch_bounds__(kB) k_cnt_reduce(const int* __restrict__ cnt, long long nkeys,
@@ -129,9 +143,11 @@ __global__ void __launch_bounds__(kB) k_cnt_reduce(const int* __restrict__ cnt, 
     const long long s = key_seg(nkeys, gridDim.x);
     const long long b0 = blockIdx.x * s, b1 = min(nkeys, b0 + s);
     long long acc = 0;
-    for (long long i = b0 + 4 * threadIdx.x; i < b1; i += 4 * kB) {
-        const int4 c = load_cnt4(cnt, i, b1);
-        acc += pack_cnt(c.x) + pack_cnt(c.y) + pack_cnt(c.z) + pack_cnt(c.w);
+    for (long long i = b0 + kKeysPT * threadIdx.x; i < b1; i += kKeysPT * kB) {
+        int c[kKeysPT];
+        load_cnt_tile(cnt, i, b1, c);
+#pragma unroll
+        for (int u = 0; u < kKeysPT; u++) acc += pack_cnt(c[u]);
     }
     long long excl;
     const long long tot = block_excl_scan(acc, excl, sm);
@@ -161,27 +177,31 @@ __global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long lon
         ctr->M = M;
         if (fits) cell_off[M] = (int)P;
     }
-    for (long long base = b0; base < b1; base += 4 * kB) {
-        const long long i = base + 4 * threadIdx.x;
-        const int4 c4 = load_cnt4(cnt, i, b1);
-        const int c[4] = {c4.x, c4.y, c4.z, c4.w};
-        long long excl;
-        const long long tot =
-            block_excl_scan(pack_cnt(c[0]) + pack_cnt(c[1]) + pack_cnt(c[2]) + pack_cnt(c[3]), excl, sm);
-        long long run = carry + excl;
+    for (long long base = b0; base < b1; base += kKeysPT * kB) {
+        const long long i = base + kKeysPT * threadIdx.x;
+        int c[kKeysPT];
+        load_cnt_tile(cnt, i, b1, c);
+        long long mine = 0;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (c[j] > 0) {
-                const long long key = i + j;
-                if (fits) {
-                    const int m = (int)(run & 0xffffffffLL);
-                    cells[m] = (unsigned)key;
-                    cell_off[m] = (int)(run >> 32);
-                    idx_map[key] = m;
+        for (int u = 0; u < kKeysPT; u++) mine += pack_cnt(c[u]);
+        long long excl;
+        const long long tot = block_excl_scan(mine, excl, sm);
+        if (mine != 0) {  // keys with pairs are rare: most threads skip the walk
+            long long run = carry + excl;
+#pragma unroll
+            for (int u = 0; u < kKeysPT; u++) {
+                if (c[u] > 0) {
+                    const long long key = i + u;
+                    if (fits) {
+                        const int m = (int)(run & 0xffffffffLL);
+                        cells[m] = (unsigned)key;
+                        cell_off[m] = (int)(run >> 32);
+                        idx_map[key] = m;
+                    }
+                    cnt[key] = 0;
                 }
-                cnt[key] = 0;
+                run += pack_cnt(c[u]);
             }
-            run += pack_cnt(c[j]);
         }
         carry += tot;
     }
@@ -202,28 +222,39 @@ __global__ void __launch_bounds__(kB) k_place(const unsigned* __restrict__ keys,
     }
 }
 
-// Shell sort (gaps 57, 23, 10, 4, 1) of one cell's slots; cells rarely hold
-// more than a dozen pairs, and those arrive nearly in order.
+// One warp per cell: every slot's place in the cell is the number of smaller
+// slots of the cell (slots are distinct).  Up to 32 pairs the lanes hold the
+// slots and count by shuffles, then write in place; a larger cell is ranked
+// from memory into tmp and copied back.
 __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
-                                                   long long max_cells, const ft_counters* ctr) {
+                                                   unsigned* __restrict__ tmp, long long max_cells,
+                                                   const ft_counters* ctr) {
     const long long M = ctr->M;
     if (M > max_cells) return;
-    for (long long m = (long long)blockIdx.x * kB + threadIdx.x; m < M; m += (long long)gridDim.x * kB) {
-        unsigned* v = svals + cell_off[m];
-        const int n = cell_off[m + 1] - cell_off[m];
-        const int gaps[5] = {57, 23, 10, 4, 1};
-        for (int gi = 0; gi < 5; gi++) {
-            const int gap = gaps[gi];
-            for (int a = gap; a < n; a++) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (kB / 32);
+    for (long long m = ((long long)blockIdx.x * kB + threadIdx.x) >> 5; m < M; m += nw) {
+        const int q0 = cell_off[m], n = cell_off[m + 1] - q0;
+        if (n <= 1) continue;
+        unsigned* v = svals + q0;
+        if (n <= 32) {
+            const unsigned x = (lane < n) ? v[lane] : 0xffffffffu;
+            int r = 0;
+            for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, x, o) < x) ? 1 : 0;
+            __syncwarp();
+            if (lane < n) v[r] = x;
+        } else {
+            unsigned* t = tmp + q0;
+            for (int a = lane; a < n; a += 32) {
                 const unsigned x = v[a];
-                int b = a;
-                while (b >= gap && v[b - gap] > x) {
-                    v[b] = v[b - gap];
-                    b -= gap;
-                }
-                v[b] = x;
+                int r = 0;
+                for (int b = 0; b < n; b++) r += (v[b] < x) ? 1 : 0;
+                t[r] = x;
             }
+            __syncwarp();
+            for (int a = lane; a < n; a += 32) v[a] = t[a];
         }
+        __syncwarp();
     }
 }
 
@@ -337,7 +368,8 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
                                 ws->ctr);
     k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->idx_map, ws->cell_off, ws->keys[1],
                                             ws->vals[1], ws->max_cells, ws->ctr);
-    k_cell_order<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->max_cells, ws->ctr);
+    // the ranks in vals[0] are spent once placed: that buffer is the scratch of large cells
+    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], ws->max_cells, ws->ctr);
     k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
     ws->sorted_buf = 1;
     return cudaGetLastError();
