@@ -146,7 +146,7 @@ int ft_bin_pairs(ft_workspace* ws, int64_t cap, uint32_t* keys, int32_t* tris, v
  * binary64 without contraction); the cell keeps the triangle iff every stage
  * leaves >= 3 vertices, the fan area vector is not zero, and the fragment does
  * not lie entirely in one of the cell's upper faces.  The kept (cell, triangle)
- * pairs are radix-sorted by cell key (triangles ascending within a cell); their
+ * pairs are put in cell-key order (triangles ascending within a cell); their
  * fragment moments are kept in the workspace for the next steps.  Requires
  * f->nt <= capacity.max_nt.  p->delta_max_h sets the grid margin. */
 int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* stream);
@@ -285,7 +285,7 @@ int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, const ft_par
  * simulation).  Many independent fronts, each with its own grid, run through
  * one launch sequence: their cells share one batch-global key space (front b's
  * cell with local key q has key key_base[b] + q, key_base[b] = sum of the
- * earlier fronts' n0*n1*n2), one radix sort and one interfacial-cell worklist,
+ * earlier fronts' n0*n1*n2), one pair placement and one interfacial-cell worklist,
  * so small fronts do not each pay a launch sequence.  Every front's results are
  * bit for bit those of the one-front calls on that front alone (each cell's
  * sums run over the same fragments in the same order).  Errors of one front (outside
@@ -393,8 +393,8 @@ typedef struct {
                                    6 resident blocks per SM (fewer registers each)   */
     int32_t ppic_dynamic;       /* PPIC cells from a global work counter (1) or
                                    interleaved over the warps (0, default)           */
-    int32_t sort_blocks;        /* segments of the radix sort and the scans (1 to the
-                                   SM count; 0: the SM count, default)               */
+    int32_t sort_blocks;        /* segments of the triangle-count scan of the binning
+                                   (1 to the SM count; 0: the SM count, default)     */
     int32_t pad;
     /* outputs of ft_autotune: what the tuned workload needed, for sizing a
      * workspace (ft_capacity / ft_batch_capacity) to it */

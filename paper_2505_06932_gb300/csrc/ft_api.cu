@@ -94,7 +94,7 @@ int allocate(ft_workspace* ws, long long map_cells) {
     e = e ? e : alloc(&ws->cell_cnt, (size_t)map_cells, &tot);
     e = e ? e : alloc(&ws->cell_L, Mx, &tot);
     e = e ? e : alloc(&ws->cell_P, Mx, &tot);
-    e = e ? e : alloc(&ws->partials, 2 * (size_t)(ws->grid_blocks + 1), &tot);
+    e = e ? e : alloc(&ws->partials, 2 * (size_t)(4 * ws->grid_blocks + 1), &tot);
     if (ws->batch) {
         const size_t F = (size_t)ws->max_fronts;
         e = e ? e : alloc(&ws->fdesc, F, &tot);

@@ -78,7 +78,7 @@ struct ft_tune {
     int fill_bps;   // k_alpha_fill blocks per SM
     int ppic_min_blocks;  // FP32 k_ppic_acc compiled for 4 (more registers) or 6 resident blocks per SM
     int ppic_dynamic;     // k_ppic_acc cells from a global work counter (1) or interleaved (0)
-    int seg_blocks;       // segments (blocks) of the radix sort and the scans, <= grid_blocks
+    int seg_blocks;       // segments (blocks) of the device scans, <= grid_blocks
 };
 
 struct ft_workspace {
@@ -117,7 +117,7 @@ struct ft_workspace {
     int* cell_cnt;         // index-map entries: kept pairs per cell key while binning, else all zero
     double* cell_L;        // max_cells
     double* cell_P;        // max_cells
-    int* partials;         // 2 (grid_blocks + 1): per-block sums of the segmented scans
+    int* partials;         // 2 (4 grid_blocks + 1): per-block sums (int64) of the segmented scans
     int sorted_buf;        // which keys/vals buffer holds the pairs in cell order
     ft_tune tune;
 

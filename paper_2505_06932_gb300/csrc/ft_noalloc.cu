@@ -37,7 +37,7 @@ constexpr size_t kOffCnt = kOffCellOff + up256(sizeof(int) * (kMaxIcells + 1));
 constexpr size_t kOffCellL = kOffCnt + up256(sizeof(int) * kMaxCells);
 constexpr size_t kOffCellP = kOffCellL + up256(sizeof(double) * kMaxIcells);
 constexpr size_t kOffPartials = kOffCellP + up256(sizeof(double) * kMaxIcells);
-constexpr size_t kEnd = kOffPartials + up256(sizeof(long long) * 2 * (kBlocks + 1));
+constexpr size_t kEnd = kOffPartials + up256(sizeof(long long) * (4 * kBlocks + 1));
 static_assert(kEnd <= FT_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the static array");
 
 // The scratch itself.  Every device that loads the library holds one copy

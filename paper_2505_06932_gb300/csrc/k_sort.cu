@@ -165,10 +165,16 @@ __global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long lon
     const long long b0 = blockIdx.x * s, b1 = min(nkeys, b0 + s);
     long long carry, all;
     {
-        const long long p = (threadIdx.x < gridDim.x) ? partials[threadIdx.x] : 0;
+        // the partials of the blocks before this one (gridDim.x may exceed kB)
+        long long pc = 0, pa = 0;
+        for (int t = threadIdx.x; t < (int)gridDim.x; t += kB) {
+            const long long p = partials[t];
+            pa += p;
+            if (t < (int)blockIdx.x) pc += p;
+        }
         long long excl;
-        carry = block_excl_scan((threadIdx.x < blockIdx.x) ? p : 0, excl, sm);
-        all = block_excl_scan(p, excl, sm);
+        carry = block_excl_scan(pc, excl, sm);
+        all = block_excl_scan(pa, excl, sm);
     }
     const long long P = all >> 32, M = all & 0xffffffffLL;
     const bool fits = M <= max_cells;
@@ -360,7 +366,9 @@ cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const 
 }
 
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s) {
-    const int G = ws->tune.seg_blocks;
+    // the key range is read once per scan kernel: 4 blocks per SM (up to
+    // 4 grid_blocks partials) keep enough loads in flight
+    const int G = 4 * ws->grid_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     count_launches(5);
     k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
