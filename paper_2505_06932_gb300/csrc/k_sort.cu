@@ -1,10 +1,9 @@
-// k_sort.cu -- front_bin, part 2: device-wide exclusive scans, and the
-// (cell key, candidate slot) pairs put into cell order by counting, with the
-// interfacial-cell list, its pair offsets and the index map.
+// k_sort.cu -- front_bin, part 2: the (cell key, candidate slot) pairs put
+// into cell order by counting, with the interfacial-cell list, its pair
+// offsets and the index map; the record gather and the per-front cell ranges.
 //
-// Element counts live in device memory (no host round trip), so every kernel
-// here splits its range into gridDim.x contiguous segments computed on the
-// device.  No kernel waits on another block: a scan is a reduce launch and a
+// Pair and cell counts live in device memory (no host round trip).  No kernel
+// waits on another block: the key-range scan is a reduce launch and a
 // down-sweep launch (the down-sweep combines the per-block partials itself).
 #include "ft_internal.cuh"
 
@@ -12,12 +11,7 @@ namespace {
 
 constexpr int kB = 256;             // threads per block
 
-__device__ __forceinline__ long long seg_len(long long n, int G) {
-    long long s = (n + G - 1) / G;
-    return (s + kB - 1) / kB * kB;  // whole tiles per segment
-}
-
-// exclusive block scan of one int per thread; returns the block total
+// exclusive block scan of one value per thread; returns the block total
 __device__ __forceinline__ long long block_excl_scan(long long v, long long& excl, long long* sm_warp) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     long long x = v;
@@ -45,52 +39,6 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long& exc
     return total;
 }
 
-struct LoadCounts {
-    const int* in;
-    __device__ long long operator()(long long i) const { return in[i]; }
-};
-
-template <class L>
-__global__ void __launch_bounds__(kB) k_scan_reduce(L ld, const long long* n_ptr, long long* partials) {
-    __shared__ long long sm[kB / 32];
-    const long long n = *n_ptr;
-    const long long s = seg_len(n, gridDim.x);
-    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
-    long long acc = 0;
-    for (long long i = b0 + threadIdx.x; i < b1; i += kB) acc += ld(i);
-    long long excl;
-    const long long tot = block_excl_scan(acc, excl, sm);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-}
-
-// The down-sweep: each block sums the reduce partials of the blocks before it
-// (gridDim <= kB, one per thread) for its carry, block 0 also writes the total;
-// then its segment is scanned tile by tile.
-template <class L>
-__global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, const long long* partials,
-                                                  int* out, long long* total) {
-    __shared__ long long sm[kB / 32];
-    const long long n = *n_ptr;
-    const long long s = seg_len(n, gridDim.x);
-    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
-    long long carry;
-    {
-        const long long p = (threadIdx.x < gridDim.x) ? partials[threadIdx.x] : 0;
-        long long excl;
-        carry = block_excl_scan((threadIdx.x < blockIdx.x) ? p : 0, excl, sm);
-        const long long all = block_excl_scan(p, excl, sm);
-        if (blockIdx.x == 0 && threadIdx.x == 0) *total = all;
-    }
-    for (long long base = b0; base < b1; base += kB) {
-        const long long i = base + threadIdx.x;
-        const long long v = (i < b1) ? ld(i) : 0;
-        long long excl;
-        const long long tot = block_excl_scan(v, excl, sm);
-        if (i < b1) out[i] = (int)(carry + excl);
-        carry += tot;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Pairs into cell order by counting.  k_clip counted every kept pair into
 // cell_cnt[key]; the atomic's return value, the pair's rank among its cell's
@@ -101,8 +49,8 @@ __global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, 
 //    idx_map), and its count goes back to zero, so that cell_cnt is all zero
 //    again for the next binning;
 //  k_place -- every kept pair to cell_off[m] + rank;
-//  k_cell_order -- each cell's pairs into ascending slot order, the order of a
-//    stable sort by key (pairs are generated in slot order).
+//  k_cell_order -- each cell's pairs into ascending triangle order (the
+//    candidate ranges of the triangles are laid out in any order).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ long long pack_cnt(int c) { return ((long long)c << 32) | (c > 0 ? 1 : 0); }
@@ -228,13 +176,14 @@ __global__ void __launch_bounds__(kB) k_place(const unsigned* __restrict__ keys,
     }
 }
 
-// One warp per cell: every slot's place in the cell is the number of smaller
-// slots of the cell (slots are distinct).  Up to 32 pairs the lanes hold the
-// slots and count by shuffles, then write in place; a larger cell is ranked
-// from memory into tmp and copied back.
+// One warp per cell puts the cell's pairs in triangle order (a triangle meets
+// a cell at most once, so the triangles of a cell are distinct): a pair's
+// place is the number of pairs of the cell with a smaller triangle.  Up to 32
+// pairs the lanes hold them and count by shuffles, then write in place; a
+// larger cell is ranked from memory into tmp and copied back.
 __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
-                                                   unsigned* __restrict__ tmp, long long max_cells,
-                                                   const ft_counters* ctr) {
+                                                   const int* __restrict__ cand_tri, unsigned* __restrict__ tmp,
+                                                   long long max_cells, const ft_counters* ctr) {
     const long long M = ctr->M;
     if (M > max_cells) return;
     const int lane = threadIdx.x & 31;
@@ -244,17 +193,19 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
         if (n <= 1) continue;
         unsigned* v = svals + q0;
         if (n <= 32) {
-            const unsigned x = (lane < n) ? v[lane] : 0xffffffffu;
+            const unsigned x = (lane < n) ? v[lane] : 0u;
+            const int tr = (lane < n) ? cand_tri[x] : 0x7fffffff;
             int r = 0;
-            for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, x, o) < x) ? 1 : 0;
+            for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, tr, o) < tr) ? 1 : 0;
             __syncwarp();
             if (lane < n) v[r] = x;
         } else {
             unsigned* t = tmp + q0;
             for (int a = lane; a < n; a += 32) {
                 const unsigned x = v[a];
+                const int tr = cand_tri[x];
                 int r = 0;
-                for (int b = 0; b < n; b++) r += (v[b] < x) ? 1 : 0;
+                for (int b = 0; b < n; b++) r += (cand_tri[v[b]] < tr) ? 1 : 0;
                 t[r] = x;
             }
             __syncwarp();
@@ -354,21 +305,10 @@ cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys,
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n, long long* total,
-                               cudaStream_t s) {
-    const int G = ws->tune.seg_blocks;
-    long long* part = reinterpret_cast<long long*>(ws->partials);
-    LoadCounts ld{in};
-    count_launches(2);
-    k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
-    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out, total);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s) {
-    // the key range is read once per scan kernel: 4 blocks per SM (up to
-    // 4 grid_blocks partials) keep enough loads in flight
-    const int G = 4 * ws->grid_blocks;
+    // the key range is read once per scan kernel: four blocks per segment of
+    // the tuning (up to 4 grid_blocks partials) keep enough loads in flight
+    const int G = 4 * ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     count_launches(5);
     k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
@@ -377,7 +317,8 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
     k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->idx_map, ws->cell_off, ws->keys[1],
                                             ws->vals[1], ws->max_cells, ws->ctr);
     // the ranks in vals[0] are spent once placed: that buffer is the scratch of large cells
-    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], ws->max_cells, ws->ctr);
+    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->cand_tri, ws->vals[0], ws->max_cells,
+                                                 ws->ctr);
     k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
     ws->sorted_buf = 1;
     return cudaGetLastError();
