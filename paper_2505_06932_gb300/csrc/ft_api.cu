@@ -328,8 +328,7 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     if (f->nt > 0 && (!f->verts || !f->tris)) return FT_ERR_ARG;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     cudaStream_t s = as_stream(stream);
-    cudaError_t e = ft::launch_clear_map(ws, s);
-    if (e == cudaSuccess) e = ft::launch_bin(ws, f, p, s);
+    cudaError_t e = ft::launch_bin(ws, f, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
@@ -424,8 +423,7 @@ int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream) {
     if (ws->nf < 1) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     cudaStream_t s = as_stream(stream);
-    cudaError_t e = ft::launch_clear_map(ws, s);
-    if (e == cudaSuccess) e = ft::launch_bin_batch(ws, p, s);
+    cudaError_t e = ft::launch_bin_batch(ws, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);

@@ -152,7 +152,6 @@ cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, 
 // (the counts k_clip left in cell_cnt over keys [0, nkeys)); resets cell_cnt
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s);
 cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s);
-cudaError_t launch_clear_map(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s);
 cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s);
 cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, unsigned* cell_keys,

@@ -88,8 +88,12 @@ template <class F>
 __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int margin, long long max_cand,
                                                         int* __restrict__ tri_cnt, int* __restrict__ tri_off,
                                                         int* __restrict__ tri_box,
-                                                        double* __restrict__ tri_nrm, ft_counters* ctr) {
+                                                        double* __restrict__ tri_nrm, const unsigned* __restrict__ cells,
+                                                        int* __restrict__ idx_map, ft_counters* ctr) {
     const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
+    // first the index map entries of the previous binning's cells go back to -1
+    const long long M_prev = ctr->M;
+    for (long long m = t; m < M_prev; m += (long long)gridDim.x * kThreads) idx_map[cells[m]] = -1;
     if (t == 0) ctr->T = T;
     if (t >= T) return;
     const int b = fr.by_tri(t);
@@ -662,10 +666,9 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
     static_assert(offsetof(ft_counters, C_need) == offsetof(ft_counters, T) + sizeof(long long), "layout");
     cudaError_t e = cudaMemsetAsync(&ws->ctr->T, 0, 2 * sizeof(long long), s);
     if (e != cudaSuccess) return e;
-    if (T > 0)
-        k_tri_setup<F><<<nb, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_off, ws->tri_box,
-                                               ws->tri_nrm, ws->ctr);
-    count_launches(T > 0 ? 3 : 2);
+    count_launches(3);
+    k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_off,
+                                                    ws->tri_box, ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
     k_expand<<<nb ? nb : 1, kThreads, 0, s>>>(ws->tri_cnt, ws->tri_off, T, ws->max_cand, ws->cand_tri, ws->ctr);
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;

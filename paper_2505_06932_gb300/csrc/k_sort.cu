@@ -223,14 +223,6 @@ __global__ void k_cap_cells(long long max_cells, ft_counters* ctr) {
     }
 }
 
-// reset the index map entries of the previous bins
-__global__ void __launch_bounds__(kB) k_clear_map(const unsigned* __restrict__ cells, int* __restrict__ idx_map,
-                                                  const ft_counters* ctr) {
-    const long long M = ctr->M;
-    for (long long m = (long long)blockIdx.x * kB + threadIdx.x; m < M; m += (long long)gridDim.x * kB)
-        idx_map[cells[m]] = -1;
-}
-
 __global__ void __launch_bounds__(kB) k_export_pairs(const unsigned* __restrict__ skeys, const unsigned* __restrict__ svals,
                                                      const int* __restrict__ cand_tri, long long cap,
                                                      unsigned* __restrict__ keys, int* __restrict__ tris,
@@ -327,12 +319,6 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
 cudaError_t launch_cell_ranges(ft_workspace* ws, long long* off, cudaStream_t s) {
     count_launches(1);
     k_cell_ranges<<<(ws->nf + 1 + kB - 1) / kB, kB, 0, s>>>(ws->cells, ws->fbase, ws->nf, off, ws->ctr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_clear_map(ft_workspace* ws, cudaStream_t s) {
-    count_launches(1);
-    k_clear_map<<<ws->sm_count * 2, kB, 0, s>>>(ws->cells, ws->idx_map, ws->ctr);
     return cudaGetLastError();
 }
 
