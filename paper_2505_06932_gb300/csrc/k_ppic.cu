@@ -680,8 +680,14 @@ __device__ __forceinline__ double ldlt_solve(const double (&S)[21], const double
     return minp / tr;
 }
 
+// One thread per cell on kSolveLanes lanes of each warp, in blocks of
+// kSolveThreads: the solve is bound by the float64 pipe of the SM sub-partition
+// a warp runs on, so the cells are spread over as many warps as possible.
+constexpr int kSolveThreads = 128;
+constexpr int kSolveLanes = 32;
+
 template <class F>
-__global__ void __launch_bounds__(128) k_ppic_solve(F fr, const ft_cellsys* __restrict__ sys, const int* __restrict__ fit_info,
+__global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cellsys* __restrict__ sys, const int* __restrict__ fit_info,
                                                     const unsigned* __restrict__ cells, int fp32, long long cap, ft_counters* ctr, unsigned* __restrict__ out_keys,
                                                     double* __restrict__ out_kappa, double* __restrict__ out_normal,
                                                     double* __restrict__ out_coeffs, int8_t* __restrict__ out_status) {
@@ -690,7 +696,11 @@ __global__ void __launch_bounds__(128) k_ppic_solve(F fr, const ft_cellsys* __re
         if (blockIdx.x == 0 && threadIdx.x == 0) ft_flag(ctr, FT_ST_CAPACITY);
         return;
     }
-    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    if (lane >= kSolveLanes) return;
+    const long long wid = ((long long)blockIdx.x * kSolveThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kSolveThreads) >> 5;
+    for (long long m = wid * kSolveLanes + lane; m < M; m += nw * kSolveLanes) {
         double S[21], B[6], n[3], z0;
         if (fp32) {
             const float* v = reinterpret_cast<const float*>(sys[m].v);
@@ -774,7 +784,7 @@ cudaError_t ppic_with(ft_workspace* ws, const F& fr, const ft_params* p, long lo
         k_ppic_acc<double, F, 3><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
                                                         ws->ctr, ws->sys, ws->fit_info);
     }
-    k_ppic_solve<F><<<ws->sm_count * 4, 128, 0, s>>>(fr, ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, cap,
+    k_ppic_solve<F><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(fr, ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, cap,
                                                     ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
     return cudaGetLastError();
 }
