@@ -41,7 +41,7 @@ PARAB_FP64_FLOPS_PER_CELL = 72252.0  # FP64 flops (add + mul + 2 fma) executed p
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "fp32c"], default="fp32c")
