@@ -393,9 +393,10 @@ typedef struct {
                                    6 resident blocks per SM (fewer registers each)   */
     int32_t ppic_dynamic;       /* PPIC cells from a global work counter (1) or
                                    interleaved over the warps (0, default)           */
-    int32_t sort_blocks;        /* segments of the key-range scan of the binning, four
-                                   blocks each (1 to the SM count; 0: the SM count,
-                                   default)                                          */
+    int32_t sort_blocks;        /* segments of the binning's scans: the triangle counts
+                                   (one block each) and the key range (four blocks
+                                   each); 1 to the SM count, 0: the SM count
+                                   (default)                                         */
     int32_t pad;
     /* outputs of ft_autotune: what the tuned workload needed, for sizing a
      * workspace (ft_capacity / ft_batch_capacity) to it */

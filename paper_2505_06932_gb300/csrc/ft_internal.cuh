@@ -20,7 +20,7 @@ struct ft_counters {
     long long M;           // interfacial cells (also: entries set in the index map)
     long long fit_pairs;   // (cell, fragment) pairs inside the support, last PPIC
     long long work;        // next cell of the dynamically scheduled PPIC accumulation
-    long long scratch;     // sink for totals nobody reads (later sort passes)
+    long long big;         // cells with more than 32 pairs (worklist of the per-cell ordering)
 };
 
 // Fragment record (cell-local, lengths in units of h, relative to the centre of
@@ -78,7 +78,7 @@ struct ft_tune {
     int fill_bps;   // k_alpha_fill blocks per SM
     int ppic_min_blocks;  // FP32 k_ppic_acc compiled for 4 (more registers) or 6 resident blocks per SM
     int ppic_dynamic;     // k_ppic_acc cells from a global work counter (1) or interleaved (0)
-    int seg_blocks;       // segments of the key-range scan (four blocks each), <= grid_blocks
+    int seg_blocks;       // segments of the binning's scans (key range: four blocks each), <= grid_blocks
 };
 
 struct ft_workspace {
@@ -148,6 +148,8 @@ cudaError_t launch_ppic_frame(ft_workspace* ws, long long cap, double* frame, cu
 void count_launches(int n);  // kernels launched by this library (ft_launch_count)
 
 cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s);
+cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n,
+                               long long* total, cudaStream_t s);
 // the kept pairs into cell order: interfacial cell list, offsets, index map
 // (the counts k_clip left in cell_cnt over keys [0, nkeys)); resets cell_cnt
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s);

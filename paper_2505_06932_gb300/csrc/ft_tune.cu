@@ -1,6 +1,6 @@
 // ft_tune.cu -- ft_autotune: picks the launch shapes of the grid-stride kernels
 // (canonical clip, column parity fill, PPIC accumulation, CSF dense pass), the
-// segment count of the key-range scan, and
+// segment count of the binning's scans, and
 // the register/occupancy variant and cell schedule of the PPIC accumulation for the workload
 // on a workspace, by timing each step with CUDA events, one parameter at a
 // time, and installs the fastest.  The results of the steps do not depend on

@@ -6,8 +6,6 @@
 // step is one IEEE binary64 operation with round-to-nearest (the __d*_rn
 // intrinsics are never contracted into FMA), so every decision is reproducible
 // bit for bit by any implementation that follows the same definition.
-#include <stddef.h>
-
 #include "ft_internal.cuh"
 
 namespace {
@@ -86,8 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(F fr) {
 // and the owning front per triangle (8 ints).
 template <class F>
 __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int margin, long long max_cand,
-                                                        int* __restrict__ tri_cnt, int* __restrict__ tri_off,
-                                                        int* __restrict__ tri_box,
+                                                        int* __restrict__ tri_cnt, int* __restrict__ tri_box,
                                                         double* __restrict__ tri_nrm, const unsigned* __restrict__ cells,
                                                         int* __restrict__ idx_map, ft_counters* ctr) {
     const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -151,28 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
         ft_flag(ctr, err);
         fr.flag(b, err);
     }
-    const int my = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
-    tri_cnt[t] = my;
-    // the triangle's range of candidate slots: one atomic per warp on the
-    // running total (ctr->C_need, zero at launch).  The ranges land in any order;
-    // the pairs of a cell are put in triangle order after placement.
-    {
-        const int lane = threadIdx.x & 31;
-        const long long nact = T - (t - lane);  // lanes of this warp with a triangle
-        const unsigned am = nact >= 32 ? 0xffffffffu : ((1u << nact) - 1u);
-        long long incl = my;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(am, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int last = 31 - __clz(am);
-        const long long tot = __shfl_sync(am, incl, last);
-        unsigned long long base = 0;
-        if (lane == last) base = atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->C_need), (unsigned long long)tot);
-        base = __shfl_sync(am, base, last);
-        tri_off[t] = (int)((long long)base + incl - my);
-    }
+    tri_cnt[t] = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
     // normal direction (orientation of every fragment of the triangle; zero if
     // degenerate): twice the area vector in units of h^2.  Only its direction
     // matters -- the moments use ratios of areas signed along it.
@@ -662,13 +638,14 @@ template <class F>
 cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params* p, cudaStream_t s) {
     const int margin = 2 + (int)ceil(p->delta_max_h);
     const unsigned nb = (unsigned)((T + kThreads - 1) / kThreads);
-    // T and C_need are adjacent: one reset (k_tri_setup sets T and adds into C_need)
-    static_assert(offsetof(ft_counters, C_need) == offsetof(ft_counters, T) + sizeof(long long), "layout");
-    cudaError_t e = cudaMemsetAsync(&ws->ctr->T, 0, 2 * sizeof(long long), s);
+    // (always launched: it also clears the index map of the previous binning, and sets T)
+    count_launches(1);
+    k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_box,
+                                                    ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
+    // candidate ranges in triangle order, so that slot order is triangle order
+    cudaError_t e = launch_scan_counts(ws, ws->tri_cnt, ws->tri_off, &ws->ctr->T, &ws->ctr->C_need, s);
     if (e != cudaSuccess) return e;
-    count_launches(3);
-    k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_off,
-                                                    ws->tri_box, ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
+    count_launches(2);
     k_expand<<<nb ? nb : 1, kThreads, 0, s>>>(ws->tri_cnt, ws->tri_off, T, ws->max_cand, ws->cand_tri, ws->ctr);
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;

@@ -11,6 +11,11 @@ namespace {
 
 constexpr int kB = 256;             // threads per block
 
+__device__ __forceinline__ long long seg_len(long long n, int G) {
+    long long s = (n + G - 1) / G;
+    return (s + kB - 1) / kB * kB;  // whole tiles per segment
+}
+
 // exclusive block scan of one value per thread; returns the block total
 __device__ __forceinline__ long long block_excl_scan(long long v, long long& excl, long long* sm_warp) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -39,6 +44,52 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long& exc
     return total;
 }
 
+struct LoadCounts {
+    const int* in;
+    __device__ long long operator()(long long i) const { return in[i]; }
+};
+
+template <class L>
+__global__ void __launch_bounds__(kB) k_scan_reduce(L ld, const long long* n_ptr, long long* partials) {
+    __shared__ long long sm[kB / 32];
+    const long long n = *n_ptr;
+    const long long s = seg_len(n, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
+    long long acc = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += kB) acc += ld(i);
+    long long excl;
+    const long long tot = block_excl_scan(acc, excl, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// The down-sweep: each block sums the reduce partials of the blocks before it
+// (gridDim <= kB, one per thread) for its carry, block 0 also writes the total;
+// then its segment is scanned tile by tile.
+template <class L>
+__global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, const long long* partials,
+                                                  int* out, long long* total) {
+    __shared__ long long sm[kB / 32];
+    const long long n = *n_ptr;
+    const long long s = seg_len(n, gridDim.x);
+    const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
+    long long carry;
+    {
+        const long long p = (threadIdx.x < gridDim.x) ? partials[threadIdx.x] : 0;
+        long long excl;
+        carry = block_excl_scan((threadIdx.x < blockIdx.x) ? p : 0, excl, sm);
+        const long long all = block_excl_scan(p, excl, sm);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *total = all;
+    }
+    for (long long base = b0; base < b1; base += kB) {
+        const long long i = base + threadIdx.x;
+        const long long v = (i < b1) ? ld(i) : 0;
+        long long excl;
+        const long long tot = block_excl_scan(v, excl, sm);
+        if (i < b1) out[i] = (int)(carry + excl);
+        carry += tot;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Pairs into cell order by counting.  k_clip counted every kept pair into
 // cell_cnt[key]; the atomic's return value, the pair's rank among its cell's
@@ -49,8 +100,9 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long& exc
 //    idx_map), and its count goes back to zero, so that cell_cnt is all zero
 //    again for the next binning;
 //  k_place -- every kept pair to cell_off[m] + rank;
-//  k_cell_order -- each cell's pairs into ascending triangle order (the
-//    candidate ranges of the triangles are laid out in any order).
+//  k_cell_order, k_cell_order_big -- each cell's pairs into ascending slot
+//    order, the order of a stable sort by key (pairs are generated in slot
+//    order, and slot order is triangle order).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ long long pack_cnt(int c) { return ((long long)c << 32) | (c > 0 ? 1 : 0); }
@@ -129,6 +181,7 @@ __global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long lon
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->P = P;
         ctr->M = M;
+        ctr->big = 0;
         if (fits) cell_off[M] = (int)P;
     }
     for (long long base = b0; base < b1; base += kKeysPT * kB) {
@@ -176,14 +229,12 @@ __global__ void __launch_bounds__(kB) k_place(const unsigned* __restrict__ keys,
     }
 }
 
-// One warp per cell puts the cell's pairs in triangle order (a triangle meets
-// a cell at most once, so the triangles of a cell are distinct): a pair's
-// place is the number of pairs of the cell with a smaller triangle.  Up to 32
-// pairs the lanes hold them and count by shuffles, then write in place; a
-// larger cell is ranked from memory into tmp and copied back.
+// The pairs of a cell in slot order (slot order is triangle order; slots are
+// distinct).  One warp per cell: up to 32 pairs, a pair's place is the number
+// of smaller slots of the cell, counted by shuffles, and the warp writes in
+// place; a larger cell goes to a worklist for k_cell_order_big.
 __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
-                                                   const int* __restrict__ cand_tri, unsigned* __restrict__ tmp,
-                                                   long long max_cells, const ft_counters* ctr) {
+                                                   int* __restrict__ big, long long max_cells, ft_counters* ctr) {
     const long long M = ctr->M;
     if (M > max_cells) return;
     const int lane = threadIdx.x & 31;
@@ -191,27 +242,88 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
     for (long long m = ((long long)blockIdx.x * kB + threadIdx.x) >> 5; m < M; m += nw) {
         const int q0 = cell_off[m], n = cell_off[m + 1] - q0;
         if (n <= 1) continue;
-        unsigned* v = svals + q0;
-        if (n <= 32) {
-            const unsigned x = (lane < n) ? v[lane] : 0u;
-            const int tr = (lane < n) ? cand_tri[x] : 0x7fffffff;
-            int r = 0;
-            for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, tr, o) < tr) ? 1 : 0;
-            __syncwarp();
-            if (lane < n) v[r] = x;
-        } else {
-            unsigned* t = tmp + q0;
-            for (int a = lane; a < n; a += 32) {
-                const unsigned x = v[a];
-                const int tr = cand_tri[x];
-                int r = 0;
-                for (int b = 0; b < n; b++) r += (cand_tri[v[b]] < tr) ? 1 : 0;
-                t[r] = x;
-            }
-            __syncwarp();
-            for (int a = lane; a < n; a += 32) v[a] = t[a];
+        if (n > 32) {
+            if (lane == 0) big[atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->big), 1ull)] = (int)m;
+            continue;
         }
+        unsigned* v = svals + q0;
+        const unsigned x = (lane < n) ? v[lane] : 0xffffffffu;
+        int r = 0;
+        for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, x, o) < x) ? 1 : 0;
         __syncwarp();
+        if (lane < n) v[r] = x;
+        __syncwarp();
+    }
+}
+
+constexpr int kSortCap = 4096;  // slots a block sorts in shared memory at once
+
+// One block per cell of the worklist: chunks of up to kSortCap slots sorted in
+// shared memory (bitonic network), then sorted runs merged pairwise through
+// tmp (each slot's place: its offset in its run plus, by binary search, the
+// number of smaller slots in the partner run).
+__global__ void __launch_bounds__(kB) k_cell_order_big(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
+                                                       unsigned* __restrict__ tmp, const int* __restrict__ big,
+                                                       long long max_cells, const ft_counters* ctr) {
+    __shared__ unsigned sh[kSortCap];
+    if (ctr->M > max_cells) return;
+    const long long nbig = ctr->big;
+    for (long long w = blockIdx.x; w < nbig; w += gridDim.x) {
+        const int m = big[w];
+        const int q0 = cell_off[m], n = cell_off[m + 1] - q0;
+        unsigned* v = svals + q0;
+        for (int c0 = 0; c0 < n; c0 += kSortCap) {
+            const int len = min(kSortCap, n - c0);
+            int N = 1;
+            while (N < len) N <<= 1;
+            for (int i = threadIdx.x; i < N; i += kB) sh[i] = (i < len) ? v[c0 + i] : 0xffffffffu;
+            __syncthreads();
+            for (int k = 2; k <= N; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int i = threadIdx.x; i < N; i += kB) {
+                        const int l = i ^ j;
+                        if (l > i) {
+                            const unsigned a = sh[i], b = sh[l];
+                            if ((a > b) == ((i & k) == 0)) {
+                                sh[i] = b;
+                                sh[l] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int i = threadIdx.x; i < len; i += kB) v[c0 + i] = sh[i];
+            __syncthreads();
+        }
+        unsigned* src = v;
+        unsigned* dst = tmp + q0;
+        for (int L = kSortCap; L < n; L <<= 1) {
+            for (int i = threadIdx.x; i < n; i += kB) {
+                const int a0 = (i / L) * L;  // this slot's run
+                const bool left = ((i / L) & 1) == 0;
+                const int p0 = left ? a0 : a0 - L;  // the merged pair of runs starts here
+                const int b0 = left ? a0 + L : a0 - L;  // the partner run
+                const int bl = left ? min(L, n - b0) : L;
+                const unsigned x = src[i];
+                int lo = 0, hi = bl > 0 ? bl : 0;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (src[b0 + mid] < x)
+                        lo = mid + 1;
+                    else
+                        hi = mid;
+                }
+                dst[p0 + (i - a0) + lo] = x;
+            }
+            __syncthreads();
+            unsigned* sw = src;
+            src = dst;
+            dst = sw;
+        }
+        if (src != v)
+            for (int i = threadIdx.x; i < n; i += kB) v[i] = src[i];
+        __syncthreads();
     }
 }
 
@@ -297,20 +409,35 @@ cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys,
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n, long long* total,
+                               cudaStream_t s) {
+    const int G = ws->tune.seg_blocks;
+    long long* part = reinterpret_cast<long long*>(ws->partials);
+    LoadCounts ld{in};
+    count_launches(2);
+    k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
+    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out, total);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s) {
     // the key range is read once per scan kernel: four blocks per segment of
     // the tuning (up to 4 grid_blocks partials) keep enough loads in flight
     const int G = 4 * ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
-    count_launches(5);
+    count_launches(6);
     k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
     k_cnt_down<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
                                 ws->ctr);
     k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->idx_map, ws->cell_off, ws->keys[1],
                                             ws->vals[1], ws->max_cells, ws->ctr);
     // the ranks in vals[0] are spent once placed: that buffer is the scratch of large cells
-    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->cand_tri, ws->vals[0], ws->max_cells,
-                                                 ws->ctr);
+    // large cells: the ranks in vals[0] are spent once placed, so that buffer is
+    // their merge scratch; cell_L (filled only by the volume fraction) holds the worklist
+    int* big = reinterpret_cast<int*>(ws->cell_L);
+    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], big, ws->max_cells, ws->ctr);
+    k_cell_order_big<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], big, ws->max_cells,
+                                                     ws->ctr);
     k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
     ws->sorted_buf = 1;
     return cudaGetLastError();

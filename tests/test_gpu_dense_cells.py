@@ -1,0 +1,38 @@
+"""Fronts much finer than the grid: thousands of (cell, triangle) pairs per
+cell.  The binning puts each cell's pairs in triangle order with a warp per
+cell up to 32 pairs and a block per larger cell (shared-memory sort of chunks
+of 4,096 slots, then merges of the sorted runs); the pairs must equal the
+oracle's bit for bit on every path, and alpha match it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_06932_gb300 import _front as F
+from paper_2505_06932_gb300 import inputs as I
+from gpucase import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("s,expect_max", [(6, 32), (8, 4096)])
+def test_dense_cells_pairs_and_alpha(s, expect_max):
+    N = 24
+    w = I.small_sphere(s, 2.5 / N, N, seed=11)
+    g = w["grid"]
+    keys, tids, st = oracle.bin_pairs(w["verts"], w["tris"], g)
+    assert st == 0
+    per_cell = np.unique(keys, return_counts=True)[1]
+    assert per_cell.max() > expect_max  # the path under test is taken
+    for precision in (F.FT_FP64, F.FT_FP32C):
+        gpu = run_gpu(w, precision=precision)
+        assert gpu["status"] == 0
+        assert np.array_equal(gpu["pair_keys"], keys)
+        assert np.array_equal(gpu["pair_tris"], tids)
+    # alpha: each cell's terms are summed in another order on either side; with
+    # up to n = 22,349 fragment terms of magnitude <= 1 per cell the two sums
+    # differ by at most about 2 n 2^-53 per cell, carried down a column of 24
+    al, st2 = oracle.alpha(w["verts"], w["tris"], g)
+    assert st2 == 0
+    gpu = run_gpu(w, precision=F.FT_FP64)
+    tol = 2 * 24 * 2.0 * per_cell.max() * 2.0 ** -53
+    assert np.max(np.abs(gpu["alpha"] - al)) <= tol
