@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kB) k_cnt_reduce(const int* __restrict__ cnt, 
 }
 
 // Writes nothing but the totals and the count reset when M exceeds the
-// capacity (k_cap_cells then flags it and resets M and P).
+// capacity (k_cell_order_big then flags it and resets M and P).
 __global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long long nkeys,
                                                  const long long* __restrict__ partials, unsigned* __restrict__ cells,
                                                  int* __restrict__ cell_off, int* __restrict__ idx_map,
@@ -266,7 +266,17 @@ __global__ void __launch_bounds__(kB) k_cell_order_big(const int* __restrict__ c
                                                        unsigned* __restrict__ tmp, const int* __restrict__ big,
                                                        long long max_cells, const ft_counters* ctr) {
     __shared__ unsigned sh[kSortCap];
-    if (ctr->M > max_cells) return;
+    if (ctr->M > max_cells) {
+        // the last kernel of the placement: flag the capacity and leave no cells.
+        // A block that reads M after this reset finds no worklist (nothing was
+        // placed or listed), so the order of the blocks does not matter.
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ft_flag(ctr, FT_ST_CAPACITY);
+            ctr->M = 0;
+            ctr->P = 0;
+        }
+        return;
+    }
     const long long nbig = ctr->big;
     for (long long w = blockIdx.x; w < nbig; w += gridDim.x) {
         const int m = big[w];
@@ -324,14 +334,6 @@ __global__ void __launch_bounds__(kB) k_cell_order_big(const int* __restrict__ c
         if (src != v)
             for (int i = threadIdx.x; i < n; i += kB) v[i] = src[i];
         __syncthreads();
-    }
-}
-
-__global__ void k_cap_cells(long long max_cells, ft_counters* ctr) {
-    if (ctr->M > max_cells) {
-        ft_flag(ctr, FT_ST_CAPACITY);
-        ctr->M = 0;
-        ctr->P = 0;
     }
 }
 
@@ -425,7 +427,7 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
     // the tuning (up to 4 grid_blocks partials) keep enough loads in flight
     const int G = 4 * ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
-    count_launches(6);
+    count_launches(5);
     k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
     k_cnt_down<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
                                 ws->ctr);
@@ -438,7 +440,6 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
     k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], big, ws->max_cells, ws->ctr);
     k_cell_order_big<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], big, ws->max_cells,
                                                      ws->ctr);
-    k_cap_cells<<<1, 1, 0, s>>>(ws->max_cells, ws->ctr);
     ws->sorted_buf = 1;
     return cudaGetLastError();
 }
