@@ -264,7 +264,7 @@ constexpr int kSortCap = 4096;  // slots a block sorts in shared memory at once
 // number of smaller slots in the partner run).
 __global__ void __launch_bounds__(kB) k_cell_order_big(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
                                                        unsigned* __restrict__ tmp, const int* __restrict__ big,
-                                                       long long max_cells, const ft_counters* ctr) {
+                                                       long long max_cells, ft_counters* ctr) {
     __shared__ unsigned sh[kSortCap];
     if (ctr->M > max_cells) {
         // the last kernel of the placement: flag the capacity and leave no cells.
