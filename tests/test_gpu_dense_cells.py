@@ -36,3 +36,38 @@ def test_dense_cells_pairs_and_alpha(s, expect_max):
     gpu = run_gpu(w, precision=F.FT_FP64)
     tol = 2 * 24 * 2.0 * per_cell.max() * 2.0 ** -53
     assert np.max(np.abs(gpu["alpha"] - al)) <= tol
+
+
+def test_cell_capacity_overflow_then_recovery():
+    """More interfacial cells than the workspace holds: the binning flags the
+    capacity and leaves no cells; the per-key counters are back to zero, so the
+    next binning on the same workspace (a front that fits) equals the oracle."""
+    import torch
+    dev = torch.device("cuda", 0)
+    N = 32
+    big = I.small_sphere(4, 0.25, N, seed=3)
+    small = I.small_sphere(3, 0.12, N, seed=4)
+    prm = F.make_params(precision=F.FT_FP64)
+    nt = max(big["tris"].shape[0], small["tris"].shape[0])
+    M_small = len(np.unique(oracle.bin_pairs(small["verts"], small["tris"], small["grid"])[0]))
+    M_big = len(np.unique(oracle.bin_pairs(big["verts"], big["tris"], big["grid"])[0]))
+    assert M_small < M_big
+    ws = F.Workspace(big["grid"], nt, max_cells=M_small)
+    for w, over in ((big, True), (small, False), (big, True), (small, False)):
+        v = torch.from_numpy(w["verts"]).to(dev)
+        t = torch.from_numpy(w["tris"]).to(dev)
+        F.front_bin(ws, v, t, prm)
+        c, st = ws.counts(), ws.status()
+        if over:
+            assert st & 0x01 and c["M"] == 0 and c["P"] == 0
+        else:
+            assert st == 0
+            keys, tids, _ = oracle.bin_pairs(w["verts"], w["tris"], w["grid"])
+            P = c["P"]
+            k = torch.empty(P, dtype=torch.int32, device=dev)
+            tr = torch.empty(P, dtype=torch.int32, device=dev)
+            F.ft_bin_pairs(ws, k, tr)
+            assert c["M"] == M_small
+            assert np.array_equal(k.cpu().numpy().view(np.uint32), keys)
+            assert np.array_equal(tr.cpu().numpy(), tids)
+    ws.close()
