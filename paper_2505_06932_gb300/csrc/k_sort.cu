@@ -229,10 +229,13 @@ __global__ void __launch_bounds__(kB) k_place(const unsigned* __restrict__ keys,
     }
 }
 
+constexpr int kWarpSlots = 8;  // slots per lane of the warp path: cells of up to 256 pairs
+
 // The pairs of a cell in slot order (slot order is triangle order; slots are
-// distinct).  One warp per cell: up to 32 pairs, a pair's place is the number
-// of smaller slots of the cell, counted by shuffles, and the warp writes in
-// place; a larger cell goes to a worklist for k_cell_order_big.
+// distinct).  One warp per cell of up to 32 kWarpSlots pairs, each lane
+// holding kWarpSlots of them: a pair's place is the number of smaller slots of
+// the cell, counted by shuffles, and the warp writes in place.  A larger cell
+// goes to a worklist for k_cell_order_big.
 __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
                                                    int* __restrict__ big, long long max_cells, ft_counters* ctr) {
     const long long M = ctr->M;
@@ -242,16 +245,36 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
     for (long long m = ((long long)blockIdx.x * kB + threadIdx.x) >> 5; m < M; m += nw) {
         const int q0 = cell_off[m], n = cell_off[m + 1] - q0;
         if (n <= 1) continue;
-        if (n > 32) {
+        if (n > 32 * kWarpSlots) {
             if (lane == 0) big[atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->big), 1ull)] = (int)m;
             continue;
         }
         unsigned* v = svals + q0;
-        const unsigned x = (lane < n) ? v[lane] : 0xffffffffu;
-        int r = 0;
-        for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, x, o) < x) ? 1 : 0;
+        const int J = (n + 31) >> 5;  // slots per lane in use (warp-uniform)
+        unsigned x[kWarpSlots];
+        int r[kWarpSlots];
+#pragma unroll
+        for (int j = 0; j < kWarpSlots; j++) {
+            const int a = lane + 32 * j;
+            x[j] = (j < J && a < n) ? v[a] : 0xffffffffu;  // padding sorts after every slot
+            r[j] = 0;
+        }
+#pragma unroll
+        for (int jj = 0; jj < kWarpSlots; jj++) {
+            if (jj < J) {
+                for (int o = 0; o < 32; o++) {
+                    const unsigned y = __shfl_sync(0xffffffffu, x[jj], o);
+#pragma unroll
+                    for (int j = 0; j < kWarpSlots; j++) r[j] += (y < x[j]) ? 1 : 0;
+                }
+            }
+        }
         __syncwarp();
-        if (lane < n) v[r] = x;
+#pragma unroll
+        for (int j = 0; j < kWarpSlots; j++) {
+            const int a = lane + 32 * j;
+            if (j < J && a < n) v[r[j]] = x[j];
+        }
         __syncwarp();
     }
 }

@@ -1,6 +1,6 @@
 """Fronts much finer than the grid: thousands of (cell, triangle) pairs per
 cell.  The binning puts each cell's pairs in triangle order with a warp per
-cell up to 32 pairs and a block per larger cell (shared-memory sort of chunks
+cell up to 256 pairs and a block per larger cell (shared-memory sort of chunks
 of 4,096 slots, then merges of the sorted runs); the pairs must equal the
 oracle's bit for bit on every path, and alpha match it."""
 import numpy as np
@@ -14,7 +14,7 @@ from gpucase import run_gpu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("s,expect_max", [(6, 32), (8, 4096)])
+@pytest.mark.parametrize("s,expect_max", [(6, 256), (8, 4096)])
 def test_dense_cells_pairs_and_alpha(s, expect_max):
     N = 24
     w = I.small_sphere(s, 2.5 / N, N, seed=11)
