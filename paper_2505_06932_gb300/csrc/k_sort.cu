@@ -250,6 +250,15 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
             continue;
         }
         unsigned* v = svals + q0;
+        if (n <= 32) {  // most cells: one slot per lane
+            const unsigned x = (lane < n) ? v[lane] : 0xffffffffu;
+            int r = 0;
+            for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, x, o) < x) ? 1 : 0;
+            __syncwarp();
+            if (lane < n) v[r] = x;
+            __syncwarp();
+            continue;
+        }
         const int J = (n + 31) >> 5;  // slots per lane in use (warp-uniform)
         unsigned x[kWarpSlots];
         int r[kWarpSlots];
