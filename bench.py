@@ -453,7 +453,9 @@ def run_ours(a):
     stag = a.e2e_mode in ("staggered", "graph")
     if stag:
         e2e_streams = dict(sd=torch.cuda.Stream(device=dev), up=torch.cuda.Stream(device=dev),
-                           dns=[torch.cuda.Stream(device=dev) for _ in fcs])
+                           dns=[torch.cuda.Stream(device=dev) for _ in fcs],
+                           sas=[torch.cuda.Stream(device=dev) for _ in fcs],
+                           sis=[torch.cuda.Stream(device=dev) for _ in fcs])
     else:
         e2e_streams = dict(sides=[torch.cuda.Stream(device=dev) for _ in fcs],
                            copies=[torch.cuda.Stream(device=dev) for _ in fcs])
@@ -461,7 +463,8 @@ def run_ours(a):
     def e2e_enqueue(cs):
         if stag:
             sd, up, dns = e2e_streams["sd"], e2e_streams["up"], e2e_streams["dns"]
-            for x in [sd, up] + dns:
+            sas, sis = e2e_streams["sas"], e2e_streams["sis"]
+            for x in [sd, up] + dns + sas + sis:
                 x.wait_stream(cs)
             vt_in = [torch.cuda.Event() for _ in fcs]
             faces_in = [torch.cuda.Event() for _ in fcs]
@@ -475,18 +478,27 @@ def run_ours(a):
                         dst.copy_(src, non_blocking=True)
                     ev.record(up)
             for f, ((v, t, fa), fc, o, c, dn) in enumerate(zip(dfr, fcs, hout, counts, dns)):
+                # each front as the DAG of the graph step: alpha beside the PPIC fit,
+                # the interpolation beside both (once the faces are up)
                 alpha_ready, force_ready, vel_ready = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+                sa, si = sas[f], sis[f]
                 with torch.cuda.stream(sd):
                     sd.wait_event(vt_in[f])
                     F.front_bin(fc.ws, v, t, prm)
+                sa.wait_stream(sd)
+                with torch.cuda.stream(sa):
                     F.front_volume_fraction(fc.ws, fc.alpha)
-                    alpha_ready.record(sd)
+                    alpha_ready.record(sa)
+                with torch.cuda.stream(si):
+                    si.wait_event(vt_in[f])
+                    si.wait_event(faces_in[f])
+                    F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+                    vel_ready.record(si)
+                with torch.cuda.stream(sd):
                     F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
+                    sd.wait_event(alpha_ready)
                     F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
                     force_ready.record(sd)
-                    sd.wait_event(faces_in[f])
-                    F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
-                    vel_ready.record(sd)
                 with torch.cuda.stream(dn):
                     M = c["M"]
                     dn.wait_event(alpha_ready)
@@ -497,7 +509,7 @@ def run_ours(a):
                     o["normal"].copy_(fc.normal[:M], non_blocking=True)
                     dn.wait_event(vel_ready)
                     o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
-            for x in [sd, up] + dns:
+            for x in [sd, up] + dns + sas + sis:
                 cs.wait_stream(x)
         else:
             sides, copies = e2e_streams["sides"], e2e_streams["copies"]
@@ -591,7 +603,8 @@ def run_ours(a):
                 "mode": a.e2e_mode,
                 "launch": (("one CUDA graph per step: " if a.e2e_mode == "graph" else "eager calls; ") +
                            ("the fronts one after the other on one compute stream (the first front's outputs go "
-                            "down while the second is computed), one upload stream, a download stream per front"
+                            "down while the second is computed), each front's calls as the DAG of the graph step, "
+                            "one upload stream, a download stream per front"
                             if stag else
                             "per front a compute stream and a copy stream (faces up and alpha down overlap the "
                             "binning and the fit), the two fronts concurrently"))},
