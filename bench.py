@@ -195,7 +195,8 @@ def cpu_baseline(fronts, budget_s=10.0):
         passes += 1
     dt = time.perf_counter() - t0
     return dict(value=cells / dt, unit="interfacial cells/s", cores=oracle.get_threads(), kind="oracle",
-                sample=f"{passes} passes of the five steps over the whole workload ({cells // passes} interfacial "
+                sample=f"{passes} pass{'es' if passes != 1 else ''} of the five steps over the whole workload "
+                       f"({cells // passes} interfacial "
                        f"cells per pass, every cell fitted), {dt:.1f} s; cells/s = cells / time")
 
 
