@@ -97,12 +97,13 @@ __global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, 
 //  k_cnt_reduce, k_cnt_down -- one exclusive scan over the whole key range of
 //    the packed counts (pairs << 32 | has pairs): a key with pairs becomes
 //    interfacial cell m with pair offset cell_off[m] (cells, cell_off,
-//    idx_map), and its count goes back to zero, so that cell_cnt is all zero
-//    again for the next binning;
-//  k_place -- every kept pair to cell_off[m] + rank;
+//    idx_map), and its count is replaced by that offset;
+//  k_place -- every kept pair to its cell's offset + rank;
 //  k_cell_order, k_cell_order_big -- each cell's pairs into ascending slot
 //    order, the order of a stable sort by key (pairs are generated in slot
-//    order, and slot order is triangle order).
+//    order, and slot order is triangle order); k_cell_order also sets each
+//    cell's counter back to zero, so that cell_cnt is all zero again for the
+//    next binning.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ long long pack_cnt(int c) { return ((long long)c << 32) | (c > 0 ? 1 : 0); }
@@ -205,7 +206,9 @@ __global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long lon
                         cell_off[m] = (int)(run >> 32);
                         idx_map[key] = m;
                     }
-                    cnt[key] = 0;
+                    // the count becomes the cell's pair offset, read by k_place and
+                    // reset by k_cell_order (zero at once when nothing is placed)
+                    cnt[key] = fits ? (int)(run >> 32) : 0;
                 }
                 run += pack_cnt(c[u]);
             }
@@ -215,15 +218,15 @@ __global__ void __launch_bounds__(kB) k_cnt_down(int* __restrict__ cnt, long lon
 }
 
 __global__ void __launch_bounds__(kB) k_place(const unsigned* __restrict__ keys, const unsigned* __restrict__ ranks,
-                                              const int* __restrict__ idx_map, const int* __restrict__ cell_off,
-                                              unsigned* __restrict__ skeys, unsigned* __restrict__ svals,
-                                              long long max_cells, const ft_counters* ctr) {
+                                              const int* __restrict__ cnt, unsigned* __restrict__ skeys,
+                                              unsigned* __restrict__ svals, long long max_cells,
+                                              const ft_counters* ctr) {
     const long long C = ctr->C;
     if (ctr->M > max_cells) return;
     for (long long c = (long long)blockIdx.x * kB + threadIdx.x; c < C; c += (long long)gridDim.x * kB) {
         const unsigned k = keys[c];
         if (k == FT_SENTINEL) continue;
-        const long long dst = (long long)cell_off[idx_map[k]] + ranks[c];
+        const long long dst = (long long)cnt[k] + ranks[c];  // the cell's pair offset (k_cnt_down)
         skeys[dst] = k;
         svals[dst] = (unsigned)c;
     }
@@ -236,7 +239,8 @@ constexpr int kWarpSlots = 8;  // slots per lane of the warp path: cells of up t
 // holding kWarpSlots of them: a pair's place is the number of smaller slots of
 // the cell, counted by shuffles, and the warp writes in place.  A larger cell
 // goes to a worklist for k_cell_order_big.
-__global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
+__global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, const unsigned* __restrict__ cells,
+                                                   unsigned* __restrict__ svals, int* __restrict__ cnt,
                                                    int* __restrict__ big, long long max_cells, ft_counters* ctr) {
     const long long M = ctr->M;
     if (M > max_cells) return;
@@ -244,6 +248,7 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
     const long long nw = (long long)gridDim.x * (kB / 32);
     for (long long m = ((long long)blockIdx.x * kB + threadIdx.x) >> 5; m < M; m += nw) {
         const int q0 = cell_off[m], n = cell_off[m + 1] - q0;
+        if (lane == 0) cnt[cells[m]] = 0;  // back to zero for the next binning
         if (n <= 1) continue;
         if (n > 32 * kWarpSlots) {
             if (lane == 0) big[atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->big), 1ull)] = (int)m;
@@ -463,13 +468,13 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
     k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
     k_cnt_down<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
                                 ws->ctr);
-    k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->idx_map, ws->cell_off, ws->keys[1],
-                                            ws->vals[1], ws->max_cells, ws->ctr);
-    // the ranks in vals[0] are spent once placed: that buffer is the scratch of large cells
+    k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->cell_cnt, ws->keys[1], ws->vals[1],
+                                            ws->max_cells, ws->ctr);
     // large cells: the ranks in vals[0] are spent once placed, so that buffer is
     // their merge scratch; cell_L (filled only by the volume fraction) holds the worklist
     int* big = reinterpret_cast<int*>(ws->cell_L);
-    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->vals[1], big, ws->max_cells, ws->ctr);
+    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->cells, ws->vals[1], ws->cell_cnt, big,
+                                                 ws->max_cells, ws->ctr);
     k_cell_order_big<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], big, ws->max_cells,
                                                      ws->ctr);
     ws->sorted_buf = 1;
