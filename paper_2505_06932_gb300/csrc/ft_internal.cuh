@@ -148,8 +148,9 @@ cudaError_t launch_ppic_frame(ft_workspace* ws, long long cap, double* frame, cu
 void count_launches(int n);  // kernels launched by this library (ft_launch_count)
 
 cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s);
-cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n,
-                               long long* total, cudaStream_t s);
+// candidate offsets of the triangles (a scan of their counts, in triangle order)
+// and the triangle index of every candidate slot; sets C_need and C
+cudaError_t launch_candidates(ft_workspace* ws, cudaStream_t s);
 // the kept pairs into cell order: interfacial cell list, offsets, index map
 // (the counts k_clip left in cell_cnt over keys [0, nkeys)); resets cell_cnt
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s);

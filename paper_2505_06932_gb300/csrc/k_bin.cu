@@ -171,21 +171,6 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
     bx[1] = make_int4(box[4], box[5], b, 0);
 }
 
-__global__ void __launch_bounds__(kThreads) k_expand(const int* __restrict__ tri_cnt, const int* __restrict__ tri_off,
-                                                     long long T, long long max_cand, int* __restrict__ cand_tri,
-                                                     ft_counters* ctr) {
-    const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
-    const long long need = ctr->C_need;
-    const bool ok = need <= max_cand;
-    if (t == 0) {
-        ctr->C = ok ? need : 0;
-        if (!ok) ft_flag(ctr, FT_ST_CAPACITY);
-    }
-    if (!ok || t >= T) return;
-    const int off = tri_off[t], cnt = tri_cnt[t];
-    for (int l = 0; l < cnt; l++) cand_tri[off + l] = (int)t;
-}
-
 // ---------------------------------------------------------------------------
 // canonical clip
 // ---------------------------------------------------------------------------
@@ -643,10 +628,9 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
     k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_box,
                                                     ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
     // candidate ranges in triangle order, so that slot order is triangle order
-    cudaError_t e = launch_scan_counts(ws, ws->tri_cnt, ws->tri_off, &ws->ctr->T, &ws->ctr->C_need, s);
+    cudaError_t e = launch_candidates(ws, s);
     if (e != cudaSuccess) return e;
-    count_launches(2);
-    k_expand<<<nb ? nb : 1, kThreads, 0, s>>>(ws->tri_cnt, ws->tri_off, T, ws->max_cand, ws->cand_tri, ws->ctr);
+    count_launches(1);
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     ws->last_precision = fp32 ? FT_FP32C : FT_FP64;

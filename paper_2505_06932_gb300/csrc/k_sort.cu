@@ -62,30 +62,42 @@ __global__ void __launch_bounds__(kB) k_scan_reduce(L ld, const long long* n_ptr
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
-// The down-sweep: each block sums the reduce partials of the blocks before it
-// (gridDim <= kB, one per thread) for its carry, block 0 also writes the total;
-// then its segment is scanned tile by tile.
-template <class L>
-__global__ void __launch_bounds__(kB) k_scan_down(L ld, const long long* n_ptr, const long long* partials,
-                                                  int* out, long long* total) {
+// The down-sweep of the triangle counts: each block sums the reduce partials
+// of the blocks before it (gridDim <= kB, one per thread) for its carry; then
+// its segment is scanned tile by tile into the candidate offsets, and every
+// triangle's candidate slots are filled with its index (when the total fits
+// max_cand; block 0 sets the candidate count C, 0 and the capacity flag if not).
+__global__ void __launch_bounds__(kB) k_scan_expand(const int* __restrict__ cnt, const long long* n_ptr,
+                                                    const long long* __restrict__ partials, int* __restrict__ off,
+                                                    long long max_cand, int* __restrict__ cand_tri, ft_counters* ctr) {
     __shared__ long long sm[kB / 32];
     const long long n = *n_ptr;
     const long long s = seg_len(n, gridDim.x);
     const long long b0 = blockIdx.x * s, b1 = min(n, b0 + s);
-    long long carry;
+    long long carry, all;
     {
         const long long p = (threadIdx.x < gridDim.x) ? partials[threadIdx.x] : 0;
         long long excl;
         carry = block_excl_scan((threadIdx.x < blockIdx.x) ? p : 0, excl, sm);
-        const long long all = block_excl_scan(p, excl, sm);
-        if (blockIdx.x == 0 && threadIdx.x == 0) *total = all;
+        all = block_excl_scan(p, excl, sm);
+    }
+    const bool ok = all <= max_cand;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->C_need = all;
+        ctr->C = ok ? all : 0;
+        if (!ok) ft_flag(ctr, FT_ST_CAPACITY);
     }
     for (long long base = b0; base < b1; base += kB) {
         const long long i = base + threadIdx.x;
-        const long long v = (i < b1) ? ld(i) : 0;
+        const int v = (i < b1) ? cnt[i] : 0;
         long long excl;
         const long long tot = block_excl_scan(v, excl, sm);
-        if (i < b1) out[i] = (int)(carry + excl);
+        if (i < b1) {
+            const long long o = carry + excl;
+            off[i] = (int)o;
+            if (ok)
+                for (int l = 0; l < v; l++) cand_tri[o + l] = (int)i;
+        }
         carry += tot;
     }
 }
@@ -448,14 +460,13 @@ cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys,
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_counts(ft_workspace* ws, const int* in, int* out, const long long* n, long long* total,
-                               cudaStream_t s) {
+cudaError_t launch_candidates(ft_workspace* ws, cudaStream_t s) {
     const int G = ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
-    LoadCounts ld{in};
+    LoadCounts ld{ws->tri_cnt};
     count_launches(2);
-    k_scan_reduce<<<G, kB, 0, s>>>(ld, n, part);
-    k_scan_down<<<G, kB, 0, s>>>(ld, n, part, out, total);
+    k_scan_reduce<<<G, kB, 0, s>>>(ld, &ws->ctr->T, part);
+    k_scan_expand<<<G, kB, 0, s>>>(ws->tri_cnt, &ws->ctr->T, part, ws->tri_off, ws->max_cand, ws->cand_tri, ws->ctr);
     return cudaGetLastError();
 }
 
