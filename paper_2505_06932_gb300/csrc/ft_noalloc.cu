@@ -86,7 +86,9 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
 
     ft_workspace ws = {};
     ws.device = dev;
-    cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        ws.sm_count < 1)
+        return FT_ERR_CUDA;
     ws.grid_blocks = kBlocks;
     ws.tune = ft_tune{4, 4, 16, 8, 4, 0, kBlocks};
     ws.g = *g;
@@ -114,12 +116,17 @@ extern "C" int ft_volume_fraction_noalloc(const ft_grid* g, const ft_front* f, c
     ws.cell_P = reinterpret_cast<double*>(base + kOffCellP);
     ws.partials = reinterpret_cast<int*>(base + kOffPartials);
 
+    // the scratch holds float64 fragment records only: this call always computes
+    // in float64, whatever p->precision asks for
+    ft_params p64 = *p;
+    p64.precision = FT_FP64;
+
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: reset counters, index map and cell counts
     cudaError_t e = cudaMemsetAsync(ws.ctr, 0, sizeof(ft_counters), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.idx_map, 0xff, sizeof(int) * (size_t)ncells, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.cell_cnt, 0, sizeof(int) * (size_t)ncells, s);
-    if (e == cudaSuccess) e = ft::launch_bin(&ws, f, p, s);
+    if (e == cudaSuccess) e = ft::launch_bin(&ws, f, &p64, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(&ws, ncells, s);
     if (e == cudaSuccess) e = ft::launch_alpha(&ws, alpha, s);
     if (e == cudaSuccess) {

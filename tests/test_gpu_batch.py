@@ -100,7 +100,7 @@ def test_batch_fronts_match_oracle():
         gpu["pair_keys"], gpu["pair_tris"] = _batch_pairs(bc, b)
         orc = run_oracle(w)
         orc["_faces"] = w["faces"]
-        compare(gpu, orc, name=f"batch_front_{b}")
+        compare(gpu, orc)
 
 
 def test_batch_cell_ranges():

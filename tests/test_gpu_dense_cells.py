@@ -36,6 +36,10 @@ def test_dense_cells_pairs_and_alpha(s, expect_max):
     gpu = run_gpu(w, precision=F.FT_FP64)
     tol = 2 * 24 * 2.0 * per_cell.max() * 2.0 ** -53
     assert np.max(np.abs(gpu["alpha"] - al)) <= tol
+    # the FP32 form sums thousands of float fragment terms per cell with
+    # compensated (two-sum) accumulation: it keeps the form's stated 1e-6
+    gpu32 = run_gpu(w, precision=F.FT_FP32C)
+    assert np.max(np.abs(gpu32["alpha"] - al)) <= 1e-6
 
 
 def test_cell_capacity_overflow_then_recovery():
