@@ -32,8 +32,8 @@ class _Grid(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("delta_h", C.c_double), ("delta_growth", C.c_double), ("delta_max_h", C.c_double),
-                ("sigma", C.c_double), ("fit_min", C.c_int32), ("pad", C.c_int32),
-                ("frame_angle", C.c_double)]
+                ("sigma", C.c_double), ("fit_min", C.c_int32), ("fit_ring", C.c_int32),
+                ("frame_angle", C.c_double), ("frame_vertex", C.c_int32), ("pad", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +72,10 @@ def lib():
             L.og_alpha.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int32, P, P]
             L.og_ppic.restype = C.c_int
             L.og_ppic.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_int64, P, P, P, P, P, P]
+            L.og_closest_vertex.restype = None
+            L.og_closest_vertex.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, P, P, P]
+            L.og_ring.restype = C.c_int64
+            L.og_ring.argtypes = [C.c_int64, P, C.c_int64, C.c_int64, C.c_int32, P, C.c_int64]
             L.og_csf.restype = C.c_int
             L.og_csf.argtypes = [P, P, C.c_int64, P, P, P, C.c_double, P]
             L.og_face_force.restype = C.c_int
@@ -191,12 +195,14 @@ def alpha(verts, tris, g, margin=None):
 
 def ppic(verts, tris, g, cells, params=None, frame_angle=0.0, frame=False):
     """PPIC curvature, paraboloid normal, coefficients and status in the given
-    cells (and, with ``frame=True``, each cell's frame (t1, t2, n) as (M, 9))."""
+    cells (and, with ``frame=True``, each cell's frame (t1, t2, n) as (M, 9)).
+    params may set fit_ring (0: fragments; k: whole triangles of the k-ring of
+    the closest vertex) and frame_vertex (1: the closest vertex's normal)."""
     p = dict(DEFAULT_PARAMS)
     if params:
         p.update(params)
-    ps = _Params(p["delta_h"], p["delta_growth"], p["delta_max_h"], p["sigma"], int(p["fit_min"]), 0,
-                 float(frame_angle))
+    ps = _Params(p["delta_h"], p["delta_growth"], p["delta_max_h"], p["sigma"], int(p["fit_min"]),
+                 int(p.get("fit_ring", 0)), float(frame_angle), int(p.get("frame_vertex", 0)), 0)
     v, t = _front(verts, tris)
     gs = _grid(g)
     cells = np.ascontiguousarray(cells, dtype=np.uint32)
@@ -213,6 +219,28 @@ def ppic(verts, tris, g, cells, params=None, frame_angle=0.0, frame=False):
     if frame:
         return kappa, normal, coeffs, status, fr
     return kappa, normal, coeffs, status
+
+
+def closest_vertex(verts, tris, g, cells):
+    """Per cell the index of the front vertex closest to its centre and that
+    vertex's normal (M, 3)."""
+    v, t = _front(verts, tris)
+    cells = np.ascontiguousarray(cells, dtype=np.uint32)
+    idx = np.empty(cells.shape[0], np.int32)
+    nrm = np.empty((cells.shape[0], 3), np.float64)
+    lib().og_closest_vertex(_ptr(v), v.shape[0], _ptr(t), t.shape[0], C.byref(_grid(g)), cells.shape[0],
+                            _ptr(cells), _ptr(idx), _ptr(nrm))
+    return idx, nrm
+
+
+def ring(verts, tris, v, k):
+    """The k-ring of triangles around vertex v, ascending triangle ids."""
+    vv, t = _front(verts, tris)
+    cap = 4096
+    out = np.empty(cap, np.int32)
+    n = lib().og_ring(vv.shape[0], _ptr(t), t.shape[0], int(v), int(k), _ptr(out), cap)
+    assert n <= cap
+    return out[:n].copy()
 
 
 def csf(g, alpha_dense, cells, kappa, normal, sigma=1.0):

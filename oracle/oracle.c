@@ -443,6 +443,146 @@ int og_alpha(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, c
     return st ? -1 : 0;
 }
 
+/* vertex -> incident triangles, each list in ascending triangle order */
+typedef struct {
+    int64_t* off; /* nv + 1 */
+    int32_t* tri; /* 3 nt   */
+} og_inc;
+
+static og_inc og_incidence(int64_t nv, const int32_t* tris, int64_t nt) {
+    og_inc I;
+    I.off = (int64_t*)calloc((size_t)nv + 1, sizeof(int64_t));
+    I.tri = (int32_t*)malloc(sizeof(int32_t) * (size_t)(3 * nt + 1));
+    for (int64_t t = 0; t < nt; t++)
+        for (int c = 0; c < 3; c++) I.off[tris[3 * t + c] + 1]++;
+    for (int64_t v = 0; v < nv; v++) I.off[v + 1] += I.off[v];
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nv + 1));
+    memcpy(cur, I.off, sizeof(int64_t) * (size_t)(nv + 1));
+    for (int64_t t = 0; t < nt; t++) /* ascending t: lists come out sorted */
+        for (int c = 0; c < 3; c++) I.tri[cur[tris[3 * t + c]]++] = (int32_t)t;
+    free(cur);
+    return I;
+}
+
+static void og_inc_free(og_inc* I) {
+    free(I->off);
+    free(I->tri);
+}
+
+static int og_cmp_i32(const void* a, const void* b) {
+    const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* The k-ring of triangles around vertex v (k >= 1): the triangles incident to
+ * v; then, k - 1 times, every triangle sharing a vertex with the ring so far.
+ * Returns a malloc'ed ascending list and its length. */
+static int32_t* og_ring_list(const og_inc* I, const int32_t* tris, int64_t v, int32_t k, int64_t* count) {
+    int64_t n = I->off[v + 1] - I->off[v];
+    int32_t* ring = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    memcpy(ring, I->tri + I->off[v], sizeof(int32_t) * (size_t)n);
+    for (int32_t r = 2; r <= k; r++) {
+        int64_t cap = 0;
+        for (int64_t q = 0; q < n; q++)
+            for (int c = 0; c < 3; c++) {
+                const int64_t u = tris[3 * (int64_t)ring[q] + c];
+                cap += I->off[u + 1] - I->off[u];
+            }
+        int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap + 1));
+        int64_t m = 0;
+        for (int64_t q = 0; q < n; q++)
+            for (int c = 0; c < 3; c++) {
+                const int64_t u = tris[3 * (int64_t)ring[q] + c];
+                for (int64_t e = I->off[u]; e < I->off[u + 1]; e++) cand[m++] = I->tri[e];
+            }
+        qsort(cand, (size_t)m, sizeof(int32_t), og_cmp_i32);
+        int64_t u = 0;
+        for (int64_t q = 0; q < m; q++)
+            if (q == 0 || cand[q] != cand[q - 1]) cand[u++] = cand[q];
+        free(ring);
+        ring = cand;
+        n = u;
+    }
+    *count = n;
+    return ring;
+}
+
+int64_t og_ring(int64_t nv, const int32_t* tris, int64_t nt, int64_t v, int32_t k, int32_t* out, int64_t cap) {
+    og_inc I = og_incidence(nv, tris, nt);
+    int64_t n = 0;
+    int32_t* r = og_ring_list(&I, tris, v, k, &n);
+    for (int64_t q = 0; q < n && q < cap; q++) out[q] = r[q];
+    free(r);
+    og_inc_free(&I);
+    return n;
+}
+
+/* cell centre of (i, j, k): origin + (index + 1/2) h, each operation rounded */
+static void og_cell_centre(const og_grid* g, int64_t i, int64_t j, int64_t k, double* xc) {
+    xc[0] = g->origin[0] + ((double)i + 0.5) * g->h;
+    xc[1] = g->origin[1] + ((double)j + 0.5) * g->h;
+    xc[2] = g->origin[2] + ((double)k + 0.5) * g->h;
+}
+
+/* The front vertex closest to xc: |x - xc|^2 = (dx dx + dy dy) + dz dz with
+ * every operation rounded; the lowest index among equal distances. */
+static int64_t og_closest_one(const double* verts, int64_t nv, const double* xc) {
+    int64_t best = -1;
+    double bd = INFINITY;
+    for (int64_t v = 0; v < nv; v++) {
+        const double dx = verts[3 * v] - xc[0], dy = verts[3 * v + 1] - xc[1], dz = verts[3 * v + 2] - xc[2];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 < bd) {
+            bd = d2;
+            best = v;
+        }
+    }
+    return best;
+}
+
+/* Normal of vertex v: the normalized sum of the area vectors (b - a) x (c - a)
+ * of its triangles (a, b, c), in ascending triangle order; -1 if the sum is 0. */
+static int og_vertex_normal(const double* verts, const int32_t* tris, const og_inc* I, int64_t v, double* n) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t q = I->off[v]; q < I->off[v + 1]; q++) {
+        const int64_t t = I->tri[q];
+        const double* a = verts + 3 * (int64_t)tris[3 * t];
+        const double* b = verts + 3 * (int64_t)tris[3 * t + 1];
+        const double* c = verts + 3 * (int64_t)tris[3 * t + 2];
+        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        s[0] += e1[1] * e2[2] - e1[2] * e2[1];
+        s[1] += e1[2] * e2[0] - e1[0] * e2[2];
+        s[2] += e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    const double l = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (!(l > 0.0)) return -1;
+    for (int d = 0; d < 3; d++) n[d] = s[d] / l;
+    return 0;
+}
+
+void og_closest_vertex(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, const og_grid* g,
+                       int64_t ncells, const uint32_t* cells, int32_t* closest, double* vnormal) {
+    og_inc I = og_incidence(nv, tris, nt);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < ncells; c++) {
+        const uint64_t key = cells[c];
+        const int64_t k = (int64_t)(key % (uint64_t)g->n[2]);
+        const int64_t j = (int64_t)((key / (uint64_t)g->n[2]) % (uint64_t)g->n[1]);
+        const int64_t i = (int64_t)(key / ((uint64_t)g->n[2] * (uint64_t)g->n[1]));
+        double xc[3];
+        og_cell_centre(g, i, j, k, xc);
+        const int64_t v = og_closest_one(verts, nv, xc);
+        closest[c] = (int32_t)v;
+        if (vnormal) {
+            double n[3] = {0.0, 0.0, 0.0};
+            if (v >= 0) og_vertex_normal(verts, tris, &I, v, n);
+            for (int d = 0; d < 3; d++) vnormal[3 * c + d] = n[d];
+        }
+    }
+    og_inc_free(&I);
+}
+
 /* ------------------------------------------------------------------------ */
 /* PPIC volume fit                                                           */
 /* ------------------------------------------------------------------------ */
@@ -576,6 +716,10 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
     const int32_t margin = 2 + (int32_t)ceil(p->delta_max_h);
     og_frags F = og_build_frags(verts, nv, tris, nt, g, margin);
     const double h = g->h;
+    /* the paper's own neighbourhood and frame (Sec. 3.2) need the mesh incidence */
+    const int variant = p->fit_ring > 0 || p->frame_vertex;
+    og_inc I = {NULL, NULL};
+    if (variant) I = og_incidence(nv, tris, nt);
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 8) reduction(| : err)
     for (int64_t c = 0; c < ncells; c++) {
@@ -617,7 +761,24 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
             nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
             stc |= 4;
         }
-        const double n[3] = {N[0] / nn, N[1] / nn, N[2] / nn};
+        double n[3] = {N[0] / nn, N[1] / nn, N[2] / nn};
+        /* the paper's reading: the front vertex closest to the cell centre gives
+         * the frame normal and the centre of the k-ring of fit triangles */
+        int64_t vc = -1;
+        if (variant) {
+            vc = og_closest_one(verts, nv, xc);
+            double nv_[3];
+            if (p->frame_vertex) {
+                if (vc >= 0 && og_vertex_normal(verts, tris, &I, vc, nv_) == 0) {
+                    for (int d = 0; d < 3; d++) n[d] = nv_[d];
+                    stc &= ~4;
+                } else {
+                    stc |= 4; /* no usable vertex normal: the fragment normal stays */
+                }
+            }
+        }
+        int64_t nring = 0;
+        int32_t* ring = (p->fit_ring > 0 && vc >= 0) ? og_ring_list(&I, tris, vc, p->fit_ring, &nring) : NULL;
         double t1[3], t2[3];
         og_basis(n, t1, t2);
         if (p->frame_angle != 0.0) {
@@ -634,7 +795,31 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
             memset(M, 0, sizeof M);
             memset(b, 0, sizeof b);
             int64_t count = 0;
-            const int64_t R = (int64_t)ceil(delta - 0.5);
+            /* whole triangles of the ring: the Wendland distance from the triangle's centre */
+            for (int64_t q = 0; q < nring; q++) {
+                const int64_t t = ring[q];
+                for (int m = 0; m < 3; m++)
+                    for (int d = 0; d < 3; d++) rv[m][d] = (verts[3 * (int64_t)tris[3 * t + m] + d] - xc[d]) / h;
+                double cf[3];
+                for (int d = 0; d < 3; d++) cf[d] = (rv[0][d] + rv[1][d] + rv[2][d]) / 3.0;
+                const double dist = sqrt(cf[0] * cf[0] + cf[1] * cf[1] + cf[2] * cf[2]);
+                if (!(dist < delta)) continue;
+                count++;
+                const double w = og_wendland(dist / delta);
+                double xs[3], ys[3], mom[6];
+                for (int m = 0; m < 3; m++) {
+                    xs[m] = t1[0] * rv[m][0] + t1[1] * rv[m][1] + t1[2] * rv[m][2];
+                    ys[m] = t2[0] * rv[m][0] + t2[1] * rv[m][1] + t2[2] * rv[m][2];
+                }
+                og_green_moments(xs, ys, 3, mom);
+                const double zc = n[0] * cf[0] + n[1] * cf[1] + n[2] * cf[2];
+                const double G = mom[0] * zc;
+                for (int r = 0; r < 6; r++) {
+                    for (int s2 = 0; s2 < 6; s2++) M[r * 6 + s2] += w * mom[r] * mom[s2];
+                    b[r] += w * G * mom[r];
+                }
+            }
+            const int64_t R = (p->fit_ring > 0) ? -1 : (int64_t)ceil(delta - 0.5);
             for (int64_t di = -R; di <= R; di++)
                 for (int64_t dj = -R; dj <= R; dj++)
                     for (int64_t dk = -R; dk <= R; dk++) {
@@ -709,7 +894,9 @@ int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, co
                 frame[9 * c + 6 + d] = n[d];
             }
         fit_status[c] = stc;
+        free(ring);
     }
+    if (variant) og_inc_free(&I);
     free(F.keys); free(F.off); free(F.voff); free(F.pv);
     return err ? -1 : 0;
 }
@@ -954,32 +1141,6 @@ int og_get_threads(void) {
 /* ------------------------------------------------------------------------ */
 /* local roughness detection and smoothing (Sec. 3.4)                        */
 /* ------------------------------------------------------------------------ */
-
-/* vertex -> incident triangles, each list in ascending triangle order */
-typedef struct {
-    int64_t* off; /* nv + 1 */
-    int32_t* tri; /* 3 nt   */
-} og_inc;
-
-static og_inc og_incidence(int64_t nv, const int32_t* tris, int64_t nt) {
-    og_inc I;
-    I.off = (int64_t*)calloc((size_t)nv + 1, sizeof(int64_t));
-    I.tri = (int32_t*)malloc(sizeof(int32_t) * (size_t)(3 * nt + 1));
-    for (int64_t t = 0; t < nt; t++)
-        for (int c = 0; c < 3; c++) I.off[tris[3 * t + c] + 1]++;
-    for (int64_t v = 0; v < nv; v++) I.off[v + 1] += I.off[v];
-    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nv + 1));
-    memcpy(cur, I.off, sizeof(int64_t) * (size_t)(nv + 1));
-    for (int64_t t = 0; t < nt; t++) /* ascending t: lists come out sorted */
-        for (int c = 0; c < 3; c++) I.tri[cur[tris[3 * t + c]]++] = (int32_t)t;
-    free(cur);
-    return I;
-}
-
-static void og_inc_free(og_inc* I) {
-    free(I->off);
-    free(I->tri);
-}
 
 /* position of vertex v in triangle t (0..2), -1 if absent */
 static int og_slot(const int32_t* tris, int64_t t, int64_t v) {

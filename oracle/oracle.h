@@ -35,8 +35,13 @@ typedef struct {
     double delta_max_h;  /* largest support / h                                 */
     double sigma;        /* surface tension coefficient (Eq. csf)               */
     int32_t fit_min;     /* minimum number of non-zero weights (Sec. 3.2: 24)   */
-    int32_t pad;
+    int32_t fit_ring;    /* 0: clipped fragments within delta (default);
+                            k = 1..3: whole triangles of the k-ring of the
+                            front vertex closest to the cell centre (Sec. 3.2) */
     double frame_angle;  /* test hook: rotate (t1,t2) about n by this angle     */
+    int32_t frame_vertex;/* 0: n from the cell's fragment area vectors (default);
+                            1: the normal of the closest front vertex (Sec. 3.2) */
+    int32_t pad;
 } og_params;
 
 /* status bits */
@@ -82,6 +87,20 @@ int og_alpha(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
 int og_ppic(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
             const og_grid* g, const og_params* p, int64_t ncells, const uint32_t* cells,
             double* kappa, double* normal, double* coeffs, int8_t* fit_status, double* frame);
+
+/* The front vertex closest to each cell centre (brute force over every vertex;
+ * distance^2 rounded operation by operation, ties to the lowest index) and its
+ * normal, the normalized sum of the area vectors (b - a) x (c - a) of its
+ * triangles in ascending triangle order.  closest (ncells) and vnormal
+ * (ncells x 3, may be NULL). */
+void og_closest_vertex(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, const og_grid* g,
+                       int64_t ncells, const uint32_t* cells, int32_t* closest, double* vnormal);
+
+/* The k-ring of triangles around vertex v (k >= 1): the triangles incident to
+ * v, then repeatedly every triangle sharing a vertex with the previous ring;
+ * ascending triangle ids into out (capacity cap).  Returns the count (which
+ * may exceed cap; only cap are written). */
+int64_t og_ring(int64_t nv, const int32_t* tris, int64_t nt, int64_t v, int32_t k, int32_t* out, int64_t cap);
 
 /* CSF source S = sigma kappa grad(alpha) (Eq. csf) with the weighted curvature
  * smoothing of Sec. 3.3 in non-interfacial cells.  force is (3, n0*n1*n2). */
