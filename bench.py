@@ -32,9 +32,137 @@ sys.path.insert(0, ROOT)
 
 METRIC = "interfacial cells/s for alpha+kappa (full five-step hot path per step)"
 FLOPS_PER_FIT_PAIR = 130.0   # per (cell, fragment-in-support) pair of the volume fit
-FLOPS_PER_FIT_SOLVE = 150.0  # per cell: the 6x6 solve
+FLOPS_PER_FIT_SOLVE = 260.0  # per cell: 6x6 LDL^T (144), two triangular solves (72), curvature and normal
+FLOPS_PER_CAND = 60.0        # clip: per candidate pair, cell-unit coordinates and the plane stages
+FLOPS_PER_KEPT = 150.0       # clip: per kept pair, the fragment moments
 FP64_PEAK_TFLOPS = 1.25      # GB300 nominal float64 (profiling recipe table)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz
+HBM_FALLBACK_GBS = 6800.0    # profiling recipe fallback, used only without MEASURED_PEAKS.json
+
+
+def hbm_peak():
+    """Measured STREAM-style copy bandwidth of the GB300s (GB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "of fallback (profiling recipe, 6.8 TB/s)"
+
+
+# Algorithmic work of one launch of each kernel on one front, from the work
+# counts of that front (T triangles, V vertices, N grid cells, C candidate
+# pairs, P kept pairs, M interfacial cells, fit_pairs, ring cells of the CSF
+# step): ("hbm", bytes) or ("fp32" | "fp64", flops).
+def kernel_work(name, w, fp32):
+    T, V, N, C, P, M = w["T"], w["V"], w["N"], w["C"], w["P"], w["M"]
+    R, FP = w["ring"], w["fit_pairs"]
+    table = {
+        "k_tri_setup": ("hbm", 152 * T + 8 * M, "84 B of indices and coordinates read, 68 B of box, count and "
+                        "normal written per triangle; the previous cells' index-map entries reset"),
+        "k_scan_reduce": ("hbm", 4 * T, "the triangle counts read"),
+        "k_scan_expand": ("hbm", 8 * T + 4 * C, "counts read, offsets written, the triangle id of every "
+                          "candidate slot written"),
+        "k_cnt_reduce": ("hbm", 4 * N, "the per-key pair counts read"),
+        "k_cnt_down": ("hbm", 4 * N + 16 * M, "counts read; cell key, offset, index map and counter written "
+                       "per interfacial cell"),
+        "k_place": ("hbm", 4 * C + 16 * P, "every candidate's key read; per kept pair its rank and its cell's "
+                    "offset read, key and slot written"),
+        "k_cell_order": ("hbm", 12 * M + 8 * P, "per cell its offsets and counter; per pair its slot read and "
+                         "written"),
+        "k_gather": ("hbm", (116 if fp32 else 212) * P, "per pair its slot read, its record read and written "
+                     "in cell order, its float centroid written"),
+        "k_alpha_cells32": ("hbm", 24 * M + 8 * P, "per pair the two record values of the column moment; "
+                            "per cell offsets read, L and P written"),
+        "k_alpha_cells": ("hbm", 24 * M + 16 * P, "per pair the two record values of the column moment; "
+                          "per cell offsets read, L and P written"),
+        "k_alpha_fill": ("hbm", 12 * N + 16 * M, "per grid cell the index map read and alpha written; per "
+                         "interfacial cell L and P read"),
+        "force clear (memset)": ("hbm", 24 * N, "the three force components written in every grid cell"),
+        "k_csf_cells": ("hbm", 84 * M + 4 * R, "per interfacial cell its key, six alpha values, kappa, the "
+                        "force written; the ring list"),
+        "k_csf_ring": ("hbm", 176 * R, "per ring cell 26 index-map entries, six alpha values, the force "
+                       "written"),
+        "k_interp": ("hbm", 288 * V, "per vertex its position read, its velocity written and about 30 face "
+                     "values gathered"),
+        "k_clip32": ("fp32", FLOPS_PER_CAND * C + FLOPS_PER_KEPT * P,
+                     f"{FLOPS_PER_CAND:.0f} flops per candidate pair (cell-unit coordinates, plane stages, "
+                     f"crossings), {FLOPS_PER_KEPT:.0f} per kept pair (fragment moments)"),
+        "k_clip": ("fp64", FLOPS_PER_CAND * C + FLOPS_PER_KEPT * P,
+                   f"{FLOPS_PER_CAND:.0f} flops per candidate pair, {FLOPS_PER_KEPT:.0f} per kept pair"),
+        "k_ppic_acc<float>": ("fp32", FLOPS_PER_FIT_PAIR * FP, f"{FLOPS_PER_FIT_PAIR:.0f} flops per (cell, "
+                              "fragment-in-support) pair"),
+        "k_ppic_acc<double>": ("fp64", FLOPS_PER_FIT_PAIR * FP, f"{FLOPS_PER_FIT_PAIR:.0f} flops per (cell, "
+                               "fragment-in-support) pair"),
+        "k_ppic_solve": ("fp64", FLOPS_PER_FIT_SOLVE * M, f"{FLOPS_PER_FIT_SOLVE:.0f} flops per cell"),
+    }
+    return table.get(name)
+
+
+def read_traffic(workload):
+    """DRAM bytes per launch of each kernel from the committed ncu summary of
+    this workload (profiles/dram_traffic_<workload>.md), keyed by kernel name,
+    with the source hash the capture was taken on: a kernel whose source file
+    changed since then gets null."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.md")
+    out = {}
+    if not os.path.exists(path):
+        return out, None
+    for line in open(path):
+        c = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(c) < 5 or not c[0].startswith("`"):
+            continue
+        name, src, sha = c[0].strip("`"), c[1].strip("`"), c[2].strip("`")
+        try:
+            per_launch = float(c[4].replace(",", ""))
+        except ValueError:
+            continue
+        fp = os.path.join(ROOT, "paper_2505_06932_gb300", "csrc", src)
+        ok = os.path.exists(fp) and hashlib.sha256(open(fp, "rb").read()).hexdigest()[:12] == sha
+        out[name] = per_launch if ok else None
+    return out, os.path.relpath(path, ROOT)
+
+
+def roofline_list(trace, works, fp32, workload_tag):
+    """Per-kernel roofline entries from a trace of eager steps: the kernel's
+    algorithmic work per launch (mean over the fronts) divided by its mean
+    CUDA-event duration, against its bound's peak."""
+    hbm, hbm_src = hbm_peak()
+    traffic, tsrc = read_traffic(workload_tag)
+    items = [(k, v) for k, v in trace.items() if k is not None]
+    total = sum(ms for _, (n, ms) in items)
+    out = []
+    for name, (n, ms) in items:
+        if n == 0:
+            continue
+        per = [kernel_work(name, w, fp32) for w in works]
+        t_launch = ms / n * 1e-3
+        e = {"kernel": name, "launches": n, "us_per_launch": round(1e3 * ms / n, 2),
+             "share": round(ms / total, 4) if total else None}
+        if per[0] is None:
+            e.update(bound=None, note="no algorithmic work model (per-cell ordering of large cells)")
+        else:
+            kind, _, what = per[0]
+            amount = sum(p[1] for p in per) / len(per)
+            if kind == "hbm":
+                ach = amount / t_launch / 1e9
+                e.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
+                         algorithmic_per_launch=int(amount), peak_source=hbm_src)
+            else:
+                peak = FP32_PEAK_TFLOPS if kind == "fp32" else FP64_PEAK_TFLOPS
+                ach = amount / t_launch / 1e12
+                e.update(bound="alu", achieved=round(ach, 4), peak=round(peak, 3), unit="TFLOP/s",
+                         frac=round(ach / peak, 4), algorithmic_per_launch=int(amount),
+                         peak_source=("FP32: 152 SM x 128 FMA/clk x 2 x 2.07 GHz (recipe unit counts and clock)"
+                                      if kind == "fp32" else "FP64: nominal 1.25 TFLOP/s (recipe table)"))
+            e["work_model"] = what
+            tr = traffic.get(name)
+            e["traffic"] = tr
+            if tr is not None:
+                e["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch ({tsrc})"
+        out.append(e)
+    out.sort(key=lambda e: -(e["share"] or 0))
+    return out
 PARAB_FP64_FLOPS_PER_CELL = 72252.0  # FP64 flops (add + mul + 2 fma) executed per cell by k_parab_ppic on this workload (ncu)
 
 
@@ -49,7 +177,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager launches instead of one CUDA graph per step")
-    ap.add_argument("--phase-steps", type=int, default=20, help="eager steps timed per phase")
+    ap.add_argument("--phase-steps", type=int, default=20,
+                    help="eager steps timed per phase (and as many traced per kernel)")
+    ap.add_argument("--config-steps", type=int, default=10,
+                    help="timed steps of the 32^3 droplet and 256^3 droplet/bubble legs, both forms (0: skip)")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="only run this many eager steps of the 512-front batch (for a profiler's launch list)")
     ap.add_argument("--paraboloid-reps", type=int, default=5,
@@ -68,7 +199,10 @@ def parse():
                     help="timed steps of the batched form (512 fronts); 0: skip")
     ap.add_argument("--batch-fronts", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per served run; 0: skip")
-    ap.add_argument("--serve-rates", type=str, default="10,100,1000", help="Poisson arrival rates (req/s)")
+    ap.add_argument("--serve-rates", type=str, default="10,30,100,300,1000,2000",
+                    help="Poisson arrival rates (req/s)")
+    ap.add_argument("--serve-policies", type=str, default="fifo,backfill",
+                    help="admission policies timed at every rate (serve.Scheduler)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="device memory for resident requests")
     return ap.parse_args()
 
@@ -182,9 +316,10 @@ def oracle_pass(w, sel=None):
     return len(cells), dict(zip(PHASES, (t[k + 1] - t[k] for k in range(5))))
 
 
-def cpu_baseline(fronts, budget_s=10.0):
-    """The oracle (FP64 C, all host cores) on the whole workload: passes of the
-    five steps over every front until budget_s has elapsed (at least one)."""
+def cpu_baseline(fronts, budget_s=10.0, one_core_budget_s=10.0):
+    """The oracle (FP64 C) on the whole workload: passes of the five steps over
+    every front on all host cores until budget_s has elapsed (at least one);
+    then on one core, passes over the first front until one_core_budget_s."""
     import oracle
     oracle.set_threads(os.cpu_count() or 1)
     cells = passes = 0
@@ -194,10 +329,25 @@ def cpu_baseline(fronts, budget_s=10.0):
             cells += oracle_pass(w)[0]
         passes += 1
     dt = time.perf_counter() - t0
-    return dict(value=cells / dt, unit="interfacial cells/s", cores=oracle.get_threads(), kind="oracle",
-                sample=f"{passes} pass{'es' if passes != 1 else ''} of the five steps over the whole workload "
-                       f"({cells // passes} interfacial "
-                       f"cells per pass, every cell fitted), {dt:.1f} s; cells/s = cells / time")
+    out = dict(value=cells / dt, unit="interfacial cells/s", cores=oracle.get_threads(), kind="oracle",
+               sample=f"{passes} pass{'es' if passes != 1 else ''} of the five steps over the whole workload "
+                      f"({cells // passes} interfacial "
+                      f"cells per pass, every cell fitted), {dt:.1f} s; cells/s = cells / time")
+    if one_core_budget_s > 0:
+        oracle.set_threads(1)
+        c1 = p1 = 0
+        t0 = time.perf_counter()
+        while p1 == 0 or time.perf_counter() - t0 < one_core_budget_s:
+            c1 += oracle_pass(fronts[0])[0]
+            p1 += 1
+        d1 = time.perf_counter() - t0
+        out["one_core"] = dict(value=round(c1 / d1, 1), unit="interfacial cells/s", cores=oracle.get_threads(),
+                               kind="oracle",
+                               sample=f"{p1} pass{'es' if p1 != 1 else ''} of the five steps over "
+                                      f"{fronts[0]['name']} ({c1 // p1} interfacial cells, every cell fitted), "
+                                      f"{d1:.1f} s, one thread")
+        oracle.set_threads(os.cpu_count() or 1)
+    return out
 
 
 PHASES = ("bin", "alpha", "ppic", "csf", "interp")
@@ -222,7 +372,7 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
-    def make(precision):
+    def make(precision, fronts=fronts):
         prm = F.make_params(precision=precision)
         fcs = [F.FrontCoupling(w["grid"], w["tris"].shape[0], w["verts"].shape[0], params=prm, device=local)
                for w in fronts]
@@ -245,7 +395,7 @@ def run_ours(a):
             else:
                 call()
 
-    def step(prm, fcs, ev=None):
+    def step(prm, fcs, ev=None, dfr=dfr):
         for (v, t, fa), fc in zip(dfr, fcs):
             step_one(prm, fc, v, t, fa, ev)
 
@@ -265,7 +415,7 @@ def run_ours(a):
             sd.wait_stream(sa)
             F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
 
-    def capture(prm, fcs):
+    def capture(prm, fcs, dfr=dfr):
         """One CUDA graph for a whole step; the fronts are independent, so each
         runs on its own streams forked from (and joined back to) the capture
         stream: as the DAG of step_forked, or (--no-fork) in order on one stream."""
@@ -288,32 +438,46 @@ def run_ours(a):
                     cs.wait_stream(x)
         return g
 
-    def measure(precision, steps, warmup, clocks=False):
-        prm, fcs = make(precision)
+    def measure(precision, steps, warmup, clocks=False, fronts=fronts, dfr=dfr, phase_steps=None):
+        phase_steps = a.phase_steps if phase_steps is None else phase_steps
+        prm, fcs = make(precision, fronts)
         for _ in range(max(3, warmup)):
-            step(prm, fcs)
+            step(prm, fcs, dfr=dfr)
         torch.cuda.synchronize()
         tunings = None
         if a.autotune:
             tunings = [F.ft_autotune(fc.ws, prm, reps=3, verts=v, tris=t) for (v, t, fa), fc in zip(dfr, fcs)]
             for _ in range(max(3, warmup)):
-                step(prm, fcs)
+                step(prm, fcs, dfr=dfr)
             torch.cuda.synchronize()
         counts = [fc.ws.counts() for fc in fcs]
+        works = []
+        for fc, w in zip(fcs, fronts):
+            wc = fc.ws.work_counts()
+            wc.update(V=int(w["verts"].shape[0]), N=int(w["grid"].ncells))
+            works.append(wc)
         status = [fc.ws.status() for fc in fcs]
         if any(status):
             raise RuntimeError(f"device status after warm-up: {[F.status_names(x) for x in status]}")
-        # eager steps with an event pair around every call: the per-phase breakdown
+        # eager steps with an event pair around every call (the per-phase
+        # breakdown), then eager steps with an event pair around every kernel
+        # (the per-kernel roofline); L2 flushed before each step
         ph = {n: [] for n in PHASES}
         l0 = F.launch_count()
-        for _ in range(a.phase_steps):
+        for _ in range(phase_steps):
             flush.zero_()
-            step(prm, fcs, ph)
+            step(prm, fcs, ph, dfr=dfr)
         torch.cuda.synchronize()
-        kernels_per_step = (F.launch_count() - l0) / max(1, a.phase_steps)
-        phase_ms = {n: sum(e0.elapsed_time(e1) for e0, e1 in ph[n]) / max(1, a.phase_steps) for n in PHASES}
+        kernels_per_step = (F.launch_count() - l0) / max(1, phase_steps)
+        phase_ms = {n: sum(e0.elapsed_time(e1) for e0, e1 in ph[n]) / max(1, phase_steps) for n in PHASES}
         ppic_ms_eager = [e0.elapsed_time(e1) for e0, e1 in ph["ppic"]]
-        graph = None if a.no_graph else capture(prm, fcs)
+        F.trace_start(64 * max(1, phase_steps) * len(fcs))
+        for _ in range(phase_steps):
+            flush.zero_()
+            step(prm, fcs, dfr=dfr)
+        torch.cuda.synchronize()
+        trace = F.trace_stop()
+        graph = None if a.no_graph else capture(prm, fcs, dfr=dfr)
         if graph is not None:
             graph.replay()
             torch.cuda.synchronize()
@@ -331,7 +495,7 @@ def run_ours(a):
             if graph is not None:
                 graph.replay()
             else:
-                step(prm, fcs)
+                step(prm, fcs, dfr=dfr)
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -339,8 +503,9 @@ def run_ours(a):
         launches = (kernels_per_step * steps) if graph is not None else (F.launch_count() - l0)
         clk = clk.stop() if clk else None
         total_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
-        return dict(prm=prm, fcs=fcs, counts=counts, total_ms=total_ms, phase_ms=phase_ms,
-                    ppic_ms=ppic_ms_eager, launches=launches, clocks=clk, graph=graph, tunings=tunings)
+        return dict(prm=prm, fcs=fcs, counts=counts, works=works, total_ms=total_ms, phase_ms=phase_ms,
+                    ppic_ms=ppic_ms_eager, launches=launches, clocks=clk, graph=graph, tunings=tunings,
+                    trace=trace, kernels_per_step=kernels_per_step)
 
     def measure_batch_of_fronts(precision, steps):
         """The same fronts as one batch (one launch sequence for both), one CUDA
@@ -384,29 +549,24 @@ def run_ours(a):
     tmax = allmax(ws, r["total_ms"])
     value = allsum(ws, cells_per_step * a.steps) / (tmax * 1e-3)
 
-    # roofline of the fit (k_ppic_acc + k_ppic_solve), ALU-bound
-    nf = len(fronts)
-    flops = [FLOPS_PER_FIT_PAIR * fit_pairs[i] + FLOPS_PER_FIT_SOLVE * counts[i]["M"] for i in range(nf)]
-    ppic_ms = r["ppic_ms"]
-    ach = sum(flops[i % nf] for i in range(len(ppic_ms))) / (sum(ppic_ms) * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS if prec == F.FT_FP64 else FP32_PEAK_TFLOPS
+    # per-kernel rooflines from the traced eager steps; the headline object is
+    # the kernel with the largest share of the traced device time
+    tag = "fp32c_two_fronts_128" if prec == F.FT_FP32C else "fp64_two_fronts_128"
+    kernels = roofline_list(r["trace"], r["works"], prec == F.FT_FP32C, tag)
+    dom = next(e for e in kernels if e.get("bound"))
+    roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof.update(kernel=dom["kernel"], share_of_traced_time=dom["share"], us_per_launch=dom["us_per_launch"],
+                algorithmic_per_launch=dom["algorithmic_per_launch"], work_model=dom["work_model"],
+                peak_source=dom["peak_source"],
+                timing="CUDA events around every launch of the kernel (ft_trace_start/stop) in "
+                       f"{a.phase_steps} eager steps, L2 flushed before each step; the launch's own stream")
+    if dom.get("traffic_source"):
+        roof["traffic_source"] = dom["traffic_source"]
     try:
         probe = F.probe_fma_rate(0 if prec == F.FT_FP64 else 1, local) / 1e12
+        roof["probe_measured_fma_peak"] = round(probe, 4)
     except Exception:
-        probe = None
-    # DRAM bytes of one call (k_ppic_acc<float> + k_ppic_solve) from one ncu capture on the ellipsoid front
-    traffic = (13.446400e6 + 0.000256e6 + 3.779328e6) if prec == F.FT_FP32C else None
-    roof = {"kernel": "k_ppic_acc + k_ppic_solve", "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of each kernel on the "
-                              "ellipsoid front (profiles/k_ppic_acc_fp32c_ellipsoid_128.md, "
-                              "profiles/k_ppic_solve_fp32c_ellipsoid_128.md)" if traffic else None,
-            "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if prec == F.FT_FP64
-            else "152 SM x 128 FP32 FMA/clk x 2 x 2.07 GHz (recipe unit counts and clock)",
-            "probe_measured_peak": round(probe, 4) if probe else None,
-            "share_of_step": round(r["phase_ms"]["ppic"] / sum(r["phase_ms"].values()), 4),
-            "timing": "CUDA events around front_curvature_ppic in eager steps",
-            "flops_model": f"{FLOPS_PER_FIT_PAIR:.0f} per fit pair + {FLOPS_PER_FIT_SOLVE:.0f} per cell"}
+        pass
     phases = {n: round(v, 4) for n, v in r["phase_ms"].items()}
 
     alt = None
@@ -417,11 +577,55 @@ def run_ours(a):
         alt = {"precision": "fp64" if other == F.FT_FP64 else "fp32c", "steps": a.alt_steps,
                "value": round(allsum(ws, cells_per_step * a.alt_steps) / (ta * 1e-3), 1),
                "ms_per_step": round(ta / a.alt_steps, 4),
-               "phases_ms": {n: round(v, 4) for n, v in ra["phase_ms"].items()}}
+               "phases_ms": {n: round(v, 4) for n, v in ra["phase_ms"].items()},
+               "roofline_kernels": roofline_list(ra["trace"], ra["works"], other == F.FT_FP32C,
+                                                 "fp32c_two_fronts_128" if other == F.FT_FP32C
+                                                 else "fp64_two_fronts_128")}
         for fc in ra["fcs"]:
             fc.ws.close()
 
     one_batch = measure_batch_of_fronts(prec, a.steps) if a.alt_steps > 0 else None
+
+    def config_leg(title, ws_fronts, tag, steps):
+        """Another workload of the paper's shapes, both forms: cells/s of the
+        graph step and the per-kernel rooflines of traced eager steps."""
+        d_in = []
+        for w in ws_fronts:
+            d_in.append((torch.from_numpy(w["verts"]).to(dev), torch.from_numpy(w["tris"]).to(dev),
+                         [torch.from_numpy(f).to(dev) for f in w["faces"]]))
+        out = {"workload": title, "fronts": [w["name"] for w in ws_fronts],
+               "triangles": [int(w["tris"].shape[0]) for w in ws_fronts],
+               "l2": "flushed (512 MB write) before every timed step", "launch": "as the main line"}
+        for precision, ptag in ((F.FT_FP32C, "fp32c"), (F.FT_FP64, "fp64")):
+            rr = measure(precision, steps, 3, fronts=ws_fronts, dfr=d_in, phase_steps=max(2, min(5, steps)))
+            tt = allmax(ws, rr["total_ms"])
+            M = sum(c["M"] for c in rr["counts"])
+            out[ptag] = {"value": round(allsum(ws, M * steps) / (tt * 1e-3), 1), "unit": "interfacial cells/s",
+                         "ms_per_step": round(tt / steps, 4), "steps": steps, "cells_per_step": M,
+                         "fit_pairs_per_step": sum(c["fit_pairs"] for c in rr["counts"]),
+                         "clip_pairs_decided_in_fp64": sum(w["clip_f64"] for w in rr["works"]),
+                         "candidate_pairs": sum(w["C"] for w in rr["works"]),
+                         "phases_ms": {n: round(v, 4) for n, v in rr["phase_ms"].items()},
+                         "roofline_kernels": roofline_list(rr["trace"], rr["works"], precision == F.FT_FP32C,
+                                                           f"{ptag}_{tag}")}
+            for fc in rr["fcs"]:
+                fc.ws.close()
+            del rr
+        torch.cuda.empty_cache()
+        return out
+
+    configs = None
+    if a.config_steps > 0:
+        from paper_2505_06932_gb300 import inputs as I
+        configs = {
+            "laplace_droplet_32": config_leg("icosphere s4 (5,120 triangles) R 0.25, 32^3 grid (the paper's "
+                                             "Laplace-equilibrium droplet shape)", [I.laplace_droplet_32(1)],
+                                             "droplet_32", max(a.config_steps, 20)),
+            "sh_droplet_bubble_256": config_leg(
+                "icosphere s7 (327,680 triangles) R 0.2 with real SH deformation l 2..8 (oscillating droplet) "
+                "and the flattened, dimpled bubble, 256^3 grid, Taylor-Green faces",
+                [I.sh_droplet_256(seed=4), I.sh_droplet_256(seed=4, bubble=True)], "sh_droplet_bubble_256",
+                a.config_steps)}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     prm, fcs = r["prm"], r["fcs"]
@@ -596,8 +800,10 @@ def run_ours(a):
         "phases_ms": phases,
         "phases_note": "eager per-call CUDA-event times per step (sum over fronts), not the graph replay",
         "roofline": roof,
+        "roofline_kernels": kernels,
         "alt_precision": alt,
         "same_workload_as_one_batch": one_batch,
+        "other_configs": configs,
         "paraboloid": parab,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
@@ -852,17 +1058,35 @@ def run_served(a, local):
                      max_grid_cells=min(2 ** 32 - 2, budget // 56),
                      max_nt=sum(r.tris.shape[0] for r in probe),
                      max_cand=sum(S.candidate_estimate(r) for r in probe))
+    policies = [x for x in a.serve_policies.split(",") if x]
+    small = {r["rid"] for r in base if max(r["grid"].n) <= 128}
     out = {"workload": f"{a.serve_requests} requests per rate: icosphere s4-8 with real SH deformation "
                        f"(l 2-8, c ~ N(0,(0.05R)^2)), grids 32^3-512^3, 1-50 steps of dt = 0.25h each "
                        f"(bin, alpha, PPIC, CSF, RK4 advection), solid-body rotation about the front centre",
-           "budget_bytes": budget, "admission": "FIFO by device footprint and batch capacities",
+           "budget_bytes": budget,
+           "admission": "by device footprint and batch capacities; fifo: the queue head blocks the requests "
+                        "behind it; backfill: requests that fit pass a blocked head until it has waited 1 s",
+           "classes": f"small: grid <= 128^3 ({len(small)} requests), large: 256^3 and 512^3 "
+                      f"({len(base) - len(small)} requests)",
            "precision": "fp32c", "rates": {}}
+
+    def by_class(outs):
+        res = {}
+        for cls, sel in (("small", lambda rid: rid in small), ("large", lambda rid: rid not in small)):
+            lat = [o.latency for o in outs.values() if sel(o.rid) and not o.rejected and o.latency == o.latency]
+            if lat:
+                res[cls] = {"n": len(lat), "p50_ms": round(1e3 * statistics.median(lat), 3),
+                            "p99_ms": round(1e3 * sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))], 3)}
+        return res
+
     ex = S.BatchExecutor(cap, F.make_params(precision=F.FT_FP32C), device=local)
     S.serve(requests(rates[0])[:2], ex, cap, realtime=False)          # warm-up
     for rate in rates:
-        torch.cuda.synchronize()
-        _, st = S.serve(requests(rate), ex, cap, realtime=True)
-        out["rates"][str(int(rate))] = st
+        for pol in policies:
+            torch.cuda.synchronize()
+            outs, st = S.serve(requests(rate), ex, cap, realtime=True, policy=pol)
+            st["by_class"] = by_class(outs)
+            out["rates"].setdefault(str(int(rate)), {})[pol] = st
     ex.close()
     seq = S.SequentialExecutor(F.make_params(precision=F.FT_FP64), device=local)
     _, st = S.serve_sequential(requests(rates[0]), seq, realtime=True)

@@ -70,7 +70,20 @@ typedef struct {
     double sigma;        /* surface tension coefficient of Eq. csf (1.0)         */
     int32_t fit_min;     /* minimum fragments with non-zero weight (paper: 24)   */
     int32_t precision;   /* FT_FP64 (plain) or FT_FP32C (FP32 + compensation)    */
+    int32_t fit_ring;    /* PPIC fit elements: 0 (default) the clipped fragments
+                            within delta of the cell centre; k = 1..3 the whole
+                            triangles of the k-ring around the front vertex
+                            closest to the cell centre (Sec. 3.2: k = 3)       */
+    int32_t frame;       /* PPIC frame normal: FT_FRAME_FRAGMENTS (default) or
+                            FT_FRAME_VERTEX, the normal of the closest front
+                            vertex (Sec. 3.2)                                  */
 } ft_params;
+
+enum {
+    FT_FRAME_FRAGMENTS = 0, /* normalized sum of the cell's fragment area vectors */
+    FT_FRAME_VERTEX = 1     /* normalized sum of the area vectors of the triangles
+                               at the front vertex closest to the cell centre */
+};
 
 /* Workspace capacities; 0 selects a default derived from max_nt. */
 typedef struct {
@@ -132,6 +145,16 @@ int ft_status(ft_workspace* ws, void* stream, uint32_t* bits);
  * the (cell, fragment) pairs inside the support of the last PPIC call. */
 int ft_counts(ft_workspace* ws, void* stream, int64_t* out5);
 
+/* Synchronize `stream` and write the first n (at most FT_WORK_COUNTS) of:
+ * triangles T of the last binning, interfacial cells M, binned pairs P,
+ * candidate pairs used and needed, (cell, fragment) pairs in the support of
+ * the last PPIC call, pairs of the last FP32-form binning that the binary64
+ * canonical clip decided (near-degenerate pairs; 0 in the FP64 path), and the
+ * non-interfacial cells of the last CSF call's ring (host int64).  The work
+ * counts behind the per-kernel roofline figures. */
+#define FT_WORK_COUNTS 8
+int ft_work_counts(ft_workspace* ws, void* stream, int64_t* out, int32_t n);
+
 const char* ft_status_string(int code);
 
 /* Copy the sorted (cell key, triangle) pairs of the last front_bin into
@@ -167,7 +190,23 @@ int front_volume_fraction(ft_workspace* ws, double* alpha, void* stream);
  * 2017); fit data: fragments of cells within ceil(delta - 1/2) cells whose area
  * centroid lies closer than delta to the cell centre, Wendland weights, volume
  * fit normal equations solved in float64.  `cap` is the length of the output
- * arrays; M > cap sets FT_ST_CAPACITY and writes nothing.  Needs front_bin. */
+ * arrays; M > cap sets FT_ST_CAPACITY and writes nothing.  Needs front_bin.
+ * The paper's own neighbourhood and frame (p->fit_ring > 0 and/or p->frame =
+ * FT_FRAME_VERTEX; one-front workspaces only, else FT_ERR_ARG): the closest
+ * front vertex to a cell centre is the argmin of |x - x_c|^2 (each operation
+ * rounded, ties to the lowest vertex index) over the vertices of the front's
+ * triangles, x_c =
+ * origin + (i + 1/2) h per axis; its normal is the normalized sum of the area
+ * vectors (b - a) x (c - a) of its triangles; the k-ring is its triangles, then
+ * k - 1 times every triangle sharing a vertex with the ring; each ring
+ * triangle enters the fit whole, its Wendland distance taken from its centre
+ * (vertex mean), the support growing while fewer than fit_min triangles lie
+ * inside it.  The ring fit runs in float64 in both precisions (at most 512
+ * ring triangles per cell, else FT_ST_CAPACITY).  These variants read the
+ * vertices and triangles passed to the last front_bin (keep them alive and
+ * unchanged), and the first such call on a workspace, or one with a larger
+ * front, allocates device memory for the mesh incidence: make it before any
+ * stream capture. */
 int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint32_t* cell_keys,
                          double* kappa, double* normal, double* coeffs, int8_t* fit_status,
                          void* stream);
@@ -180,6 +219,28 @@ int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint
  * outputs of front_curvature_ppic for the same bins. */
 int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                     const double* normal, double* force, void* stream);
+
+/* (a4, compact) The CSF source of front_csf_force written only where it can be
+ * non-zero (the interfacial cells and their face neighbours, Sec. 3.3): per
+ * slot a cell key (keys, uint32) and its force (force, 3 float64: x, y, z).
+ * Slots [0, M) are the interfacial cells in the order of front_curvature_ppic;
+ * slots [M, *count) the other cells with a non-zero gradient, in unspecified
+ * order.  *count (device int64) receives the slot count; slots at or beyond
+ * `cap` are not written and set FT_ST_CAPACITY.  Every cell not listed has a
+ * zero force.  One-front workspaces only.  No dense array is written (or
+ * cleared): the form for callers that move the force off the device. */
+int front_csf_force_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                            const double* normal, int64_t cap, uint32_t* keys, double* force, int64_t* count,
+                            void* stream);
+
+/* (a2, compact) The volume fraction of front_volume_fraction in two parts:
+ * full_bits (device, ceil(n0*n1*n2 / 32) uint32) with bit q % 32 of word q / 32
+ * set iff alpha[q] > 1/2 (the exact value of every non-interfacial cell, which
+ * is 0 or 1), and alpha_cells (device, M float64) the values at the interfacial
+ * cells in the order of front_curvature_ppic (M > cap sets FT_ST_CAPACITY and
+ * writes no values).  alpha is the array front_volume_fraction wrote. */
+int front_alpha_pack(ft_workspace* ws, const double* alpha, int64_t cap, uint32_t* full_bits, double* alpha_cells,
+                     void* stream);
 
 /* Balanced-force face term of the surface tension (Sec. 3.3, Eq. mwi_disc: the
  * term that enters the face fluxes of the pressure-velocity coupling): on the
@@ -261,9 +322,10 @@ int front_advect_rk4(const ft_grid* g, const double* U, const double* V, const d
  * library routine.
  *
  * Arguments: grid g and front f as for front_bin (device verts/tris), method
- * parameters p (delta_max_h sets the grid margin), alpha (device, n0*n1*n2
- * float64, by key) and status (device, one uint32 that receives the FT_ST_*
- * bits of this call).  Runs on the current device and `stream`.
+ * parameters p (delta_max_h sets the grid margin; p->precision is ignored: the
+ * scratch holds float64 fragment records only, so this call always computes
+ * the plain float64 path), alpha (device, n0*n1*n2 float64, by key) and status
+ * (device, one uint32 that receives the FT_ST_* bits of this call).  Runs on the current device and `stream`.
  * Limits: n0*n1*n2 <= FT_NOALLOC_MAX_GRID_CELLS and nt <= FT_NOALLOC_MAX_TRIANGLES,
  * else FT_ERR_CAPACITY is returned before any work; more than
  * FT_NOALLOC_MAX_CANDIDATES (triangle, candidate cell) pairs or interfacial
@@ -468,6 +530,25 @@ int front_roughness_smooth(ft_rough* r, double* verts, int64_t nv, const int32_t
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all workspaces). */
 int64_t ft_launch_count(void);
+
+/* Per-kernel timing (no counterpart in the paper).  ft_trace_start creates
+ * `capacity` pairs of CUDA events on the current device and opens a trace:
+ * from then on every launch of the five steps' kernels that is not made during
+ * stream capture is bracketed by an event pair recorded on its own stream
+ * (launches beyond `capacity` are counted as dropped).  ft_trace_stop waits
+ * for the recorded events, closes the trace, frees the events and writes, per
+ * distinct kernel in order of first launch, its name (host, max_kernels rows
+ * of FT_TRACE_NAME chars, NUL-terminated), its launch count (host int64) and
+ * its summed device time in milliseconds (host double); *n_kernels (host)
+ * receives the number of rows and *dropped (host, may be NULL) the launches
+ * not traced.  FT_ERR_STATE if no trace is open (or one is already open for
+ * start); FT_ERR_CAPACITY if more than max_kernels distinct kernels ran (the
+ * first max_kernels are written).  The events add a few microseconds between
+ * launches: trace eager steps, never the timed graph replays. */
+#define FT_TRACE_NAME 48
+int ft_trace_start(int64_t capacity);
+int ft_trace_stop(int32_t max_kernels, char* names, int64_t* launches, double* total_ms, int32_t* n_kernels,
+                  int64_t* dropped);
 
 /* Throughput probe (no counterpart in the paper): runs dependent FMA chains on
  * every SM (kind 0: float64, 1: float32) and writes the achieved FLOP/s

@@ -32,7 +32,8 @@ class FtFront(C.Structure):
 
 class FtParams(C.Structure):
     _fields_ = [("delta_h", C.c_double), ("delta_growth", C.c_double), ("delta_max_h", C.c_double),
-                ("sigma", C.c_double), ("fit_min", C.c_int32), ("precision", C.c_int32)]
+                ("sigma", C.c_double), ("fit_min", C.c_int32), ("precision", C.c_int32), ("fit_ring", C.c_int32),
+                ("frame", C.c_int32)]
 
 
 class FtCapacity(C.Structure):
@@ -88,6 +89,11 @@ def lib():
                 "front_interp_velocity": (I32, [P, P, P, P, P, I64, P, P]),
                 "ft_probe_fma_rate": (I32, [I32, I32, C.POINTER(C.c_double)]),
                 "ft_launch_count": (I64, []),
+                "ft_work_counts": (I32, [P, P, P, I32]),
+                "front_csf_force_compact": (I32, [P, P, P, P, P, I64, P, P, P, P]),
+                "front_alpha_pack": (I32, [P, P, I64, P, P, P]),
+                "ft_trace_start": (I32, [I64]),
+                "ft_trace_stop": (I32, [I32, P, P, P, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
                 "ft_volume_fraction_noalloc": (I32, [P, P, P, P, P, P]),
                 "ft_batch_workspace_create": (I32, [C.POINTER(P), P, I32, C.POINTER(C.c_size_t)]),
                 "ft_batch_set": (I32, [P, I32, P, P]),
@@ -156,9 +162,16 @@ def make_grid(g) -> FtGrid:
     return s
 
 
-def make_params(delta_h=2.5, delta_growth=1.25, delta_max_h=4.0, sigma=1.0, fit_min=24, precision=FT_FP64):
+FT_FRAME_FRAGMENTS, FT_FRAME_VERTEX = 0, 1
+
+
+def make_params(delta_h=2.5, delta_growth=1.25, delta_max_h=4.0, sigma=1.0, fit_min=24, precision=FT_FP64,
+                fit_ring=0, frame=FT_FRAME_FRAGMENTS):
+    """ft_params; fit_ring = k > 0 and frame = FT_FRAME_VERTEX select the
+    paper's own PPIC neighbourhood (whole triangles of the k-ring of the
+    closest front vertex) and frame (that vertex's normal)."""
     return FtParams(float(delta_h), float(delta_growth), float(delta_max_h), float(sigma), int(fit_min),
-                    int(precision))
+                    int(precision), int(fit_ring), int(frame))
 
 
 class Workspace:
@@ -196,6 +209,13 @@ class Workspace:
         out = (C.c_int64 * 5)()
         _check(lib().ft_counts(self.handle, _stream(stream), out), "ft_counts")
         return dict(M=out[0], P=out[1], C=out[2], C_need=out[3], fit_pairs=out[4])
+
+    def work_counts(self, stream=None) -> dict:
+        """ft_work_counts: the work of the last calls (per-kernel roofline units)."""
+        out = (C.c_int64 * 8)()
+        _check(lib().ft_work_counts(self.handle, _stream(stream), C.cast(out, C.c_void_p), 8), "ft_work_counts")
+        return dict(T=out[0], M=out[1], P=out[2], C=out[3], C_need=out[4], fit_pairs=out[5], clip_f64=out[6],
+                    ring=out[7])
 
 
 class BatchWorkspace(Workspace):
@@ -303,6 +323,28 @@ def front_csf_force(ws: Workspace, params: FtParams, alpha, kappa, normal, force
     _check(lib().front_csf_force(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),
                                  _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
                                  _ptr(force, torch.float64, "force"), _stream(stream)), "front_csf_force")
+
+
+def front_csf_force_compact(ws: Workspace, params: FtParams, alpha, kappa, normal, keys, force, count, stream=None):
+    """Compact CSF force: keys (int32/uint32 view, cap), force (cap, 3) float64,
+    count (1) int64 on the device receives the number of slots."""
+    cap = keys.numel()
+    if force.numel() < 3 * cap or count.numel() < 1:
+        raise FrontError("force must hold 3 values per key slot and count one int64")
+    _check(lib().front_csf_force_compact(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),
+                                         _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
+                                         cap, _ptr(keys, torch.int32, "keys"), _ptr(force, torch.float64, "force"),
+                                         _ptr(count, torch.int64, "count"), _stream(stream)), "front_csf_force_compact")
+
+
+def front_alpha_pack(ws: Workspace, alpha, full_bits, alpha_cells, stream=None):
+    """Compact alpha: full_bits (ceil(ncells/32) int32 words), alpha_cells (cap) float64."""
+    if full_bits.numel() < (ws.grid.ncells + 31) // 32:
+        raise FrontError("full_bits must hold ceil(n0*n1*n2/32) words")
+    _check(lib().front_alpha_pack(ws.handle, _ptr(alpha, torch.float64, "alpha"), alpha_cells.numel(),
+                                  _ptr(full_bits, torch.int32, "full_bits"),
+                                  _ptr(alpha_cells, torch.float64, "alpha_cells"), _stream(stream)),
+           "front_alpha_pack")
 
 
 def front_face_force(ws: Workspace, params: FtParams, alpha, kappa, normal, fx, fy, fz, stream=None):
@@ -519,6 +561,35 @@ class Roughness:
 
 def launch_count() -> int:
     return int(lib().ft_launch_count())
+
+
+TRACE_NAME = 48  # FT_TRACE_NAME
+
+
+def trace_start(capacity: int = 65536):
+    """Open a per-kernel trace: event pairs around the library's launches
+    (eager launches only; see ft_trace_start)."""
+    _check(lib().ft_trace_start(int(capacity)), "ft_trace_start")
+
+
+def trace_stop(max_kernels: int = 64) -> dict:
+    """Close the trace; returns {kernel name: (launches, summed device ms)}
+    in order of first launch, plus the count of launches not traced under the
+    key None."""
+    names = C.create_string_buffer(max_kernels * TRACE_NAME)
+    launches = (C.c_int64 * max_kernels)()
+    ms = (C.c_double * max_kernels)()
+    nk = C.c_int32(0)
+    dropped = C.c_int64(0)
+    _check(lib().ft_trace_stop(max_kernels, C.cast(names, C.c_void_p), C.cast(launches, C.c_void_p),
+                               C.cast(ms, C.c_void_p), C.byref(nk), C.byref(dropped)), "ft_trace_stop")
+    out = {}
+    raw = names.raw
+    for k in range(nk.value):
+        nm = raw[k * TRACE_NAME:(k + 1) * TRACE_NAME].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[k]), float(ms[k]))
+    out[None] = int(dropped.value)
+    return out
 
 
 def probe_fma_rate(kind: int, device: int = 0) -> float:

@@ -32,7 +32,8 @@ bool grid_ok(const ft_grid* g) {
 bool params_ok(const ft_params* p) {
     return p && p->delta_h > 0.0 && p->delta_max_h >= p->delta_h && p->delta_max_h <= 7.0 &&
            p->delta_growth > 1.0 && p->fit_min >= 0 && (p->precision == FT_FP64 || p->precision == FT_FP32C) &&
-           isfinite(p->sigma);
+           isfinite(p->sigma) && p->fit_ring >= 0 && p->fit_ring <= 3 && (p->frame == FT_FRAME_FRAGMENTS ||
+                                                                        p->frame == FT_FRAME_VERTEX);
 }
 
 template <class T>
@@ -48,7 +49,8 @@ void release(ft_workspace* ws) {
                     ws->keys[0], ws->keys[1], ws->vals[0],  ws->vals[1],  ws->rec,     ws->cells,
                     ws->cell_off, ws->cell_cnt, ws->cell_L,   ws->cell_P,   ws->partials,
                     ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info, ws->srec, ws->srec32, ws->scen,
-                    ws->fdesc,   ws->fbase,   ws->fstatus, ws->tri_nrm, ws->planes};
+                    ws->fdesc,   ws->fbase,   ws->fstatus, ws->tri_nrm, ws->planes,
+                    ws->inc_cnt, ws->inc_off, ws->inc_cur, ws->inc_part, ws->inc, ws->cv, ws->vn};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (ws->h_fdesc) cudaFreeHost(ws->h_fdesc);
@@ -146,6 +148,7 @@ int ft_workspace_create(ft_workspace** out, const ft_grid* g, const ft_capacity*
     if (!ws) return FT_ERR_ALLOC;
     ws->device = device;
     ws->g = *g;
+    ws->clip32_ok = ft_clip32_grid_ok(*g);
     ws->ncells = (long long)g->n[0] * g->n[1] * g->n[2];
     ws->max_nt = cap->max_nt > 0 ? cap->max_nt : 1;
     ws->max_cand = cap->max_cand > 0 ? cap->max_cand : 16 * ws->max_nt + 1024;
@@ -236,8 +239,10 @@ int ft_batch_set(ft_workspace* ws, int32_t nf, const ft_batch_front* fr, void* s
     long long* vb = tb + (nf + 1);
     kb[0] = cb[0] = tb[0] = vb[0] = 0;
     long long pofs = 0;
+    ws->clip32_ok = true;
     for (int b = 0; b < nf; b++) {
         const ft_batch_front& f = fr[b];
+        ws->clip32_ok = ws->clip32_ok && ft_clip32_grid_ok(f.grid);
         ft_fdesc& d = ws->h_fdesc[b];
         d = ft_fdesc{};
         d.g = f.grid;
@@ -316,6 +321,17 @@ int ft_counts(ft_workspace* ws, void* stream, int64_t* out5) {
     return cuda_err(e);
 }
 
+int ft_work_counts(ft_workspace* ws, void* stream, int64_t* out, int32_t n) {
+    if (!ws || !out || n < 0) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    ft_counters c;
+    cudaError_t e = cudaMemcpyAsync(&c, ws->ctr, sizeof(c), cudaMemcpyDeviceToHost, as_stream(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(as_stream(stream));
+    const int64_t v[FT_WORK_COUNTS] = {c.T, c.M, c.P, c.C, c.C_need, c.fit_pairs, c.clip_f64, (int64_t)c.pad};
+    for (int i = 0; i < n && i < FT_WORK_COUNTS; i++) out[i] = v[i];
+    return cuda_err(e);
+}
+
 int ft_bin_pairs(ft_workspace* ws, int64_t cap, uint32_t* keys, int32_t* tris, void* stream) {
     if (!ws || cap < 0 || !keys || !tris) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
@@ -328,6 +344,10 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     if (f->nt > 0 && (!f->verts || !f->tris)) return FT_ERR_ARG;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     cudaStream_t s = as_stream(stream);
+    ws->f_verts = f->verts;
+    ws->f_tris = f->tris;
+    ws->f_nv = f->nv;
+    ws->f_nt = f->nt;
     cudaError_t e = ft::launch_bin(ws, f, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     if (e == cudaSuccess) e = ft::launch_gather(ws, s);
@@ -346,6 +366,7 @@ int front_volume_fraction(ft_workspace* ws, double* alpha, void* stream) {
 int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint32_t* cell_keys, double* kappa,
                          double* normal, double* coeffs, int8_t* fit_status, void* stream) {
     if (!ws || !params_ok(p) || cap < 0 || !cell_keys || !kappa || !normal || !fit_status) return FT_ERR_ARG;
+    if ((p->fit_ring > 0 || p->frame != FT_FRAME_FRAGMENTS) && ws->batch) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     const cudaError_t e = ft::launch_ppic(ws, p, cap, cell_keys, kappa, normal, coeffs, fit_status, as_stream(stream));
@@ -400,6 +421,25 @@ int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, c
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream)));
+}
+
+int front_csf_force_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                            const double* normal, int64_t cap, uint32_t* keys, double* force, int64_t* count,
+                            void* stream) {
+    if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || cap < 0 || !keys || !force || !count)
+        return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_csf_compact(ws, p, alpha, kappa, normal, cap, keys, force,
+                                           reinterpret_cast<long long*>(count), as_stream(stream)));
+}
+
+int front_alpha_pack(ft_workspace* ws, const double* alpha, int64_t cap, uint32_t* full_bits, double* alpha_cells,
+                     void* stream) {
+    if (!ws || ws->batch || !alpha || cap < 0 || !full_bits || !alpha_cells) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_alpha_pack(ws, alpha, cap, full_bits, alpha_cells, as_stream(stream)));
 }
 
 int front_interp_velocity(const ft_grid* g, const double* U, const double* V, const double* W, const double* verts,

@@ -21,6 +21,8 @@ struct ft_counters {
     long long fit_pairs;   // (cell, fragment) pairs inside the support, last PPIC
     long long work;        // next cell of the dynamically scheduled PPIC accumulation
     long long big;         // cells with more than 32 pairs (worklist of the per-cell ordering)
+    long long clip_f64;    // FP32 clip: pairs decided by the binary64 canonical clip, last front_bin
+    unsigned long long lmax2_bits;  // longest triangle edge squared (float64 bits), paper-neighbourhood fit
 };
 
 // Fragment record (cell-local, lengths in units of h, relative to the centre of
@@ -92,6 +94,8 @@ struct ft_workspace {
     bool binned;
     bool fitted;           // front_curvature_ppic ran since the last bin
     int last_precision;
+    bool sys_fp32;         // the last PPIC call left its normal equations as float pairs
+    bool clip32_ok;        // every grid keeps |coordinate| / h within the float32 clip's bounds
 
     ft_counters* ctr;
     int* idx_map;          // ncells: interfacial index or -1
@@ -121,6 +125,21 @@ struct ft_workspace {
     int sorted_buf;        // which keys/vals buffer holds the pairs in cell order
     ft_tune tune;
 
+    // the front of the last front_bin (the paper-neighbourhood fit reads it)
+    const double* f_verts;
+    const int* f_tris;
+    long long f_nv, f_nt;
+    // paper-neighbourhood fit (allocated on first use, grown with the front):
+    // vertex -> triangles incidence and per-cell closest vertex and its normal
+    long long inc_nv_cap, inc_nt_cap;
+    int* inc_cnt;          // inc_nv_cap + 1
+    int* inc_off;          // inc_nv_cap + 1
+    int* inc_cur;          // inc_nv_cap + 1
+    int* inc_part;         // inc_nv_cap / 1024 + 2
+    int* inc;              // 3 inc_nt_cap
+    int* cv;               // max_cells
+    double* vn;            // 3 max_cells
+
     // batched form (nf > 0 after ft_batch_set; 0 for a one-front workspace)
     bool batch;
     int nf, max_fronts;
@@ -147,7 +166,25 @@ cudaError_t launch_ppic_frame(ft_workspace* ws, long long cap, double* frame, cu
 
 void count_launches(int n);  // kernels launched by this library (ft_launch_count)
 
+// While a trace is open (ft_trace_start), brackets the launches made in its
+// scope on stream s with two CUDA events attributed to `name` (a string
+// literal); a no-op otherwise and during stream capture.
+class Trace {
+  public:
+    Trace(cudaStream_t s, const char* name);
+    ~Trace();
+    Trace(const Trace&) = delete;
+    Trace& operator=(const Trace&) = delete;
+
+  private:
+    long long slot_;
+    cudaStream_t s_;
+};
+
 cudaError_t launch_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, cudaStream_t s);
+// vertex -> incident triangles (CSR, ascending lists), no host synchronization
+cudaError_t launch_incidence(const int* tris, long long nt, long long nv, int* cnt, int* off, int* cur, int* inc,
+                             int* part, unsigned* status, cudaStream_t s);
 // candidate offsets of the triangles (a scan of their counts, in triangle order)
 // and the triangle index of every candidate slot; sets C_need and C
 cudaError_t launch_candidates(ft_workspace* ws, cudaStream_t s);
@@ -162,6 +199,13 @@ cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, uns
                         cudaStream_t s);
 cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha,
                        const double* kappa, const double* normal, double* force, cudaStream_t s);
+// compact outputs (one front): force at the interfacial and ring cells with their
+// keys; alpha as a bit per cell (alpha > 1/2) and the interfacial cells' values
+cudaError_t launch_csf_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                               const double* normal, long long cap, unsigned* keys, double* force, long long* count,
+                               cudaStream_t s);
+cudaError_t launch_alpha_pack(ft_workspace* ws, const double* alpha, long long cap, unsigned* bits, double* acells,
+                              cudaStream_t s);
 cudaError_t launch_interp(const ft_grid* g, const double* U, const double* V, const double* W,
                           const double* verts, long long nv, double* vel, cudaStream_t s);
 // batched form: the fronts of the workspace's table
@@ -216,6 +260,17 @@ __device__ __forceinline__ double ft_plane(double o, double h, long long idx) {
 
 // entries of a front's plane table: (n0 + 1) + (n1 + 1) + (n2 + 1)
 inline long long ft_plane_count(const ft_grid& g) { return (long long)g.n[0] + g.n[1] + g.n[2] + 3; }
+
+// The float32 clip's error bounds hold while binary64 rounding of a coordinate,
+// in cell units, stays far below float32 rounding: |coordinate| / h <= 1e8 on
+// the whole grid (unit-cube grids: n <= 1e8).
+inline bool ft_clip32_grid_ok(const ft_grid& g) {
+    for (int d = 0; d < 3; d++) {
+        const double ext = (g.origin[d] < 0 ? -g.origin[d] : g.origin[d]) + (double)g.n[d] * g.h;
+        if (!(ext / g.h <= 1e8)) return false;
+    }
+    return true;
+}
 
 // ---------------------------------------------------------------------------
 // Front lookups.  Kernels are instantiated for one of two policies:

@@ -42,10 +42,13 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells(const int* __restrict_
     }
 }
 
+// error-free sum (Knuth's two-sum), every operation rounded on its own: with
+// plain operators the compiler may fuse the caller's product into s = a + b, and
+// e would then describe a differently rounded b
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // FP32 form: float fragment terms, combined over the warp with compensated
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells32(const int* __restric
             const ft_frag32* f = rec + (vals ? vals[q] : (unsigned)q);
             const float az = f->an[2];
             float s, e;
-            two_sum(Lh, az * (f->c[2] + 0.5f), s, e);
+            two_sum(Lh, __fmul_rn(az, __fadd_rn(f->c[2], 0.5f)), s, e);
             Lh = s;
             Ll += e;
             two_sum(Ph, az, s, e);
@@ -177,14 +180,18 @@ cudaError_t alpha_with(ft_workspace* ws, const F& fr, cudaStream_t s) {
     const bool sorted = fp32 ? ws->srec32 != nullptr : ws->srec != nullptr;
     const unsigned* vals = sorted ? nullptr : ws->vals[ws->sorted_buf];
     count_launches(2);
-    if (fp32)
+    if (fp32) {
+        Trace t(s, "k_alpha_cells32");
         k_alpha_cells32<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, sorted ? ws->srec32 : ws->rec32,
                                                               ws->cell_L, ws->cell_P, ws->ctr);
-    else
+    } else {
+        Trace t(s, "k_alpha_cells");
         k_alpha_cells<<<ws->sm_count * 8, kThreads, 0, s>>>(ws->cell_off, vals, sorted ? ws->srec : ws->rec,
                                                             ws->cell_L, ws->cell_P, ws->ctr);
+    }
     // the column parity of a closed front is an integer up to rounding of the fragment terms
     const double closure_tol = fp32 ? 1e-5 : 1e-9;
+    Trace t(s, "k_alpha_fill");
     k_alpha_fill<F><<<ws->sm_count * ws->tune.fill_bps, kThreads, 0, s>>>(fr, ws->idx_map, ws->cell_L, ws->cell_P,
                                                                           closure_tol, ws->ctr);
     return cudaGetLastError();

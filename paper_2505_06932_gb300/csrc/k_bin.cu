@@ -91,7 +91,10 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
     // first the index map entries of the previous binning's cells go back to -1
     const long long M_prev = ctr->M;
     for (long long m = t; m < M_prev; m += (long long)gridDim.x * kThreads) idx_map[cells[m]] = -1;
-    if (t == 0) ctr->T = T;
+    if (t == 0) {
+        ctr->T = T;
+        ctr->clip_f64 = 0;
+    }
     if (t >= T) return;
     const int b = fr.by_tri(t);
     const ft_fdesc& D = fr.desc(b);
@@ -615,6 +618,311 @@ __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 clip of the FP32-compensated form.
+//
+// The decision whether a (triangle, cell) pair is kept stays the binary64
+// canonical predicate above; this kernel reaches the same decision without
+// binary64 crossing points wherever a float32 computation certifies it:
+//  * the triangle's own vertices are classified against the six planes exactly
+//    (order-preserving integer keys of the binary64 values, as the predicate
+//    does);
+//  * the clip runs in float32 in cell units (x - X_i)/h, the polygons in
+//    per-lane shared-memory buffers, each vertex carrying a bound on its
+//    distance to the vertex of the exact-arithmetic clip (rounding of the
+//    conversions and of every crossing, amplified by the conditioning of the
+//    crossing, as derived below);
+//  * a crossing vertex whose distance to a later plane does not exceed its
+//    bound, a crossing edge too close to parallel to its plane, a stage with
+//    more than two crossings or a polygon that outgrows its buffer makes the
+//    pair undecided.
+// When every classification is certain, the binary64 clip classifies every
+// vertex the same way (its own errors are far below the float bounds, so both
+// polygons have the same vertex sequence): a polygon that dies is rejected,
+// and one whose float area exceeds its bound by far (and that does not lie
+// within its bounds of an upper face) is kept.  Everything else -- undecided
+// pairs, small areas, fragments near an upper face -- runs the binary64
+// canonical clip (the plane-edge sign tests and crossings of near-degenerate
+// vertices stay float64), so the kept set, the cell list and the parity fill are
+// those of the float64 path bit for bit.  Kept fragments' float32 records come
+// from the float32 polygon (or, for pairs decided in float64, from the binary64
+// polygon).
+// ---------------------------------------------------------------------------
+
+constexpr int kClip32Threads = 128;
+constexpr int kClip32Warps = kClip32Threads / 32;
+constexpr int kPV = 10;          // float polygon capacity (the exact clip of a triangle has at most 9)
+constexpr float kEps = 3e-7f;    // relative bound of a few float32 roundings (2^-24 = 6e-8 each)
+// A kept fragment whose vertex bound exceeds this (crossings of edges nearly
+// parallel to their plane) takes its record from the binary64 polygon, so that
+// float32 records stay within about 1e-7 cells of the exact fragment's.
+constexpr float kEmaxRecord = 3e-4f;
+
+// Float32 fragment moments of the polygon buf[0..n) (cell units, lower corner
+// at the origin; the x, y, z of each float4), as frag_moments32 computes them
+// from a binary64 polygon.  tn: the triangle's normal direction.
+__device__ void frag_moments_f(const float4 (*buf)[32], int lane, int n, const float tn[3], ft_frag32& f,
+                               float& absum) {
+    float an[3] = {0.f, 0.f, 0.f}, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0}, As = 0.f;
+    absum = 0.f;
+    const float4 p0 = buf[0][lane];
+    const float4 p1 = buf[1][lane];
+    float e1[3] = {p1.x - p0.x, p1.y - p0.y, p1.z - p0.z}, e2[3];
+    for (int m = 1; m + 1 < n; m++) {
+        const float4 pm = buf[m + 1][lane];
+        e2[0] = pm.x - p0.x;
+        e2[1] = pm.y - p0.y;
+        e2[2] = pm.z - p0.z;
+        const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+        const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+        const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+        absum += fmaxf(fabsf(e1[0]), fmaxf(fabsf(e1[1]), fabsf(e1[2]))) *
+                 fmaxf(fabsf(e2[0]), fmaxf(fabsf(e2[1]), fabsf(e2[2])));
+        an[0] += 0.5f * cr0;
+        an[1] += 0.5f * cr1;
+        an[2] += 0.5f * cr2;
+        const float a = 0.5f * (cr0 * tn[0] + cr1 * tn[1] + cr2 * tn[2]);
+        As += a;
+        const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+        const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
+        for (int d = 0; d < 3; d++) m1[d] += a3 * s[d];
+        m2[0] += a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+        m2[1] += a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+        m2[2] += a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+        m2[3] += a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+        m2[4] += a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+        m2[5] += a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
+        for (int d = 0; d < 3; d++) e1[d] = e2[d];
+    }
+    const float q0[3] = {p0.x - 0.5f, p0.y - 0.5f, p0.z - 0.5f};
+    if (As > 0.f) {
+        const float ia = 1.f / As;
+        const float c[3] = {m1[0] * ia, m1[1] * ia, m1[2] * ia};
+        f.k[0] = m2[0] * ia - c[0] * c[0];
+        f.k[1] = m2[1] * ia - c[1] * c[1];
+        f.k[2] = m2[2] * ia - c[2] * c[2];
+        f.k[3] = m2[3] * ia - c[0] * c[1];
+        f.k[4] = m2[4] * ia - c[0] * c[2];
+        f.k[5] = m2[5] * ia - c[1] * c[2];
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d] + c[d];
+    } else {
+        for (int d = 0; d < 6; d++) f.k[d] = 0.f;
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d];
+    }
+    for (int d = 0; d < 3; d++) f.an[d] = an[d];
+}
+
+__device__ __forceinline__ float comp(const float4& v, int ax) { return ax == 0 ? v.x : (ax == 1 ? v.y : v.z); }
+
+// Outcome of the float32 clip of one pair.
+enum : int { kUndecided = 0, kRejected = 1, kKept = 2 };
+
+// The float32 clip of triangle (tv, in cell units) against the cell [0, top]:
+// exact flags of the triangle's vertices (bit st: inside for stage st), the
+// polygon left in bufs[*res] (n vertices).  Vertex w: < 0 for a triangle
+// vertex (-(1 + flags)), else the distance bound of a crossing vertex.
+__device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const float top[3], float4 (*b0)[32],
+                        float4 (*b1)[32], int lane, int& n_out, float4 (**res)[32], float& emax) {
+    float4(*src)[32] = b0;
+    float4(*dst)[32] = b1;
+    for (int c = 0; c < 3; c++) src[c][lane] = make_float4(tv[c][0], tv[c][1], tv[c][2], -(float)(1 + vflags[c]));
+    int n = 3;
+    for (int st = 0; st < 6; st++) {
+        const int ax = st >> 1;
+        const bool ge = (st & 1) == 0;
+        const float pl = ge ? 0.f : top[ax];
+        const float epl = kEps * fabsf(pl);
+        // inside flags of the polygon's vertices
+        unsigned in = 0;
+        for (int i = 0; i < n; i++) {
+            const float4 v = src[i][lane];
+            bool ins;
+            if (v.w < 0.f) {
+                ins = (((unsigned)(-v.w) - 1u) >> st) & 1u;
+            } else {
+                const float x = comp(v, ax);
+                const float d = x - pl;
+                const float m = 1.01f * (v.w + epl + kEps * (fabsf(x) + fabsf(pl))) + 1e-30f;
+                if (!(fabsf(d) > m)) return kUndecided;
+                ins = ge ? (d > 0.f) : (d < 0.f);
+            }
+            if (ins) in |= 1u << i;
+        }
+        if (in == 0u) return kRejected;  // the polygon dies at this stage (every vertex outside)
+        const unsigned prevf = (in << 1 | in >> (n - 1)) & ((1u << n) - 1u);
+        const unsigned cross = in ^ prevf;
+        if (__popc(cross) > 2) return kUndecided;
+        int m = 0;
+        for (int i = 0; i < n; i++) {
+            const float4 b_cur = src[i][lane];
+            if ((cross >> i) & 1u) {
+                // interpolate from the edge's end nearer to the plane (the smaller
+                // step t (b - a) keeps the rounding of q small); a is that end
+                float4 a = src[i == 0 ? n - 1 : i - 1][lane];
+                float4 b = b_cur;
+                if (fabsf(pl - comp(a, ax)) > fabsf(pl - comp(b, ax))) {
+                    const float4 tmp = a;
+                    a = b;
+                    b = tmp;
+                }
+                const float ea = a.w < 0.f ? kEps * fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))) : a.w;
+                const float eb = b.w < 0.f ? kEps * fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z))) : b.w;
+                const float aa = comp(a, ax), ba = comp(b, ax);
+                const float D = ba - aa;
+                const float den = fabsf(D) - 1.01f * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)));
+                if (!(den > 0.f)) return kUndecided;
+                const float t = __fdiv_rn(pl - aa, D);
+                const float tt = fmaxf(fabsf(t), 1.f);
+                // |t - t*| <= (errors of the numerator + |t*| errors of D) / |D*| + the division's rounding
+                const float dt = ((ea + epl + kEps * (fabsf(aa) + fabsf(pl))) +
+                                  tt * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)))) / den + 4.f * kEps * tt;
+                const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+                const float L = fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz)));
+                const float amax = fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z)));
+                const float bmax = fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z)));
+                float4 q;
+                q.x = (ax == 0) ? pl : __fadd_rn(a.x, __fmul_rn(t, dx));
+                q.y = (ax == 1) ? pl : __fadd_rn(a.y, __fmul_rn(t, dy));
+                q.z = (ax == 2) ? pl : __fadd_rn(a.z, __fmul_rn(t, dz));
+                // |q - q*| <= max(ea, eb) + |b - a| |t - t*| + the roundings of q
+                q.w = 1.01f * (fmaxf(ea, eb) + L * dt + 2.f * kEps * tt * (amax + bmax + 1.f));
+                if (m >= kPV) return kUndecided;
+                dst[m++][lane] = q;
+            }
+            if ((in >> i) & 1u) {
+                if (m >= kPV) return kUndecided;
+                dst[m++][lane] = b_cur;
+            }
+        }
+        if (m < 3) return kRejected;
+        n = m;
+        float4(*tmp)[32] = src;
+        src = dst;
+        dst = tmp;
+    }
+    float e = 0.f;
+    for (int i = 0; i < n; i++) {
+        const float4 v = src[i][lane];
+        e = fmaxf(e, v.w < 0.f ? kEps * fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))) : v.w);
+    }
+    // a fragment within its bounds of an upper face may lie in it exactly in binary64
+    for (int ax = 0; ax < 3; ax++) {
+        bool all = true;
+        for (int i = 0; i < n && all; i++) {
+            const float4 v = src[i][lane];
+            const float x = comp(v, ax);
+            const float ev = v.w < 0.f ? kEps * fabsf(x) : v.w;
+            all = fabsf(x - top[ax]) <= 2.02f * (ev + kEps * (fabsf(x) + 2.f * fabsf(top[ax]))) + 1e-30f;
+        }
+        if (all) return kUndecided;
+    }
+    n_out = n;
+    *res = src;
+    emax = e;
+    return kKept;
+}
+
+template <class F>
+__global__ void __launch_bounds__(kClip32Threads) k_clip32(F fr, const int* __restrict__ cand_tri,
+                                                           const int* __restrict__ tri_off,
+                                                           const int* __restrict__ tri_box,
+                                                           const double* __restrict__ tri_nrm,
+                                                           unsigned* __restrict__ keys, unsigned* __restrict__ ranks,
+                                                           int* __restrict__ cell_cnt, ft_frag32* __restrict__ rec32,
+                                                           ft_counters* ctr) {
+    __shared__ float4 s_poly[kClip32Warps][2][kPV][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long C = ctr->C;
+    const long long nthreads = (long long)gridDim.x * kClip32Threads;
+    unsigned long long n_f64 = 0;
+    for (long long c = (long long)blockIdx.x * kClip32Threads + threadIdx.x; c < C; c += nthreads) {
+        const int t = cand_tri[c];
+        const int l = (int)(c - tri_off[t]);
+        const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
+        const int4 bb0 = bx[0], bb1 = bx[1];
+        const int e1 = bb1.x, e2 = bb1.y;
+        const int b = bb1.z;
+        const int idx[3] = {bb0.x + l / (e1 * e2), bb0.y + (l / e2) % e1, bb0.z + l % e2};
+        const ft_fdesc& D = fr.desc(b);
+        const ft_grid g = D.g;
+        const Planes P(D);
+        const long long tl = t - fr.tri_base(b);
+        double v[3][3];
+        for (int a = 0; a < 3; a++) {
+            const long long vi = D.tris[3 * tl + a];
+            for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
+        }
+        // exact flags of the triangle's vertices and their cell-unit coordinates
+        const float ih = d2f_rn(D.inv_h);
+        float tv[3][3], top[3];
+        unsigned vflags[3] = {0u, 0u, 0u};
+        unsigned on_top = 7u;  // axes whose upper plane holds all three vertices
+        for (int ax = 0; ax < 3; ax++) {
+            const double lo = P.at(ax, idx[ax]), hi = P.at(ax, idx[ax] + 1);
+            const long long klo = okey(lo), khi = okey(hi);
+            top[ax] = d2f_rn(__dmul_rn(__dsub_rn(hi, lo), D.inv_h));
+            for (int a = 0; a < 3; a++) {
+                const long long k = okey(v[a][ax]);
+                if (k >= klo) vflags[a] |= 1u << (2 * ax);
+                if (k <= khi) vflags[a] |= 1u << (2 * ax + 1);
+                if (k != khi) on_top &= ~(1u << ax);
+                tv[a][ax] = d2f_rn(__dmul_rn(__dsub_rn(v[a][ax], lo), D.inv_h));
+            }
+        }
+        int n = 0;
+        float4(*poly)[32] = nullptr;
+        float emax = 0.f;
+        int verdict = on_top ? kRejected : clip_f32(tv, vflags, top, s_poly[w][0], s_poly[w][1], lane, n, &poly,
+                                                    emax);
+        unsigned key = FT_SENTINEL;
+        ft_frag32 f;
+        const double2* tnp = reinterpret_cast<const double2*>(tri_nrm + 4 * (long long)t);
+        const double2 tn01 = tnp[0], tn2 = tnp[1];
+        const float tn[3] = {d2f_rn(tn01.x), d2f_rn(tn01.y), d2f_rn(tn2.x)};
+        if (verdict == kKept && emax > kEmaxRecord) verdict = kUndecided;  // ill-conditioned: record in float64
+        if (verdict == kKept) {
+            float absum;
+            frag_moments_f(poly, lane, n, tn, f, absum);
+            // Moving the vertices p_i by d_i changes the area vector by
+            // (1/2) sum_i d_i x (p_i+1 - p_i-1) + O(d^2): at most emax S2 + n emax^2
+            // per component, S2 = sum_i |p_i+1 - p_i-1| (max norm, widened by the
+            // vertex errors); the fan sum adds its own rounding (a few ulps of
+            // its terms)
+            float S2 = 0.f;
+            for (int i = 0; i < n; i++) {
+                const float4 pp = poly[i + 1 < n ? i + 1 : 0][lane], pm = poly[i > 0 ? i - 1 : n - 1][lane];
+                S2 += fmaxf(fabsf(pp.x - pm.x), fmaxf(fabsf(pp.y - pm.y), fabsf(pp.z - pm.z)));
+            }
+            const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
+            const float bound = 1.01f * (emax * (S2 + 2.f * (float)n * emax) + (float)n * emax * emax) +
+                                32.f * kEps * absum + 1e-30f;
+            if (!(a > bound)) verdict = kUndecided;
+        }
+        if (verdict == kUndecided) {
+            // the binary64 canonical clip decides (and gives the record)
+            n_f64++;
+            double wide[32][3];
+            const int nc = canon_stages_wide(v, g, idx, wide);
+            verdict = kRejected;
+            if (nc >= 3) {
+                float q0[3];
+                for (int d = 0; d < 3; d++) q0[d] = d2f_rn(wide[0][d] - P.at(d, idx[d])) * ih - 0.5f;
+                frag_moments32(wide, nc, q0, tn, ih, f);
+                const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
+                if ((a > 1e-4f) || canon_area_nonzero(wide, nc)) verdict = kKept;
+            }
+        }
+        if (verdict == kKept) {
+            rec32[c] = f;
+            key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
+        }
+        keys[c] = key;
+        if (key != FT_SENTINEL) ranks[c] = (unsigned)atomicAdd(&cell_cnt[key], 1);
+    }
+    n_f64 = (unsigned long long)ft_warp_sum_ll((long long)n_f64);
+    if (lane == 0 && n_f64) atomicAdd((unsigned long long*)&ctr->clip_f64, n_f64);
+}
+
 }  // namespace
 
 namespace ft {
@@ -625,8 +933,11 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
     const unsigned nb = (unsigned)((T + kThreads - 1) / kThreads);
     // (always launched: it also clears the index map of the previous binning, and sets T)
     count_launches(1);
-    k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_box,
-                                                    ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
+    {
+        Trace t(s, "k_tri_setup");
+        k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_box,
+                                                        ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
+    }
     // candidate ranges in triangle order, so that slot order is triangle order
     cudaError_t e = launch_candidates(ws, s);
     if (e != cudaSuccess) return e;
@@ -634,6 +945,21 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     ws->last_precision = fp32 ? FT_FP32C : FT_FP64;
+    if (fp32 && ws->clip32_ok) {
+        // a grid-stride loop: at most the blocks that are resident at once (the
+        // polygon buffers limit them), so that no block waits for a second wave
+        static int occ = 0;
+        if (occ == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_clip32<F>, kClip32Threads, 0) !=
+                             cudaSuccess || occ < 1))
+            occ = 1;
+        const int bps = min(occ, 2 * ws->tune.clip_bps);
+        Trace t(s, "k_clip32");
+        k_clip32<F><<<ws->sm_count * bps, kClip32Threads, 0, s>>>(
+            fr, ws->cand_tri, ws->tri_off, ws->tri_box, ws->tri_nrm, ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec32,
+            ws->ctr);
+        return cudaGetLastError();
+    }
+    Trace t(s, "k_clip");
     k_clip<F><<<ws->sm_count * ws->tune.clip_bps, kClipThreads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
                                                                     ws->tri_nrm, ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec, ws->rec32,
                                                                     ws->cen32, fp32 ? 1 : 0, ws->ctr);

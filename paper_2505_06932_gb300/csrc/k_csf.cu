@@ -23,6 +23,16 @@ namespace {
 
 constexpr int kThreads = 128;  // one block per column; 128 and 256 cell columns fill it
 
+// Compact force output (one front): the interfacial cells first (slot m = the
+// cell's row of front_curvature_ppic), then the ring cells; keys == NULL
+// selects the dense force arrays of the front descriptor.
+struct CsfOut {
+    unsigned* keys;
+    double* f;        // 3 per slot (x, y, z)
+    long long cap;
+    long long* count;
+};
+
 // zero the force arrays of every front (the batched form).  A block clears a
 // tile of 8 x 128 consecutive cells of the batch-wide cell index (one front
 // search per tile, then a step to the next front where the tile crosses one),
@@ -58,7 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_csf_cells(F fr, double sigma, cons
                                                         const int* __restrict__ idx_map,
                                                         const double* __restrict__ kappa,
                                                         unsigned* __restrict__ ring, unsigned* __restrict__ nring,
-                                                        long long ring_cap, ft_counters* ctr) {
+                                                        long long ring_cap, ft_counters* ctr, CsfOut out) {
     const long long M = ctr->M;
     for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < 7 * M; w += (long long)gridDim.x * kThreads) {
         const long long m = w / 7;
@@ -85,10 +95,21 @@ __global__ void __launch_bounds__(kThreads) k_csf_cells(F fr, double sigma, cons
             }
             const double ih2 = 0.5 * D.inv_h;
             const double f = sigma * kappa[m];
-            double* __restrict__ force = D.force;
-            force[key] = f * ((a[0] - a[1]) * ih2);
-            force[NC + key] = f * ((a[2] - a[3]) * ih2);
-            force[2 * NC + key] = f * ((a[4] - a[5]) * ih2);
+            const double fx = f * ((a[0] - a[1]) * ih2), fy = f * ((a[2] - a[3]) * ih2),
+                         fz = f * ((a[4] - a[5]) * ih2);
+            if (out.keys) {
+                if (m < out.cap) {
+                    out.keys[m] = key;
+                    out.f[3 * m] = fx;
+                    out.f[3 * m + 1] = fy;
+                    out.f[3 * m + 2] = fz;
+                }
+            } else {
+                double* __restrict__ force = D.force;
+                force[key] = fx;
+                force[NC + key] = fy;
+                force[2 * NC + key] = fz;
+            }
             continue;
         }
         const int e = task - 1, ax = e >> 1, sg = (e & 1) ? -1 : 1;
@@ -121,8 +142,13 @@ template <class F>
 __global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int* __restrict__ idx_map,
                                                   const double* __restrict__ kappa, const double* __restrict__ normal,
                                                   const unsigned* __restrict__ ring, const unsigned* __restrict__ nring,
-                                                  long long ring_cap) {
+                                                  long long ring_cap, ft_counters* ctr, CsfOut out) {
     const long long nr = min((long long)*nring, ring_cap);
+    if (out.keys && blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long total = ctr->M + nr;
+        *out.count = total;
+        if (total > out.cap) ft_flag(ctr, FT_ST_CAPACITY);
+    }
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
          r += (long long)gridDim.x * blockDim.x) {
         const long long gkey = ring[r];
@@ -174,11 +200,47 @@ __global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int*
         const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
         const double kp = (den > 0.0) ? num / den : (cnt ? ks / cnt : 0.0);
         const double f = sigma * kp;
-        double* __restrict__ force = D.force;
-        force[key] = f * gx;
-        force[NC + key] = f * gy;
-        force[2 * NC + key] = f * gz;
+        if (out.keys) {
+            const long long slot = ctr->M + r;
+            if (slot < out.cap) {
+                out.keys[slot] = ukey;
+                out.f[3 * slot] = f * gx;
+                out.f[3 * slot + 1] = f * gy;
+                out.f[3 * slot + 2] = f * gz;
+            }
+        } else {
+            double* __restrict__ force = D.force;
+            force[key] = f * gx;
+            force[NC + key] = f * gy;
+            force[2 * NC + key] = f * gz;
+        }
     }
+}
+
+// Compact volume fraction (one front): bit q % 32 of word q / 32 is set when
+// alpha[q] > 1/2 (a warp per 32 consecutive cells, one ballot), and the values
+// at the interfacial cells in cell order.
+__global__ void __launch_bounds__(256) k_alpha_pack(const double* __restrict__ alpha, long long ncells,
+                                                    const unsigned* __restrict__ cells, long long cap,
+                                                    unsigned* __restrict__ bits, double* __restrict__ acells,
+                                                    ft_counters* ctr) {
+    const int lane = threadIdx.x & 31;
+    const long long nwords = (ncells + 31) / 32;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = gw; w < nwords; w += nw) {
+        const long long q = 32 * w + lane;
+        const bool full = q < ncells && alpha[q] > 0.5;
+        const unsigned b = __ballot_sync(0xffffffffu, full);
+        if (lane == 0) bits[w] = b;
+    }
+    const long long M = ctr->M;
+    if (M > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ft_flag(ctr, FT_ST_CAPACITY);
+        return;
+    }
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x)
+        acells[m] = alpha[cells[m]];
 }
 
 // Cell curvature of the surface-tension terms (Sec. 3.3): the cell's own kappa
@@ -285,22 +347,46 @@ namespace ft {
 
 template <class F>
 cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const double* kappa, const double* normal,
-                     cudaStream_t s) {
+                     cudaStream_t s, CsfOut out = CsfOut{nullptr, nullptr, 0, nullptr}) {
     // the ring list lives in the sort's spare key buffer (max_cand entries)
     unsigned* ring = ws->keys[ws->sorted_buf ^ 1];
     unsigned* nring = &ws->ctr->pad;
     cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
-    if constexpr (std::is_same<F, FrontsOne>::value) {
+    if (out.keys) {
+        // compact output: no dense array to clear
+    } else if constexpr (std::is_same<F, FrontsOne>::value) {
+        Trace t(s, "force clear (memset)");
         cudaMemsetAsync(fr.d0.force, 0, 3 * sizeof(double) * (size_t)fr.ncells, s);
     } else {
         count_launches(1);
+        Trace t(s, "k_zero_force");
         k_zero_force<F><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr);
     }
     count_launches(2);
-    k_csf_cells<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, p->sigma, ws->cells, ws->idx_map, kappa, ring, nring,
-                                                         ws->max_cand, ws->ctr);
+    {
+        Trace t(s, "k_csf_cells");
+        k_csf_cells<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, p->sigma, ws->cells, ws->idx_map, kappa, ring, nring,
+                                                             ws->max_cand, ws->ctr, out);
+    }
+    Trace t(s, "k_csf_ring");
     k_csf_ring<F><<<ws->sm_count * 4, 128, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, normal, ring, nring,
-                                                   ws->max_cand);
+                                                   ws->max_cand, ws->ctr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csf_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                               const double* normal, long long cap, unsigned* keys, double* force, long long* count,
+                               cudaStream_t s) {
+    FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
+    fr.d0.alpha = const_cast<double*>(alpha);  // read only here
+    return csf_with(ws, fr, p, kappa, normal, s, CsfOut{keys, force, cap, count});
+}
+
+cudaError_t launch_alpha_pack(ft_workspace* ws, const double* alpha, long long cap, unsigned* bits, double* acells,
+                              cudaStream_t s) {
+    count_launches(1);
+    Trace t(s, "k_alpha_pack");
+    k_alpha_pack<<<ws->sm_count * 8, 256, 0, s>>>(alpha, ws->ncells, ws->cells, cap, bits, acells, ws->ctr);
     return cudaGetLastError();
 }
 

@@ -159,6 +159,7 @@ cudaError_t launch_interp(const ft_grid* g, const double* U, const double* V, co
     fr.ncols = 0;
     const unsigned nb = (unsigned)((nv + kThreads - 1) / kThreads);
     count_launches(1);
+    Trace t(s, "k_interp");
     k_interp<FrontsOne><<<nb, kThreads, 0, s>>>(fr, nv);
     return cudaGetLastError();
 }
@@ -200,6 +201,7 @@ cudaError_t launch_interp_batch(ft_workspace* ws, cudaStream_t s) {
     if (nv <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((nv + kThreads - 1) / kThreads);
     count_launches(1);
+    Trace t(s, "k_interp");
     k_interp<FrontsMany><<<nb, kThreads, 0, s>>>(ft_many(ws), nv);
     return cudaGetLastError();
 }

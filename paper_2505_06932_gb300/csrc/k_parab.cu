@@ -202,7 +202,7 @@ static cudaError_t parab_with(ft_workspace* ws, const F& fr, const double* coeff
                               double* kappa, double* normal, int8_t* status, cudaStream_t s) {
     ParabOut out{nullptr, area, kappa, normal, status};
     count_launches(1);
-    k_parab_ppic<F><<<ws->sm_count * 16, kThreads, 0, s>>>(fr, ws->sys, ws->last_precision == FT_FP32C ? 1 : 0,
+    k_parab_ppic<F><<<ws->sm_count * 16, kThreads, 0, s>>>(fr, ws->sys, ws->sys_fp32 ? 1 : 0,
                                                           ws->cells, coeffs, cap, ws->ctr, rule(), out);
     return cudaGetLastError();
 }
@@ -221,7 +221,7 @@ cudaError_t launch_parab_ppic_batch(ft_workspace* ws, const double* coeffs, long
 
 cudaError_t launch_ppic_frame(ft_workspace* ws, long long cap, double* frame, cudaStream_t s) {
     count_launches(1);
-    k_ppic_frame<<<ws->sm_count * 4, kThreads, 0, s>>>(ws->sys, ws->last_precision == FT_FP32C ? 1 : 0, cap,
+    k_ppic_frame<<<ws->sm_count * 4, kThreads, 0, s>>>(ws->sys, ws->sys_fp32 ? 1 : 0, cap,
                                                        ws->ctr, frame);
     return cudaGetLastError();
 }

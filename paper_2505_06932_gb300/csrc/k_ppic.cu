@@ -27,6 +27,8 @@
 //    curvature of z = P(x, y) at the origin and the outputs.
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "frame.cuh"
 #include "ft_internal.cuh"
 
@@ -92,11 +94,12 @@ template <> struct Rec<float> {
     }
 };
 
-// error-free sum (Knuth's two-sum)
+// error-free sum (Knuth's two-sum), each operation rounded on its own (no
+// contraction with the surrounding code)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // Transposed warp reduction of 32 values per lane: each round a lane keeps one
@@ -204,17 +207,13 @@ __device__ __forceinline__ void accumulate(const Rec<T>& rec, const float4 qe, T
                                           const T n[3], const T t1[3], const T t2[3], const T c11[6],
                                           const T c12[6], const T c22[6], T z0, Acc<T>& acc, int& count);
 
-template <>
-__device__ __forceinline__ void accumulate<double>(const Rec<double>& rec, const float4 qe, double delta,
-                                                   double inv_delta, const double n[3], const double t1[3],
-                                                   const double t2[3], const double c11[6], const double c12[6],
-                                                   const double c22[6], double z0, Acc<double>& acc, int& count) {
-    const unsigned ri = __float_as_uint(qe.w);
-    const int dcode = __float_as_int(qe.x);
-    double an[3], c[3], k[6];
-    rec.load(ri, an, c, k);
-    const double p[3] = {c[0] + (double)(((dcode >> 8) & 15) - 8), c[1] + (double)(((dcode >> 4) & 15) - 8),
-                         c[2] + (double)((dcode & 15) - 8)};
+// One fit element (area vector an, centroid p relative to the cell centre and
+// central second moment per unit area k, lengths in cells) into the float64
+// normal equations, if its centroid lies inside the support.
+__device__ __forceinline__ void accum_d(const double an[3], const double p[3], const double k[6], double delta,
+                                        double inv_delta, const double n[3], const double t1[3], const double t2[3],
+                                        const double c11[6], const double c12[6], const double c22[6], double z0,
+                                        Acc<double>& acc, int& count) {
     const double d2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
     const double dist = sqrt(d2);
     if (!(dist < delta)) return;
@@ -244,6 +243,20 @@ __device__ __forceinline__ void accumulate<double>(const Rec<double>& rec, const
         for (int j = i; j < 6; j++) acc.S[r++] += uv * v[j];
         acc.B[i] += uv * z;
     }
+}
+
+template <>
+__device__ __forceinline__ void accumulate<double>(const Rec<double>& rec, const float4 qe, double delta,
+                                                   double inv_delta, const double n[3], const double t1[3],
+                                                   const double t2[3], const double c11[6], const double c12[6],
+                                                   const double c22[6], double z0, Acc<double>& acc, int& count) {
+    const unsigned ri = __float_as_uint(qe.w);
+    const int dcode = __float_as_int(qe.x);
+    double an[3], c[3], k[6];
+    rec.load(ri, an, c, k);
+    const double p[3] = {c[0] + (double)(((dcode >> 8) & 15) - 8), c[1] + (double)(((dcode >> 4) & 15) - 8),
+                         c[2] + (double)((dcode & 15) - 8)};
+    accum_d(an, p, k, delta, inv_delta, n, t1, t2, c11, c12, c22, z0, acc, count);
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -315,7 +328,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                                                        const int* __restrict__ cell_off, Rec<T> rec,
                                                        const float4* __restrict__ cen,
                                                        const int* __restrict__ idx_map, ft_counters* ctr,
-                                                       ft_cellsys* __restrict__ sys, int* __restrict__ fit_info) {
+                                                       ft_cellsys* __restrict__ sys, int* __restrict__ fit_info,
+                                                       const double* __restrict__ n_over) {
     __shared__ float4 s_q[kWarps][kQueue];
     const long long M = ctr->M;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -380,7 +394,22 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
             AC[2] += __shfl_xor_sync(0xffffffffu, AC[2], o);
         }
         T nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-        if (nn < (T)1e-3 * sa) {
+        bool given = false;
+        if (n_over) {
+            // the frame normal given per cell (the closest vertex's normal);
+            // a zero vector keeps the fragment normal
+            const double o0 = n_over[3 * m], o1 = n_over[3 * m + 1], o2 = n_over[3 * m + 2];
+            if (o0 != 0.0 || o1 != 0.0 || o2 != 0.0) {
+                N[0] = (T)o0;
+                N[1] = (T)o1;
+                N[2] = (T)o2;
+                nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+                given = true;
+            } else {
+                st |= FT_FIT_NORMAL;
+            }
+        }
+        if (!given && nn < (T)1e-3 * sa) {
             // opposing sheets: normal of the largest fragment (first on ties)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -754,9 +783,392 @@ __global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cel
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The paper's own fit neighbourhood and frame (Sec. 3.2): the front vertex
+// closest to the cell centre, its normal as the frame normal, and the whole
+// triangles of the k-ring of triangles around it as the fit elements (the
+// Wendland distance taken from each triangle's centre), in float64.
+//  * k_edge_max -- the longest triangle edge of the front (squared), which
+//    bounds how far the closest vertex can be from an interfacial cell centre;
+//  * k_closest -- one warp per interfacial cell: the closest vertex among the
+//    vertices of the triangles binned within that distance (|x - x_c|^2
+//    rounded operation by operation, ties to the lowest index) and its normal,
+//    the normalized sum of its triangles' area vectors in ascending order;
+//  * k_ppic_ring -- one warp per cell: the k-ring (sorted, unique) in shared
+//    memory, then the volume fit over its triangles as k_ppic_acc does over
+//    fragments.
+// ---------------------------------------------------------------------------
+constexpr int kRingCap = 512;    // triangles of one k-ring
+constexpr int kRingCand = 1024;  // incident-triangle entries gathered for one ring step
+
+struct RingArgs {
+    const double* verts;
+    const int* tris;
+    const int* inc_off;  // nv + 1
+    const int* inc;      // 3 nt: triangles of each vertex, ascending
+    long long nv;
+    int ring;            // k (0: not used)
+    int frame_vertex;
+};
+
+__global__ void k_edge_max(const double* __restrict__ verts, const int* __restrict__ tris, long long nt,
+                           unsigned long long* out) {
+    double best = 0.0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (long long)gridDim.x * blockDim.x) {
+        const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        const int e[3][2] = {{a, b}, {b, c}, {c, a}};
+        for (int q = 0; q < 3; q++) {
+            double l2 = 0.0;
+            for (int d = 0; d < 3; d++) {
+                const double x = verts[3 * (long long)e[q][1] + d] - verts[3 * (long long)e[q][0] + d];
+                l2 += x * x;
+            }
+            best = fmax(best, l2);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(best));
+}
+
+__device__ __forceinline__ double cell_centre(double o, double h, int i) {
+    return __dadd_rn(o, __dmul_rn((double)i + 0.5, h));
+}
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_closest(F fr, RingArgs R, const unsigned* __restrict__ cells,
+                                                      const int* __restrict__ cell_off,
+                                                      const unsigned* __restrict__ slot_of,
+                                                      const int* __restrict__ cand_tri,
+                                                      const int* __restrict__ idx_map, const ft_counters* ctr,
+                                                      const unsigned long long* lmax2_bits, int* __restrict__ cv,
+                                                      double* __restrict__ vn) {
+    const long long M = ctr->M;
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * kWarps;
+    const ft_grid& G = fr.desc(0).g;
+    const double h = G.h;
+    // the closest vertex lies within D = (sqrt 3 / 2) h + L_max / sqrt 3 of the
+    // centre of an interfacial cell (a front point lies in the cell; every point
+    // of a triangle is within L_max / sqrt 3 of one of its vertices), so one of
+    // its triangles is binned in a cell within r_v cells
+    const double D = 0.8660254037844387 * h + sqrt(__longlong_as_double((long long)*lmax2_bits)) * 0.5773502691896258;
+    const int rv = (int)floor(D / h + 0.5) + 1;
+    for (long long m = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); m < M; m += nw) {
+        const unsigned key = cells[m];
+        const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+        const int ck = (int)(key % (unsigned)n2), cj = (int)((key / (unsigned)n2) % (unsigned)n1),
+                  ci = (int)(key / ((unsigned)n2 * (unsigned)n1));
+        const double xc[3] = {cell_centre(G.origin[0], h, ci), cell_centre(G.origin[1], h, cj),
+                              cell_centre(G.origin[2], h, ck)};
+        double bd = INFINITY;
+        int bv = 0x7fffffff;
+        const int side = 2 * rv + 1;
+        const long long nb = (long long)side * side * side;
+        for (long long l = lane; l < nb; l += 32) {
+            const int di = (int)(l / (side * side)) - rv, dj = (int)((l / side) % side) - rv, dk = (int)(l % side) - rv;
+            const int ii = ci + di, jj = cj + dj, kk = ck + dk;
+            if (ii < 0 || jj < 0 || kk < 0 || ii >= n0 || jj >= n1 || kk >= n2) continue;
+            const int m2 = idx_map[((long long)ii * n1 + jj) * n2 + kk];
+            if (m2 < 0) continue;
+            for (int q = cell_off[m2]; q < cell_off[m2 + 1]; q++) {
+                const int t = cand_tri[slot_of[q]];
+                for (int c = 0; c < 3; c++) {
+                    const int v = R.tris[3 * (long long)t + c];
+                    const double dx = __dsub_rn(R.verts[3 * (long long)v], xc[0]);
+                    const double dy = __dsub_rn(R.verts[3 * (long long)v + 1], xc[1]);
+                    const double dz = __dsub_rn(R.verts[3 * (long long)v + 2], xc[2]);
+                    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    if (d2 < bd || (d2 == bd && v < bv)) {
+                        bd = d2;
+                        bv = v;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            if (od < bd || (od == bd && ov < bv)) {
+                bd = od;
+                bv = ov;
+            }
+        }
+        if (lane == 0) {
+            cv[m] = bv;
+            // its normal: the sum of its triangles' area vectors, ascending order
+            double s[3] = {0.0, 0.0, 0.0};
+            if (bv >= 0 && bv < R.nv) {
+                for (int q = R.inc_off[bv]; q < R.inc_off[bv + 1]; q++) {
+                    const long long t = R.inc[q];
+                    const double* a = R.verts + 3 * (long long)R.tris[3 * t];
+                    const double* b = R.verts + 3 * (long long)R.tris[3 * t + 1];
+                    const double* c = R.verts + 3 * (long long)R.tris[3 * t + 2];
+                    const double e1[3] = {__dsub_rn(b[0], a[0]), __dsub_rn(b[1], a[1]), __dsub_rn(b[2], a[2])};
+                    const double e2[3] = {__dsub_rn(c[0], a[0]), __dsub_rn(c[1], a[1]), __dsub_rn(c[2], a[2])};
+                    s[0] = __dadd_rn(s[0], __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1])));
+                    s[1] = __dadd_rn(s[1], __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2])));
+                    s[2] = __dadd_rn(s[2], __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0])));
+                }
+            }
+            const double l = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+            for (int d = 0; d < 3; d++) vn[3 * m + d] = (l > 0.0) ? s[d] / l : 0.0;
+        }
+    }
+}
+
+// warp bitonic sort of s[0..n) ascending (n a power of two, <= kRingCand)
+__device__ void warp_sort(int* s, int n) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < n; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const int a = s[i], b = s[p];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        s[i] = b;
+                        s[p] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+template <class F, typename TR>
+__global__ void __launch_bounds__(kThreads) k_ppic_ring(PpicArgs A, F fr, RingArgs R, const unsigned* __restrict__ cells,
+                                                        const int* __restrict__ cell_off, Rec<TR> rec,
+                                                        ft_counters* ctr, const int* __restrict__ cv,
+                                                        const double* __restrict__ vn, ft_cellsys* __restrict__ sys,
+                                                        int* __restrict__ fit_info, unsigned* status) {
+    __shared__ int s_ring[kWarps][kRingCap];
+    __shared__ int s_cand[kWarps][kRingCand];
+    const long long M = ctr->M;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* ring = s_ring[wid];
+    int* cand = s_cand[wid];
+    const long long nw = (long long)gridDim.x * kWarps;
+    const ft_grid& G = fr.desc(0).g;
+    const double h = G.h, inv_h = fr.desc(0).inv_h;
+    unsigned long long pairs_total = 0;
+    for (long long m = (long long)blockIdx.x * kWarps + wid; m < M; m += nw) {
+        const unsigned key = cells[m];
+        const int n1 = G.n[1], n2 = G.n[2];
+        const int ck = (int)(key % (unsigned)n2), cj = (int)((key / (unsigned)n2) % (unsigned)n1),
+                  ci = (int)(key / ((unsigned)n2 * (unsigned)n1));
+        const double xc[3] = {cell_centre(G.origin[0], h, ci), cell_centre(G.origin[1], h, cj),
+                              cell_centre(G.origin[2], h, ck)};
+        int st = 0;
+        // frame normal: the closest vertex's (frame_vertex) or the cell's fragments'
+        double n[3];
+        bool given = false;
+        if (R.frame_vertex && (vn[3 * m] != 0.0 || vn[3 * m + 1] != 0.0 || vn[3 * m + 2] != 0.0)) {
+            for (int d = 0; d < 3; d++) n[d] = vn[3 * m + d];
+            given = true;
+        }
+        if (!given) {
+            if (R.frame_vertex) st |= FT_FIT_NORMAL;
+            double N[3] = {0, 0, 0}, sa = 0.0, best = -1.0;
+            int bestq = 0x7fffffff;
+            for (int q = cell_off[m] + lane; q < cell_off[m + 1]; q += 32) {
+                TR at[3];
+                rec.load_an(q, at);
+                const double an[3] = {(double)at[0], (double)at[1], (double)at[2]};
+                for (int d = 0; d < 3; d++) N[d] += an[d];
+                const double a = sqrt(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
+                sa += a;
+                if (a > best) {
+                    best = a;
+                    bestq = q;
+                }
+            }
+            for (int d = 0; d < 3; d++) N[d] = ft_warp_sum(N[d]);
+            sa = ft_warp_sum(sa);
+            double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+            if (nn < 1e-3 * sa) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oq = __shfl_xor_sync(0xffffffffu, bestq, o);
+                    if (ob > best || (ob == best && oq < bestq)) {
+                        best = ob;
+                        bestq = oq;
+                    }
+                }
+                TR at[3];
+                rec.load_an(bestq, at);
+                for (int d = 0; d < 3; d++) N[d] = (double)at[d];
+                nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+                st |= FT_FIT_NORMAL;
+            }
+            for (int d = 0; d < 3; d++) n[d] = N[d] / nn;
+        }
+        double t1[3], t2[3], c11[6], c12[6], c22[6];
+        basis<double>(n, t1, t2);
+        qform<double>(t1, t1, c11);
+        qform<double>(t1, t2, c12);
+        qform<double>(t2, t2, c22);
+        // the k-ring of the closest vertex: its triangles, then k - 1 times every
+        // triangle sharing a vertex with the ring (sorted, duplicates removed)
+        const int v0 = cv[m];
+        int nr = 0;
+        bool over = false;
+        if (v0 >= 0 && v0 < R.nv) {
+            const int b0 = R.inc_off[v0];
+            nr = R.inc_off[v0 + 1] - b0;
+            if (nr > kRingCap) {
+                over = true;
+                nr = kRingCap;
+            }
+            for (int q = lane; q < nr; q += 32) ring[q] = R.inc[b0 + q];
+            __syncwarp();
+            for (int r = 2; r <= R.ring; r++) {
+                // gather, per ring triangle and corner, that vertex's triangles
+                int nc = 0;
+                for (int q0 = 0; q0 < 3 * nr; q0 += 32) {
+                    const int q = q0 + lane;
+                    int u = -1, deg = 0;
+                    if (q < 3 * nr) {
+                        u = R.tris[3 * (long long)ring[q / 3] + q % 3];
+                        deg = R.inc_off[u + 1] - R.inc_off[u];
+                    }
+                    int incl = deg;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int base = nc + incl - deg;
+                    for (int e = 0; e < deg; e++)
+                        if (base + e < kRingCand) cand[base + e] = R.inc[R.inc_off[u] + e];
+                    nc += __shfl_sync(0xffffffffu, incl, 31);
+                }
+                if (nc > kRingCand) {
+                    over = true;
+                    nc = kRingCand;
+                }
+                int np2 = 32;
+                while (np2 < nc) np2 <<= 1;
+                for (int q = nc + lane; q < np2; q += 32) cand[q] = 0x7fffffff;
+                __syncwarp();
+                warp_sort(cand, np2);
+                // unique, in order, into the ring
+                int nu = 0;
+                for (int q0 = 0; q0 < nc; q0 += 32) {
+                    const int q = q0 + lane;
+                    const bool head = q < nc && (q == 0 || cand[q] != cand[q - 1]);
+                    const unsigned bal = __ballot_sync(0xffffffffu, head);
+                    const int pos = nu + __popc(bal & ((1u << lane) - 1u));
+                    if (head && pos < kRingCap) ring[pos] = cand[q];
+                    nu += __popc(bal);
+                }
+                if (nu > kRingCap) {
+                    over = true;
+                    nu = kRingCap;
+                }
+                nr = nu;
+                __syncwarp();
+            }
+        }
+        if (over && lane == 0) atomicOr(status, FT_ST_CAPACITY);
+        // 2-4. normal equations over the ring's triangles; the support grows
+        // while fewer than fit_min of them lie inside it
+        double delta = A.delta_h;
+        Acc<double> acc;
+        int ctot;
+        for (;;) {
+            acc.zero();
+            int count = 0;
+            const double inv_delta = 1.0 / delta;
+            for (int q = lane; q < nr; q += 32) {
+                const long long t = ring[q];
+                double p[3][3];
+                for (int c = 0; c < 3; c++)
+                    for (int d = 0; d < 3; d++)
+                        p[c][d] = (R.verts[3 * (long long)R.tris[3 * t + c] + d] - xc[d]) * inv_h;
+                double cen[3], an[3], k[6], e1[3], e2[3], r0[3], r1[3], r2[3];
+                for (int d = 0; d < 3; d++) {
+                    cen[d] = (p[0][d] + p[1][d] + p[2][d]) / 3.0;
+                    e1[d] = p[1][d] - p[0][d];
+                    e2[d] = p[2][d] - p[0][d];
+                    r0[d] = p[0][d] - cen[d];
+                    r1[d] = p[1][d] - cen[d];
+                    r2[d] = p[2][d] - cen[d];
+                }
+                an[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+                an[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+                an[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+                // central second moment per unit area of a triangle: (1/12) sum_i r_i r_i^T
+                const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+                for (int r = 0; r < 6; r++)
+                    k[r] = (r0[ia[r]] * r0[ib[r]] + r1[ia[r]] * r1[ib[r]] + r2[ia[r]] * r2[ib[r]]) * (1.0 / 12.0);
+                accum_d(an, cen, k, delta, inv_delta, n, t1, t2, c11, c12, c22, 0.0, acc, count);
+            }
+            ctot = ft_warp_sum_i(count);
+            if (ctot >= A.fit_min || delta >= A.delta_max_h) break;
+            delta = fmin(delta * A.delta_growth, A.delta_max_h);
+            st |= FT_FIT_GROWN;
+        }
+        pairs_total += (unsigned long long)ctot;
+        double S[21], B[6];
+        acc.get(S, B);
+        double v[32];
+#pragma unroll
+        for (int r = 0; r < 21; r++) v[r] = S[r];
+#pragma unroll
+        for (int r = 0; r < 6; r++) v[21 + r] = B[r];
+#pragma unroll
+        for (int r = 27; r < 32; r++) v[r] = 0.0;
+        const double tot = warp_transpose_sum(v);
+        ft_cellsys* out = sys + m;
+        if (lane < 27) out->v[lane] = tot;
+        if (lane == 0) {
+            for (int r = 0; r < 3; r++) out->v[27 + r] = n[r];
+            out->v[30] = 0.0;
+            fit_info[2 * m] = ctot;
+            fit_info[2 * m + 1] = st;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && pairs_total) atomicAdd((unsigned long long*)&ctr->fit_pairs, pairs_total);
+}
 }  // namespace
 
 namespace ft {
+
+template <class T>
+cudaError_t grow(T** p, long long n) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+// Buffers of the paper-neighbourhood fit, allocated on first use and grown
+// with the front (vertex incidence) or sized by the cell capacity.
+cudaError_t ring_buffers(ft_workspace* ws) {
+    cudaError_t e = cudaSuccess;
+    if (ws->f_nv > ws->inc_nv_cap || !ws->inc_off) {
+        const long long nv = ws->f_nv > 1 ? ws->f_nv : 1;
+        e = e ? e : grow(&ws->inc_cnt, nv + 1);
+        e = e ? e : grow(&ws->inc_off, nv + 1);
+        e = e ? e : grow(&ws->inc_cur, nv + 1);
+        e = e ? e : grow(&ws->inc_part, nv / 1024 + 2);
+        if (e == cudaSuccess) ws->inc_nv_cap = nv;
+    }
+    if (ws->f_nt > ws->inc_nt_cap || !ws->inc) {
+        const long long nt = ws->f_nt > 1 ? ws->f_nt : 1;
+        e = e ? e : grow(&ws->inc, 3 * nt);
+        if (e == cudaSuccess) ws->inc_nt_cap = nt;
+    }
+    if (!ws->cv) e = e ? e : grow(&ws->cv, ws->max_cells);
+    if (!ws->vn) e = e ? e : grow(&ws->vn, 3 * ws->max_cells);
+    return e;
+}
 
 template <class F>
 cudaError_t ppic_with(ft_workspace* ws, const F& fr, const ft_params* p, long long cap, unsigned* cell_keys,
@@ -770,23 +1182,77 @@ cudaError_t ppic_with(ft_workspace* ws, const F& fr, const ft_params* p, long lo
     // fit_pairs and the work counter are adjacent: one reset
     static_assert(offsetof(ft_counters, work) == offsetof(ft_counters, fit_pairs) + sizeof(long long), "layout");
     cudaMemsetAsync(&ws->ctr->fit_pairs, 0, 2 * sizeof(long long), s);
-    const bool fp32 = ws->last_precision == FT_FP32C;
-    count_launches(2);
+    bool fp32 = ws->last_precision == FT_FP32C;
     const unsigned nb = (unsigned)(ws->sm_count * ws->tune.ppic_bps);
+    const double* n_over = nullptr;
+    if constexpr (std::is_same<F, FrontsOne>::value) {
+        if (p->fit_ring > 0 || p->frame == FT_FRAME_VERTEX) {
+            // the paper's own neighbourhood and frame: mesh incidence, the
+            // longest edge, then the closest vertex of every cell and its normal
+            cudaError_t e = ring_buffers(ws);
+            if (e != cudaSuccess) return e;
+            RingArgs R{ws->f_verts, ws->f_tris, ws->inc_off, ws->inc, ws->f_nv, p->fit_ring,
+                       p->frame == FT_FRAME_VERTEX ? 1 : 0};
+            e = launch_incidence(ws->f_tris, ws->f_nt, ws->f_nv, ws->inc_cnt, ws->inc_off, ws->inc_cur, ws->inc,
+                                 ws->inc_part, &ws->ctr->status, s);
+            if (e != cudaSuccess) return e;
+            cudaMemsetAsync(&ws->ctr->lmax2_bits, 0, sizeof(unsigned long long), s);
+            count_launches(2);
+            {
+                Trace t(s, "k_edge_max");
+                k_edge_max<<<ws->sm_count * 2, 256, 0, s>>>(ws->f_verts, ws->f_tris, ws->f_nt, &ws->ctr->lmax2_bits);
+            }
+            {
+                Trace t(s, "k_closest");
+                k_closest<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, R, ws->cells, ws->cell_off,
+                                                                    ws->vals[ws->sorted_buf], ws->cand_tri,
+                                                                    ws->idx_map, ws->ctr, &ws->ctr->lmax2_bits,
+                                                                    ws->cv, ws->vn);
+            }
+            if (p->fit_ring > 0) {
+                // the ring fit (float64 in both forms) writes float64 normal equations
+                count_launches(2);
+                {
+                    Trace t(s, "k_ppic_ring");
+                    // (the records only give the fragment normal when the frame is the fragments')
+                    if (fp32)
+                        k_ppic_ring<F, float><<<ws->sm_count * 4, kThreads, 0, s>>>(
+                            A, fr, R, ws->cells, ws->cell_off, Rec<float>{ws->srec32}, ws->ctr, ws->cv, ws->vn,
+                            ws->sys, ws->fit_info, &ws->ctr->status);
+                    else
+                        k_ppic_ring<F, double><<<ws->sm_count * 4, kThreads, 0, s>>>(
+                            A, fr, R, ws->cells, ws->cell_off, Rec<double>{ws->srec}, ws->ctr, ws->cv, ws->vn,
+                            ws->sys, ws->fit_info, &ws->ctr->status);
+                }
+                ws->sys_fp32 = false;
+                Trace t(s, "k_ppic_solve");
+                k_ppic_solve<F><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(
+                    fr, ws->sys, ws->fit_info, ws->cells, 0, cap, ws->ctr, cell_keys, kappa, normal, coeffs,
+                    fit_status);
+                return cudaGetLastError();
+            }
+            n_over = ws->vn;
+        }
+    }
+    count_launches(2);
     // fragments are read in sorted pair order (front_bin gathers them)
     if (fp32) {
         Rec<float> r{ws->srec32};
+        Trace t(s, "k_ppic_acc<float>");
         if (ws->tune.ppic_min_blocks >= 6)
             k_ppic_acc<float, F, 6><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
-                                                           ws->ctr, ws->sys, ws->fit_info);
+                                                           ws->ctr, ws->sys, ws->fit_info, n_over);
         else
             k_ppic_acc<float, F, 4><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
-                                                           ws->ctr, ws->sys, ws->fit_info);
+                                                           ws->ctr, ws->sys, ws->fit_info, n_over);
     } else {
         Rec<double> r{ws->srec};
+        Trace t(s, "k_ppic_acc<double>");
         k_ppic_acc<double, F, 3><<<nb, kThreads, 0, s>>>(A, fr, ws->cells, ws->cell_off, r, ws->scen, ws->idx_map,
-                                                        ws->ctr, ws->sys, ws->fit_info);
+                                                        ws->ctr, ws->sys, ws->fit_info, n_over);
     }
+    ws->sys_fp32 = fp32;
+    Trace t(s, "k_ppic_solve");
     k_ppic_solve<F><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(fr, ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, cap,
                                                     ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
     return cudaGetLastError();

@@ -588,3 +588,30 @@ int front_roughness_smooth(ft_rough* r, double* verts, int64_t nv, const int32_t
 }
 
 }  // extern "C"
+
+namespace ft {
+
+// The triangles incident to each vertex of a front (CSR: off (nv + 1), inc
+// (3 nt), each list ascending), built on `s` without a host synchronization;
+// cnt, cur (nv + 1) and part (nv / 1024 + 2) are scratch.  Indices out of range
+// are skipped and flagged in *status.
+cudaError_t launch_incidence(const int* tris, long long nt, long long nv, int* cnt, int* off, int* cur, int* inc,
+                             int* part, unsigned* status, cudaStream_t s) {
+    if (nv <= 0) return cudaSuccess;
+    const unsigned nbs = (unsigned)((nv + kScanBlock - 1) / kScanBlock);
+    cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nv + 1), s);
+    count_launches(6);
+    {
+        Trace t(s, "k_count (incidence)");
+        k_count<<<blocks(nt > 0 ? nt : 1), kT, 0, s>>>(tris, nt, nv, cnt, status);
+    }
+    k_scan_blocks<<<nbs, kScanBlock, 0, s>>>(cnt, nv, part);
+    k_scan_part<<<1, 32, 0, s>>>(part, (int)nbs);
+    k_scan_down<<<nbs, kScanBlock, 0, s>>>(cnt, nv, part, off);
+    cudaMemcpyAsync(cur, off, sizeof(int) * (size_t)nv, cudaMemcpyDeviceToDevice, s);
+    k_fill<<<blocks(nt > 0 ? nt : 1), kT, 0, s>>>(tris, nt, nv, cur, inc);
+    k_sort_lists<<<blocks(nv), kT, 0, s>>>(off, nv, inc);
+    return cudaGetLastError();
+}
+
+}  // namespace ft

@@ -448,6 +448,7 @@ namespace ft {
 cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s) {
     if (!ws->srec || !ws->srec32 || !ws->scen) return cudaSuccess;  // a workspace without sorted copies
     count_launches(1);
+    Trace t(s, "k_gather");
     k_gather<<<ws->sm_count * 4, kB, 0, s>>>(ws->vals[ws->sorted_buf], ws->rec, ws->rec32, ws->srec, ws->srec32,
                                              ws->scen, ws->last_precision == FT_FP32C ? 1 : 0, ws->ctr);
     return cudaGetLastError();
@@ -465,7 +466,11 @@ cudaError_t launch_candidates(ft_workspace* ws, cudaStream_t s) {
     long long* part = reinterpret_cast<long long*>(ws->partials);
     LoadCounts ld{ws->tri_cnt};
     count_launches(2);
-    k_scan_reduce<<<G, kB, 0, s>>>(ld, &ws->ctr->T, part);
+    {
+        Trace t(s, "k_scan_reduce");
+        k_scan_reduce<<<G, kB, 0, s>>>(ld, &ws->ctr->T, part);
+    }
+    Trace t(s, "k_scan_expand");
     k_scan_expand<<<G, kB, 0, s>>>(ws->tri_cnt, &ws->ctr->T, part, ws->tri_off, ws->max_cand, ws->cand_tri, ws->ctr);
     return cudaGetLastError();
 }
@@ -476,18 +481,33 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
     const int G = 4 * ws->tune.seg_blocks;
     long long* part = reinterpret_cast<long long*>(ws->partials);
     count_launches(5);
-    k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
-    k_cnt_down<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
-                                ws->ctr);
-    k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->cell_cnt, ws->keys[1], ws->vals[1],
-                                            ws->max_cells, ws->ctr);
+    {
+        Trace t(s, "k_cnt_reduce");
+        k_cnt_reduce<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part);
+    }
+    {
+        Trace t(s, "k_cnt_down");
+        k_cnt_down<<<G, kB, 0, s>>>(ws->cell_cnt, nkeys, part, ws->cells, ws->cell_off, ws->idx_map, ws->max_cells,
+                                    ws->ctr);
+    }
+    {
+        Trace t(s, "k_place");
+        k_place<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[0], ws->vals[0], ws->cell_cnt, ws->keys[1], ws->vals[1],
+                                                ws->max_cells, ws->ctr);
+    }
     // large cells: the ranks in vals[0] are spent once placed, so that buffer is
     // their merge scratch; cell_L (filled only by the volume fraction) holds the worklist
     int* big = reinterpret_cast<int*>(ws->cell_L);
-    k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->cells, ws->vals[1], ws->cell_cnt, big,
-                                                 ws->max_cells, ws->ctr);
-    k_cell_order_big<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], big, ws->max_cells,
-                                                     ws->ctr);
+    {
+        Trace t(s, "k_cell_order");
+        k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->cells, ws->vals[1], ws->cell_cnt, big,
+                                                     ws->max_cells, ws->ctr);
+    }
+    {
+        Trace t(s, "k_cell_order_big");
+        k_cell_order_big<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], big, ws->max_cells,
+                                                         ws->ctr);
+    }
     ws->sorted_buf = 1;
     return cudaGetLastError();
 }

@@ -91,10 +91,21 @@ class Capacity:
 
 
 class Scheduler:
-    """FIFO admission by device footprint and batch capacities (host only)."""
+    """Admission by device footprint and batch capacities (host only).
 
-    def __init__(self, cap: Capacity):
+    policy "fifo": arrived requests are admitted in arrival order and the queue
+    head blocks the ones behind it.  policy "backfill": a request behind a head
+    that does not fit yet is admitted if it fits, so that small requests do not
+    wait behind a large one for memory it cannot use yet; once the head has
+    waited `starve_s` seconds nothing passes it any more, so that it is not
+    starved."""
+
+    def __init__(self, cap: Capacity, policy: str = "fifo", starve_s: float = 1.0):
+        if policy not in ("fifo", "backfill"):
+            raise ValueError(f"unknown admission policy {policy!r}")
         self.cap = cap
+        self.policy = policy
+        self.starve_s = starve_s
         self.pending = collections.deque()
         self.active = []           # requests being served
         self.left = {}             # rid -> steps left
@@ -124,23 +135,38 @@ class Scheduler:
                 and u["cells"] + need["cells"] <= c.max_grid_cells and u["nt"] + need["nt"] <= c.max_nt
                 and u["cand"] + need["cand"] <= c.max_cand)
 
+    def _take(self, req, now):
+        need = self._need[req.rid]
+        for k in self.used:
+            self.used[k] += need[k]
+        self.peak_bytes = max(self.peak_bytes, self.used["bytes"])
+        self.active.append(req)
+        self.left[req.rid] = req.steps
+        self.outcomes[req.rid].admitted = now
+
     def admit(self, now: float):
-        """Requests that have arrived by `now` and fit, in arrival order (the
-        queue head blocks the ones behind it)."""
+        """Requests that have arrived by `now` and fit, in arrival order; under
+        "fifo" the queue head blocks the ones behind it, under "backfill" the
+        ones behind it that fit pass it (until it has waited starve_s)."""
         out = []
         while self.pending and self.pending[0].arrival <= now:
             req = self.pending[0]
-            need = self._need[req.rid]
-            if not self._fits(need):
+            if not self._fits(self._need[req.rid]):
                 break
             self.pending.popleft()
-            for k in self.used:
-                self.used[k] += need[k]
-            self.peak_bytes = max(self.peak_bytes, self.used["bytes"])
-            self.active.append(req)
-            self.left[req.rid] = req.steps
-            self.outcomes[req.rid].admitted = now
+            self._take(req, now)
             out.append(req)
+        if self.policy == "backfill" and self.pending and self.pending[0].arrival <= now:
+            head = self.pending[0]
+            if now - head.arrival < self.starve_s:
+                keep = collections.deque([head])
+                for req in list(self.pending)[1:]:
+                    if req.arrival <= now and self._fits(self._need[req.rid]):
+                        self._take(req, now)
+                        out.append(req)
+                    else:
+                        keep.append(req)
+                self.pending = keep
         return out
 
     def step_done(self, now: float, cells: dict, status: dict):
@@ -273,11 +299,12 @@ class BatchExecutor:
 
 
 def serve(requests, executor, cap: Capacity, realtime: bool = True, keep_results: bool = False,
-          clock=time.perf_counter):
+          clock=time.perf_counter, policy: str = "fifo", starve_s: float = 1.0):
     """Serve the requests (arrival times relative to the start) and return
     (outcomes by rid, stats).  With realtime=False arrivals are taken as
-    already due whenever the server is idle (a closed-loop replay)."""
-    sch = Scheduler(cap)
+    already due whenever the server is idle (a closed-loop replay).  policy and
+    starve_s: the admission rule of Scheduler."""
+    sch = Scheduler(cap, policy=policy, starve_s=starve_s)
     for r in sorted(requests, key=lambda r: (r.arrival, r.rid)):
         sch.submit(r)
     t0 = clock()

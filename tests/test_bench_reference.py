@@ -29,5 +29,15 @@ def test_cpu_baseline_whole_passes():
     fronts = bench.workload()
     cells, times = bench.oracle_pass(fronts[1])
     assert cells > 10000 and set(times) == set(bench.PHASES)
-    cb = bench.cpu_baseline(fronts, budget_s=0.0)  # one pass over both fronts
+    cb = bench.cpu_baseline(fronts, budget_s=0.0, one_core_budget_s=0.0)  # one pass over both fronts
     assert cb["value"] > 0 and cb["kind"] == "oracle" and cb["sample"].startswith("1 pass of")
+    assert "one_core" not in cb
+
+
+def test_cpu_baseline_one_core():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2505_06932_gb300 import inputs as I
+    cb = bench.cpu_baseline([I.laplace_droplet_32(1)], budget_s=0.0, one_core_budget_s=0.1)
+    one = cb["one_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["kind"] == "oracle"

@@ -175,7 +175,8 @@ def test_support_growth_parity():
     compare(gpu, orc)
 
 
-@pytest.mark.parametrize("name", ["droplet_32", "sh_droplet_40", "bubble_40", "box_rotated", "general_grid"])
+@pytest.mark.parametrize("name", ["droplet_32", "sh_droplet_40", "bubble_40", "box_in_grid_planes", "box_rotated",
+                                  "general_grid"])
 def test_fp32c_small_cases(name, tmp_path):
     """FP32-compensated form: identical bins and parity fill, |d alpha| <= 1e-6,
     |d kappa| <= 1e-4 max(|kappa|, 1) against the FP64 oracle."""

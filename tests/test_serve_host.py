@@ -120,3 +120,40 @@ def test_idle_server_waits_for_arrivals():
     assert outs[1].admitted >= 5.0
     assert outs[1].latency < 1.0
     assert len(ex.history) == 4
+
+
+def _head_of_line_stream():
+    """A large resident request, then a second large one that cannot fit until
+    the first ends, then small requests arriving behind it."""
+    big0 = _req(0, 0.0, 20, N=64)
+    big1 = _req(1, 0.001, 5, N=64)
+    smalls = [_req(2 + i, 0.002 + 0.001 * i, 2) for i in range(4)]
+    budget = S.footprint(big0) + 4 * S.footprint(smalls[0])   # big1 fits only once big0 is gone
+    return [big0, big1] + smalls, _cap(budget)
+
+
+def test_fifo_head_of_line_blocks_small_requests():
+    clock = FakeClock()
+    reqs, cap = _head_of_line_stream()
+    outs, _ = S.serve(reqs, FakeExecutor(clock), cap, realtime=False, clock=clock)
+    # every small request waits until the second large one is admitted
+    for r in reqs[2:]:
+        assert outs[r.rid].admitted >= outs[1].admitted
+
+
+def test_backfill_admits_small_requests_past_a_blocked_head_without_starving_it():
+    clock = FakeClock()
+    reqs, cap = _head_of_line_stream()
+    outs, stats = S.serve(reqs, FakeExecutor(clock), cap, realtime=False, clock=clock, policy="backfill",
+                          starve_s=10.0)
+    assert stats["completed"] == len(reqs)
+    for r in reqs[2:]:
+        assert outs[r.rid].admitted < outs[1].admitted      # they passed the blocked head
+        assert outs[r.rid].finished < outs[0].finished      # and finished while the first large one ran
+    assert outs[1].admitted >= outs[0].finished             # the head still got in
+    # with a zero starvation limit nothing passes the head: the FIFO order
+    clock2 = FakeClock()
+    outs2, _ = S.serve(reqs, FakeExecutor(clock2), cap, realtime=False, clock=clock2, policy="backfill",
+                       starve_s=0.0)
+    for r in reqs[2:]:
+        assert outs2[r.rid].admitted >= outs2[1].admitted
