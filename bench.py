@@ -190,6 +190,9 @@ def parse():
                     help="e2e leg: the fronts on concurrent compute streams, or one after the other so that "
                          "the first front's outputs go down while the second is computed (eager, or that step "
                          "captured in one CUDA graph)")
+    ap.add_argument("--e2e-outputs", choices=("compact", "dense"), default="compact",
+                    help="e2e leg: download alpha and the force in the compact form (front_alpha_pack, "
+                         "front_csf_force_compact: the same information) or as dense arrays")
     ap.add_argument("--no-fork", dest="fork", action="store_false",
                     help="graph steps with each front's five calls in order on one stream, instead of the DAG "
                          "per front (volume fraction beside the PPIC fit, the interpolation beside everything)")
@@ -636,14 +639,41 @@ def run_ours(a):
         hf = [torch.from_numpy(f).pin_memory() for f in w["faces"]]
         hin.append((hv, ht, hf))
     hout = []
+    dcomp = []
     h2d = d2h = 0
+    compact = a.e2e_outputs == "compact" and a.e2e_mode != "concurrent"  # (concurrent: dense only)
     for (hv, ht, hf), fc, c in zip(hin, fcs, counts):
         M = c["M"]
-        outs = dict(alpha=torch.empty(fc.alpha.shape, dtype=torch.float64).pin_memory(),
-                    force=torch.empty(fc.force.shape, dtype=torch.float64).pin_memory(),
-                    kappa=torch.empty(M, dtype=torch.float64).pin_memory(),
+        outs = dict(kappa=torch.empty(M, dtype=torch.float64).pin_memory(),
                     normal=torch.empty((M, 3), dtype=torch.float64).pin_memory(),
                     vel=torch.empty((hv.shape[0], 3), dtype=torch.float64).pin_memory())
+        if compact:
+            # compact outputs (the same information): alpha as one bit per cell plus
+            # the interfacial values, the force at its non-zero cells with their keys;
+            # the slot count of the force is measured once and copied with margin
+            N = fc.grid.ncells
+            d = dict(bits=torch.empty((N + 31) // 32, dtype=torch.int32, device=dev),
+                     acells=torch.empty(M, dtype=torch.float64, device=dev),
+                     count=torch.zeros(1, dtype=torch.int64, device=dev))
+            cap0 = 16 * M + 1024
+            d["keys"] = torch.empty(cap0, dtype=torch.int32, device=dev)
+            d["force"] = torch.empty((cap0, 3), dtype=torch.float64, device=dev)
+            F.front_csf_force_compact(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, d["keys"], d["force"], d["count"])
+            torch.cuda.synchronize()
+            if fc.ws.status():
+                raise RuntimeError("compact force: device status")
+            cap = int(d["count"].item()) + 64 + int(d["count"].item()) // 10
+            d["cap"] = cap
+            dcomp.append(d)
+            outs.update(bits=torch.empty_like(d["bits"], device="cpu").pin_memory(),
+                        acells=torch.empty(M, dtype=torch.float64).pin_memory(),
+                        count=torch.empty(1, dtype=torch.int64).pin_memory(),
+                        keys=torch.empty(cap, dtype=torch.int32).pin_memory(),
+                        force=torch.empty((cap, 3), dtype=torch.float64).pin_memory())
+        else:
+            dcomp.append(None)
+            outs.update(alpha=torch.empty(fc.alpha.shape, dtype=torch.float64).pin_memory(),
+                        force=torch.empty(fc.force.shape, dtype=torch.float64).pin_memory())
         hout.append(outs)
         h2d += hv.numel() * 8 + ht.numel() * 4 + sum(f.numel() * 8 for f in hf)
         d2h += sum(o.numel() * o.element_size() for o in outs.values())
@@ -682,7 +712,7 @@ def run_ours(a):
                     for dst, src in zip(fa, hf):
                         dst.copy_(src, non_blocking=True)
                     ev.record(up)
-            for f, ((v, t, fa), fc, o, c, dn) in enumerate(zip(dfr, fcs, hout, counts, dns)):
+            for f, ((v, t, fa), fc, o, c, dn, d) in enumerate(zip(dfr, fcs, hout, counts, dns, dcomp)):
                 # each front as the DAG of the graph step: alpha beside the PPIC fit,
                 # the interpolation beside both (once the faces are up)
                 alpha_ready, force_ready, vel_ready = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
@@ -693,6 +723,8 @@ def run_ours(a):
                 sa.wait_stream(sd)
                 with torch.cuda.stream(sa):
                     F.front_volume_fraction(fc.ws, fc.alpha)
+                    if d is not None:
+                        F.front_alpha_pack(fc.ws, fc.alpha, d["bits"], d["acells"])
                     alpha_ready.record(sa)
                 with torch.cuda.stream(si):
                     si.wait_event(vt_in[f])
@@ -702,14 +734,27 @@ def run_ours(a):
                 with torch.cuda.stream(sd):
                     F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
                     sd.wait_event(alpha_ready)
-                    F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+                    if d is not None:
+                        F.front_csf_force_compact(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, d["keys"], d["force"],
+                                                  d["count"])
+                    else:
+                        F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
                     force_ready.record(sd)
                 with torch.cuda.stream(dn):
                     M = c["M"]
                     dn.wait_event(alpha_ready)
-                    o["alpha"].copy_(fc.alpha, non_blocking=True)
+                    if d is not None:
+                        o["bits"].copy_(d["bits"], non_blocking=True)
+                        o["acells"].copy_(d["acells"], non_blocking=True)
+                    else:
+                        o["alpha"].copy_(fc.alpha, non_blocking=True)
                     dn.wait_event(force_ready)
-                    o["force"].copy_(fc.force, non_blocking=True)
+                    if d is not None:
+                        o["count"].copy_(d["count"], non_blocking=True)
+                        o["keys"].copy_(d["keys"][:d["cap"]], non_blocking=True)
+                        o["force"].copy_(d["force"][:d["cap"]], non_blocking=True)
+                    else:
+                        o["force"].copy_(fc.force, non_blocking=True)
                     o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
                     o["normal"].copy_(fc.normal[:M], non_blocking=True)
                     dn.wait_event(vel_ready)
@@ -807,7 +852,10 @@ def run_ours(a):
         "paraboloid": parab,
         "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
-                "mode": a.e2e_mode,
+                "mode": a.e2e_mode, "outputs": a.e2e_outputs + (
+                    ": alpha as one bit per cell plus the interfacial values, the CSF force at its non-zero cells "
+                    "with their keys, kappa, normal, vertex velocities" if compact else
+                    ": dense alpha and force, kappa, normal, vertex velocities"),
                 "launch": (("one CUDA graph per step: " if a.e2e_mode == "graph" else "eager calls; ") +
                            ("the fronts one after the other on one compute stream (the first front's outputs go "
                             "down while the second is computed), each front's calls as the DAG of the graph step, "
