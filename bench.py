@@ -829,6 +829,8 @@ def run_ours(a):
         "config": {"workload": "rough icosphere s6 R0.2 + ellipsoid (0.3,0.2,0.15), 128^3 grid, 81,920 tris each",
                    "fronts": [w["name"] for w in fronts], "cells_per_step": cells_per_step,
                    "pairs_per_step": sum(c["P"] for c in counts), "fit_pairs_per_step": sum(fit_pairs),
+                   "candidate_pairs_per_step": sum(w["C"] for w in r["works"]),
+                   "clip_pairs_decided_in_fp64": sum(w["clip_f64"] for w in r["works"]),
                    "precision": a.precision,
                    "stated_error": "FP32 form: |d alpha| <= 1e-6, |d kappa| <= 1e-4 rel. vs the FP64 oracle; "
                                    "FP64 path: 1e-12 / 1e-9 (checked by tests/test_gpu_parity.py)",

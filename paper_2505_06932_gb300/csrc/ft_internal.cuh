@@ -21,7 +21,7 @@ struct ft_counters {
     long long fit_pairs;   // (cell, fragment) pairs inside the support, last PPIC
     long long work;        // next cell of the dynamically scheduled PPIC accumulation
     long long big;         // cells with more than 32 pairs (worklist of the per-cell ordering)
-    long long clip_f64;    // FP32 clip: pairs decided by the binary64 canonical clip, last front_bin
+    long long clip_f64;    // FP32 clip: pairs listed for the binary64 clip (k_clip_list), last front_bin
     unsigned long long lmax2_bits;  // longest triangle edge squared (float64 bits), paper-neighbourhood fit
 };
 

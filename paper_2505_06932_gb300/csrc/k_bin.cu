@@ -403,6 +403,7 @@ constexpr int kClipThreads = 256;
 // clip: both give the same result as this path would.
 // The surviving polygon is left in A or B (or, after the wide fallback, in
 // wide_res); *out points to it.
+template <int MAXV>
 __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g, const int idx[3], bool active,
                          ClipJob* jobs, double (*A)[3], double (*B)[3], double (*wide_res)[3],
                          const double (**out)[3]) {
@@ -434,7 +435,7 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
             // degenerate stage somewhere in the warp: lane by lane, canonically
             if (alive) {
                 int m;
-                if (!clip_half<kClipV>(src, n, dst, m, ax, pv, ge)) {
+                if (!clip_half<MAXV>(src, n, dst, m, ax, pv, ge)) {
                     wide = true;
                     alive = false;
                 } else if (m < 3) {
@@ -482,7 +483,7 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
             int m = 0, k = 0;
             for (int i = 0; i < n && !wide; i++) {
                 if ((cross >> i) & 1u) {
-                    if (m >= kClipV) {
+                    if (m >= MAXV) {
                         wide = true;
                         break;
                     }
@@ -493,7 +494,7 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
                     m++;
                 }
                 if ((flags >> i) & 1u) {
-                    if (m >= kClipV) {
+                    if (m >= MAXV) {
                         wide = true;
                         break;
                     }
@@ -529,9 +530,89 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
     return n;
 }
 
+// The canonical clip of candidate slot c on every lane of a warp (warp-
+// collective: lanes without a candidate pass active = false), its fragment
+// record and its key and rank.
+template <int MAXV, class F>
+__device__ __forceinline__ void clip_slot_warp(const F& fr, long long c, bool active, ClipJob* jobs,
+                                               const int* __restrict__ cand_tri, const int* __restrict__ tri_off,
+                                               const int* __restrict__ tri_box, const double* __restrict__ tri_nrm,
+                                               unsigned* __restrict__ keys, unsigned* __restrict__ ranks,
+                                               int* __restrict__ cell_cnt, ft_frag* __restrict__ rec,
+                                               ft_frag32* __restrict__ rec32, float4* __restrict__ cen32, int fp32,
+                                               double (*bufA)[3], double (*bufB)[3]) {
+    int idx[3] = {0, 0, 0};
+    int b = 0;
+    double v[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (active) {
+        const int t = cand_tri[c];
+        const int l = (int)(c - tri_off[t]);
+        const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
+        const int4 b0 = bx[0], b1 = bx[1];
+        const int e1 = b1.x, e2 = b1.y;
+        b = b1.z;
+        idx[0] = b0.x + l / (e1 * e2);
+        idx[1] = b0.y + (l / e2) % e1;
+        idx[2] = b0.z + l % e2;
+        const ft_fdesc& D = fr.desc(b);
+        const long long tl = t - fr.tri_base(b);
+        for (int a = 0; a < 3; a++) {
+            const long long vi = D.tris[3 * tl + a];
+            for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
+        }
+    }
+    const ft_fdesc& D = fr.desc(b);
+    const ft_grid g = D.g;
+    const Planes P(D);
+    double wide[32][3];
+    const double(*poly)[3] = bufA;
+    const int n = clip_warp<MAXV>(v, P, g, idx, active, jobs, bufA, bufB, wide, &poly);
+    if (!active) return;
+    unsigned key = FT_SENTINEL;
+    if (n >= 3) {
+        const double inv_h = D.inv_h;
+        const double2* tnp = reinterpret_cast<const double2*>(tri_nrm + 4 * (long long)cand_tri[c]);
+        const double2 tn01 = tnp[0], tn2 = tnp[1];
+        // The moments' own area vector certifies the canonical "area vector
+        // is not zero" condition whenever it exceeds its rounding bound by
+        // far (float32: 1e-4 h^2, float64: 1e-9 h^2); only smaller fragments
+        // evaluate the canonical sum.
+        bool accept;
+        if (fp32) {
+            ft_frag32 f;
+            const float tn[3] = {d2f_rn(tn01.x), d2f_rn(tn01.y), d2f_rn(tn2.x)};
+            const float ih = d2f_rn(inv_h);
+            float q0[3];
+            for (int d = 0; d < 3; d++) q0[d] = d2f_rn(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
+            frag_moments32(poly, n, q0, tn, ih, f);
+            const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
+            accept = (a > 1e-4f) || canon_area_nonzero(poly, n);
+            if (accept) rec32[c] = f;
+        } else {
+            ft_frag f;
+            const double tn[3] = {tn01.x, tn01.y, tn2.x};
+            double q0[3];
+            for (int d = 0; d < 3; d++) q0[d] = (poly[0][d] - P.at(d, idx[d])) * inv_h - 0.5;
+            frag_moments(poly, n, q0, tn, inv_h, f);
+            const double a = fmax(fabs(f.an[0]), fmax(fabs(f.an[1]), fabs(f.an[2])));
+            accept = (a > 1e-9) || canon_area_nonzero(poly, n);
+            if (accept) {
+                rec[c] = f;
+                if (cen32) cen32[c] = make_float4(d2f_rn(f.c[0]), d2f_rn(f.c[1]), d2f_rn(f.c[2]), 0.f);
+            }
+        }
+        if (accept) key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
+    }
+    keys[c] = key;
+    // the pair's rank among its cell's pairs, in arrival order (k_cell_order
+    // puts each cell's pairs back into slot order)
+    if (key != FT_SENTINEL) ranks[c] = (unsigned)atomicAdd(&cell_cnt[key], 1);
+}
+
 // 80 registers (a few bytes of spills) let three blocks of 256 threads share
 // an SM instead of two: 24 resident warps hide more of the float64 and local
-// memory latency of the clip.
+// memory latency of the clip.  With a list, only the listed slots (their
+// number in clip_f64: the pairs the FP32 clip's warps could not keep).
 template <class F>
 __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
                                                    const int* __restrict__ tri_off, const int* __restrict__ tri_box,
@@ -539,82 +620,45 @@ __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
                                                    unsigned* __restrict__ keys, unsigned* __restrict__ ranks,
                                                    int* __restrict__ cell_cnt, ft_frag* __restrict__ rec,
                                                    ft_frag32* __restrict__ rec32, float4* __restrict__ cen32, int fp32,
-                                                   const ft_counters* ctr) {
+                                                   const ft_counters* ctr, const unsigned* __restrict__ list) {
     __shared__ ClipJob s_jobs[kClipThreads / 32][kClipJobs];
     ClipJob* jobs = s_jobs[threadIdx.x >> 5];
-    const long long C = ctr->C;
+    const long long C = list ? ctr->clip_f64 : ctr->C;
     const int lane = threadIdx.x & 31;
     const long long nwarps = (long long)gridDim.x * (kClipThreads / 32);
     for (long long cb = ((long long)blockIdx.x * (kClipThreads / 32) + (threadIdx.x >> 5)) * 32; cb < C; cb += nwarps * 32) {
-        const long long c = cb + lane;
-        const bool active = c < C;
-        int idx[3] = {0, 0, 0};
-        int b = 0;
-        double v[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        if (active) {
-            const int t = cand_tri[c];
-            const int l = (int)(c - tri_off[t]);
-            const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
-            const int4 b0 = bx[0], b1 = bx[1];
-            const int e1 = b1.x, e2 = b1.y;
-            b = b1.z;
-            idx[0] = b0.x + l / (e1 * e2);
-            idx[1] = b0.y + (l / e2) % e1;
-            idx[2] = b0.z + l % e2;
-            const ft_fdesc& D = fr.desc(b);
-            const long long tl = t - fr.tri_base(b);
-            for (int a = 0; a < 3; a++) {
-                const long long vi = D.tris[3 * tl + a];
-                for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
-            }
-        }
-        const ft_fdesc& D = fr.desc(b);
-        const ft_grid g = D.g;
-        const Planes P(D);
-        double bufA[kClipV][3], bufB[kClipV][3], wide[32][3];
-        const double(*poly)[3] = bufA;
-        const int n = clip_warp(v, P, g, idx, active, jobs, bufA, bufB, wide, &poly);
-        if (!active) continue;
-        unsigned key = FT_SENTINEL;
-        if (n >= 3) {
-            const double inv_h = D.inv_h;
-            const double2* tnp = reinterpret_cast<const double2*>(tri_nrm + 4 * (long long)cand_tri[c]);
-            const double2 tn01 = tnp[0], tn2 = tnp[1];
-            // The moments' own area vector certifies the canonical "area vector
-            // is not zero" condition whenever it exceeds its rounding bound by
-            // far (float32: 1e-4 h^2, float64: 1e-9 h^2); only smaller fragments
-            // evaluate the canonical sum.
-            bool accept;
-            if (fp32) {
-                ft_frag32 f;
-                const float tn[3] = {d2f_rn(tn01.x), d2f_rn(tn01.y), d2f_rn(tn2.x)};
-                const float ih = d2f_rn(inv_h);
-                float q0[3];
-                for (int d = 0; d < 3; d++) q0[d] = d2f_rn(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
-                frag_moments32(poly, n, q0, tn, ih, f);
-                const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
-                accept = (a > 1e-4f) || canon_area_nonzero(poly, n);
-                if (accept) rec32[c] = f;
-            } else {
-                ft_frag f;
-                const double tn[3] = {tn01.x, tn01.y, tn2.x};
-                double q0[3];
-                for (int d = 0; d < 3; d++) q0[d] = (poly[0][d] - P.at(d, idx[d])) * inv_h - 0.5;
-                frag_moments(poly, n, q0, tn, inv_h, f);
-                const double a = fmax(fabs(f.an[0]), fmax(fabs(f.an[1]), fabs(f.an[2])));
-                accept = (a > 1e-9) || canon_area_nonzero(poly, n);
-                if (accept) {
-                    rec[c] = f;
-                    if (cen32) cen32[c] = make_float4(d2f_rn(f.c[0]), d2f_rn(f.c[1]), d2f_rn(f.c[2]), 0.f);
-                }
-            }
-            if (accept)
-                key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
-        }
-        keys[c] = key;
-        // the pair's rank among its cell's pairs, in arrival order (k_cell_order
-        // puts each cell's pairs back into slot order)
-        if (key != FT_SENTINEL) ranks[c] = (unsigned)atomicAdd(&cell_cnt[key], 1);
+        const bool active = cb + lane < C;
+        const long long c = list ? (active ? (long long)list[cb + lane] : 0) : cb + lane;
+        double bufA[kClipV][3], bufB[kClipV][3];
+        clip_slot_warp<kClipV>(fr, c, active, jobs, cand_tri, tri_off, tri_box, tri_nrm, keys, ranks, cell_cnt, rec, rec32,
+                       cen32, fp32, bufA, bufB);
+    }
+}
+
+// The pairs the FP32 clip left to the binary64 clip (ctr->clip_f64 slots in
+// list): few and often near-degenerate, so one warp per block with polygon
+// buffers in shared memory of twice the fast path's capacity (the wide serial
+// fallback, in local memory, is then practically never taken: no local-memory
+// round trips on a latency-bound pass).
+constexpr int kListV = 24;                   // polygon capacity (twice the fast path's; beyond it the wide serial clip)
+constexpr int kPolyStride = kListV * 3 + 1;  // doubles per lane's buffer (padded against bank conflicts)
+template <class F>
+__global__ void __launch_bounds__(32) k_clip_list(F fr, const int* __restrict__ cand_tri,
+                                                  const int* __restrict__ tri_off, const int* __restrict__ tri_box,
+                                                  const double* __restrict__ tri_nrm, unsigned* __restrict__ keys,
+                                                  unsigned* __restrict__ ranks, int* __restrict__ cell_cnt,
+                                                  ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
+                                                  const ft_counters* ctr, const unsigned* __restrict__ list) {
+    __shared__ ClipJob s_jobs[kClipJobs];
+    __shared__ double s_A[32 * kPolyStride], s_B[32 * kPolyStride];
+    const int lane = threadIdx.x;
+    const long long C = ctr->clip_f64;
+    for (long long cb = (long long)blockIdx.x * 32; cb < C; cb += (long long)gridDim.x * 32) {
+        const bool active = cb + lane < C;
+        const long long c = active ? (long long)list[cb + lane] : 0;
+        clip_slot_warp<kListV>(fr, c, active, s_jobs, cand_tri, tri_off, tri_box, tri_nrm, keys, ranks, cell_cnt, rec,
+                               rec32, nullptr, 1, reinterpret_cast<double(*)[3]>(s_A + lane * kPolyStride),
+                       reinterpret_cast<double(*)[3]>(s_B + lane * kPolyStride));
     }
 }
 
@@ -823,18 +867,17 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
 }
 
 template <class F>
-__global__ void __launch_bounds__(kClip32Threads) k_clip32(F fr, const int* __restrict__ cand_tri,
+__global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* __restrict__ cand_tri,
                                                            const int* __restrict__ tri_off,
                                                            const int* __restrict__ tri_box,
                                                            const double* __restrict__ tri_nrm,
                                                            unsigned* __restrict__ keys, unsigned* __restrict__ ranks,
                                                            int* __restrict__ cell_cnt, ft_frag32* __restrict__ rec32,
-                                                           ft_counters* ctr) {
+                                                           ft_counters* ctr, unsigned* __restrict__ undecided) {
     __shared__ float4 s_poly[kClip32Warps][2][kPV][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long C = ctr->C;
     const long long nthreads = (long long)gridDim.x * kClip32Threads;
-    unsigned long long n_f64 = 0;
     for (long long c = (long long)blockIdx.x * kClip32Threads + threadIdx.x; c < C; c += nthreads) {
         const int t = cand_tri[c];
         const int l = (int)(c - tri_off[t]);
@@ -853,7 +896,6 @@ __global__ void __launch_bounds__(kClip32Threads) k_clip32(F fr, const int* __re
             for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
         }
         // exact flags of the triangle's vertices and their cell-unit coordinates
-        const float ih = d2f_rn(D.inv_h);
         float tv[3][3], top[3];
         unsigned vflags[3] = {0u, 0u, 0u};
         unsigned on_top = 7u;  // axes whose upper plane holds all three vertices
@@ -899,18 +941,11 @@ __global__ void __launch_bounds__(kClip32Threads) k_clip32(F fr, const int* __re
             if (!(a > bound)) verdict = kUndecided;
         }
         if (verdict == kUndecided) {
-            // the binary64 canonical clip decides (and gives the record)
-            n_f64++;
-            double wide[32][3];
-            const int nc = canon_stages_wide(v, g, idx, wide);
-            verdict = kRejected;
-            if (nc >= 3) {
-                float q0[3];
-                for (int d = 0; d < 3; d++) q0[d] = d2f_rn(wide[0][d] - P.at(d, idx[d])) * ih - 0.5f;
-                frag_moments32(wide, nc, q0, tn, ih, f);
-                const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
-                if ((a > 1e-4f) || canon_area_nonzero(wide, nc)) verdict = kKept;
-            }
+            // the binary64 canonical clip decides this pair (and gives its record)
+            // in a second launch over the listed slots
+            const unsigned long long gp = atomicAdd((unsigned long long*)&ctr->clip_f64, 1ull);
+            undecided[gp] = (unsigned)c;
+            continue;
         }
         if (verdict == kKept) {
             rec32[c] = f;
@@ -919,8 +954,6 @@ __global__ void __launch_bounds__(kClip32Threads) k_clip32(F fr, const int* __re
         keys[c] = key;
         if (key != FT_SENTINEL) ranks[c] = (unsigned)atomicAdd(&cell_cnt[key], 1);
     }
-    n_f64 = (unsigned long long)ft_warp_sum_ll((long long)n_f64);
-    if (lane == 0 && n_f64) atomicAdd((unsigned long long*)&ctr->clip_f64, n_f64);
 }
 
 }  // namespace
@@ -953,16 +986,26 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
                              cudaSuccess || occ < 1))
             occ = 1;
         const int bps = min(occ, 2 * ws->tune.clip_bps);
-        Trace t(s, "k_clip32");
-        k_clip32<F><<<ws->sm_count * bps, kClip32Threads, 0, s>>>(
-            fr, ws->cand_tri, ws->tri_off, ws->tri_box, ws->tri_nrm, ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec32,
-            ws->ctr);
+        // the pairs it leaves undecided are listed in the spare key buffer (free
+        // until the placement) and clipped by the binary64 kernel right after
+        unsigned* undecided = ws->keys[1];
+        count_launches(1);
+        {
+            Trace t(s, "k_clip32");
+            k_clip32<F><<<ws->sm_count * bps, kClip32Threads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
+                                                                      ws->tri_nrm, ws->keys[0], ws->vals[0],
+                                                                      ws->cell_cnt, ws->rec32, ws->ctr, undecided);
+        }
+        Trace t(s, "k_clip_list");
+        k_clip_list<F><<<ws->sm_count * 4, 32, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box, ws->tri_nrm,
+                                                       ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec, ws->rec32,
+                                                       ws->ctr, undecided);
         return cudaGetLastError();
     }
     Trace t(s, "k_clip");
     k_clip<F><<<ws->sm_count * ws->tune.clip_bps, kClipThreads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
                                                                     ws->tri_nrm, ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec, ws->rec32,
-                                                                    ws->cen32, fp32 ? 1 : 0, ws->ctr);
+                                                                    ws->cen32, fp32 ? 1 : 0, ws->ctr, nullptr);
     return cudaGetLastError();
 }
 

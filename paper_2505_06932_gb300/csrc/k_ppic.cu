@@ -121,11 +121,25 @@ __device__ __forceinline__ double warp_transpose_sum(double (&v)[32]) {
 }
 
 // The same with float (hi, lo) pairs combined by two-sum: the lanes' rounding
-// errors are carried along instead of being lost.
+// errors are carried along instead of being lost.  The lo parts start at zero,
+// so the first round exchanges only the hi parts (lo = the two-sum error).
 __device__ __forceinline__ void warp_transpose_sum2(float (&h)[32], float (&l)[32]) {
     const int lane = threadIdx.x & 31;
+    {
+        const bool up = (lane & 16) != 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+        for (int i = 0; i < 16; i++) {
+            const float sh = up ? h[i] : h[i + 16];
+            const float kh = up ? h[i + 16] : h[i];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh, 16);
+            float s, e;
+            two_sum(kh, rh, s, e);
+            h[i] = s;
+            l[i] = e;
+        }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
         const bool up = (lane & o) != 0;
 #pragma unroll
         for (int i = 0; i < o; i++) {
@@ -620,8 +634,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
             for (int r = 0; r < 6; r++) hv[21 + r] = (float)B[r];
 #pragma unroll
             for (int r = 27; r < 32; r++) hv[r] = 0.f;
-#pragma unroll
-            for (int r = 0; r < 32; r++) lv[r] = 0.f;
             warp_transpose_sum2(hv, lv);
             float* o32 = reinterpret_cast<float*>(out->v);
             if (lane < 27) {
