@@ -92,9 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_alpha_cells32(const int* __restric
     }
 }
 
-// one warp per (i, j) column, walking k downwards in chunks of 32 cells; the
-// index map of up to four chunks (128 cells) is loaded at once, so that a
-// column of up to 128 cells costs one round trip to memory instead of four
+// one warp per (i, j) column, walking k downwards in chunks of 32 cells
 template <class F>
 __global__ void __launch_bounds__(kThreads) k_alpha_fill(F fr, const int* __restrict__ idx_map,
                                                          const double* __restrict__ cell_L,
@@ -113,21 +111,14 @@ __global__ void __launch_bounds__(kThreads) k_alpha_fill(F fr, const int* __rest
         double* __restrict__ alpha = D.alpha;
         unsigned err = 0;
         double carry = 0.0;
-        int mq[4] = {-1, -1, -1, -1};  // index map of the current group of four chunks, top chunk first
+        // the index map of the chunk below is loaded while this chunk is processed
         int k0 = ((n2 - 1) / 32) * 32;
-        for (int q = 4; k0 >= 0; k0 -= 32, q++) {
-            if (q == 4) {
-                // the next (lower) four chunks at once
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int kk = k0 - 32 * u + lane;
-                    mq[u] = (k0 - 32 * u >= 0 && kk < n2) ? idx_map[gbase + kk] : -1;
-                }
-                q = 0;
-            }
+        int m_next = (k0 + lane < n2) ? idx_map[gbase + k0 + lane] : -1;
+        for (; k0 >= 0; k0 -= 32) {
             const int k = k0 + lane;
             const bool valid = k < n2;
-            const int m = q == 0 ? mq[0] : (q == 1 ? mq[1] : (q == 2 ? mq[2] : mq[3]));
+            const int m = m_next;
+            if (k0 >= 32) m_next = idx_map[gbase + k0 - 32 + lane];
             if (__ballot_sync(0xffffffffu, m >= 0) == 0u) {
                 // no interfacial cell in this chunk: every cell takes the parity above it
                 const long long cb = __double_as_longlong(carry);

@@ -461,57 +461,53 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
             const float f_thr = (float)delta * (float)delta * 1.0001f;
             const int R = (int)ceil(delta - (T)0.5);
             const int side = 2 * R + 1;
-            const int nb = side * side * side;
-            // neighbour offsets decoded with float reciprocals: (l + 1/2)/side^k
-            // stays at least 1/(2 side^2) away from an integer for l < side^3,
-            // far beyond the float rounding, so the truncation is exact
-            const float inv_s = 1.0f / (float)side, inv_ss = inv_s * inv_s;
+            const int nrows = side * side;
+            // row offsets decoded with a float reciprocal: (l + 1/2)/side stays at
+            // least 1/(2 side) away from an integer for l < side^2, far beyond the
+            // float rounding, so the truncation is exact
+            const float inv_s = 1.0f / (float)side;
             int qn = 0;
-            // neighbour l -> offsets (di, dj, dk) and its interfacial index m2 (-1: none,
-            // outside the grid, or a box beyond the support: a fragment's centroid
-            // lies in its own cell, so such a cell holds none in the support)
-            auto neighbour = [&](int l, int& di, int& dj, int& dk) -> int {
-                const int a = (int)(((float)l + 0.5f) * inv_ss);
-                const int rem = l - a * side * side;
-                const int b = (int)(((float)rem + 0.5f) * inv_s);
-                di = a - R;
-                dj = b - R;
-                dk = rem - b * side - R;
-                const int ii = ci + di, jj = cj + dj, kk = ck + dk;
-                const float bx = fmaxf(fabsf((float)di) - 0.5f, 0.0f), by = fmaxf(fabsf((float)dj) - 0.5f, 0.0f),
-                            bz = fmaxf(fabsf((float)dk) - 0.5f, 0.0f);
-                const bool near = bx * bx + by * by + bz * bz <= f_thr;
-                if (!near || ii < 0 || jj < 0 || kk < 0 || ii >= n0 || jj >= n1 || kk >= n2) return -1;
-                return idx_map[kb + ((long long)ii * n1 + jj) * n2 + kk];
-            };
-            // the index map of the next round is read while this round runs
-            int m2_next = -1;
-            {
-                int di, dj, dk;
-                if (lane < nb) m2_next = neighbour(lane, di, dj, dk);
-            }
-            for (int cb = 0; cb < nb; cb += 32) {
+            // Neighbour rows (i + di, j + dj, k - R .. k + R): keys are k-fastest, so a
+            // row's interfacial cells are consecutive in the cell list and their
+            // fragments one contiguous range.  Cells whose box lies beyond the
+            // support hold no fragment in it (a fragment's centroid lies in its own
+            // cell): each row keeps the cells |dk| <= dkmax that pass the box test.
+            // Lane l takes row l of a round of 32 rows.
+            for (int cb = 0; cb < nrows; cb += 32) {
                 const int l = cb + lane;
                 int f0 = 0, cnt = 0, dcode = 0;
-                float ox = 0.f, oy = 0.f, oz = 0.f;
-                const int m2 = m2_next;
-                if (l + 32 < nb) {
-                    int di, dj, dk;
-                    m2_next = neighbour(l + 32, di, dj, dk);
-                }
-                if (l < nb) {
-                    const int a = (int)(((float)l + 0.5f) * inv_ss);
-                    const int rem = l - a * side * side;
-                    const int b = (int)(((float)rem + 0.5f) * inv_s);
-                    const int di = a - R, dj = b - R, dk = rem - b * side - R;
-                    if (m2 >= 0) {
-                        f0 = cell_off[m2];
-                        cnt = cell_off[m2 + 1] - f0;
+                float ox = 0.f, oy = 0.f;
+                unsigned rkey = 0;  // batch-global key of the row's cell at height ck
+                if (l < nrows) {
+                    const int a = (int)(((float)l + 0.5f) * inv_s);
+                    const int di = a - R, dj = l - a * side - R;
+                    const int ii = ci + di, jj = cj + dj;
+                    const float bx = fmaxf(fabsf((float)di) - 0.5f, 0.0f), by = fmaxf(fabsf((float)dj) - 0.5f, 0.0f);
+                    int dkmax = -1;
+                    for (int t = 0; t <= R; t++) {
+                        const float bz = fmaxf((float)t - 0.5f, 0.0f);
+                        if (bx * bx + by * by + bz * bz <= f_thr) dkmax = t;
                     }
-                    dcode = ((di + 8) << 8) | ((dj + 8) << 4) | (dk + 8);
+                    if (dkmax >= 0 && ii >= 0 && jj >= 0 && ii < n0 && jj < n1) {
+                        const int k0 = max(ck - dkmax, 0), k1 = min(ck + dkmax, n2 - 1);
+                        const long long base = kb + ((long long)ii * n1 + jj) * n2;
+                        int mf = -1, ml = -1;
+                        for (int k = k0; k <= k1; k++) {
+                            const int m2 = idx_map[base + k];
+                            if (m2 >= 0) {
+                                if (mf < 0) mf = m2;
+                                ml = m2;
+                            }
+                        }
+                        if (mf >= 0) {
+                            f0 = cell_off[mf];
+                            cnt = cell_off[ml + 1] - f0;
+                        }
+                        rkey = (unsigned)(base + ck);
+                    }
+                    dcode = ((di + 8) << 8) | ((dj + 8) << 4);
                     ox = (float)di;
                     oy = (float)dj;
-                    oz = (float)dk;
                 }
                 int incl = cnt;
 #pragma unroll
@@ -521,10 +517,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                 }
                 const int excl = incl - cnt;
                 const int total = __shfl_sync(0xffffffffu, incl, 31);
-                // candidate fi of this round -> owning neighbour lane o, record ri;
-                // the next batch's mapping and centroid load are issued before
-                // the current batch is tested (software pipelining of the loads)
-                auto map = [&](int fb, unsigned& ri, float& dx, float& dy, float& dz, int& dc, bool& valid) {
+                // candidate fi of this round -> owning row lane o, record ri; dk from
+                // the record's cell key (the w of its centroid entry); the next
+                // batch's mapping and centroid load are issued before the current
+                // batch is tested (software pipelining of the loads)
+                auto map = [&](int fb, unsigned& ri, float& dx, float& dy, unsigned& rk, int& dc, bool& valid) {
                     const int fi = fb + lane;
                     int o = 0;
 #pragma unroll
@@ -534,55 +531,56 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                     }
                     const int fo = __shfl_sync(0xffffffffu, f0, o);
                     const int eo = __shfl_sync(0xffffffffu, excl, o);
+                    rk = __shfl_sync(0xffffffffu, rkey, o);
                     if constexpr (sizeof(T) == 4) {
                         dx = __shfl_sync(0xffffffffu, ox, o);
                         dy = __shfl_sync(0xffffffffu, oy, o);
-                        dz = __shfl_sync(0xffffffffu, oz, o);
                         dc = 0;
                     } else {
                         // one shuffle of the offset code; the float64 form is issue-bound
                         dc = __shfl_sync(0xffffffffu, dcode, o);
                         dx = (float)(((dc >> 8) & 15) - 8);
                         dy = (float)(((dc >> 4) & 15) - 8);
-                        dz = (float)((dc & 15) - 8);
                     }
                     valid = fi < total;
                     ri = valid ? (unsigned)(fo + (fi - eo)) : 0u;
                 };
-                unsigned ri_n = 0;
-                float dx_n = 0.f, dy_n = 0.f, dz_n = 0.f;
+                unsigned ri_n = 0, rk_n = 0;
+                float dx_n = 0.f, dy_n = 0.f;
                 int dc_n = 0;
                 bool v_n = false;
                 float4 c4_n = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (total > 0) {
-                    map(0, ri_n, dx_n, dy_n, dz_n, dc_n, v_n);
+                    map(0, ri_n, dx_n, dy_n, rk_n, dc_n, v_n);
                     if (v_n) c4_n = cen[ri_n];
                 }
                 // (the float64 form maps each batch in turn: its registers are full)
                 constexpr bool kPipe = sizeof(T) == 4;
                 for (int fb = 0; fb < total; fb += 32) {
                     if (!kPipe && fb > 0) {
-                        map(fb, ri_n, dx_n, dy_n, dz_n, dc_n, v_n);
+                        map(fb, ri_n, dx_n, dy_n, rk_n, dc_n, v_n);
                         if (v_n) c4_n = cen[ri_n];
                     }
-                    const unsigned ri = ri_n;
-                    const float dx = dx_n, dy = dy_n, dz = dz_n;
+                    const unsigned ri = ri_n, rk = rk_n;
+                    const float dx = dx_n, dy = dy_n;
                     const int dc = dc_n;
                     const bool valid = v_n;
                     const float4 c4 = c4_n;
                     if (kPipe && fb + 32 < total) {
-                        map(fb + 32, ri_n, dx_n, dy_n, dz_n, dc_n, v_n);
+                        map(fb + 32, ri_n, dx_n, dy_n, rk_n, dc_n, v_n);
                         if (v_n) c4_n = cen[ri_n];
                     }
                     bool pass = false;
                     float4 entry = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (valid) {
-                        const float px = c4.x + dx, py = c4.y + dy, pz = c4.z + dz;
+                        // the fragment's cell lies in the row: dk = its key - the row's key at ck
+                        const int dk = (int)(__float_as_uint(c4.w) - rk);
+                        const float px = c4.x + dx, py = c4.y + dy, pz = c4.z + (float)dk;
                         pass = (px * px + py * py + pz * pz) < f_thr;
                         if (sizeof(T) == 4)
                             entry = make_float4(px, py, pz, __uint_as_float(ri));
                         else
-                            entry = make_float4(__int_as_float(dc), 0.f, 0.f, __uint_as_float(ri));
+                            entry = make_float4(__int_as_float(dc | (dk + 8)), 0.f, 0.f, __uint_as_float(ri));
                     }
                     const unsigned bal = __ballot_sync(0xffffffffu, pass);
                     if (pass) qq[qn + __popc(bal & ((1u << lane) - 1u))] = entry;

@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(kB) k_export_pairs(const unsigned* __restrict_
 }
 
 // fragment records in sorted pair order, so later kernels read a cell's
-// fragments as one contiguous range (no indirection through the slot)
-__global__ void __launch_bounds__(kB) k_gather(const unsigned* __restrict__ svals, const ft_frag* __restrict__ rec,
+// fragments as one contiguous range (no indirection through the slot); the
+// float centroid entry carries the fragment's cell key in w
+__global__ void __launch_bounds__(kB) k_gather(const unsigned* __restrict__ skeys,
+                                               const unsigned* __restrict__ svals, const ft_frag* __restrict__ rec,
                                                const ft_frag32* __restrict__ rec32, ft_frag* __restrict__ srec,
                                                ft_frag32* __restrict__ srec32, float4* __restrict__ scen, int fp32,
                                                const ft_counters* ctr) {
@@ -411,11 +413,11 @@ __global__ void __launch_bounds__(kB) k_gather(const unsigned* __restrict__ sval
         if (fp32) {
             const ft_frag32 f = rec32[c];
             srec32[q] = f;
-            scen[q] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
+            scen[q] = make_float4(f.c[0], f.c[1], f.c[2], __uint_as_float(skeys[q]));
         } else {
             const ft_frag f = rec[c];
             srec[q] = f;
-            scen[q] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], 0.f);
+            scen[q] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], __uint_as_float(skeys[q]));
         }
     }
 }
@@ -449,7 +451,8 @@ cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s) {
     if (!ws->srec || !ws->srec32 || !ws->scen) return cudaSuccess;  // a workspace without sorted copies
     count_launches(1);
     Trace t(s, "k_gather");
-    k_gather<<<ws->sm_count * 4, kB, 0, s>>>(ws->vals[ws->sorted_buf], ws->rec, ws->rec32, ws->srec, ws->srec32,
+    k_gather<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[ws->sorted_buf], ws->vals[ws->sorted_buf], ws->rec, ws->rec32,
+                                             ws->srec, ws->srec32,
                                              ws->scen, ws->last_precision == FT_FP32C ? 1 : 0, ws->ctr);
     return cudaGetLastError();
 }
