@@ -67,10 +67,9 @@ def kernel_work(name, w, fp32):
                        "per interfacial cell"),
         "k_place": ("hbm", 4 * C + 16 * P, "every candidate's key read; per kept pair its rank and its cell's "
                     "offset read, key and slot written"),
-        "k_cell_order": ("hbm", 12 * M + 8 * P, "per cell its offsets and counter; per pair its slot read and "
-                         "written"),
-        "k_gather": ("hbm", (116 if fp32 else 212) * P, "per pair its slot read, its record read and written "
-                     "in cell order, its float centroid written"),
+        "k_cell_order": ("hbm", 12 * M + (120 if fp32 else 216) * P, "per cell its offsets and counter; per "
+                         "pair its slot read and written, its record read and written in cell order, its float "
+                         "centroid written"),
         "k_alpha_cells32": ("hbm", 24 * M + 8 * P, "per pair the two record values of the column moment; "
                             "per cell offsets read, L and P written"),
         "k_alpha_cells": ("hbm", 24 * M + 16 * P, "per pair the two record values of the column moment; "

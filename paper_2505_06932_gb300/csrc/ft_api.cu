@@ -350,7 +350,6 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     ws->f_nt = f->nt;
     cudaError_t e = ft::launch_bin(ws, f, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
-    if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
     ws->fitted = false;
     return cuda_err(e);
@@ -465,7 +464,6 @@ int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream) {
     cudaStream_t s = as_stream(stream);
     cudaError_t e = ft::launch_bin_batch(ws, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
-    if (e == cudaSuccess) e = ft::launch_gather(ws, s);
     ws->binned = (e == cudaSuccess);
     ws->fitted = false;
     return cuda_err(e);

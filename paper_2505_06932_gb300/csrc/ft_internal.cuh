@@ -191,7 +191,6 @@ cudaError_t launch_candidates(ft_workspace* ws, cudaStream_t s);
 // the kept pairs into cell order: interfacial cell list, offsets, index map
 // (the counts k_clip left in cell_cnt over keys [0, nkeys)); resets cell_cnt
 cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s);
-cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s);
 cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s);
 cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, unsigned* cell_keys,

@@ -284,10 +284,11 @@ __device__ __forceinline__ void accumulate<float>(const Rec<float>& rec, const f
     rec.load(__float_as_uint(qe.w), an, c, k);
     const float p[3] = {qe.x, qe.y, qe.z};
     const float d2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
-    const float dist = sqrtf(d2);
-    if (!(dist < delta)) return;
+    // the support test on squared lengths; the distance from the fast reciprocal
+    // square root (its rounding moves the weight by about 1e-7 of itself)
+    if (!(d2 < delta * delta)) return;
     count++;
-    const float q = dist * inv_delta;
+    const float q = (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f) * inv_delta;
     const float om = 1.f - q;
     const float om2 = om * om;
     const float w = (1.f + 4.f * q) * om2 * om2;

@@ -1,6 +1,7 @@
 // k_sort.cu -- front_bin, part 2: the (cell key, candidate slot) pairs put
 // into cell order by counting, with the interfacial-cell list, its pair
-// offsets and the index map; the record gather and the per-front cell ranges.
+// offsets and the index map (the fragment records follow their slots into
+// cell order as each cell is ordered); the per-front cell ranges.
 //
 // Pair and cell counts live in device memory (no host round trip).  No kernel
 // waits on another block: the key-range scan is a reduce launch and a
@@ -113,9 +114,10 @@ __global__ void __launch_bounds__(kB) k_scan_expand(const int* __restrict__ cnt,
 //  k_place -- every kept pair to its cell's offset + rank;
 //  k_cell_order, k_cell_order_big -- each cell's pairs into ascending slot
 //    order, the order of a stable sort by key (pairs are generated in slot
-//    order, and slot order is triangle order); k_cell_order also sets each
-//    cell's counter back to zero, so that cell_cnt is all zero again for the
-//    next binning.
+//    order, and slot order is triangle order), each pair's fragment record
+//    copied to its place in cell order as soon as it is known; k_cell_order
+//    also sets each cell's counter back to zero, so that cell_cnt is all zero
+//    again for the next binning.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ long long pack_cnt(int c) { return ((long long)c << 32) | (c > 0 ? 1 : 0); }
@@ -251,17 +253,42 @@ constexpr int kWarpSlots = 8;  // slots per lane of the warp path: cells of up t
 // holding kWarpSlots of them: a pair's place is the number of smaller slots of
 // the cell, counted by shuffles, and the warp writes in place.  A larger cell
 // goes to a worklist for k_cell_order_big.
+// The fragment records in sorted pair order (so that later kernels read a
+// cell's fragments as one contiguous range), written by the per-cell ordering
+// as soon as a cell's slots are in order; the float centroid entry carries the
+// cell's key in w.  srec == NULL: a workspace without sorted copies.
+struct Gather {
+    const ft_frag* rec;
+    const ft_frag32* rec32;
+    ft_frag* srec;
+    ft_frag32* srec32;
+    float4* scen;
+    int fp32;
+    __device__ __forceinline__ void put(long long q, unsigned slot, unsigned key) const {
+        if (fp32) {
+            const ft_frag32 f = rec32[slot];
+            srec32[q] = f;
+            scen[q] = make_float4(f.c[0], f.c[1], f.c[2], __uint_as_float(key));
+        } else {
+            const ft_frag f = rec[slot];
+            srec[q] = f;
+            scen[q] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], __uint_as_float(key));
+        }
+    }
+};
+
 __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_off, const unsigned* __restrict__ cells,
                                                    unsigned* __restrict__ svals, int* __restrict__ cnt,
-                                                   int* __restrict__ big, long long max_cells, ft_counters* ctr) {
+                                                   int* __restrict__ big, long long max_cells, ft_counters* ctr,
+                                                   Gather G) {
     const long long M = ctr->M;
     if (M > max_cells) return;
     const int lane = threadIdx.x & 31;
     const long long nw = (long long)gridDim.x * (kB / 32);
     for (long long m = ((long long)blockIdx.x * kB + threadIdx.x) >> 5; m < M; m += nw) {
         const int q0 = cell_off[m], n = cell_off[m + 1] - q0;
-        if (lane == 0) cnt[cells[m]] = 0;  // back to zero for the next binning
-        if (n <= 1) continue;
+        const unsigned key = cells[m];
+        if (lane == 0) cnt[key] = 0;  // back to zero for the next binning
         if (n > 32 * kWarpSlots) {
             if (lane == 0) big[atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->big), 1ull)] = (int)m;
             continue;
@@ -272,7 +299,10 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
             int r = 0;
             for (int o = 0; o < n; o++) r += (__shfl_sync(0xffffffffu, x, o) < x) ? 1 : 0;
             __syncwarp();
-            if (lane < n) v[r] = x;
+            if (lane < n) {
+                v[r] = x;
+                if (G.srec) G.put(q0 + r, x, key);
+            }
             __syncwarp();
             continue;
         }
@@ -299,7 +329,10 @@ __global__ void __launch_bounds__(kB) k_cell_order(const int* __restrict__ cell_
 #pragma unroll
         for (int j = 0; j < kWarpSlots; j++) {
             const int a = lane + 32 * j;
-            if (j < J && a < n) v[r[j]] = x[j];
+            if (j < J && a < n) {
+                v[r[j]] = x[j];
+                if (G.srec) G.put(q0 + r[j], x[j], key);
+            }
         }
         __syncwarp();
     }
@@ -313,7 +346,8 @@ constexpr int kSortCap = 4096;  // slots a block sorts in shared memory at once
 // number of smaller slots in the partner run).
 __global__ void __launch_bounds__(kB) k_cell_order_big(const int* __restrict__ cell_off, unsigned* __restrict__ svals,
                                                        unsigned* __restrict__ tmp, const int* __restrict__ big,
-                                                       long long max_cells, ft_counters* ctr) {
+                                                       long long max_cells, ft_counters* ctr,
+                                                       const unsigned* __restrict__ cells, Gather G) {
     __shared__ unsigned sh[kSortCap];
     if (ctr->M > max_cells) {
         // the last kernel of the placement: flag the capacity and leave no cells.
@@ -380,8 +414,12 @@ __global__ void __launch_bounds__(kB) k_cell_order_big(const int* __restrict__ c
             src = dst;
             dst = sw;
         }
-        if (src != v)
-            for (int i = threadIdx.x; i < n; i += kB) v[i] = src[i];
+        const unsigned key = cells[m];
+        for (int i = threadIdx.x; i < n; i += kB) {
+            const unsigned x = src[i];
+            if (src != v) v[i] = x;
+            if (G.srec) G.put(q0 + i, x, key);
+        }
         __syncthreads();
     }
 }
@@ -396,29 +434,6 @@ __global__ void __launch_bounds__(kB) k_export_pairs(const unsigned* __restrict_
     for (long long q = (long long)blockIdx.x * kB + threadIdx.x; q < n; q += (long long)gridDim.x * kB) {
         keys[q] = skeys[q];
         tris[q] = cand_tri[svals[q]];
-    }
-}
-
-// fragment records in sorted pair order, so later kernels read a cell's
-// fragments as one contiguous range (no indirection through the slot); the
-// float centroid entry carries the fragment's cell key in w
-__global__ void __launch_bounds__(kB) k_gather(const unsigned* __restrict__ skeys,
-                                               const unsigned* __restrict__ svals, const ft_frag* __restrict__ rec,
-                                               const ft_frag32* __restrict__ rec32, ft_frag* __restrict__ srec,
-                                               ft_frag32* __restrict__ srec32, float4* __restrict__ scen, int fp32,
-                                               const ft_counters* ctr) {
-    const long long P = ctr->P;
-    for (long long q = (long long)blockIdx.x * kB + threadIdx.x; q < P; q += (long long)gridDim.x * kB) {
-        const unsigned c = svals[q];
-        if (fp32) {
-            const ft_frag32 f = rec32[c];
-            srec32[q] = f;
-            scen[q] = make_float4(f.c[0], f.c[1], f.c[2], __uint_as_float(skeys[q]));
-        } else {
-            const ft_frag f = rec[c];
-            srec[q] = f;
-            scen[q] = make_float4((float)f.c[0], (float)f.c[1], (float)f.c[2], __uint_as_float(skeys[q]));
-        }
     }
 }
 
@@ -446,16 +461,6 @@ __global__ void __launch_bounds__(kB) k_cell_ranges(const unsigned* __restrict__
 }  // namespace
 
 namespace ft {
-
-cudaError_t launch_gather(ft_workspace* ws, cudaStream_t s) {
-    if (!ws->srec || !ws->srec32 || !ws->scen) return cudaSuccess;  // a workspace without sorted copies
-    count_launches(1);
-    Trace t(s, "k_gather");
-    k_gather<<<ws->sm_count * 4, kB, 0, s>>>(ws->keys[ws->sorted_buf], ws->vals[ws->sorted_buf], ws->rec, ws->rec32,
-                                             ws->srec, ws->srec32,
-                                             ws->scen, ws->last_precision == FT_FP32C ? 1 : 0, ws->ctr);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_export_pairs(ft_workspace* ws, long long cap, unsigned* keys, int* tris, cudaStream_t s) {
     count_launches(1);
@@ -501,15 +506,20 @@ cudaError_t launch_place_pairs(ft_workspace* ws, long long nkeys, cudaStream_t s
     // large cells: the ranks in vals[0] are spent once placed, so that buffer is
     // their merge scratch; cell_L (filled only by the volume fraction) holds the worklist
     int* big = reinterpret_cast<int*>(ws->cell_L);
+    // the records follow their slots into cell order (a workspace without sorted
+    // copies, as the allocation-free one, reads them through the slot instead)
+    const bool gather = ws->srec && ws->srec32 && ws->scen;
+    const Gather gat{ws->rec, ws->rec32, gather ? ws->srec : nullptr, ws->srec32, ws->scen,
+                     ws->last_precision == FT_FP32C ? 1 : 0};
     {
         Trace t(s, "k_cell_order");
         k_cell_order<<<ws->sm_count * 8, kB, 0, s>>>(ws->cell_off, ws->cells, ws->vals[1], ws->cell_cnt, big,
-                                                     ws->max_cells, ws->ctr);
+                                                     ws->max_cells, ws->ctr, gat);
     }
     {
         Trace t(s, "k_cell_order_big");
         k_cell_order_big<<<ws->sm_count * 2, kB, 0, s>>>(ws->cell_off, ws->vals[1], ws->vals[0], big, ws->max_cells,
-                                                         ws->ctr);
+                                                         ws->ctr, ws->cells, gat);
     }
     ws->sorted_buf = 1;
     return cudaGetLastError();
