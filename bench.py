@@ -86,6 +86,9 @@ def kernel_work(name, w, fp32):
         "k_clip32": ("fp32", FLOPS_PER_CAND * C + FLOPS_PER_KEPT * P,
                      f"{FLOPS_PER_CAND:.0f} flops per candidate pair (cell-unit coordinates, plane stages, "
                      f"crossings), {FLOPS_PER_KEPT:.0f} per kept pair (fragment moments)"),
+        "k_clip_list": ("fp64", (FLOPS_PER_CAND + FLOPS_PER_KEPT) * w["clip_f64"],
+                        f"{FLOPS_PER_CAND + FLOPS_PER_KEPT:.0f} flops per pair the FP32 clip left to the binary64 "
+                        "clip (the candidate's plane stages and the fragment moments)"),
         "k_clip": ("fp64", FLOPS_PER_CAND * C + FLOPS_PER_KEPT * P,
                    f"{FLOPS_PER_CAND:.0f} flops per candidate pair, {FLOPS_PER_KEPT:.0f} per kept pair"),
         "k_ppic_acc<float>": ("fp32", FLOPS_PER_FIT_PAIR * FP, f"{FLOPS_PER_FIT_PAIR:.0f} flops per (cell, "
@@ -139,7 +142,7 @@ def roofline_list(trace, works, fp32, workload_tag):
         e = {"kernel": name, "launches": n, "us_per_launch": round(1e3 * ms / n, 2),
              "share": round(ms / total, 4) if total else None}
         if per[0] is None:
-            e.update(bound=None, note="no algorithmic work model (per-cell ordering of large cells)")
+            e.update(bound=None, note=NO_MODEL.get(name, "no algorithmic work model"))
         else:
             kind, _, what = per[0]
             amount = sum(p[1] for p in per) / len(per)
@@ -162,6 +165,8 @@ def roofline_list(trace, works, fp32, workload_tag):
         out.append(e)
     out.sort(key=lambda e: -(e["share"] or 0))
     return out
+NO_MODEL = {"k_cell_order_big": "no algorithmic work model: the block sort of the few cells with more than 256 "
+                                 "pairs (their pair count is not counted)"}
 PARAB_FP64_FLOPS_PER_CELL = 72252.0  # FP64 flops (add + mul + 2 fma) executed per cell by k_parab_ppic on this workload (ncu)
 
 
@@ -189,6 +194,9 @@ def parse():
                     help="e2e leg: the fronts on concurrent compute streams, or one after the other so that "
                          "the first front's outputs go down while the second is computed (eager, or that step "
                          "captured in one CUDA graph)")
+    ap.add_argument("--e2e-compute", choices=("per_front", "shared"), default="per_front",
+                    help="staggered/graph e2e leg: each front's calls on its own compute stream (the fronts "
+                         "computed concurrently, as in the graph step), or both fronts on one compute stream")
     ap.add_argument("--e2e-outputs", choices=("compact", "dense"), default="compact",
                     help="e2e leg: download alpha and the force in the compact form (front_alpha_pack, "
                          "front_csf_force_compact: the same information) or as dense arrays")
@@ -678,15 +686,19 @@ def run_ours(a):
         d2h += sum(o.numel() * o.element_size() for o in outs.values())
     torch.cuda.synchronize()
     # One step's transfers and calls, enqueued on streams forked from `cs` and
-    # joined back to it.  "staggered": the fronts one after the other on one
-    # compute stream, so the first front's outputs go down while the second is
-    # computed; one upload stream (vertices and triangles of every front first,
-    # then the face velocities in front order) and a download stream per front.
+    # joined back to it.  "staggered": one upload stream (vertices and
+    # triangles of every front first, then the face velocities in front order),
+    # a download stream per front, and the compute either on a stream per front
+    # (--e2e-compute per_front: the fronts concurrently, the face upload under
+    # the binning and the fit) or on one stream (shared: the first front's
+    # outputs go down while the second is computed).
     # "concurrent": each front on its own compute stream with a copy stream (face
     # velocities up and alpha down during the binning and the fit).
     stag = a.e2e_mode in ("staggered", "graph")
     if stag:
-        e2e_streams = dict(sd=torch.cuda.Stream(device=dev), up=torch.cuda.Stream(device=dev),
+        sd0 = torch.cuda.Stream(device=dev)
+        e2e_streams = dict(sds=[torch.cuda.Stream(device=dev) for _ in fcs] if a.e2e_compute == "per_front"
+                           else [sd0 for _ in fcs], up=torch.cuda.Stream(device=dev),
                            dns=[torch.cuda.Stream(device=dev) for _ in fcs],
                            sas=[torch.cuda.Stream(device=dev) for _ in fcs],
                            sis=[torch.cuda.Stream(device=dev) for _ in fcs])
@@ -696,9 +708,9 @@ def run_ours(a):
 
     def e2e_enqueue(cs):
         if stag:
-            sd, up, dns = e2e_streams["sd"], e2e_streams["up"], e2e_streams["dns"]
+            sds, up, dns = e2e_streams["sds"], e2e_streams["up"], e2e_streams["dns"]
             sas, sis = e2e_streams["sas"], e2e_streams["sis"]
-            for x in [sd, up] + dns + sas + sis:
+            for x in sds + [up] + dns + sas + sis:
                 x.wait_stream(cs)
             vt_in = [torch.cuda.Event() for _ in fcs]
             faces_in = [torch.cuda.Event() for _ in fcs]
@@ -715,7 +727,7 @@ def run_ours(a):
                 # each front as the DAG of the graph step: alpha beside the PPIC fit,
                 # the interpolation beside both (once the faces are up)
                 alpha_ready, force_ready, vel_ready = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
-                sa, si = sas[f], sis[f]
+                sd, sa, si = sds[f], sas[f], sis[f]
                 with torch.cuda.stream(sd):
                     sd.wait_event(vt_in[f])
                     F.front_bin(fc.ws, v, t, prm)
@@ -758,7 +770,7 @@ def run_ours(a):
                     o["normal"].copy_(fc.normal[:M], non_blocking=True)
                     dn.wait_event(vel_ready)
                     o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
-            for x in [sd, up] + dns + sas + sis:
+            for x in sds + [up] + dns + sas + sis:
                 cs.wait_stream(x)
         else:
             sides, copies = e2e_streams["sides"], e2e_streams["copies"]
@@ -858,9 +870,12 @@ def run_ours(a):
                     "with their keys, kappa, normal, vertex velocities" if compact else
                     ": dense alpha and force, kappa, normal, vertex velocities"),
                 "launch": (("one CUDA graph per step: " if a.e2e_mode == "graph" else "eager calls; ") +
-                           ("the fronts one after the other on one compute stream (the first front's outputs go "
-                            "down while the second is computed), each front's calls as the DAG of the graph step, "
-                            "one upload stream, a download stream per front"
+                           (("each front on its own compute stream (the fronts computed concurrently) "
+                             if a.e2e_compute == "per_front" else
+                             "the fronts one after the other on one compute stream (the first front's outputs go "
+                             "down while the second is computed), ") +
+                            "each front's calls as the DAG of the graph step, one upload stream (vertices and "
+                            "triangles of every front first, then the face velocities), a download stream per front"
                             if stag else
                             "per front a compute stream and a copy stream (faces up and alpha down overlap the "
                             "binning and the fit), the two fronts concurrently"))},

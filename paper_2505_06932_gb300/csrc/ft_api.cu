@@ -49,7 +49,7 @@ void release(ft_workspace* ws) {
                     ws->keys[0], ws->keys[1], ws->vals[0],  ws->vals[1],  ws->rec,     ws->cells,
                     ws->cell_off, ws->cell_cnt, ws->cell_L,   ws->cell_P,   ws->partials,
                     ws->rec32,   ws->cen32,   ws->sys,      ws->fit_info, ws->srec, ws->srec32, ws->scen,
-                    ws->fdesc,   ws->fbase,   ws->fstatus, ws->tri_nrm, ws->planes,
+                    ws->fdesc,   ws->fbase,   ws->fstatus, ws->tri_nrm, ws->tri32, ws->planes,
                     ws->inc_cnt, ws->inc_off, ws->inc_cur, ws->inc_part, ws->inc, ws->cv, ws->vn};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -73,6 +73,7 @@ int allocate(ft_workspace* ws, long long map_cells) {
     e = e ? e : alloc(&ws->tri_off, T, &tot);
     e = e ? e : alloc(&ws->tri_box, 8 * T, &tot);
     e = e ? e : alloc(&ws->tri_nrm, 4 * T, &tot);
+    e = e ? e : alloc(&ws->tri32, 32 * T, &tot);
     if (!ws->batch) {
         ws->planes_cap = ft_plane_count(ws->g);
         e = e ? e : alloc(&ws->planes, (size_t)ws->planes_cap, &tot);

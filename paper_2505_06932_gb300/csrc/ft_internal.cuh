@@ -103,6 +103,7 @@ struct ft_workspace {
     int* tri_off;          // max_nt
     int* tri_box;          // max_nt * 8: lo[3], ext[3], front, 0
     double* tri_nrm;       // max_nt * 4: normal direction of each triangle (x, y, z, 0)
+    float* tri32;          // max_nt * 32 (or null): the FP32 clip's triangle record (k_bin.cu, Tri32)
     double* planes;        // grid plane coordinates of every front (see ft_fdesc)
     long long planes_cap;  // entries allocated in planes
     int* cand_tri;         // max_cand
@@ -261,12 +262,14 @@ __device__ __forceinline__ double ft_plane(double o, double h, long long idx) {
 inline long long ft_plane_count(const ft_grid& g) { return (long long)g.n[0] + g.n[1] + g.n[2] + 3; }
 
 // The float32 clip's error bounds hold while binary64 rounding of a coordinate,
-// in cell units, stays far below float32 rounding: |coordinate| / h <= 1e8 on
-// the whole grid (unit-cube grids: n <= 1e8).
+// in cell units, stays far below float32 rounding: |coordinate| / h <= 2^24 on
+// the whole grid (unit-cube grids: n <= 2^24), so that binary64 plane
+// coordinates X_i = origin + i h (two roundings) are spaced h apart to within
+// 2^-51 * 2^24 h < 1e-8 h.
 inline bool ft_clip32_grid_ok(const ft_grid& g) {
     for (int d = 0; d < 3; d++) {
         const double ext = (g.origin[d] < 0 ? -g.origin[d] : g.origin[d]) + (double)g.n[d] * g.h;
-        if (!(ext / g.h <= 1e8)) return false;
+        if (!(ext / g.h <= 16777216.0)) return false;
     }
     return true;
 }

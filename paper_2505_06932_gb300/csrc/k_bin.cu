@@ -79,13 +79,34 @@ __global__ void __launch_bounds__(kThreads) k_planes(F fr) {
     }
 }
 
+// The FP32 clip's view of a triangle (32 words, eight 16-byte loads): its
+// vertices in cell units relative to the lower planes of its candidate box,
+// t = (x - X_lo) / h in binary64, kept as the float pair hi + lo (hi = t
+// rounded to float, lo = t - hi rounded to float); its normal direction in
+// float; per vertex and axis the index A (relative to the box) of the last
+// plane at or below the coordinate, X_{lo+A} <= x < X_{lo+A+1}; bit 3a+ax of
+// eq set when x == X_{lo+A} exactly.  The exact inside flags of vertex a for
+// candidate cell lo + o then follow from integers alone: x >= X_{lo+o} iff
+// o <= A, x <= X_{lo+o+1} iff o >= A - eq.
+struct __align__(16) Tri32 {
+    float hi[9];  // vertex a, axis ax at 3a + ax
+    float lo[9];
+    float tn[3];  // normal direction
+    int A[9];
+    unsigned eq;
+    int pad;
+};
+static_assert(sizeof(Tri32) == 32 * sizeof(float), "Tri32 is eight 16-byte words");
+
 // Per triangle: the candidate box (cells whose closed extent meets the
 // triangle's closed bounding box) and its size.  tri_box holds lo[3], ext[3]
-// and the owning front per triangle (8 ints).
+// and the owning front per triangle (8 ints); tri32 (when given) the record
+// above.
 template <class F>
 __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int margin, long long max_cand,
                                                         int* __restrict__ tri_cnt, int* __restrict__ tri_box,
-                                                        double* __restrict__ tri_nrm, const unsigned* __restrict__ cells,
+                                                        double* __restrict__ tri_nrm, float* __restrict__ tri32,
+                                                        const unsigned* __restrict__ cells,
                                                         int* __restrict__ idx_map, ft_counters* ctr) {
     const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
     // first the index map entries of the previous binning's cells go back to -1
@@ -172,6 +193,59 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
     int4* bx = reinterpret_cast<int4*>(tri_box + 8 * t);
     bx[0] = make_int4(box[0], box[1], box[2], box[3]);
     bx[1] = make_int4(box[4], box[5], b, 0);
+    if (tri32) {
+        float hv[9], lv[9], tn[3] = {0.f, 0.f, 0.f};
+        int A[9];
+        unsigned eq = 0u;
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            hv[q] = lv[q] = 0.f;
+            A[q] = 0;
+        }
+        if (!err) {
+            const Planes P(D);
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++) {
+                const int lo = box[ax], ext = box[3 + ax];
+                const double xlo = P.at(ax, lo);
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const double x = verts[3 * (long long)vi[a] + ax];
+                    const double tt = __dmul_rn(__dsub_rn(x, xlo), D.inv_h);
+                    const float f = d2f_rn(tt);
+                    hv[3 * a + ax] = f;
+                    lv[3 * a + ax] = d2f_rn(__dsub_rn(tt, (double)f));
+                    // Every vertex lies in [X_lo, X_{lo+ext}]: A in [0, ext - 1].  f is
+                    // within 1e-7 (1 + |f|) of the exact plane-relative position (the
+                    // planes are spaced h apart to within 1e-8 h), so away from an
+                    // integer its floor is A and the coordinate lies on no plane;
+                    // near one, the exact comparisons decide
+                    const float fl = floorf(f), fr = f - fl;
+                    const float m = 1e-5f + 1e-6f * fabsf(f);
+                    int i = (int)fminf(fmaxf(fl, 0.f), (float)(ext - 1));
+                    if (!(fr > m && fr < 1.f - m)) {
+                        const long long kx = okey(x);
+                        while (i > 0 && okey(P.at(ax, lo + i)) > kx) i--;
+                        while (i < ext - 1 && okey(P.at(ax, lo + i + 1)) <= kx) i++;
+                        if (okey(P.at(ax, lo + i)) == kx) eq |= 1u << (3 * a + ax);
+                    }
+                    A[3 * a + ax] = i;
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < 3; d++) tn[d] = d2f_rn(nrm[d]);
+        }
+        float4* o4 = reinterpret_cast<float4*>(tri32 + 32 * t);
+        int4* i4 = reinterpret_cast<int4*>(tri32 + 32 * t);
+        o4[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        o4[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        o4[2] = make_float4(hv[8], lv[0], lv[1], lv[2]);
+        o4[3] = make_float4(lv[3], lv[4], lv[5], lv[6]);
+        o4[4] = make_float4(lv[7], lv[8], tn[0], tn[1]);
+        o4[5] = make_float4(tn[2], __int_as_float(A[0]), __int_as_float(A[1]), __int_as_float(A[2]));
+        i4[6] = make_int4(A[3], A[4], A[5], A[6]);
+        i4[7] = make_int4(A[7], A[8], (int)eq, 0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -479,7 +553,8 @@ __device__ int clip_warp(const double (*v)[3], const Planes& P, const ft_grid& g
                 J.q[c] = (c == ax) ? J.pv : __dadd_rn(J.a[c], __dmul_rn(t, __dsub_rn(J.b[c], J.a[c])));
         }
         __syncwarp();
-        if (alive) {
+        // (a lane whose vertices are all inside keeps its polygon as it is)
+        if (alive && flags != (1u << n) - 1u) {
             int m = 0, k = 0;
             for (int i = 0; i < n && !wide; i++) {
                 if ((cross >> i) & 1u) {
@@ -764,9 +839,12 @@ enum : int { kUndecided = 0, kRejected = 1, kKept = 2 };
 // The float32 clip of triangle (tv, in cell units) against the cell [0, top]:
 // exact flags of the triangle's vertices (bit st: inside for stage st), the
 // polygon left in bufs[*res] (n vertices).  Vertex w: < 0 for a triangle
-// vertex (-(1 + flags)), else the distance bound of a crossing vertex.
-__device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const float top[3], float4 (*b0)[32],
-                        float4 (*b1)[32], int lane, int& n_out, float4 (**res)[32], float& emax) {
+// vertex (-(1 + flags)), else the distance bound of a crossing vertex.  A
+// triangle vertex's coordinates are within kEps (|x|max + W) of the exact ones
+// (ew = kEps W, see k_clip32).
+__device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const float top[3], float ew,
+                        float4 (*b0)[32], float4 (*b1)[32], int lane, int& n_out, float4 (**res)[32],
+                        float& emax) {
     float4(*src)[32] = b0;
     float4(*dst)[32] = b1;
     for (int c = 0; c < 3; c++) src[c][lane] = make_float4(tv[c][0], tv[c][1], tv[c][2], -(float)(1 + vflags[c]));
@@ -793,6 +871,7 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
             if (ins) in |= 1u << i;
         }
         if (in == 0u) return kRejected;  // the polygon dies at this stage (every vertex outside)
+        if (in == (1u << n) - 1u) continue;  // every vertex inside: the stage keeps the polygon as it is
         const unsigned prevf = (in << 1 | in >> (n - 1)) & ((1u << n) - 1u);
         const unsigned cross = in ^ prevf;
         if (__popc(cross) > 2) return kUndecided;
@@ -809,8 +888,8 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
                     a = b;
                     b = tmp;
                 }
-                const float ea = a.w < 0.f ? kEps * fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))) : a.w;
-                const float eb = b.w < 0.f ? kEps * fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z))) : b.w;
+                const float ea = a.w < 0.f ? kEps * fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))) + ew : a.w;
+                const float eb = b.w < 0.f ? kEps * fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z))) + ew : b.w;
                 const float aa = comp(a, ax), ba = comp(b, ax);
                 const float D = ba - aa;
                 const float den = fabsf(D) - 1.01f * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)));
@@ -847,7 +926,7 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
     float e = 0.f;
     for (int i = 0; i < n; i++) {
         const float4 v = src[i][lane];
-        e = fmaxf(e, v.w < 0.f ? kEps * fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))) : v.w);
+        e = fmaxf(e, v.w < 0.f ? kEps * fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))) + ew : v.w);
     }
     // a fragment within its bounds of an upper face may lie in it exactly in binary64
     for (int ax = 0; ax < 3; ax++) {
@@ -855,7 +934,7 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
         for (int i = 0; i < n && all; i++) {
             const float4 v = src[i][lane];
             const float x = comp(v, ax);
-            const float ev = v.w < 0.f ? kEps * fabsf(x) : v.w;
+            const float ev = v.w < 0.f ? kEps * fabsf(x) + ew : v.w;
             all = fabsf(x - top[ax]) <= 2.02f * (ev + kEps * (fabsf(x) + 2.f * fabsf(top[ax]))) + 1e-30f;
         }
         if (all) return kUndecided;
@@ -870,7 +949,7 @@ template <class F>
 __global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* __restrict__ cand_tri,
                                                            const int* __restrict__ tri_off,
                                                            const int* __restrict__ tri_box,
-                                                           const double* __restrict__ tri_nrm,
+                                                           const float* __restrict__ tri32,
                                                            unsigned* __restrict__ keys, unsigned* __restrict__ ranks,
                                                            int* __restrict__ cell_cnt, ft_frag32* __restrict__ rec32,
                                                            ft_counters* ctr, unsigned* __restrict__ undecided) {
@@ -885,42 +964,50 @@ __global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* _
         const int4 bb0 = bx[0], bb1 = bx[1];
         const int e1 = bb1.x, e2 = bb1.y;
         const int b = bb1.z;
-        const int idx[3] = {bb0.x + l / (e1 * e2), bb0.y + (l / e2) % e1, bb0.z + l % e2};
+        const int o[3] = {l / (e1 * e2), (l / e2) % e1, l % e2};  // the cell within the box
         const ft_fdesc& D = fr.desc(b);
         const ft_grid g = D.g;
-        const Planes P(D);
-        const long long tl = t - fr.tri_base(b);
-        double v[3][3];
-        for (int a = 0; a < 3; a++) {
-            const long long vi = D.tris[3 * tl + a];
-            for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
-        }
-        // exact flags of the triangle's vertices and their cell-unit coordinates
-        float tv[3][3], top[3];
+        const float4* tr = reinterpret_cast<const float4*>(tri32 + 32 * (long long)t);
+        const int4* ti = reinterpret_cast<const int4*>(tri32 + 32 * (long long)t);
+        const float4 r0 = tr[0], r1 = tr[1], r2 = tr[2], r3 = tr[3], r4 = tr[4], r5 = tr[5];
+        const int4 A1 = ti[6], A2 = ti[7];
+        const float hv[9] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
+        const float lv[9] = {r2.y, r2.z, r2.w, r3.x, r3.y, r3.z, r3.w, r4.x, r4.y};
+        const int A[9] = {__float_as_int(r5.y), __float_as_int(r5.z), __float_as_int(r5.w), A1.x, A1.y, A1.z,
+                          A1.w, A2.x, A2.y};
+        const unsigned eq = (unsigned)A2.z;
+        // exact flags of the triangle's vertices (integer comparisons with the
+        // record's plane indices) and their cell-unit coordinates (hi - o) + lo,
+        // two roundings of about |x|.  Their error against (x - X_i) / h, X_i the
+        // binary64 plane, is at most kEps |x| + ew: the pair carries the
+        // box-relative position to about 4e-15 of W (the box's largest extent + 1),
+        // and binary64 planes are spaced h apart to within 1e-8 cells (the far
+        // plane (X_i+1 - X_i) / h is taken as 1, within its own bound kEps).
+        float tv[3][3];
+        const float top[3] = {1.f, 1.f, 1.f};
         unsigned vflags[3] = {0u, 0u, 0u};
         unsigned on_top = 7u;  // axes whose upper plane holds all three vertices
+#pragma unroll
         for (int ax = 0; ax < 3; ax++) {
-            const double lo = P.at(ax, idx[ax]), hi = P.at(ax, idx[ax] + 1);
-            const long long klo = okey(lo), khi = okey(hi);
-            top[ax] = d2f_rn(__dmul_rn(__dsub_rn(hi, lo), D.inv_h));
+#pragma unroll
             for (int a = 0; a < 3; a++) {
-                const long long k = okey(v[a][ax]);
-                if (k >= klo) vflags[a] |= 1u << (2 * ax);
-                if (k <= khi) vflags[a] |= 1u << (2 * ax + 1);
-                if (k != khi) on_top &= ~(1u << ax);
-                tv[a][ax] = d2f_rn(__dmul_rn(__dsub_rn(v[a][ax], lo), D.inv_h));
+                const int Aa = A[3 * a + ax];
+                const int ea = (int)((eq >> (3 * a + ax)) & 1u);
+                if (o[ax] <= Aa) vflags[a] |= 1u << (2 * ax);
+                if (o[ax] >= Aa - ea) vflags[a] |= 1u << (2 * ax + 1);
+                if (!(ea && Aa == o[ax] + 1)) on_top &= ~(1u << ax);
+                tv[a][ax] = __fadd_rn(__fsub_rn(hv[3 * a + ax], (float)o[ax]), lv[3 * a + ax]);
             }
         }
+        const float ew = 1e-8f + 4e-15f * (float)(max(max(bb0.w, bb1.x), bb1.y) + 1);
         int n = 0;
         float4(*poly)[32] = nullptr;
         float emax = 0.f;
-        int verdict = on_top ? kRejected : clip_f32(tv, vflags, top, s_poly[w][0], s_poly[w][1], lane, n, &poly,
+        int verdict = on_top ? kRejected : clip_f32(tv, vflags, top, ew, s_poly[w][0], s_poly[w][1], lane, n, &poly,
                                                     emax);
         unsigned key = FT_SENTINEL;
         ft_frag32 f;
-        const double2* tnp = reinterpret_cast<const double2*>(tri_nrm + 4 * (long long)t);
-        const double2 tn01 = tnp[0], tn2 = tnp[1];
-        const float tn[3] = {d2f_rn(tn01.x), d2f_rn(tn01.y), d2f_rn(tn2.x)};
+        const float tn[3] = {r4.z, r4.w, r5.x};
         if (verdict == kKept && emax > kEmaxRecord) verdict = kUndecided;  // ill-conditioned: record in float64
         if (verdict == kKept) {
             float absum;
@@ -949,6 +1036,7 @@ __global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* _
         }
         if (verdict == kKept) {
             rec32[c] = f;
+            const int idx[3] = {bb0.x + o[0], bb0.y + o[1], bb0.z + o[2]};
             key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
         }
         keys[c] = key;
@@ -964,21 +1052,23 @@ template <class F>
 cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params* p, cudaStream_t s) {
     const int margin = 2 + (int)ceil(p->delta_max_h);
     const unsigned nb = (unsigned)((T + kThreads - 1) / kThreads);
+    // the FP32 form needs float records; a workspace without them computes float64 records
+    const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
+    const bool clip32 = fp32 && ws->clip32_ok && ws->tri32 != nullptr;
     // (always launched: it also clears the index map of the previous binning, and sets T)
     count_launches(1);
     {
         Trace t(s, "k_tri_setup");
         k_tri_setup<F><<<nb ? nb : 1, kThreads, 0, s>>>(fr, T, margin, ws->max_cand, ws->tri_cnt, ws->tri_box,
-                                                        ws->tri_nrm, ws->cells, ws->idx_map, ws->ctr);
+                                                        ws->tri_nrm, clip32 ? ws->tri32 : nullptr, ws->cells,
+                                                        ws->idx_map, ws->ctr);
     }
     // candidate ranges in triangle order, so that slot order is triangle order
     cudaError_t e = launch_candidates(ws, s);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    // the FP32 form needs float records; a workspace without them computes float64 records
-    const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     ws->last_precision = fp32 ? FT_FP32C : FT_FP64;
-    if (fp32 && ws->clip32_ok) {
+    if (clip32) {
         // a grid-stride loop: at most the blocks that are resident at once (the
         // polygon buffers limit them), so that no block waits for a second wave
         static int occ = 0;
@@ -993,7 +1083,7 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
         {
             Trace t(s, "k_clip32");
             k_clip32<F><<<ws->sm_count * bps, kClip32Threads, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
-                                                                      ws->tri_nrm, ws->keys[0], ws->vals[0],
+                                                                      ws->tri32, ws->keys[0], ws->vals[0],
                                                                       ws->cell_cnt, ws->rec32, ws->ctr, undecided);
         }
         Trace t(s, "k_clip_list");
