@@ -253,6 +253,19 @@ __device__ __forceinline__ int ft_warp_sum_i(int v) {
     return v;
 }
 
+// float -> double (exact) with integer operations: on this GPU the conversion
+// instruction runs on the float64 pipe at the float64 rate.  Zero and normal
+// floats are widened here; anything else takes the hardware conversion.
+__device__ __forceinline__ double ft_f2d(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if ((b << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (b & 0x80000000u) | ((e - 127u + 1023u) << 20) | ((b & 0x7fffffu) >> 3);
+    const unsigned lo = (b & 7u) << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // plane coordinate origin + idx*h, rounded once per operation (never fused)
 __device__ __forceinline__ double ft_plane(double o, double h, long long idx) {
     return __dadd_rn(o, __dmul_rn((double)idx, h));

@@ -175,9 +175,10 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
     tri_cnt[t] = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
     // normal direction (orientation of every fragment of the triangle; zero if
     // degenerate): twice the area vector in units of h^2.  Only its direction
-    // matters -- the moments use ratios of areas signed along it.
+    // matters -- the moments use ratios of areas signed along it.  (The FP32
+    // clip's record carries its own float normal instead.)
     double nrm[3] = {0.0, 0.0, 0.0};
-    if (!err) {
+    if (!err && !tri32) {
         double e1[3], e2[3];
         for (int d = 0; d < 3; d++) {
             e1[d] = (verts[3 * (long long)vi[1] + d] - verts[3 * (long long)vi[0] + d]) * D.inv_h;
@@ -187,9 +188,11 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
         nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
         nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
     }
-    double2* nb = reinterpret_cast<double2*>(tri_nrm + 4 * t);
-    nb[0] = make_double2(nrm[0], nrm[1]);
-    nb[1] = make_double2(nrm[2], 0.0);
+    if (!tri32) {
+        double2* nb = reinterpret_cast<double2*>(tri_nrm + 4 * t);
+        nb[0] = make_double2(nrm[0], nrm[1]);
+        nb[1] = make_double2(nrm[2], 0.0);
+    }
     int4* bx = reinterpret_cast<int4*>(tri_box + 8 * t);
     bx[0] = make_int4(box[0], box[1], box[2], box[3]);
     bx[1] = make_int4(box[4], box[5], b, 0);
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
                     const double tt = __dmul_rn(__dsub_rn(x, xlo), D.inv_h);
                     const float f = d2f_rn(tt);
                     hv[3 * a + ax] = f;
-                    lv[3 * a + ax] = d2f_rn(__dsub_rn(tt, (double)f));
+                    lv[3 * a + ax] = d2f_rn(__dsub_rn(tt, ft_f2d(f)));
                     // Every vertex lies in [X_lo, X_{lo+ext}]: A in [0, ext - 1].  f is
                     // within 1e-7 (1 + |f|) of the exact plane-relative position (the
                     // planes are spaced h apart to within 1e-8 h), so away from an
@@ -232,8 +235,22 @@ __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int m
                     A[3 * a + ax] = i;
                 }
             }
+            // the normal direction from the float-pair edges, each 2x2 determinant
+            // with Kahan's fused-multiply-add correction (accurate despite cancellation)
+            float e1[3], e2[3];
 #pragma unroll
-            for (int d = 0; d < 3; d++) tn[d] = d2f_rn(nrm[d]);
+            for (int d = 0; d < 3; d++) {
+                e1[d] = __fadd_rn(__fsub_rn(hv[3 + d], hv[d]), __fsub_rn(lv[3 + d], lv[d]));
+                e2[d] = __fadd_rn(__fsub_rn(hv[6 + d], hv[d]), __fsub_rn(lv[6 + d], lv[d]));
+            }
+            auto det2 = [](float a, float b, float c, float d) {  // a d - b c
+                const float w = __fmul_rn(b, c);
+                const float e = __fmaf_rn(-b, c, w);
+                return __fadd_rn(__fmaf_rn(a, d, -w), e);
+            };
+            tn[0] = det2(e1[1], e1[2], e2[1], e2[2]);
+            tn[1] = det2(e1[2], e1[0], e2[2], e2[0]);
+            tn[2] = det2(e1[0], e1[1], e2[0], e2[1]);
         }
         float4* o4 = reinterpret_cast<float4*>(tri32 + 32 * t);
         int4* i4 = reinterpret_cast<int4*>(tri32 + 32 * t);
@@ -455,6 +472,62 @@ __device__ void frag_moments32(const double (*p)[3], int n, const float q0[3], c
         for (int d = 0; d < 3; d++) f.c[d] = q0[d];
     }
     for (int d = 0; d < 3; d++) f.an[d] = an[d];
+}
+
+// frag_moments32 spread over a warp (warp-collective): lane m takes fan
+// triangle (p0, p_m, p_m+1), m = 1 .. n-2 (n <= 33), and the thirteen sums are
+// reduced over the lanes; every lane ends with the record.  The terms are those
+// of frag_moments32; only the order of their float32 sums differs.
+__device__ void frag_moments32_warp(const double (*p)[3], int n, const float q0[3], const float tn[3], float inv_h,
+                                    int lane, ft_frag32& f) {
+    float v[13];
+#pragma unroll
+    for (int r = 0; r < 13; r++) v[r] = 0.f;
+    const int m = lane + 1;
+    if (m + 1 < n) {
+        float e1[3], e2[3];
+        for (int d = 0; d < 3; d++) {
+            e1[d] = d2f_rn(p[m][d] - p[0][d]) * inv_h;
+            e2[d] = d2f_rn(p[m + 1][d] - p[0][d]) * inv_h;
+        }
+        const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+        const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+        const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+        v[0] = 0.5f * cr0;
+        v[1] = 0.5f * cr1;
+        v[2] = 0.5f * cr2;
+        const float a = 0.5f * (cr0 * tn[0] + cr1 * tn[1] + cr2 * tn[2]);
+        v[3] = a;
+        const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+        const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
+        for (int d = 0; d < 3; d++) v[4 + d] = a3 * s[d];
+        v[7] = a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+        v[8] = a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+        v[9] = a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+        v[10] = a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+        v[11] = a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+        v[12] = a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < 13; r++) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
+    const float As = v[3];
+    if (As > 0.f) {
+        const float ia = 1.f / As;
+        const float c[3] = {v[4] * ia, v[5] * ia, v[6] * ia};
+        f.k[0] = v[7] * ia - c[0] * c[0];
+        f.k[1] = v[8] * ia - c[1] * c[1];
+        f.k[2] = v[9] * ia - c[2] * c[2];
+        f.k[3] = v[10] * ia - c[0] * c[1];
+        f.k[4] = v[11] * ia - c[0] * c[2];
+        f.k[5] = v[12] * ia - c[1] * c[2];
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d] + c[d];
+    } else {
+        for (int d = 0; d < 6; d++) f.k[d] = 0.f;
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d];
+    }
+    for (int d = 0; d < 3; d++) f.an[d] = v[d];
 }
 
 // One queued edge-plane crossing: the edge prev -> cur of a lane's polygon and
@@ -711,29 +784,146 @@ __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
 }
 
 // The pairs the FP32 clip left to the binary64 clip (ctr->clip_f64 slots in
-// list): few and often near-degenerate, so one warp per block with polygon
-// buffers in shared memory of twice the fast path's capacity (the wide serial
-// fallback, in local memory, is then practically never taken: no local-memory
-// round trips on a latency-bound pass).
-constexpr int kListV = 24;                   // polygon capacity (twice the fast path's; beyond it the wide serial clip)
-constexpr int kPolyStride = kListV * 3 + 1;  // doubles per lane's buffer (padded against bank conflicts)
+// list): few, so one warp per pair, the polygon one vertex per lane.  Each
+// stage is the Sutherland-Hodgman step written lane-parallel: lane i owns the
+// edge from vertex i-1 (cyclically) to vertex i and computes its crossing with
+// the canonical operations (t = (pv - a)/(b - a), q = a + t (b - a), the clipped
+// coordinate set to pv); an exclusive scan of the per-lane output counts
+// (crossing first, then the vertex if inside) places the outputs in exactly the
+// serial order.  A polygon that would outgrow 32 vertices is redone by the wide
+// serial clip on one lane.  The moments (float32 record) and the canonical area
+// test run on lane 0, as for the binary64 records of the other paths.
+constexpr int kListWarps = 4;
 template <class F>
-__global__ void __launch_bounds__(32) k_clip_list(F fr, const int* __restrict__ cand_tri,
-                                                  const int* __restrict__ tri_off, const int* __restrict__ tri_box,
-                                                  const double* __restrict__ tri_nrm, unsigned* __restrict__ keys,
-                                                  unsigned* __restrict__ ranks, int* __restrict__ cell_cnt,
-                                                  ft_frag* __restrict__ rec, ft_frag32* __restrict__ rec32,
-                                                  const ft_counters* ctr, const unsigned* __restrict__ list) {
-    __shared__ ClipJob s_jobs[kClipJobs];
-    __shared__ double s_A[32 * kPolyStride], s_B[32 * kPolyStride];
-    const int lane = threadIdx.x;
-    const long long C = ctr->clip_f64;
-    for (long long cb = (long long)blockIdx.x * 32; cb < C; cb += (long long)gridDim.x * 32) {
-        const bool active = cb + lane < C;
-        const long long c = active ? (long long)list[cb + lane] : 0;
-        clip_slot_warp<kListV>(fr, c, active, s_jobs, cand_tri, tri_off, tri_box, tri_nrm, keys, ranks, cell_cnt, rec,
-                               rec32, nullptr, 1, reinterpret_cast<double(*)[3]>(s_A + lane * kPolyStride),
-                       reinterpret_cast<double(*)[3]>(s_B + lane * kPolyStride));
+__global__ void __launch_bounds__(kListWarps * 32) k_clip_list(F fr, const int* __restrict__ cand_tri,
+                                                              const int* __restrict__ tri_off,
+                                                              const int* __restrict__ tri_box,
+                                                              const float* __restrict__ tri32,
+                                                              unsigned* __restrict__ keys,
+                                                              unsigned* __restrict__ ranks,
+                                                              int* __restrict__ cell_cnt,
+                                                              ft_frag32* __restrict__ rec32, const ft_counters* ctr,
+                                                              const unsigned* __restrict__ list) {
+    __shared__ double s_poly[kListWarps][2][32][3];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long L = ctr->clip_f64;
+    for (long long j = (long long)blockIdx.x * kListWarps + w; j < L; j += (long long)gridDim.x * kListWarps) {
+        const long long c = (long long)list[j];
+        const int t = cand_tri[c];
+        const int l = (int)(c - tri_off[t]);
+        const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
+        const int4 b0 = bx[0], b1 = bx[1];
+        const int e1 = b1.x, e2 = b1.y, b = b1.z;
+        const int idx[3] = {b0.x + l / (e1 * e2), b0.y + (l / e2) % e1, b0.z + l % e2};
+        const ft_fdesc& D = fr.desc(b);
+        const ft_grid g = D.g;
+        const Planes P(D);
+        const long long tl = t - fr.tri_base(b);
+        // lane i < n holds polygon vertex i; the triangle first
+        double x[3] = {0.0, 0.0, 0.0};
+        if (lane < 3) {
+            const long long vi = D.tris[3 * tl + lane];
+            for (int d = 0; d < 3; d++) x[d] = D.verts[3 * vi + d];
+        }
+        int n = 3;
+        bool alive = true, wide = false;
+        for (int st = 0; st < 6 && alive && !wide; st++) {
+            const int ax = st >> 1;
+            const bool ge = (st & 1) == 0;
+            const double pv = P.at(ax, idx[ax] + (st & 1));
+            const long long kp = okey(pv);
+            const bool act = lane < n;
+            const long long kc = okey(x[ax]);
+            const bool cin = act && (ge ? (kc >= kp) : (kc <= kp));
+            const int pl = (lane == 0) ? n - 1 : lane - 1;  // the edge's first vertex
+            double pr[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) pr[d] = __shfl_sync(0xffffffffu, x[d], pl);
+            const bool pin = __shfl_sync(0xffffffffu, cin ? 1 : 0, pl) != 0;
+            const bool cross = act && (cin != pin);
+            double q[3] = {0.0, 0.0, 0.0};
+            if (cross) {
+                const double tt = __ddiv_rn(__dsub_rn(pv, pr[ax]), __dsub_rn(x[ax], pr[ax]));
+#pragma unroll
+                for (int d = 0; d < 3; d++) q[d] = (d == ax) ? pv : __dadd_rn(pr[d], __dmul_rn(tt, __dsub_rn(x[d], pr[d])));
+            }
+            const int cnt = (cross ? 1 : 0) + (cin ? 1 : 0);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int m = __shfl_sync(0xffffffffu, incl, 31);
+            if (m > 32) {
+                wide = true;
+                break;
+            }
+            if (m < 3) {
+                alive = false;
+                break;
+            }
+            double(*dst)[3] = s_poly[w][st & 1];
+            const int pos = incl - cnt;
+            if (cross)
+                for (int d = 0; d < 3; d++) dst[pos][d] = q[d];
+            if (cin)
+                for (int d = 0; d < 3; d++) dst[pos + (cross ? 1 : 0)][d] = x[d];
+            __syncwarp();
+            n = m;
+            if (lane < n)
+                for (int d = 0; d < 3; d++) x[d] = dst[lane][d];
+            __syncwarp();
+        }
+        const double(*poly)[3] = s_poly[w][1];  // the last stage's output
+        if (wide) {
+            // the wide serial clip of the triangle, on lane 0
+            int nw = 0;
+            if (lane == 0) {
+                double v[3][3];
+                for (int a = 0; a < 3; a++) {
+                    const long long vi = D.tris[3 * tl + a];
+                    for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
+                }
+                nw = canon_stages_wide(v, g, idx, s_poly[w][0]);
+            }
+            n = __shfl_sync(0xffffffffu, nw, 0);
+            alive = n >= 3;
+            poly = s_poly[w][0];
+        } else if (alive) {
+            // a polygon lying in an upper face of the cell belongs to the next cell
+            for (int ax = 0; ax < 3; ax++) {
+                const long long ku = okey(P.at(ax, idx[ax] + 1));
+                const unsigned on = __ballot_sync(0xffffffffu, lane < n && okey(x[ax]) == ku);
+                if (on == (n == 32 ? 0xffffffffu : ((1u << n) - 1u))) alive = false;
+            }
+        }
+        __syncwarp();
+        ft_frag32 f;
+        if (alive) {
+            const float4 r4 = reinterpret_cast<const float4*>(tri32 + 32 * (long long)t)[4];
+            const float r5x = tri32[32 * (long long)t + 20];
+            const float tn[3] = {r4.z, r4.w, r5x};
+            const float ih = d2f_rn(D.inv_h);
+            float q0[3];
+            for (int d = 0; d < 3; d++) q0[d] = d2f_rn(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
+            frag_moments32_warp(poly, n, q0, tn, ih, lane, f);
+        }
+        if (lane == 0) {
+            unsigned key = FT_SENTINEL;
+            if (alive) {
+                // the moments' own area vector certifies the canonical "area vector
+                // is not zero" condition whenever it exceeds its rounding bound by far
+                const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
+                if ((a > 1e-4f) || canon_area_nonzero(poly, n)) {
+                    rec32[c] = f;
+                    key = (unsigned)(fr.key_base(b) + ((long long)idx[0] * g.n[1] + idx[1]) * g.n[2] + idx[2]);
+                }
+            }
+            keys[c] = key;
+            if (key != FT_SENTINEL) ranks[c] = (unsigned)atomicAdd(&cell_cnt[key], 1);
+        }
+        __syncwarp();
     }
 }
 
@@ -1087,9 +1277,9 @@ cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params
                                                                       ws->cell_cnt, ws->rec32, ws->ctr, undecided);
         }
         Trace t(s, "k_clip_list");
-        k_clip_list<F><<<ws->sm_count * 4, 32, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box, ws->tri_nrm,
-                                                       ws->keys[0], ws->vals[0], ws->cell_cnt, ws->rec, ws->rec32,
-                                                       ws->ctr, undecided);
+        k_clip_list<F><<<ws->sm_count * 8, kListWarps * 32, 0, s>>>(fr, ws->cand_tri, ws->tri_off, ws->tri_box,
+                                                                    ws->tri32, ws->keys[0], ws->vals[0],
+                                                                    ws->cell_cnt, ws->rec32, ws->ctr, undecided);
         return cudaGetLastError();
     }
     Trace t(s, "k_clip");

@@ -656,19 +656,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
     if (lane == 0 && pairs_total) atomicAdd((unsigned long long*)&ctr->fit_pairs, pairs_total);
 }
 
-// float -> double (exact) with integer operations: on this GPU the conversion
-// instruction runs on the float64 pipe at the float64 rate.  Zero and normal
-// floats are widened here; anything else takes the hardware conversion.
-__device__ __forceinline__ double f2d(float x) {
-    const unsigned b = __float_as_uint(x);
-    const unsigned e = (b >> 23) & 0xffu;
-    if ((b << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));
-    if (e == 0u || e == 0xffu) return (double)x;
-    const unsigned hi = (b & 0x80000000u) | ((e - 127u + 1023u) << 20) | ((b & 0x7fffffu) >> 3);
-    const unsigned lo = (b & 7u) << 29;
-    return __hiloint2double((int)hi, (int)lo);
-}
-
 // LDL^T solve of the leading N x N block of the packed symmetric 6x6 system
 // (N a compile-time size: every loop unrolls, the factors stay in registers).
 // Returns the smallest pivot relative to the trace (-1 if a pivot is not > 0).
@@ -720,6 +707,88 @@ __device__ __forceinline__ double ldlt_solve(const double (&S)[21], const double
     return minp / tr;
 }
 
+// Double-float numbers hi + lo (Dekker's double-length arithmetic: two-sum and
+// the fused-multiply-add exact product, renormalised after every operation),
+// about 48 significant bits on the float32 pipe.  The FP32 form solves its
+// normal equations in them: their sums arrive as compensated float pairs, and
+// on this GPU a float64 instruction costs the SM sub-partition as much as
+// dozens of float32 ones.
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl df_fast(float s, float e) {  // |s| >= |e|
+    const float h = __fadd_rn(s, e);
+    return dfl{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl df_norm(float a, float b) {
+    float s, e;
+    two_sum(a, b, s, e);
+    return dfl{s, e};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return df_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, dfl{-b.hi, -b.lo}); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);  // the product's rounding error, exactly
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast(p, e);
+}
+__device__ __forceinline__ dfl df_rcp(dfl b) {  // 1 / b: a float quotient and one correction
+    const float q1 = 1.f / b.hi;
+    const dfl r = df_sub(dfl{1.f, 0.f}, df_mul(dfl{q1, 0.f}, b));
+    return df_fast(q1, __fmul_rn(r.hi, q1));
+}
+
+// ldlt_solve in double-float (same steps; the relative pivot in float).
+template <int N>
+__device__ __forceinline__ float ldlt_solve_df(const dfl (&S)[21], const dfl (&B)[6], dfl (&a)[6]) {
+    dfl Lm[N][N], d[N], inv_d[N];
+    float tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < N; i++) tr += S[packed(i, i)].hi;
+    float minp = INFINITY;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        dfl dj = S[packed(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; k++) dj = df_sub(dj, df_mul(df_mul(Lm[j][k], Lm[j][k]), d[k]));
+        d[j] = dj;
+        minp = fminf(minp, dj.hi);
+        ok = ok && (dj.hi > 0.f);
+        inv_d[j] = df_rcp(dj);
+#pragma unroll
+        for (int i = j + 1; i < N; i++) {
+            dfl v = S[packed(j, i)];
+#pragma unroll
+            for (int k = 0; k < j; k++) v = df_sub(v, df_mul(df_mul(Lm[i][k], Lm[j][k]), d[k]));
+            Lm[i][j] = df_mul(v, inv_d[j]);
+        }
+    }
+    if (!ok) return -1.f;
+    dfl y[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        dfl v = B[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) v = df_sub(v, df_mul(Lm[i][k], y[k]));
+        y[i] = v;
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
+        dfl v = df_mul(y[i], inv_d[i]);
+#pragma unroll
+        for (int k = i + 1; k < N; k++) v = df_sub(v, df_mul(Lm[k][i], a[k]));
+        a[i] = v;
+    }
+    return minp / tr;
+}
+
 // One thread per cell on kSolveLanes lanes of each warp, in blocks of
 // kSolveThreads.  The solve is bound by the float64 pipe of the SM
 // sub-partition each warp runs on; spreading the cells over more warps with
@@ -744,38 +813,52 @@ __global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cel
     const long long wid = ((long long)blockIdx.x * kSolveThreads + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * kSolveThreads) >> 5;
     for (long long m = wid * kSolveLanes + lane; m < M; m += nw * kSolveLanes) {
-        double S[21], B[6], n[3], z0;
+        double n[3], z0;
+        double a[6] = {0, 0, 0, 0, 0, 0};
+        int st = fit_info[2 * m + 1];
         if (fp32) {
+            // the FP32 form: the compensated pairs as double-float numbers
             const float* v = reinterpret_cast<const float*>(sys[m].v);
+            dfl S[21], B[6], ad[6];
 #pragma unroll
-            for (int r = 0; r < 21; r++) S[r] = f2d(v[2 * r]) + f2d(v[2 * r + 1]);
+            for (int r = 0; r < 21; r++) S[r] = df_norm(v[2 * r], v[2 * r + 1]);
 #pragma unroll
-            for (int r = 0; r < 6; r++) B[r] = f2d(v[42 + 2 * r]) + f2d(v[43 + 2 * r]);
-            z0 = f2d(v[60]);
+            for (int r = 0; r < 6; r++) B[r] = df_norm(v[42 + 2 * r], v[43 + 2 * r]);
+            z0 = ft_f2d(v[60]);
+            const float rel = ldlt_solve_df<6>(S, B, ad);
+            if (rel >= 1e-12f) {
+#pragma unroll
+                for (int r = 0; r < 6; r++) a[r] = ft_f2d(ad[r].hi) + ft_f2d(ad[r].lo);
+            } else {
+                // singular: plane fit on the leading 3x3 block, kappa = 0
+                dfl a3[6];
+                if (ldlt_solve_df<3>(S, B, a3) > 0.f)
+                    for (int r = 0; r < 3; r++) a[r] = ft_f2d(a3[r].hi) + ft_f2d(a3[r].lo);
+                st |= FT_FIT_SINGULAR;
+            }
         } else {
+            double S[21], B[6];
 #pragma unroll
             for (int r = 0; r < 21; r++) S[r] = sys[m].v[r];
 #pragma unroll
             for (int r = 0; r < 6; r++) B[r] = sys[m].v[21 + r];
             z0 = sys[m].v[30];
+            const double rel = ldlt_solve<6>(S, B, a);
+            if (!(rel >= 1e-12)) {
+                // singular: plane fit on the leading 3x3 block, kappa = 0
+                for (int r = 0; r < 6; r++) a[r] = 0.0;
+                double a3[6] = {0, 0, 0, 0, 0, 0};
+                if (ldlt_solve<3>(S, B, a3) > 0.0) {
+                    a[0] = a3[0];
+                    a[1] = a3[1];
+                    a[2] = a3[2];
+                }
+                st |= FT_FIT_SINGULAR;
+            }
         }
         sys_normal(sys[m], fp32 != 0, n);
-        int st = fit_info[2 * m + 1];
         double t1[3], t2[3];
         basis<double>(n, t1, t2);
-        double a[6] = {0, 0, 0, 0, 0, 0};
-        const double rel = ldlt_solve<6>(S, B, a);
-        if (!(rel >= 1e-12)) {
-            // singular: plane fit on the leading 3x3 block, kappa = 0
-            for (int r = 0; r < 6; r++) a[r] = 0.0;
-            double a3[6] = {0, 0, 0, 0, 0, 0};
-            if (ldlt_solve<3>(S, B, a3) > 0.0) {
-                a[0] = a3[0];
-                a[1] = a3[1];
-                a[2] = a3[2];
-            }
-            st |= FT_FIT_SINGULAR;
-        }
         a[0] += z0;  // undo the height shift (it changes a1 only)
         // mean curvature of the graph z = P(x, y) at the origin, kappa = div n
         const double g2 = 1.0 + a[1] * a[1] + a[2] * a[2];
