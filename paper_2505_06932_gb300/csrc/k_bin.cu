@@ -474,62 +474,6 @@ __device__ void frag_moments32(const double (*p)[3], int n, const float q0[3], c
     for (int d = 0; d < 3; d++) f.an[d] = an[d];
 }
 
-// frag_moments32 spread over a warp (warp-collective): lane m takes fan
-// triangle (p0, p_m, p_m+1), m = 1 .. n-2 (n <= 33), and the thirteen sums are
-// reduced over the lanes; every lane ends with the record.  The terms are those
-// of frag_moments32; only the order of their float32 sums differs.
-__device__ void frag_moments32_warp(const double (*p)[3], int n, const float q0[3], const float tn[3], float inv_h,
-                                    int lane, ft_frag32& f) {
-    float v[13];
-#pragma unroll
-    for (int r = 0; r < 13; r++) v[r] = 0.f;
-    const int m = lane + 1;
-    if (m + 1 < n) {
-        float e1[3], e2[3];
-        for (int d = 0; d < 3; d++) {
-            e1[d] = d2f_rn(p[m][d] - p[0][d]) * inv_h;
-            e2[d] = d2f_rn(p[m + 1][d] - p[0][d]) * inv_h;
-        }
-        const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
-        const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
-        const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
-        v[0] = 0.5f * cr0;
-        v[1] = 0.5f * cr1;
-        v[2] = 0.5f * cr2;
-        const float a = 0.5f * (cr0 * tn[0] + cr1 * tn[1] + cr2 * tn[2]);
-        v[3] = a;
-        const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
-        const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
-        for (int d = 0; d < 3; d++) v[4 + d] = a3 * s[d];
-        v[7] = a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
-        v[8] = a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
-        v[9] = a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
-        v[10] = a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
-        v[11] = a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
-        v[12] = a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int r = 0; r < 13; r++) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
-    const float As = v[3];
-    if (As > 0.f) {
-        const float ia = 1.f / As;
-        const float c[3] = {v[4] * ia, v[5] * ia, v[6] * ia};
-        f.k[0] = v[7] * ia - c[0] * c[0];
-        f.k[1] = v[8] * ia - c[1] * c[1];
-        f.k[2] = v[9] * ia - c[2] * c[2];
-        f.k[3] = v[10] * ia - c[0] * c[1];
-        f.k[4] = v[11] * ia - c[0] * c[2];
-        f.k[5] = v[12] * ia - c[1] * c[2];
-        for (int d = 0; d < 3; d++) f.c[d] = q0[d] + c[d];
-    } else {
-        for (int d = 0; d < 6; d++) f.k[d] = 0.f;
-        for (int d = 0; d < 3; d++) f.c[d] = q0[d];
-    }
-    for (int d = 0; d < 3; d++) f.an[d] = v[d];
-}
-
 // One queued edge-plane crossing: the edge prev -> cur of a lane's polygon and
 // the plane value; the result q is written back for the owning lane.
 struct ClipJob {
@@ -784,16 +728,79 @@ __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
 }
 
 // The pairs the FP32 clip left to the binary64 clip (ctr->clip_f64 slots in
-// list): few, so one warp per pair, the polygon one vertex per lane.  Each
-// stage is the Sutherland-Hodgman step written lane-parallel: lane i owns the
-// edge from vertex i-1 (cyclically) to vertex i and computes its crossing with
-// the canonical operations (t = (pv - a)/(b - a), q = a + t (b - a), the clipped
-// coordinate set to pv); an exclusive scan of the per-lane output counts
-// (crossing first, then the vertex if inside) places the outputs in exactly the
-// serial order.  A polygon that would outgrow 32 vertices is redone by the wide
-// serial clip on one lane.  The moments (float32 record) and the canonical area
-// test run on lane 0, as for the binary64 records of the other paths.
+// list): few, so a segment of kSeg lanes per pair (two pairs per warp), the
+// polygon one vertex per lane.  Each stage is the Sutherland-Hodgman step
+// written lane-parallel: lane i of a segment owns the edge from vertex i-1
+// (cyclically) to vertex i and computes its crossing with the canonical
+// operations (t = (pv - a)/(b - a), q = a + t (b - a), the clipped coordinate
+// set to pv); an exclusive scan of the per-lane output counts (crossing first,
+// then the vertex if inside) places the outputs in exactly the serial order.  A
+// polygon that would outgrow the segment is redone by the wide serial clip on
+// the segment's first lane.  The float32 record's moments are spread over the
+// segment's lanes; the canonical area test runs on its first lane.  Two pairs
+// per warp halve the float64 instructions per pair (a float64 warp instruction
+// costs the same however few lanes it has).
 constexpr int kListWarps = 4;
+constexpr int kSeg = 16;                 // lanes per listed pair (polygons up to 16 vertices)
+constexpr int kSegPerWarp = 32 / kSeg;
+// frag_moments32 spread over a segment of kSeg lanes (collective over the
+// warp, each segment with its own polygon): lane m-1 of the segment takes fan
+// triangle (p0, p_m, p_m+1), m = 1 .. n-2 (n <= kSeg + 1; n = 0: no polygon),
+// and the thirteen sums are reduced over the segment; every lane of it ends
+// with the record.  The terms are those of frag_moments32; only the order of
+// their float32 sums differs.
+__device__ void frag_moments32_seg(const double (*p)[3], int n, const float q0[3], const float tn[3], float inv_h,
+                                   int lane, ft_frag32& f) {
+    float v[13];
+#pragma unroll
+    for (int r = 0; r < 13; r++) v[r] = 0.f;
+    const int m = lane + 1;
+    if (m + 1 < n) {
+        float e1[3], e2[3];
+        for (int d = 0; d < 3; d++) {
+            e1[d] = d2f_rn(p[m][d] - p[0][d]) * inv_h;
+            e2[d] = d2f_rn(p[m + 1][d] - p[0][d]) * inv_h;
+        }
+        const float cr0 = e1[1] * e2[2] - e1[2] * e2[1];
+        const float cr1 = e1[2] * e2[0] - e1[0] * e2[2];
+        const float cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+        v[0] = 0.5f * cr0;
+        v[1] = 0.5f * cr1;
+        v[2] = 0.5f * cr2;
+        const float a = 0.5f * (cr0 * tn[0] + cr1 * tn[1] + cr2 * tn[2]);
+        v[3] = a;
+        const float s[3] = {e1[0] + e2[0], e1[1] + e2[1], e1[2] + e2[2]};
+        const float a3 = a * (1.f / 3.f), a12 = a * (1.f / 12.f);
+        for (int d = 0; d < 3; d++) v[4 + d] = a3 * s[d];
+        v[7] = a12 * (s[0] * s[0] + e1[0] * e1[0] + e2[0] * e2[0]);
+        v[8] = a12 * (s[1] * s[1] + e1[1] * e1[1] + e2[1] * e2[1]);
+        v[9] = a12 * (s[2] * s[2] + e1[2] * e1[2] + e2[2] * e2[2]);
+        v[10] = a12 * (s[0] * s[1] + e1[0] * e1[1] + e2[0] * e2[1]);
+        v[11] = a12 * (s[0] * s[2] + e1[0] * e1[2] + e2[0] * e2[2]);
+        v[12] = a12 * (s[1] * s[2] + e1[1] * e1[2] + e2[1] * e2[2]);
+    }
+#pragma unroll
+    for (int o = kSeg / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < 13; r++) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
+    const float As = v[3];
+    if (As > 0.f) {
+        const float ia = 1.f / As;
+        const float c[3] = {v[4] * ia, v[5] * ia, v[6] * ia};
+        f.k[0] = v[7] * ia - c[0] * c[0];
+        f.k[1] = v[8] * ia - c[1] * c[1];
+        f.k[2] = v[9] * ia - c[2] * c[2];
+        f.k[3] = v[10] * ia - c[0] * c[1];
+        f.k[4] = v[11] * ia - c[0] * c[2];
+        f.k[5] = v[12] * ia - c[1] * c[2];
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d] + c[d];
+    } else {
+        for (int d = 0; d < 6; d++) f.k[d] = 0.f;
+        for (int d = 0; d < 3; d++) f.c[d] = q0[d];
+    }
+    for (int d = 0; d < 3; d++) f.an[d] = v[d];
+}
+
 template <class F>
 __global__ void __launch_bounds__(kListWarps * 32) k_clip_list(F fr, const int* __restrict__ cand_tri,
                                                               const int* __restrict__ tri_off,
@@ -805,111 +812,124 @@ __global__ void __launch_bounds__(kListWarps * 32) k_clip_list(F fr, const int* 
                                                               ft_frag32* __restrict__ rec32, const ft_counters* ctr,
                                                               const unsigned* __restrict__ list) {
     __shared__ double s_poly[kListWarps][2][32][3];
+    __shared__ double s_wide[kListWarps][kSegPerWarp][32][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int seg = lane / kSeg, sl = lane % kSeg, base = seg * kSeg;
+    const unsigned segmask = (kSeg == 32 ? 0xffffffffu : ((1u << kSeg) - 1u)) << base;
     const long long L = ctr->clip_f64;
-    for (long long j = (long long)blockIdx.x * kListWarps + w; j < L; j += (long long)gridDim.x * kListWarps) {
-        const long long c = (long long)list[j];
-        const int t = cand_tri[c];
-        const int l = (int)(c - tri_off[t]);
-        const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
-        const int4 b0 = bx[0], b1 = bx[1];
-        const int e1 = b1.x, e2 = b1.y, b = b1.z;
-        const int idx[3] = {b0.x + l / (e1 * e2), b0.y + (l / e2) % e1, b0.z + l % e2};
+    const long long step = (long long)gridDim.x * kListWarps * kSegPerWarp;
+    for (long long j0 = ((long long)blockIdx.x * kListWarps + w) * kSegPerWarp; j0 < L; j0 += step) {
+        const long long j = j0 + seg;
+        const bool has = j < L;  // (the warp's second segment may have no pair)
+        const long long c = has ? (long long)list[j] : 0;
+        int t = 0, idx[3] = {0, 0, 0}, b = 0;
+        if (has) {
+            t = cand_tri[c];
+            const int l = (int)(c - tri_off[t]);
+            const int4* bx = reinterpret_cast<const int4*>(tri_box + 8 * (long long)t);
+            const int4 b0 = bx[0], b1 = bx[1];
+            const int e1 = b1.x, e2 = b1.y;
+            b = b1.z;
+            idx[0] = b0.x + l / (e1 * e2);
+            idx[1] = b0.y + (l / e2) % e1;
+            idx[2] = b0.z + l % e2;
+        }
         const ft_fdesc& D = fr.desc(b);
         const ft_grid g = D.g;
         const Planes P(D);
         const long long tl = t - fr.tri_base(b);
-        // lane i < n holds polygon vertex i; the triangle first
+        // lane i < n of the segment holds polygon vertex i; the triangle first
         double x[3] = {0.0, 0.0, 0.0};
-        if (lane < 3) {
-            const long long vi = D.tris[3 * tl + lane];
+        if (has && sl < 3) {
+            const long long vi = D.tris[3 * tl + sl];
             for (int d = 0; d < 3; d++) x[d] = D.verts[3 * vi + d];
         }
         int n = 3;
-        bool alive = true, wide = false;
-        for (int st = 0; st < 6 && alive && !wide; st++) {
+        bool alive = has, wide = false;
+        for (int st = 0; st < 6; st++) {
+            // (every lane takes part in the shuffles; a finished segment's lanes idle)
+            const bool go = alive && !wide;
             const int ax = st >> 1;
             const bool ge = (st & 1) == 0;
             const double pv = P.at(ax, idx[ax] + (st & 1));
             const long long kp = okey(pv);
-            const bool act = lane < n;
+            const bool act = go && sl < n;
             const long long kc = okey(x[ax]);
             const bool cin = act && (ge ? (kc >= kp) : (kc <= kp));
-            const int pl = (lane == 0) ? n - 1 : lane - 1;  // the edge's first vertex
+            const int pl = (sl == 0) ? n - 1 : sl - 1;  // the edge's first vertex (in the segment)
             double pr[3];
 #pragma unroll
-            for (int d = 0; d < 3; d++) pr[d] = __shfl_sync(0xffffffffu, x[d], pl);
-            const bool pin = __shfl_sync(0xffffffffu, cin ? 1 : 0, pl) != 0;
+            for (int d = 0; d < 3; d++) pr[d] = __shfl_sync(0xffffffffu, x[d], pl, kSeg);
+            const bool pin = __shfl_sync(0xffffffffu, cin ? 1 : 0, pl, kSeg) != 0;
             const bool cross = act && (cin != pin);
             double q[3] = {0.0, 0.0, 0.0};
             if (cross) {
                 const double tt = __ddiv_rn(__dsub_rn(pv, pr[ax]), __dsub_rn(x[ax], pr[ax]));
 #pragma unroll
-                for (int d = 0; d < 3; d++) q[d] = (d == ax) ? pv : __dadd_rn(pr[d], __dmul_rn(tt, __dsub_rn(x[d], pr[d])));
+                for (int d = 0; d < 3; d++)
+                    q[d] = (d == ax) ? pv : __dadd_rn(pr[d], __dmul_rn(tt, __dsub_rn(x[d], pr[d])));
             }
             const int cnt = (cross ? 1 : 0) + (cin ? 1 : 0);
             int incl = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+            for (int o = 1; o < kSeg; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, kSeg);
+                if (sl >= o) incl += y;
             }
-            const int m = __shfl_sync(0xffffffffu, incl, 31);
-            if (m > 32) {
-                wide = true;
-                break;
+            const int m = __shfl_sync(0xffffffffu, incl, kSeg - 1, kSeg);
+            if (go && m > kSeg) wide = true;
+            if (go && m < 3) alive = false;
+            double(*dst)[3] = s_poly[w][st & 1] + base;
+            if (go && alive && !wide) {
+                const int pos = incl - cnt;
+                if (cross)
+                    for (int d = 0; d < 3; d++) dst[pos][d] = q[d];
+                if (cin)
+                    for (int d = 0; d < 3; d++) dst[pos + (cross ? 1 : 0)][d] = x[d];
             }
-            if (m < 3) {
-                alive = false;
-                break;
-            }
-            double(*dst)[3] = s_poly[w][st & 1];
-            const int pos = incl - cnt;
-            if (cross)
-                for (int d = 0; d < 3; d++) dst[pos][d] = q[d];
-            if (cin)
-                for (int d = 0; d < 3; d++) dst[pos + (cross ? 1 : 0)][d] = x[d];
             __syncwarp();
-            n = m;
-            if (lane < n)
-                for (int d = 0; d < 3; d++) x[d] = dst[lane][d];
+            if (go && alive && !wide) {
+                n = m;
+                if (sl < n)
+                    for (int d = 0; d < 3; d++) x[d] = dst[sl][d];
+            }
             __syncwarp();
         }
-        const double(*poly)[3] = s_poly[w][1];  // the last stage's output
+        const double(*poly)[3] = s_poly[w][1] + base;  // the last stage's output
         if (wide) {
-            // the wide serial clip of the triangle, on lane 0
+            // the wide serial clip of the triangle, on the segment's first lane
             int nw = 0;
-            if (lane == 0) {
+            if (sl == 0) {
                 double v[3][3];
                 for (int a = 0; a < 3; a++) {
                     const long long vi = D.tris[3 * tl + a];
                     for (int d = 0; d < 3; d++) v[a][d] = D.verts[3 * vi + d];
                 }
-                nw = canon_stages_wide(v, g, idx, s_poly[w][0]);
+                nw = canon_stages_wide(v, g, idx, s_wide[w][seg]);
             }
-            n = __shfl_sync(0xffffffffu, nw, 0);
+            n = __shfl_sync(segmask, nw, base);
             alive = n >= 3;
-            poly = s_poly[w][0];
-        } else if (alive) {
-            // a polygon lying in an upper face of the cell belongs to the next cell
-            for (int ax = 0; ax < 3; ax++) {
-                const long long ku = okey(P.at(ax, idx[ax] + 1));
-                const unsigned on = __ballot_sync(0xffffffffu, lane < n && okey(x[ax]) == ku);
-                if (on == (n == 32 ? 0xffffffffu : ((1u << n) - 1u))) alive = false;
-            }
+            poly = s_wide[w][seg];
+        }
+        // a polygon lying in an upper face of the cell belongs to the next cell
+        // (the wide clip has applied this test itself)
+        for (int ax = 0; ax < 3; ax++) {
+            const long long ku = okey(P.at(ax, idx[ax] + 1));
+            const unsigned on = __ballot_sync(0xffffffffu, sl < n && okey(x[ax]) == ku) & segmask;
+            const unsigned all = (n >= 32 ? 0xffffffffu : ((1u << n) - 1u)) << base;
+            if (alive && !wide && on == (all & segmask)) alive = false;
         }
         __syncwarp();
         ft_frag32 f;
-        if (alive) {
-            const float4 r4 = reinterpret_cast<const float4*>(tri32 + 32 * (long long)t)[4];
-            const float r5x = tri32[32 * (long long)t + 20];
-            const float tn[3] = {r4.z, r4.w, r5x};
+        {
+            const float* tr = tri32 + 32 * (long long)t;
+            const float tn[3] = {tr[18], tr[19], tr[20]};
             const float ih = d2f_rn(D.inv_h);
             float q0[3];
-            for (int d = 0; d < 3; d++) q0[d] = d2f_rn(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f;
-            frag_moments32_warp(poly, n, q0, tn, ih, lane, f);
+            for (int d = 0; d < 3; d++) q0[d] = alive ? d2f_rn(poly[0][d] - P.at(d, idx[d])) * ih - 0.5f : 0.f;
+            frag_moments32_seg(poly, alive ? n : 0, q0, tn, ih, sl, f);
         }
-        if (lane == 0) {
+        if (has && sl == 0) {
             unsigned key = FT_SENTINEL;
             if (alive) {
                 // the moments' own area vector certifies the canonical "area vector

@@ -798,11 +798,15 @@ __device__ __forceinline__ float ldlt_solve_df(const dfl (&S)[21], const dfl (&B
 constexpr int kSolveThreads = 128;
 constexpr int kSolveLanes = 32;
 
-template <class F>
-__global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cellsys* __restrict__ sys, const int* __restrict__ fit_info,
-                                                    const unsigned* __restrict__ cells, int fp32, long long cap, ft_counters* ctr, unsigned* __restrict__ out_keys,
-                                                    double* __restrict__ out_kappa, double* __restrict__ out_normal,
-                                                    double* __restrict__ out_coeffs, int8_t* __restrict__ out_status) {
+template <class F, bool FP32>
+__global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cellsys* __restrict__ sys,
+                                                              const int* __restrict__ fit_info,
+                                                              const unsigned* __restrict__ cells, long long cap,
+                                                              ft_counters* ctr, unsigned* __restrict__ out_keys,
+                                                              double* __restrict__ out_kappa,
+                                                              double* __restrict__ out_normal,
+                                                              double* __restrict__ out_coeffs,
+                                                              int8_t* __restrict__ out_status) {
     const long long M = ctr->M;
     if (M > cap) {  // the caller's arrays are too short: write nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) ft_flag(ctr, FT_ST_CAPACITY);
@@ -813,36 +817,59 @@ __global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cel
     const long long wid = ((long long)blockIdx.x * kSolveThreads + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * kSolveThreads) >> 5;
     for (long long m = wid * kSolveLanes + lane; m < M; m += nw * kSolveLanes) {
-        double n[3], z0;
-        double a[6] = {0, 0, 0, 0, 0, 0};
         int st = fit_info[2 * m + 1];
-        if (fp32) {
-            // the FP32 form: the compensated pairs as double-float numbers
+        const unsigned key = cells[m];
+        out_keys[m] = key;
+        if constexpr (FP32) {
+            // The FP32 form, without float64 instructions: the compensated pairs as
+            // double-float numbers, the frame rebuilt in float from the stored float
+            // normal exactly as the accumulation built it, the curvature and the
+            // normal in float (their tolerance is 1e-4), widened by integer operations
             const float* v = reinterpret_cast<const float*>(sys[m].v);
             dfl S[21], B[6], ad[6];
 #pragma unroll
             for (int r = 0; r < 21; r++) S[r] = df_norm(v[2 * r], v[2 * r + 1]);
 #pragma unroll
             for (int r = 0; r < 6; r++) B[r] = df_norm(v[42 + 2 * r], v[43 + 2 * r]);
-            z0 = ft_f2d(v[60]);
-            const float rel = ldlt_solve_df<6>(S, B, ad);
-            if (rel >= 1e-12f) {
+            const float z0 = v[60];
+            const float n[3] = {v[54], v[56], v[58]};
 #pragma unroll
-                for (int r = 0; r < 6; r++) a[r] = ft_f2d(ad[r].hi) + ft_f2d(ad[r].lo);
-            } else {
+            for (int r = 0; r < 6; r++) ad[r] = dfl{0.f, 0.f};
+            const float rel = ldlt_solve_df<6>(S, B, ad);
+            if (!(rel >= 1e-12f)) {
                 // singular: plane fit on the leading 3x3 block, kappa = 0
                 dfl a3[6];
+#pragma unroll
+                for (int r = 0; r < 6; r++) ad[r] = dfl{0.f, 0.f};
                 if (ldlt_solve_df<3>(S, B, a3) > 0.f)
-                    for (int r = 0; r < 3; r++) a[r] = ft_f2d(a3[r].hi) + ft_f2d(a3[r].lo);
+                    for (int r = 0; r < 3; r++) ad[r] = a3[r];
                 st |= FT_FIT_SINGULAR;
             }
+            ad[0] = df_add(ad[0], dfl{z0, 0.f});  // undo the height shift (it changes a1 only)
+            float a[6];
+#pragma unroll
+            for (int r = 0; r < 6; r++) a[r] = __fadd_rn(ad[r].hi, ad[r].lo);
+            float t1[3], t2[3];
+            basis<float>(n, t1, t2);
+            // mean curvature of the graph z = P(x, y) at the origin, kappa = div n
+            const float g2 = 1.f + a[1] * a[1] + a[2] * a[2];
+            const float kl = -(2.f * a[3] * (1.f + a[2] * a[2]) - 2.f * a[1] * a[2] * a[4] +
+                               2.f * a[5] * (1.f + a[1] * a[1])) / (g2 * sqrtf(g2));
+            float nv[3];
+            for (int d = 0; d < 3; d++) nv[d] = n[d] - a[1] * t1[d] - a[2] * t2[d];
+            const float il = 1.f / sqrtf(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+            out_kappa[m] = ft_f2d(kl * (float)fr.desc(fr.by_key(key)).inv_h);
+            for (int d = 0; d < 3; d++) out_normal[3 * m + d] = ft_f2d(nv[d] * il);
+            if (out_coeffs)
+                for (int r = 0; r < 6; r++) out_coeffs[6 * m + r] = ft_f2d(ad[r].hi) + ft_f2d(ad[r].lo);
         } else {
-            double S[21], B[6];
+            double S[21], B[6], n[3];
+            double a[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int r = 0; r < 21; r++) S[r] = sys[m].v[r];
 #pragma unroll
             for (int r = 0; r < 6; r++) B[r] = sys[m].v[21 + r];
-            z0 = sys[m].v[30];
+            const double z0 = sys[m].v[30];
             const double rel = ldlt_solve<6>(S, B, a);
             if (!(rel >= 1e-12)) {
                 // singular: plane fit on the leading 3x3 block, kappa = 0
@@ -855,28 +882,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_ppic_solve(F fr, const ft_cel
                 }
                 st |= FT_FIT_SINGULAR;
             }
+            sys_normal(sys[m], false, n);
+            double t1[3], t2[3];
+            basis<double>(n, t1, t2);
+            a[0] += z0;  // undo the height shift (it changes a1 only)
+            // mean curvature of the graph z = P(x, y) at the origin, kappa = div n
+            const double g2 = 1.0 + a[1] * a[1] + a[2] * a[2];
+            const double kl = -(2.0 * a[3] * (1.0 + a[2] * a[2]) - 2.0 * a[1] * a[2] * a[4] +
+                                2.0 * a[5] * (1.0 + a[1] * a[1])) / (g2 * sqrt(g2));
+            double nv[3];
+            for (int d = 0; d < 3; d++) nv[d] = n[d] - a[1] * t1[d] - a[2] * t2[d];
+            const double il = 1.0 / sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+            out_kappa[m] = kl * fr.desc(fr.by_key(key)).inv_h;
+            for (int d = 0; d < 3; d++) out_normal[3 * m + d] = nv[d] * il;
+            if (out_coeffs)
+                for (int r = 0; r < 6; r++) out_coeffs[6 * m + r] = a[r];
         }
-        sys_normal(sys[m], fp32 != 0, n);
-        double t1[3], t2[3];
-        basis<double>(n, t1, t2);
-        a[0] += z0;  // undo the height shift (it changes a1 only)
-        // mean curvature of the graph z = P(x, y) at the origin, kappa = div n
-        const double g2 = 1.0 + a[1] * a[1] + a[2] * a[2];
-        const double kl = -(2.0 * a[3] * (1.0 + a[2] * a[2]) - 2.0 * a[1] * a[2] * a[4] +
-                            2.0 * a[5] * (1.0 + a[1] * a[1])) / (g2 * sqrt(g2));
-        double nv[3];
-        for (int d = 0; d < 3; d++) nv[d] = n[d] - a[1] * t1[d] - a[2] * t2[d];
-        const double il = 1.0 / sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-        const unsigned key = cells[m];
-        out_keys[m] = key;
-        out_kappa[m] = kl * fr.desc(fr.by_key(key)).inv_h;
-        for (int d = 0; d < 3; d++) out_normal[3 * m + d] = nv[d] * il;
-        if (out_coeffs)
-            for (int r = 0; r < 6; r++) out_coeffs[6 * m + r] = a[r];
         out_status[m] = (int8_t)st;
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // The paper's own fit neighbourhood and frame (Sec. 3.2): the front vertex
@@ -1320,8 +1344,8 @@ cudaError_t ppic_with(ft_workspace* ws, const F& fr, const ft_params* p, long lo
                 }
                 ws->sys_fp32 = false;
                 Trace t(s, "k_ppic_solve");
-                k_ppic_solve<F><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(
-                    fr, ws->sys, ws->fit_info, ws->cells, 0, cap, ws->ctr, cell_keys, kappa, normal, coeffs,
+                k_ppic_solve<F, false><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(
+                    fr, ws->sys, ws->fit_info, ws->cells, cap, ws->ctr, cell_keys, kappa, normal, coeffs,
                     fit_status);
                 return cudaGetLastError();
             }
@@ -1347,8 +1371,12 @@ cudaError_t ppic_with(ft_workspace* ws, const F& fr, const ft_params* p, long lo
     }
     ws->sys_fp32 = fp32;
     Trace t(s, "k_ppic_solve");
-    k_ppic_solve<F><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(fr, ws->sys, ws->fit_info, ws->cells, fp32 ? 1 : 0, cap,
-                                                    ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
+    if (fp32)
+        k_ppic_solve<F, true><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(
+            fr, ws->sys, ws->fit_info, ws->cells, cap, ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
+    else
+        k_ppic_solve<F, false><<<ws->sm_count * (512 / kSolveThreads), kSolveThreads, 0, s>>>(
+            fr, ws->sys, ws->fit_info, ws->cells, cap, ws->ctr, cell_keys, kappa, normal, coeffs, fit_status);
     return cudaGetLastError();
 }
 
