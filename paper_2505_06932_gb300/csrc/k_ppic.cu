@@ -492,12 +492,26 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppic_acc(PpicArgs A, F
                     if (dkmax >= 0 && ii >= 0 && jj >= 0 && ii < n0 && jj < n1) {
                         const int k0 = max(ck - dkmax, 0), k1 = min(ck + dkmax, n2 - 1);
                         const long long base = kb + ((long long)ii * n1 + jj) * n2;
+                        // the first and last interfacial cells of the row's k range (up to
+                        // nine entries loaded at once; wider supports loop)
                         int mf = -1, ml = -1;
-                        for (int k = k0; k <= k1; k++) {
-                            const int m2 = idx_map[base + k];
-                            if (m2 >= 0) {
-                                if (mf < 0) mf = m2;
-                                ml = m2;
+                        if (k1 - k0 < 9) {
+                            int mm[9];
+#pragma unroll
+                            for (int t = 0; t < 9; t++) mm[t] = (k0 + t <= k1) ? __ldg(idx_map + base + k0 + t) : -1;
+#pragma unroll
+                            for (int t = 0; t < 9; t++)
+                                if (mm[t] >= 0) {
+                                    if (mf < 0) mf = mm[t];
+                                    ml = mm[t];
+                                }
+                        } else {
+                            for (int k = k0; k <= k1; k++) {
+                                const int m2 = idx_map[base + k];
+                                if (m2 >= 0) {
+                                    if (mf < 0) mf = m2;
+                                    ml = m2;
+                                }
                             }
                         }
                         if (mf >= 0) {
