@@ -57,8 +57,9 @@ def kernel_work(name, w, fp32):
     T, V, N, C, P, M = w["T"], w["V"], w["N"], w["C"], w["P"], w["M"]
     R, FP = w["ring"], w["fit_pairs"]
     table = {
-        "k_tri_setup": ("hbm", 152 * T + 8 * M, "84 B of indices and coordinates read, 68 B of box, count and "
-                        "normal written per triangle; the previous cells' index-map entries reset"),
+        "k_tri_setup": ("hbm", (248 if fp32 else 152) * T + 8 * M,
+                        "84 B of indices and coordinates read, box and count (36 B) and the normal (32 B) or the "
+                        "FP32 clip's 128 B record written per triangle; the previous cells' index-map entries reset"),
         "k_scan_reduce": ("hbm", 4 * T, "the triangle counts read"),
         "k_scan_expand": ("hbm", 8 * T + 4 * C, "counts read, offsets written, the triangle id of every "
                           "candidate slot written"),
