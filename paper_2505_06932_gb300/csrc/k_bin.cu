@@ -102,166 +102,166 @@ static_assert(sizeof(Tri32) == 32 * sizeof(float), "Tri32 is eight 16-byte words
 // triangle's closed bounding box) and its size.  tri_box holds lo[3], ext[3]
 // and the owning front per triangle (8 ints); tri32 (when given) the record
 // above.
-// Four threads per triangle (one per axis, the fourth idle), so that the axes'
-// exact plane searches and coordinate conversions run side by side; the three
-// axis threads exchange what the others need (extents, edge components) by
-// shuffles within their group of four.
 template <class F>
 __global__ void __launch_bounds__(kThreads) k_tri_setup(F fr, long long T, int margin, long long max_cand,
                                                         int* __restrict__ tri_cnt, int* __restrict__ tri_box,
                                                         double* __restrict__ tri_nrm, float* __restrict__ tri32,
                                                         const unsigned* __restrict__ cells,
                                                         int* __restrict__ idx_map, ft_counters* ctr) {
-    const long long tid = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const long long t = (long long)blockIdx.x * kThreads + threadIdx.x;
     // first the index map entries of the previous binning's cells go back to -1
     const long long M_prev = ctr->M;
-    for (long long m = tid; m < M_prev; m += (long long)gridDim.x * kThreads) idx_map[cells[m]] = -1;
-    if (tid == 0) {
+    for (long long m = t; m < M_prev; m += (long long)gridDim.x * kThreads) idx_map[cells[m]] = -1;
+    if (t == 0) {
         ctr->T = T;
         ctr->clip_f64 = 0;
     }
-    if (T == 0) return;
-    const int lane = threadIdx.x & 31, g0 = lane & ~3, ax = lane & 3;
-    const long long t = tid >> 2;
-    const bool act = t < T;  // (every lane takes part in the group's shuffles)
-    const bool axl = act && ax < 3;
-    const int b = fr.by_tri(act ? t : T - 1);
+    if (t >= T) return;
+    const int b = fr.by_tri(t);
     const ft_fdesc& D = fr.desc(b);
     const ft_grid g = D.g;
-    const long long tl = (act ? t : T - 1) - fr.tri_base(b);
+    const long long tl = t - fr.tri_base(b);
     const long long nv = D.nv;
     const double* __restrict__ verts = D.verts;
-    unsigned err = 0;
-    int vi[3] = {0, 0, 0};
-    if (act)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            vi[c] = D.tris[3 * tl + c];
-            if (vi[c] < 0 || vi[c] >= nv) err |= FT_ST_BAD_INDEX;
-        }
-    // this thread's axis: the three coordinates, their extent by exact integer-key
-    // comparisons, the candidate range
-    double x[3] = {0.0, 0.0, 0.0};
-    int i0 = 0, ext = 1;
-    if (axl && !err) {
-        double lo = 0.0, hi = 0.0;
-        long long klo = 0, khi = 0;
-        bool finite = true;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            x[c] = verts[3 * (long long)vi[c] + ax];
-            const long long bits = __double_as_longlong(x[c]);
-            finite = finite && ((bits & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
-            const long long kx = okey(x[c]);
-            if (c == 0 || kx < klo) { klo = kx; lo = x[c]; }
-            if (c == 0 || kx > khi) { khi = kx; hi = x[c]; }
-        }
-        if (!finite) {
-            err |= FT_ST_OUTSIDE_GRID;
-        } else {
-            int i1;
-            const Planes P(D);
-            const int n_ax = ax == 0 ? g.n[0] : (ax == 1 ? g.n[1] : g.n[2]);
-            cand_range(P, ax, D.inv_h, n_ax, lo, hi, i0, i1);
-            if (i0 < margin || i1 > n_ax - 1 - margin) err |= FT_ST_OUTSIDE_GRID;
-            ext = i1 - i0 + 1;
-        }
-    }
-    // the group's status and extents
-    err |= __shfl_xor_sync(0xffffffffu, err, 1);
-    err |= __shfl_xor_sync(0xffffffffu, err, 2);
-    const int ext0 = __shfl_sync(0xffffffffu, ext, g0), ext1 = __shfl_sync(0xffffffffu, ext, g0 + 1),
-              ext2 = __shfl_sync(0xffffffffu, ext, g0 + 2);
-    const int lo0 = __shfl_sync(0xffffffffu, i0, g0), lo1 = __shfl_sync(0xffffffffu, i0, g0 + 1),
-              lo2 = __shfl_sync(0xffffffffu, i0, g0 + 2);
     int cnt = 0;
+    int box[6] = {0, 0, 0, 1, 1, 1};
+    unsigned err = 0;
+    int vi[3];
+    for (int c = 0; c < 3; c++) {
+        vi[c] = D.tris[3 * tl + c];
+        if (vi[c] < 0 || vi[c] >= nv) err |= FT_ST_BAD_INDEX;
+    }
     if (!err) {
-        long long total = (long long)ext0 * ext1 * ext2;
-        if (total > max_cand) {
-            err |= FT_ST_CAPACITY;
-            total = max_cand + 1;  // still counted so that the total exceeds the capacity
-        }
-        cnt = (int)total;
-    }
-    if (act && ax == 0) {
-        if (err) {
-            ft_flag(ctr, err);
-            fr.flag(b, err);
-        }
-        tri_cnt[t] = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
-        int4* bx = reinterpret_cast<int4*>(tri_box + 8 * t);
-        bx[0] = make_int4(lo0, lo1, lo2, ext0);
-        bx[1] = make_int4(ext1, ext2, b, 0);
-    }
-    const bool ok = !err;
-    if (!tri32) {
-        // normal direction (orientation of every fragment of the triangle; zero if
-        // degenerate): twice the area vector in units of h^2.  Only its direction
-        // matters -- the moments use ratios of areas signed along it.
-        const double e1 = ok && axl ? (x[1] - x[0]) * D.inv_h : 0.0, e2 = ok && axl ? (x[2] - x[0]) * D.inv_h : 0.0;
-        const int p1 = g0 + (ax + 1) % 3, p2 = g0 + (ax + 2) % 3;
-        const double e1p = __shfl_sync(0xffffffffu, e1, p1), e1q = __shfl_sync(0xffffffffu, e1, p2);
-        const double e2p = __shfl_sync(0xffffffffu, e2, p1), e2q = __shfl_sync(0xffffffffu, e2, p2);
-        if (act) {
-            if (axl) tri_nrm[4 * t + ax] = ok ? e1p * e2q - e1q * e2p : 0.0;
-            else tri_nrm[4 * t + 3] = 0.0;
-        }
-        return;
-    }
-    // The FP32 clip's record (layout: Tri32), the entries of this thread's axis
-    float hv[3] = {0.f, 0.f, 0.f}, lv[3] = {0.f, 0.f, 0.f};
-    int A[3] = {0, 0, 0};
-    unsigned eq = 0u;
-    if (ok && axl) {
-        const Planes P(D);
-        const double xlo = P.at(ax, i0);
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const double tt = __dmul_rn(__dsub_rn(x[a], xlo), D.inv_h);
-            const float f = d2f_rn(tt);
-            hv[a] = f;
-            lv[a] = d2f_rn(__dsub_rn(tt, ft_f2d(f)));
-            // Every vertex lies in [X_lo, X_{lo+ext}]: A in [0, ext - 1].  f is
-            // within 1e-7 (1 + |f|) of the exact plane-relative position (the
-            // planes are spaced h apart to within 1e-8 h), so away from an
-            // integer its floor is A and the coordinate lies on no plane;
-            // near one, the exact comparisons decide
-            const float fl = floorf(f), fr_ = f - fl;
-            const float m = 1e-5f + 1e-6f * fabsf(f);
-            int i = (int)fminf(fmaxf(fl, 0.f), (float)(ext - 1));
-            if (!(fr_ > m && fr_ < 1.f - m)) {
-                const long long kx = okey(x[a]);
-                while (i > 0 && okey(P.at(ax, i0 + i)) > kx) i--;
-                while (i < ext - 1 && okey(P.at(ax, i0 + i + 1)) <= kx) i++;
-                if (okey(P.at(ax, i0 + i)) == kx) eq |= 1u << (3 * a + ax);
+        // extent per axis by exact integer-key comparisons (no float64 arithmetic)
+        double mn[3], mx[3];
+        bool finite = true;
+        for (int ax = 0; ax < 3; ax++) {
+            double lo = 0.0, hi = 0.0;
+            long long klo = 0, khi = 0;
+            for (int c = 0; c < 3; c++) {
+                const double x = verts[3 * (long long)vi[c] + ax];
+                const long long bits = __double_as_longlong(x);
+                finite = finite && ((bits & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
+                const long long kx = okey(x);
+                if (c == 0 || kx < klo) { klo = kx; lo = x; }
+                if (c == 0 || kx > khi) { khi = kx; hi = x; }
             }
-            A[a] = i;
+            mn[ax] = lo;
+            mx[ax] = hi;
+        }
+        if (!finite) err |= FT_ST_OUTSIDE_GRID;
+        long long total = 1;
+        const Planes P(D);
+        for (int ax = 0; ax < 3 && !err; ax++) {
+            int i0, i1;
+            cand_range(P, ax, D.inv_h, g.n[ax], mn[ax], mx[ax], i0, i1);
+            if (i0 < margin || i1 > g.n[ax] - 1 - margin) err |= FT_ST_OUTSIDE_GRID;
+            box[ax] = i0;
+            box[3 + ax] = i1 - i0 + 1;
+            total *= (long long)(i1 - i0 + 1);
+        }
+        if (!err) {
+            if (total > max_cand) {
+                err |= FT_ST_CAPACITY;
+                total = max_cand + 1;  // still counted so that the total exceeds the capacity
+            }
+            cnt = (int)total;
         }
     }
-    // the normal direction from the float-pair edges, each 2x2 determinant with
-    // Kahan's fused-multiply-add correction (accurate despite cancellation)
-    const float e1 = __fadd_rn(__fsub_rn(hv[1], hv[0]), __fsub_rn(lv[1], lv[0]));
-    const float e2 = __fadd_rn(__fsub_rn(hv[2], hv[0]), __fsub_rn(lv[2], lv[0]));
-    const int p1 = g0 + (ax + 1) % 3, p2 = g0 + (ax + 2) % 3;
-    const float e1p = __shfl_sync(0xffffffffu, e1, p1), e1q = __shfl_sync(0xffffffffu, e1, p2);
-    const float e2p = __shfl_sync(0xffffffffu, e2, p1), e2q = __shfl_sync(0xffffffffu, e2, p2);
-    eq |= __shfl_xor_sync(0xffffffffu, eq, 1);
-    eq |= __shfl_xor_sync(0xffffffffu, eq, 2);
-    if (!act) return;
-    float* r = tri32 + 32 * t;
-    if (axl) {
-        const float w = __fmul_rn(e1q, e2p);
-        const float tn = ok ? __fadd_rn(__fmaf_rn(e1p, e2q, -w), __fmaf_rn(-e1q, e2p, w)) : 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            r[3 * a + ax] = hv[a];
-            r[9 + 3 * a + ax] = lv[a];
-            reinterpret_cast<int*>(r)[21 + 3 * a + ax] = A[a];
+    if (err) {
+        ft_flag(ctr, err);
+        fr.flag(b, err);
+    }
+    tri_cnt[t] = (err & ~FT_ST_CAPACITY) ? 0 : cnt;
+    // normal direction (orientation of every fragment of the triangle; zero if
+    // degenerate): twice the area vector in units of h^2.  Only its direction
+    // matters -- the moments use ratios of areas signed along it.  (The FP32
+    // clip's record carries its own float normal instead.)
+    double nrm[3] = {0.0, 0.0, 0.0};
+    if (!err && !tri32) {
+        double e1[3], e2[3];
+        for (int d = 0; d < 3; d++) {
+            e1[d] = (verts[3 * (long long)vi[1] + d] - verts[3 * (long long)vi[0] + d]) * D.inv_h;
+            e2[d] = (verts[3 * (long long)vi[2] + d] - verts[3 * (long long)vi[0] + d]) * D.inv_h;
         }
-        r[18 + ax] = tn;
-    } else {
-        reinterpret_cast<int*>(r)[30] = (int)eq;
-        reinterpret_cast<int*>(r)[31] = 0;
+        nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    if (!tri32) {
+        double2* nb = reinterpret_cast<double2*>(tri_nrm + 4 * t);
+        nb[0] = make_double2(nrm[0], nrm[1]);
+        nb[1] = make_double2(nrm[2], 0.0);
+    }
+    int4* bx = reinterpret_cast<int4*>(tri_box + 8 * t);
+    bx[0] = make_int4(box[0], box[1], box[2], box[3]);
+    bx[1] = make_int4(box[4], box[5], b, 0);
+    if (tri32) {
+        float hv[9], lv[9], tn[3] = {0.f, 0.f, 0.f};
+        int A[9];
+        unsigned eq = 0u;
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            hv[q] = lv[q] = 0.f;
+            A[q] = 0;
+        }
+        if (!err) {
+            const Planes P(D);
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++) {
+                const int lo = box[ax], ext = box[3 + ax];
+                const double xlo = P.at(ax, lo);
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const double x = verts[3 * (long long)vi[a] + ax];
+                    const double tt = __dmul_rn(__dsub_rn(x, xlo), D.inv_h);
+                    const float f = d2f_rn(tt);
+                    hv[3 * a + ax] = f;
+                    lv[3 * a + ax] = d2f_rn(__dsub_rn(tt, ft_f2d(f)));
+                    // Every vertex lies in [X_lo, X_{lo+ext}]: A in [0, ext - 1].  f is
+                    // within 1e-7 (1 + |f|) of the exact plane-relative position (the
+                    // planes are spaced h apart to within 1e-8 h), so away from an
+                    // integer its floor is A and the coordinate lies on no plane;
+                    // near one, the exact comparisons decide
+                    const float fl = floorf(f), fr = f - fl;
+                    const float m = 1e-5f + 1e-6f * fabsf(f);
+                    int i = (int)fminf(fmaxf(fl, 0.f), (float)(ext - 1));
+                    if (!(fr > m && fr < 1.f - m)) {
+                        const long long kx = okey(x);
+                        while (i > 0 && okey(P.at(ax, lo + i)) > kx) i--;
+                        while (i < ext - 1 && okey(P.at(ax, lo + i + 1)) <= kx) i++;
+                        if (okey(P.at(ax, lo + i)) == kx) eq |= 1u << (3 * a + ax);
+                    }
+                    A[3 * a + ax] = i;
+                }
+            }
+            // the normal direction from the float-pair edges, each 2x2 determinant
+            // with Kahan's fused-multiply-add correction (accurate despite cancellation)
+            float e1[3], e2[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                e1[d] = __fadd_rn(__fsub_rn(hv[3 + d], hv[d]), __fsub_rn(lv[3 + d], lv[d]));
+                e2[d] = __fadd_rn(__fsub_rn(hv[6 + d], hv[d]), __fsub_rn(lv[6 + d], lv[d]));
+            }
+            auto det2 = [](float a, float b, float c, float d) {  // a d - b c
+                const float w = __fmul_rn(b, c);
+                const float e = __fmaf_rn(-b, c, w);
+                return __fadd_rn(__fmaf_rn(a, d, -w), e);
+            };
+            tn[0] = det2(e1[1], e1[2], e2[1], e2[2]);
+            tn[1] = det2(e1[2], e1[0], e2[2], e2[0]);
+            tn[2] = det2(e1[0], e1[1], e2[0], e2[1]);
+        }
+        float4* o4 = reinterpret_cast<float4*>(tri32 + 32 * t);
+        int4* i4 = reinterpret_cast<int4*>(tri32 + 32 * t);
+        o4[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        o4[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        o4[2] = make_float4(hv[8], lv[0], lv[1], lv[2]);
+        o4[3] = make_float4(lv[3], lv[4], lv[5], lv[6]);
+        o4[4] = make_float4(lv[7], lv[8], tn[0], tn[1]);
+        o4[5] = make_float4(tn[2], __int_as_float(A[0]), __int_as_float(A[1]), __int_as_float(A[2]));
+        i4[6] = make_int4(A[3], A[4], A[5], A[6]);
+        i4[7] = make_int4(A[7], A[8], (int)eq, 0);
     }
 }
 
@@ -1261,7 +1261,7 @@ namespace ft {
 template <class F>
 cudaError_t bin_with(ft_workspace* ws, const F& fr, long long T, const ft_params* p, cudaStream_t s) {
     const int margin = 2 + (int)ceil(p->delta_max_h);
-    const unsigned nb = (unsigned)((4 * T + kThreads - 1) / kThreads);  // four threads per triangle
+    const unsigned nb = (unsigned)((T + kThreads - 1) / kThreads);
     // the FP32 form needs float records; a workspace without them computes float64 records
     const bool fp32 = p->precision == FT_FP32C && ws->rec32 != nullptr;
     const bool clip32 = fp32 && ws->clip32_ok && ws->tri32 != nullptr;
