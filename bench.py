@@ -198,6 +198,9 @@ def parse():
     ap.add_argument("--e2e-compute", choices=("per_front", "shared"), default="per_front",
                     help="staggered/graph e2e leg: each front's calls on its own compute stream (the fronts "
                          "computed concurrently, as in the graph step), or both fronts on one compute stream")
+    ap.add_argument("--e2e-upload-streams", type=int, default=1,
+                    help="staggered/graph e2e leg: copy streams the face-velocity uploads are spread over "
+                         "(round robin over the face arrays; vertices and triangles go first on the first)")
     ap.add_argument("--e2e-outputs", choices=("compact", "dense"), default="compact",
                     help="e2e leg: download alpha and the force in the compact form (front_alpha_pack, "
                          "front_csf_force_compact: the same information) or as dense arrays")
@@ -699,7 +702,8 @@ def run_ours(a):
     if stag:
         sd0 = torch.cuda.Stream(device=dev)
         e2e_streams = dict(sds=[torch.cuda.Stream(device=dev) for _ in fcs] if a.e2e_compute == "per_front"
-                           else [sd0 for _ in fcs], up=torch.cuda.Stream(device=dev),
+                           else [sd0 for _ in fcs],
+                           ups=[torch.cuda.Stream(device=dev) for _ in range(max(1, a.e2e_upload_streams))],
                            dns=[torch.cuda.Stream(device=dev) for _ in fcs],
                            sas=[torch.cuda.Stream(device=dev) for _ in fcs],
                            sis=[torch.cuda.Stream(device=dev) for _ in fcs])
@@ -709,21 +713,31 @@ def run_ours(a):
 
     def e2e_enqueue(cs):
         if stag:
-            sds, up, dns = e2e_streams["sds"], e2e_streams["up"], e2e_streams["dns"]
+            sds, ups, dns = e2e_streams["sds"], e2e_streams["ups"], e2e_streams["dns"]
             sas, sis = e2e_streams["sas"], e2e_streams["sis"]
-            for x in sds + [up] + dns + sas + sis:
+            for x in sds + ups + dns + sas + sis:
                 x.wait_stream(cs)
             vt_in = [torch.cuda.Event() for _ in fcs]
-            faces_in = [torch.cuda.Event() for _ in fcs]
-            with torch.cuda.stream(up):
+            faces_in = [[] for _ in fcs]  # per front: an event on every upload stream that carried its faces
+            with torch.cuda.stream(ups[0]):
                 for (hv, ht, hf), (v, t, fa), ev in zip(hin, dfr, vt_in):
                     v.copy_(hv, non_blocking=True)
                     t.copy_(ht, non_blocking=True)
-                    ev.record(up)
-                for (hv, ht, hf), (v, t, fa), ev in zip(hin, dfr, faces_in):
-                    for dst, src in zip(fa, hf):
+                    ev.record(ups[0])
+            j = 0
+            for f, ((hv, ht, hf), (v, t, fa)) in enumerate(zip(hin, dfr)):
+                used = []
+                for dst, src in zip(fa, hf):
+                    u = ups[j % len(ups)]
+                    j += 1
+                    with torch.cuda.stream(u):
                         dst.copy_(src, non_blocking=True)
-                    ev.record(up)
+                    if u not in used:
+                        used.append(u)
+                for u in used:
+                    ev = torch.cuda.Event()
+                    ev.record(u)
+                    faces_in[f].append(ev)
             for f, ((v, t, fa), fc, o, c, dn, d) in enumerate(zip(dfr, fcs, hout, counts, dns, dcomp)):
                 # each front as the DAG of the graph step: alpha beside the PPIC fit,
                 # the interpolation beside both (once the faces are up)
@@ -740,7 +754,8 @@ def run_ours(a):
                     alpha_ready.record(sa)
                 with torch.cuda.stream(si):
                     si.wait_event(vt_in[f])
-                    si.wait_event(faces_in[f])
+                    for ev in faces_in[f]:
+                        si.wait_event(ev)
                     F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
                     vel_ready.record(si)
                 with torch.cuda.stream(sd):
@@ -771,7 +786,7 @@ def run_ours(a):
                     o["normal"].copy_(fc.normal[:M], non_blocking=True)
                     dn.wait_event(vel_ready)
                     o["vel"].copy_(fc.vel[:v.shape[0]], non_blocking=True)
-            for x in sds + [up] + dns + sas + sis:
+            for x in sds + ups + dns + sas + sis:
                 cs.wait_stream(x)
         else:
             sides, copies = e2e_streams["sides"], e2e_streams["copies"]
