@@ -1059,7 +1059,28 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
     float4(*dst)[32] = b1;
     for (int c = 0; c < 3; c++) src[c][lane] = make_float4(tv[c][0], tv[c][1], tv[c][2], -(float)(1 + vflags[c]));
     int n = 3;
+    // Stages whose half-space holds all three triangle vertices by more than
+    // 1e-5 cells plus 2e-6 of the coordinate (the float coordinates are within
+    // kEps |x| + ew of the exact ones) keep every polygon derived from the
+    // triangle as it is: its points
+    // are convex combinations of the vertices, and the binary64 crossings lie
+    // within 1e-12 cells of them, so the canonical stage finds every vertex
+    // inside too.  Those stages are skipped without reading the polygon.
+    unsigned skip = 0u;
+#pragma unroll
     for (int st = 0; st < 6; st++) {
+        const int ax = st >> 1;
+        const bool ge = (st & 1) == 0;
+        bool all = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float x = tv[c][ax], mg = 1e-5f + 2e-6f * fabsf(x);
+            all = all && (ge ? x > mg : top[ax] - x > mg);
+        }
+        if (all) skip |= 1u << st;
+    }
+    for (int st = 0; st < 6; st++) {
+        if ((skip >> st) & 1u) continue;
         const int ax = st >> 1;
         const bool ge = (st & 1) == 0;
         const float pl = ge ? 0.f : top[ax];
