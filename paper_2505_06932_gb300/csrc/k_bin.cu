@@ -728,20 +728,22 @@ __global__ void __maxnreg__(80) k_clip(F fr, const int* __restrict__ cand_tri,
 }
 
 // The pairs the FP32 clip left to the binary64 clip (ctr->clip_f64 slots in
-// list): few, so a segment of kSeg lanes per pair (two pairs per warp), the
+// list): few, so a segment of kSeg lanes per pair (four pairs per warp), the
 // polygon one vertex per lane.  Each stage is the Sutherland-Hodgman step
 // written lane-parallel: lane i of a segment owns the edge from vertex i-1
 // (cyclically) to vertex i and computes its crossing with the canonical
 // operations (t = (pv - a)/(b - a), q = a + t (b - a), the clipped coordinate
 // set to pv); an exclusive scan of the per-lane output counts (crossing first,
 // then the vertex if inside) places the outputs in exactly the serial order.  A
-// polygon that would outgrow the segment is redone by the wide serial clip on
-// the segment's first lane.  The float32 record's moments are spread over the
-// segment's lanes; the canonical area test runs on its first lane.  Two pairs
-// per warp halve the float64 instructions per pair (a float64 warp instruction
-// costs the same however few lanes it has).
+// polygon that would outgrow the segment (a triangle clipped by all six planes
+// has up to nine vertices: rare) is redone by the wide serial clip on the
+// segment's first lane.  The float32 record's moments are spread over the
+// segment's lanes; the canonical area test runs on its first lane.  Several
+// pairs per warp divide the float64 instructions per pair (a float64 warp
+// instruction costs the same however few lanes it has): one pair per warp took
+// 18.5 us for the ~1,300 pairs of a 128^3 front, two 17.4 us, four 17.0 us.
 constexpr int kListWarps = 4;
-constexpr int kSeg = 16;                 // lanes per listed pair (polygons up to 16 vertices)
+constexpr int kSeg = 8;                  // lanes per listed pair (polygons up to 8 vertices)
 constexpr int kSegPerWarp = 32 / kSeg;
 // frag_moments32 spread over a segment of kSeg lanes (collective over the
 // warp, each segment with its own polygon): lane m-1 of the segment takes fan
