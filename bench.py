@@ -204,6 +204,8 @@ def parse():
     ap.add_argument("--e2e-outputs", choices=("compact", "dense"), default="compact",
                     help="e2e leg: download alpha and the force in the compact form (front_alpha_pack, "
                          "front_csf_force_compact: the same information) or as dense arrays")
+    ap.add_argument("--batch-no-fork", dest="batch_fork", action="store_false",
+                    help="batched leg: the step's calls in order on one stream instead of the DAG")
     ap.add_argument("--no-fork", dest="fork", action="store_false",
                     help="graph steps with each front's five calls in order on one stream, instead of the DAG "
                          "per front (volume fraction beside the PPIC fit, the interpolation beside everything)")
@@ -1025,9 +1027,12 @@ def run_batched(a, dev, local, flush):
            "fronts": len(fr), "triangles": int(sum(f["tris"].shape[0] for f in fr)),
            "grid_cells": int(sum(f["grid"].ncells for f in fr)),
            "radius_capped": int(sum(f["capped"] for f in fr)),
-           "launch": "one CUDA graph per step: front_bin_batch, front_volume_fraction_batch, "
-                     "front_curvature_ppic, front_csf_force_batch, ft_batch_cell_ranges, "
-                     "front_interp_velocity_batch",
+           "launch": ("one CUDA graph per step, a DAG on three streams: front_bin_batch, then "
+                      "front_volume_fraction_batch beside front_curvature_ppic, then front_csf_force_batch and "
+                      "ft_batch_cell_ranges; front_interp_velocity_batch beside all of them" if a.batch_fork else
+                      "one CUDA graph per step: front_bin_batch, front_volume_fraction_batch, "
+                      "front_curvature_ppic, front_csf_force_batch, ft_batch_cell_ranges, "
+                      "front_interp_velocity_batch"),
            "l2": "inputs larger than L2 (dense fields alone 1.4 GB) and a 512 MB flush before every timed step"}
     tuning = None
     for prec, tag in ((F.FT_FP32C, "fp32c"), (F.FT_FP64, "fp64")):
@@ -1052,8 +1057,28 @@ def run_batched(a, dev, local, flush):
             raise RuntimeError(f"batched form: device status {F.status_names(st)}")
         c = bc.ws.counts()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            bc.step()
+        if a.batch_fork:
+            # the step as a DAG (as each front's step in the main leg): the volume
+            # fraction beside the PPIC fit (both need only the binning), the CSF
+            # force after both, the interpolation beside everything
+            sa, si = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+            with torch.cuda.graph(g):
+                cs = torch.cuda.current_stream()
+                si.wait_stream(cs)
+                with torch.cuda.stream(si):
+                    F.front_interp_velocity_batch(bc.ws)
+                F.front_bin_batch(bc.ws, prm)
+                sa.wait_stream(cs)
+                with torch.cuda.stream(sa):
+                    F.front_volume_fraction_batch(bc.ws)
+                F.front_curvature_ppic(bc.ws, prm, bc.cell_keys, bc.kappa, bc.normal, bc.coeffs, bc.fit_status)
+                cs.wait_stream(sa)
+                F.front_csf_force_batch(bc.ws, prm, bc.kappa, bc.normal)
+                F.ft_batch_cell_ranges(bc.ws, bc.off)
+                cs.wait_stream(si)
+        else:
+            with torch.cuda.graph(g):
+                bc.step()
         g.replay()
         torch.cuda.synchronize()
         steps = a.batch_steps if prec == F.FT_FP32C else max(1, a.batch_steps // 2)
