@@ -982,7 +982,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_clip_list(F fr, const int* 
 
 constexpr int kClip32Threads = 128;
 constexpr int kClip32Warps = kClip32Threads / 32;
-constexpr int kPV = 10;          // float polygon capacity (the exact clip of a triangle has at most 9)
+constexpr int kPV = 9;           // float polygon capacity (the exact clip of a triangle has at most 9)
 constexpr float kEps = 3e-7f;    // relative bound of a few float32 roundings (2^-24 = 6e-8 each)
 // A kept fragment whose vertex bound exceeds this (crossings of edges nearly
 // parallel to their plane) takes its record from the binary64 polygon, so that
@@ -1050,13 +1050,14 @@ enum : int { kUndecided = 0, kRejected = 1, kKept = 2 };
 
 // The float32 clip of triangle (tv, in cell units) against the cell [0, top]:
 // exact flags of the triangle's vertices (bit st: inside for stage st), the
-// polygon left in bufs[*res] (n vertices).  Vertex w: < 0 for a triangle
+// polygon left in bufs[*res] (n vertices), its largest vertex bound (emax) and
+// its S2 sum (below).  Vertex w: < 0 for a triangle
 // vertex (-(1 + flags)), else the distance bound of a crossing vertex.  A
 // triangle vertex's coordinates are within kEps (|x|max + W) of the exact ones
 // (ew = kEps W, see k_clip32).
 __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const float top[3], float ew,
                         float4 (*b0)[32], float4 (*b1)[32], int lane, int& n_out, float4 (**res)[32],
-                        float& emax) {
+                        float& emax, float& S2) {
     float4(*src)[32] = b0;
     float4(*dst)[32] = b1;
     for (int c = 0; c < 3; c++) src[c][lane] = make_float4(tv[c][0], tv[c][1], tv[c][2], -(float)(1 + vflags[c]));
@@ -1081,8 +1082,12 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
         }
         if (all) skip |= 1u << st;
     }
-    for (int st = 0; st < 6; st++) {
-        if ((skip >> st) & 1u) continue;
+    // Each lane walks only its own remaining stages, in stage order (a skipped
+    // stage leaves the polygon as it is): the warp's lanes run their first
+    // remaining stage together, then their second, and so on, instead of each
+    // stage idling the lanes that skip it.
+    for (unsigned act = ~skip & 63u; act; act &= act - 1u) {
+        const int st = __ffs(act) - 1;
         const int ax = st >> 1;
         const bool ge = (st & 1) == 0;
         const float pl = ge ? 0.f : top[ax];
@@ -1108,78 +1113,94 @@ __device__ int clip_f32(const float tv[3][3], const unsigned vflags[3], const fl
         const unsigned prevf = (in << 1 | in >> (n - 1)) & ((1u << n) - 1u);
         const unsigned cross = in ^ prevf;
         if (__popc(cross) > 2) return kUndecided;
-        int m = 0;
-        for (int i = 0; i < n; i++) {
-            const float4 b_cur = src[i][lane];
-            if ((cross >> i) & 1u) {
-                // interpolate from the edge's end nearer to the plane (the smaller
-                // step t (b - a) keeps the rounding of q small); a is that end
-                float4 a = src[i == 0 ? n - 1 : i - 1][lane];
-                float4 b = b_cur;
-                if (fabsf(pl - comp(a, ax)) > fabsf(pl - comp(b, ax))) {
-                    const float4 tmp = a;
-                    a = b;
-                    b = tmp;
-                }
-                const float ea = a.w < 0.f ? kEps * fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))) + ew : a.w;
-                const float eb = b.w < 0.f ? kEps * fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z))) + ew : b.w;
-                const float aa = comp(a, ax), ba = comp(b, ax);
-                const float D = ba - aa;
-                const float den = fabsf(D) - 1.01f * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)));
-                if (!(den > 0.f)) return kUndecided;
-                const float t = __fdiv_rn(pl - aa, D);
-                const float tt = fmaxf(fabsf(t), 1.f);
-                // |t - t*| <= (errors of the numerator + |t*| errors of D) / |D*| + the division's rounding
-                const float dt = ((ea + epl + kEps * (fabsf(aa) + fabsf(pl))) +
-                                  tt * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)))) / den + 4.f * kEps * tt;
-                const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-                const float L = fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz)));
-                const float amax = fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z)));
-                const float bmax = fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z)));
-                float4 q;
-                q.x = (ax == 0) ? pl : __fadd_rn(a.x, __fmul_rn(t, dx));
-                q.y = (ax == 1) ? pl : __fadd_rn(a.y, __fmul_rn(t, dy));
-                q.z = (ax == 2) ? pl : __fadd_rn(a.z, __fmul_rn(t, dz));
-                // |q - q*| <= max(ea, eb) + |b - a| |t - t*| + the roundings of q
-                q.w = 1.01f * (fmaxf(ea, eb) + L * dt + 2.f * kEps * tt * (amax + bmax + 1.f));
-                if (m >= kPV) return kUndecided;
-                dst[m++][lane] = q;
+        // Exactly two crossings now (in is neither empty nor full), on the edges
+        // i1-1 -> i1 and i2-1 -> i2; both are computed in straight-line code on
+        // every lane (no per-vertex branch over which lanes cross where).  Each
+        // crossing interpolates from the edge's end nearer to the plane (the
+        // smaller step t (b - a) keeps the rounding of q small); a is that end.
+        const int i1 = __ffs(cross) - 1, i2 = 31 - __clz(cross);
+        const int nin = __popc(in);
+        if (nin + 2 > kPV) return kUndecided;
+        bool bad = false;
+        float4 qv[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const int i = k ? i2 : i1;
+            float4 a = src[i == 0 ? n - 1 : i - 1][lane];
+            float4 b = src[i][lane];
+            if (fabsf(pl - comp(a, ax)) > fabsf(pl - comp(b, ax))) {
+                const float4 tmp = a;
+                a = b;
+                b = tmp;
             }
-            if ((in >> i) & 1u) {
-                if (m >= kPV) return kUndecided;
-                dst[m++][lane] = b_cur;
-            }
+            const float ea = a.w < 0.f ? kEps * fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))) + ew : a.w;
+            const float eb = b.w < 0.f ? kEps * fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z))) + ew : b.w;
+            const float aa = comp(a, ax), ba = comp(b, ax);
+            const float D = ba - aa;
+            const float den = fabsf(D) - 1.01f * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)));
+            bad = bad || !(den > 0.f);
+            const float t = __fdiv_rn(pl - aa, D);
+            const float tt = fmaxf(fabsf(t), 1.f);
+            // |t - t*| <= (errors of the numerator + |t*| errors of D) / |D*| + the division's rounding
+            const float dt = ((ea + epl + kEps * (fabsf(aa) + fabsf(pl))) +
+                              tt * (ea + eb + kEps * (fabsf(aa) + fabsf(ba)))) / den + 4.f * kEps * tt;
+            const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+            const float L = fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz)));
+            const float amax = fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z)));
+            const float bmax = fmaxf(fabsf(b.x), fmaxf(fabsf(b.y), fabsf(b.z)));
+            float4 q;
+            q.x = (ax == 0) ? pl : __fadd_rn(a.x, __fmul_rn(t, dx));
+            q.y = (ax == 1) ? pl : __fadd_rn(a.y, __fmul_rn(t, dy));
+            q.z = (ax == 2) ? pl : __fadd_rn(a.z, __fmul_rn(t, dz));
+            // |q - q*| <= max(ea, eb) + |b - a| |t - t*| + the roundings of q
+            q.w = 1.01f * (fmaxf(ea, eb) + L * dt + 2.f * kEps * tt * (amax + bmax + 1.f));
+            qv[k] = q;
         }
-        if (m < 3) return kRejected;
-        n = m;
+        if (bad) return kUndecided;
+        // The output in Sutherland-Hodgman order (for i = 0 .. n-1: the crossing
+        // of edge i-1 -> i, then vertex i if inside), each entry stored at the
+        // position that order gives it.
+        for (int i = 0; i < n; i++)
+            if ((in >> i) & 1u) dst[__popc(in & ((1u << i) - 1u)) + (i1 <= i) + (i2 <= i)][lane] = src[i][lane];
+        dst[__popc(in & ((1u << i1) - 1u))][lane] = qv[0];
+        dst[__popc(in & ((1u << i2) - 1u)) + 1][lane] = qv[1];
+        n = nin + 2;
         float4(*tmp)[32] = src;
         src = dst;
         dst = tmp;
     }
-    float e = 0.f;
+    // One pass over the surviving polygon: the largest vertex bound; S2, the
+    // sum over vertices i of |p_i+1 - p_i-1| (max norm), which bounds the
+    // area's error for the caller; and per axis whether every vertex lies within
+    // its bounds of the upper face (such a fragment may lie in it exactly in
+    // binary64).
+    float e = 0.f, s2 = 0.f;
+    bool on[3] = {true, true, true};
+    float4 vp = src[n - 1][lane], v = src[0][lane];
     for (int i = 0; i < n; i++) {
-        const float4 v = src[i][lane];
-        e = fmaxf(e, v.w < 0.f ? kEps * fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))) + ew : v.w);
-    }
-    // a fragment within its bounds of an upper face may lie in it exactly in binary64
-    for (int ax = 0; ax < 3; ax++) {
-        bool all = true;
-        for (int i = 0; i < n && all; i++) {
-            const float4 v = src[i][lane];
+        const float4 vn = src[i + 1 < n ? i + 1 : 0][lane];
+        s2 += fmaxf(fabsf(vn.x - vp.x), fmaxf(fabsf(vn.y - vp.y), fabsf(vn.z - vp.z)));
+        const bool tri = v.w < 0.f;
+        e = fmaxf(e, tri ? kEps * fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))) + ew : v.w);
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
             const float x = comp(v, ax);
-            const float ev = v.w < 0.f ? kEps * fabsf(x) + ew : v.w;
-            all = fabsf(x - top[ax]) <= 2.02f * (ev + kEps * (fabsf(x) + 2.f * fabsf(top[ax]))) + 1e-30f;
+            const float ev = tri ? kEps * fabsf(x) + ew : v.w;
+            on[ax] = on[ax] && fabsf(x - top[ax]) <= 2.02f * (ev + kEps * (fabsf(x) + 2.f * fabsf(top[ax]))) + 1e-30f;
         }
-        if (all) return kUndecided;
+        vp = v;
+        v = vn;
     }
+    if (on[0] || on[1] || on[2]) return kUndecided;
     n_out = n;
     *res = src;
     emax = e;
+    S2 = s2;
     return kKept;
 }
 
 template <class F>
-__global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* __restrict__ cand_tri,
+__global__ void __launch_bounds__(kClip32Threads, 6) k_clip32(F fr, const int* __restrict__ cand_tri,
                                                            const int* __restrict__ tri_off,
                                                            const int* __restrict__ tri_box,
                                                            const float* __restrict__ tri32,
@@ -1235,9 +1256,9 @@ __global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* _
         const float ew = 1e-8f + 4e-15f * (float)(max(max(bb0.w, bb1.x), bb1.y) + 1);
         int n = 0;
         float4(*poly)[32] = nullptr;
-        float emax = 0.f;
+        float emax = 0.f, S2 = 0.f;
         int verdict = on_top ? kRejected : clip_f32(tv, vflags, top, ew, s_poly[w][0], s_poly[w][1], lane, n, &poly,
-                                                    emax);
+                                                    emax, S2);
         unsigned key = FT_SENTINEL;
         ft_frag32 f;
         const float tn[3] = {r4.z, r4.w, r5.x};
@@ -1248,13 +1269,8 @@ __global__ void __launch_bounds__(kClip32Threads, 5) k_clip32(F fr, const int* _
             // Moving the vertices p_i by d_i changes the area vector by
             // (1/2) sum_i d_i x (p_i+1 - p_i-1) + O(d^2): at most emax S2 + n emax^2
             // per component, S2 = sum_i |p_i+1 - p_i-1| (max norm, widened by the
-            // vertex errors); the fan sum adds its own rounding (a few ulps of
-            // its terms)
-            float S2 = 0.f;
-            for (int i = 0; i < n; i++) {
-                const float4 pp = poly[i + 1 < n ? i + 1 : 0][lane], pm = poly[i > 0 ? i - 1 : n - 1][lane];
-                S2 += fmaxf(fabsf(pp.x - pm.x), fmaxf(fabsf(pp.y - pm.y), fabsf(pp.z - pm.z)));
-            }
+            // vertex errors; summed by clip_f32); the fan sum adds its own
+            // rounding (a few ulps of its terms)
             const float a = fmaxf(fabsf(f.an[0]), fmaxf(fabsf(f.an[1]), fabsf(f.an[2])));
             const float bound = 1.01f * (emax * (S2 + 2.f * (float)n * emax) + (float)n * emax * emax) +
                                 32.f * kEps * absum + 1e-30f;
