@@ -418,9 +418,13 @@ def run_ours(a):
     def step_forked(prm, fc, v, t, fa, sd, sa, si):
         """One front's step as a small DAG: the volume fraction and the PPIC fit
         both need only the binning (they may share a workspace on two streams),
-        the CSF force needs both, the interpolation only the face velocities."""
+        the CSF force needs both, the interpolation only the face velocities.
+        The force's clear needs nothing: it runs beside the binning
+        (front_force_clear, then front_csf_force_cells after the fit)."""
         with torch.cuda.stream(si):
             F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+        with torch.cuda.stream(sa):
+            F.front_force_clear(fc.ws, fc.force)
         with torch.cuda.stream(sd):
             F.front_bin(fc.ws, v, t, prm)
         sa.wait_stream(sd)
@@ -429,7 +433,7 @@ def run_ours(a):
         with torch.cuda.stream(sd):
             F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
             sd.wait_stream(sa)
-            F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+            F.front_csf_force_cells(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
 
     def capture(prm, fcs, dfr=dfr):
         """One CUDA graph for a whole step; the fronts are independent, so each
@@ -745,6 +749,9 @@ def run_ours(a):
                 # the interpolation beside both (once the faces are up)
                 alpha_ready, force_ready, vel_ready = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
                 sd, sa, si = sds[f], sas[f], sis[f]
+                if d is None:
+                    with torch.cuda.stream(sa):
+                        F.front_force_clear(fc.ws, fc.force)  # beside the binning
                 with torch.cuda.stream(sd):
                     sd.wait_event(vt_in[f])
                     F.front_bin(fc.ws, v, t, prm)
@@ -767,7 +774,7 @@ def run_ours(a):
                         F.front_csf_force_compact(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, d["keys"], d["force"],
                                                   d["count"])
                     else:
-                        F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+                        F.front_csf_force_cells(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
                     force_ready.record(sd)
                 with torch.cuda.stream(dn):
                     M = c["M"]
@@ -865,8 +872,8 @@ def run_ours(a):
                                    "FP64 path: 1e-12 / 1e-9 (checked by tests/test_gpu_parity.py)",
                    "l2": "flushed (512 MB write) before every timed step",
                    "launch": "eager" if a.no_graph else (
-                       "one CUDA graph per step, per front a DAG on three streams (alpha beside the PPIC fit, "
-                       "the interpolation beside both)" if a.fork else
+                       "one CUDA graph per step, per front a DAG on three streams (the force clear beside the "
+                       "binning, alpha beside the PPIC fit, the interpolation beside all)" if a.fork else
                        "one CUDA graph per step, the two fronts on two streams"),
                    "parallelism": f"replicas x{ws}",
                    "launch_shapes": ([{k: t[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm",
@@ -1027,9 +1034,10 @@ def run_batched(a, dev, local, flush):
            "fronts": len(fr), "triangles": int(sum(f["tris"].shape[0] for f in fr)),
            "grid_cells": int(sum(f["grid"].ncells for f in fr)),
            "radius_capped": int(sum(f["capped"] for f in fr)),
-           "launch": ("one CUDA graph per step, a DAG on three streams: front_bin_batch, then "
-                      "front_volume_fraction_batch beside front_curvature_ppic, then front_csf_force_batch and "
-                      "ft_batch_cell_ranges; front_interp_velocity_batch beside all of them" if a.batch_fork else
+           "launch": ("one CUDA graph per step, a DAG on three streams: front_force_clear_batch beside "
+                      "front_bin_batch, then front_volume_fraction_batch beside front_curvature_ppic, then "
+                      "front_csf_force_cells_batch and ft_batch_cell_ranges; front_interp_velocity_batch beside all "
+                      "of them" if a.batch_fork else
                       "one CUDA graph per step: front_bin_batch, front_volume_fraction_batch, "
                       "front_curvature_ppic, front_csf_force_batch, ft_batch_cell_ranges, "
                       "front_interp_velocity_batch"),
@@ -1058,22 +1066,26 @@ def run_batched(a, dev, local, flush):
         c = bc.ws.counts()
         g = torch.cuda.CUDAGraph()
         if a.batch_fork:
-            # the step as a DAG (as each front's step in the main leg): the volume
-            # fraction beside the PPIC fit (both need only the binning), the CSF
-            # force after both, the interpolation beside everything
+            # the step as a DAG (as each front's step in the main leg): the force
+            # clear beside the binning, the volume fraction beside the PPIC fit
+            # (both need only the binning), the CSF force after both, the
+            # interpolation beside everything
             sa, si = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
             with torch.cuda.graph(g):
                 cs = torch.cuda.current_stream()
                 si.wait_stream(cs)
+                sa.wait_stream(cs)
                 with torch.cuda.stream(si):
                     F.front_interp_velocity_batch(bc.ws)
+                with torch.cuda.stream(sa):
+                    F.front_force_clear_batch(bc.ws)
                 F.front_bin_batch(bc.ws, prm)
                 sa.wait_stream(cs)
                 with torch.cuda.stream(sa):
                     F.front_volume_fraction_batch(bc.ws)
                 F.front_curvature_ppic(bc.ws, prm, bc.cell_keys, bc.kappa, bc.normal, bc.coeffs, bc.fit_status)
                 cs.wait_stream(sa)
-                F.front_csf_force_batch(bc.ws, prm, bc.kappa, bc.normal)
+                F.front_csf_force_cells_batch(bc.ws, prm, bc.kappa, bc.normal)
                 F.ft_batch_cell_ranges(bc.ws, bc.off)
                 cs.wait_stream(si)
         else:

@@ -220,6 +220,21 @@ int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint
 int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                     const double* normal, double* force, void* stream);
 
+/* (a4, split) front_csf_force as two calls, so that the clear of the dense
+ * force arrays (the one part of Eq. csf that needs no front data: S_P = 0 in
+ * every cell that is neither interfacial nor a face neighbour of one, Sec. 3.3)
+ * can run early in the step, beside the binning, instead of after the PPIC fit.
+ * front_force_clear sets force (3 x n0*n1*n2 float64, device, caller-owned) to
+ * zero; it needs no binning.  front_csf_force_cells writes S_P of
+ * front_csf_force in the interfacial cells and their face neighbours and
+ * leaves every other cell of force as it is: after front_force_clear (both
+ * calls ordered on one stream, or by an event), force holds exactly what
+ * front_csf_force writes.  Arguments and errors as for front_csf_force;
+ * FT_ERR_ARG on a batch workspace. */
+int front_force_clear(ft_workspace* ws, double* force, void* stream);
+int front_csf_force_cells(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                          const double* normal, double* force, void* stream);
+
 /* (a4, compact) The CSF source of front_csf_force written only where it can be
  * non-zero (the interfacial cells and their face neighbours, Sec. 3.3): per
  * slot a cell key (keys, uint32) and its force (force, 3 float64: x, y, z).
@@ -414,6 +429,12 @@ int front_volume_fraction_batch(ft_workspace* ws, void* stream);
 /* (a4) front_csf_force of every front from its alpha into its force. */
 int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
                           void* stream);
+
+/* (a4, split) front_force_clear and front_csf_force_cells of every front of
+ * the table (the table's force arrays; FT_ERR_STATE before ft_batch_set). */
+int front_force_clear_batch(ft_workspace* ws, void* stream);
+int front_csf_force_cells_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                                void* stream);
 
 /* front_face_force of every front, from its alpha into its face_force arrays. */
 int front_face_force_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,

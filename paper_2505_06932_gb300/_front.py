@@ -86,6 +86,8 @@ def lib():
                 "front_volume_fraction": (I32, [P, P, P]),
                 "front_curvature_ppic": (I32, [P, P, I64, P, P, P, P, P, P]),
                 "front_csf_force": (I32, [P, P, P, P, P, P, P]),
+                "front_force_clear": (I32, [P, P, P]),
+                "front_csf_force_cells": (I32, [P, P, P, P, P, P, P]),
                 "front_interp_velocity": (I32, [P, P, P, P, P, I64, P, P]),
                 "ft_probe_fma_rate": (I32, [I32, I32, C.POINTER(C.c_double)]),
                 "ft_launch_count": (I64, []),
@@ -100,6 +102,8 @@ def lib():
                 "front_bin_batch": (I32, [P, P, P]),
                 "front_volume_fraction_batch": (I32, [P, P]),
                 "front_csf_force_batch": (I32, [P, P, P, P, P]),
+                "front_force_clear_batch": (I32, [P, P]),
+                "front_csf_force_cells_batch": (I32, [P, P, P, P, P]),
                 "front_interp_velocity_batch": (I32, [P, P]),
                 "ft_batch_cell_ranges": (I32, [P, P, P]),
                 "ft_batch_status": (I32, [P, P, P]),
@@ -325,6 +329,24 @@ def front_csf_force(ws: Workspace, params: FtParams, alpha, kappa, normal, force
                                  _ptr(force, torch.float64, "force"), _stream(stream)), "front_csf_force")
 
 
+def front_force_clear(ws: Workspace, force, stream=None):
+    """The dense force arrays set to zero (the first half of front_csf_force)."""
+    if force.numel() != 3 * ws.grid.ncells:
+        raise FrontError("force must hold 3*n0*n1*n2 values")
+    _check(lib().front_force_clear(ws.handle, _ptr(force, torch.float64, "force"), _stream(stream)),
+           "front_force_clear")
+
+
+def front_csf_force_cells(ws: Workspace, params: FtParams, alpha, kappa, normal, force, stream=None):
+    """front_csf_force without the clear: only the cells where the force can be
+    non-zero are written (the rest of force must be zero already)."""
+    if force.numel() != 3 * ws.grid.ncells:
+        raise FrontError("force must hold 3*n0*n1*n2 values")
+    _check(lib().front_csf_force_cells(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),
+                                       _ptr(kappa, torch.float64, "kappa"), _ptr(normal, torch.float64, "normal"),
+                                       _ptr(force, torch.float64, "force"), _stream(stream)), "front_csf_force_cells")
+
+
 def front_csf_force_compact(ws: Workspace, params: FtParams, alpha, kappa, normal, keys, force, count, stream=None):
     """Compact CSF force: keys (int32/uint32 view, cap), force (cap, 3) float64,
     count (1) int64 on the device receives the number of slots."""
@@ -466,6 +488,16 @@ def front_csf_force_batch(ws: BatchWorkspace, params: FtParams, kappa, normal, s
     _check(lib().front_csf_force_batch(ws.handle, C.byref(params), _ptr(kappa, torch.float64, "kappa"),
                                        _ptr(normal, torch.float64, "normal"), _stream(stream)),
            "front_csf_force_batch")
+
+
+def front_force_clear_batch(ws: BatchWorkspace, stream=None):
+    _check(lib().front_force_clear_batch(ws.handle, _stream(stream)), "front_force_clear_batch")
+
+
+def front_csf_force_cells_batch(ws: BatchWorkspace, params: FtParams, kappa, normal, stream=None):
+    _check(lib().front_csf_force_cells_batch(ws.handle, C.byref(params), _ptr(kappa, torch.float64, "kappa"),
+                                             _ptr(normal, torch.float64, "normal"), _stream(stream)),
+           "front_csf_force_cells_batch")
 
 
 def front_interp_velocity_batch(ws: BatchWorkspace, stream=None):

@@ -420,7 +420,21 @@ int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, c
     if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || !force) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream)));
+    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream), true));
+}
+
+int front_force_clear(ft_workspace* ws, double* force, void* stream) {
+    if (!ws || ws->batch || !force) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_force_clear(ws, force, as_stream(stream)));
+}
+
+int front_csf_force_cells(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
+                          const double* normal, double* force, void* stream) {
+    if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || !force) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream), false));
 }
 
 int front_csf_force_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
@@ -486,7 +500,26 @@ int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* ka
     for (int b = 0; b < ws->nf; b++)
         if (!ws->h_fdesc[b].alpha || !ws->h_fdesc[b].force) return FT_ERR_ARG;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream)));
+    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream), true));
+}
+
+int front_force_clear_batch(ft_workspace* ws, void* stream) {
+    if (!ws || !ws->batch) return FT_ERR_ARG;
+    if (ws->nf < 1) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++)
+        if (!ws->h_fdesc[b].force) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_force_clear_batch(ws, as_stream(stream)));
+}
+
+int front_csf_force_cells_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
+                                void* stream) {
+    if (!ws || !ws->batch || !params_ok(p) || !kappa || !normal) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    for (int b = 0; b < ws->nf; b++)
+        if (!ws->h_fdesc[b].alpha || !ws->h_fdesc[b].force) return FT_ERR_ARG;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream), false));
 }
 
 int front_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,

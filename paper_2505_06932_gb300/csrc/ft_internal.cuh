@@ -197,8 +197,10 @@ cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s);
 cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, unsigned* cell_keys,
                         double* kappa, double* normal, double* coeffs, int8_t* fit_status,
                         cudaStream_t s);
+// the CSF force; clear: zero the dense arrays first (else the caller has)
 cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha,
-                       const double* kappa, const double* normal, double* force, cudaStream_t s);
+                       const double* kappa, const double* normal, double* force, cudaStream_t s, bool clear);
+cudaError_t launch_force_clear(ft_workspace* ws, double* force, cudaStream_t s);
 // compact outputs (one front): force at the interfacial and ring cells with their
 // keys; alpha as a bit per cell (alpha > 1/2) and the interfacial cells' values
 cudaError_t launch_csf_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
@@ -212,7 +214,8 @@ cudaError_t launch_interp(const ft_grid* g, const double* U, const double* V, co
 cudaError_t launch_bin_batch(ft_workspace* ws, const ft_params* p, cudaStream_t s);
 cudaError_t launch_alpha_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
-                             cudaStream_t s);
+                             cudaStream_t s, bool clear);
+cudaError_t launch_force_clear_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_interp_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_advect(const ft_grid* g, const double* U, const double* V, const double* W,
                           const double* verts, long long nv, double dt, double* verts_out, double* vel,

@@ -345,22 +345,34 @@ __global__ void __launch_bounds__(kThreads) k_face_force(F fr, double sigma, con
 
 namespace ft {
 
+// the dense force arrays of every front of fr set to zero
 template <class F>
-cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const double* kappa, const double* normal,
-                     cudaStream_t s, CsfOut out = CsfOut{nullptr, nullptr, 0, nullptr}) {
-    // the ring list lives in the sort's spare key buffer (max_cand entries)
-    unsigned* ring = ws->keys[ws->sorted_buf ^ 1];
-    unsigned* nring = &ws->ctr->pad;
-    cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
-    if (out.keys) {
-        // compact output: no dense array to clear
-    } else if constexpr (std::is_same<F, FrontsOne>::value) {
+cudaError_t clear_with(ft_workspace* ws, const F& fr, cudaStream_t s) {
+    if constexpr (std::is_same<F, FrontsOne>::value) {
         Trace t(s, "force clear (memset)");
-        cudaMemsetAsync(fr.d0.force, 0, 3 * sizeof(double) * (size_t)fr.ncells, s);
+        const cudaError_t e = cudaMemsetAsync(fr.d0.force, 0, 3 * sizeof(double) * (size_t)fr.ncells, s);
+        if (e != cudaSuccess) return e;
     } else {
         count_launches(1);
         Trace t(s, "k_zero_force");
         k_zero_force<F><<<ws->sm_count * ws->tune.csf_bps, kThreads, 0, s>>>(fr);
+    }
+    return cudaGetLastError();
+}
+
+// The force in the cells where it can be non-zero, after the dense arrays are
+// cleared here (clear) or by the caller beforehand (!clear); the compact output
+// has no dense array.
+template <class F>
+cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const double* kappa, const double* normal,
+                     cudaStream_t s, bool clear, CsfOut out = CsfOut{nullptr, nullptr, 0, nullptr}) {
+    // the ring list lives in the sort's spare key buffer (max_cand entries)
+    unsigned* ring = ws->keys[ws->sorted_buf ^ 1];
+    unsigned* nring = &ws->ctr->pad;
+    cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
+    if (clear && !out.keys) {
+        const cudaError_t e = clear_with(ws, fr, s);
+        if (e != cudaSuccess) return e;
     }
     count_launches(2);
     {
@@ -379,7 +391,7 @@ cudaError_t launch_csf_compact(ft_workspace* ws, const ft_params* p, const doubl
                                cudaStream_t s) {
     FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
     fr.d0.alpha = const_cast<double*>(alpha);  // read only here
-    return csf_with(ws, fr, p, kappa, normal, s, CsfOut{keys, force, cap, count});
+    return csf_with(ws, fr, p, kappa, normal, s, false, CsfOut{keys, force, cap, count});
 }
 
 cudaError_t launch_alpha_pack(ft_workspace* ws, const double* alpha, long long cap, unsigned* bits, double* acells,
@@ -391,17 +403,25 @@ cudaError_t launch_alpha_pack(ft_workspace* ws, const double* alpha, long long c
 }
 
 cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
-                       const double* normal, double* force, cudaStream_t s) {
+                       const double* normal, double* force, cudaStream_t s, bool clear) {
     FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
     fr.d0.alpha = const_cast<double*>(alpha);  // read only here
     fr.d0.force = force;
-    return csf_with(ws, fr, p, kappa, normal, s);
+    return csf_with(ws, fr, p, kappa, normal, s, clear);
 }
 
 cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
-                             cudaStream_t s) {
-    return csf_with(ws, ft_many(ws), p, kappa, normal, s);
+                             cudaStream_t s, bool clear) {
+    return csf_with(ws, ft_many(ws), p, kappa, normal, s, clear);
 }
+
+cudaError_t launch_force_clear(ft_workspace* ws, double* force, cudaStream_t s) {
+    FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
+    fr.d0.force = force;
+    return clear_with(ws, fr, s);
+}
+
+cudaError_t launch_force_clear_batch(ft_workspace* ws, cudaStream_t s) { return clear_with(ws, ft_many(ws), s); }
 
 cudaError_t launch_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                               const double* normal, double* fx, double* fy, double* fz, cudaStream_t s) {
