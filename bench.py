@@ -78,10 +78,11 @@ def kernel_work(name, w, fp32):
         "k_alpha_fill": ("hbm", 12 * N + 16 * M, "per grid cell the index map read and alpha written; per "
                          "interfacial cell L and P read"),
         "force clear (memset)": ("hbm", 24 * N, "the three force components written in every grid cell"),
-        "k_csf_cells": ("hbm", 84 * M + 4 * R, "per interfacial cell its key, six alpha values, kappa, the "
-                        "force written; the ring list"),
-        "k_csf_ring": ("hbm", 176 * R, "per ring cell 26 index-map entries, six alpha values, the force "
-                       "written"),
+        "k_csf_ring_list": ("hbm", 28 * M + 4 * R, "per interfacial cell its key and six face neighbours' "
+                            "index-map entries read; the ring list written"),
+        "k_csf_force": ("hbm", 84 * M + 176 * R, "per interfacial cell its key, six alpha values and kappa read "
+                        "and the force written; per ring cell 26 index-map entries and six alpha values read and "
+                        "the force written"),
         "k_interp": ("hbm", 288 * V, "per vertex its position read, its velocity written and about 30 face "
                      "values gathered"),
         "k_clip32": ("fp32", FLOPS_PER_CAND * C + FLOPS_PER_KEPT * P,
@@ -419,8 +420,9 @@ def run_ours(a):
         """One front's step as a small DAG: the volume fraction and the PPIC fit
         both need only the binning (they may share a workspace on two streams),
         the CSF force needs both, the interpolation only the face velocities.
-        The force's clear needs nothing: it runs beside the binning
-        (front_force_clear, then front_csf_force_cells after the fit)."""
+        The force's clear needs nothing: it runs beside the binning; its ring
+        list needs only the binning: it runs beside the fit (front_force_clear,
+        front_csf_prepare, then front_csf_force_cells after the fit)."""
         with torch.cuda.stream(si):
             F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
         with torch.cuda.stream(sa):
@@ -430,6 +432,7 @@ def run_ours(a):
         sa.wait_stream(sd)
         with torch.cuda.stream(sa):
             F.front_volume_fraction(fc.ws, fc.alpha)
+            F.front_csf_prepare(fc.ws)
         with torch.cuda.stream(sd):
             F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
             sd.wait_stream(sa)
@@ -760,6 +763,8 @@ def run_ours(a):
                     F.front_volume_fraction(fc.ws, fc.alpha)
                     if d is not None:
                         F.front_alpha_pack(fc.ws, fc.alpha, d["bits"], d["acells"])
+                    else:
+                        F.front_csf_prepare(fc.ws)  # the ring list beside the fit
                     alpha_ready.record(sa)
                 with torch.cuda.stream(si):
                     si.wait_event(vt_in[f])
@@ -873,7 +878,8 @@ def run_ours(a):
                    "l2": "flushed (512 MB write) before every timed step",
                    "launch": "eager" if a.no_graph else (
                        "one CUDA graph per step, per front a DAG on three streams (the force clear beside the "
-                       "binning, alpha beside the PPIC fit, the interpolation beside all)" if a.fork else
+                       "binning, alpha and the CSF ring list beside the PPIC fit, the interpolation beside all)"
+                       if a.fork else
                        "one CUDA graph per step, the two fronts on two streams"),
                    "parallelism": f"replicas x{ws}",
                    "launch_shapes": ([{k: t[k] for k in ("clip_blocks_per_sm", "ppic_blocks_per_sm",
@@ -1035,9 +1041,9 @@ def run_batched(a, dev, local, flush):
            "grid_cells": int(sum(f["grid"].ncells for f in fr)),
            "radius_capped": int(sum(f["capped"] for f in fr)),
            "launch": ("one CUDA graph per step, a DAG on three streams: front_force_clear_batch beside "
-                      "front_bin_batch, then front_volume_fraction_batch beside front_curvature_ppic, then "
-                      "front_csf_force_cells_batch and ft_batch_cell_ranges; front_interp_velocity_batch beside all "
-                      "of them" if a.batch_fork else
+                      "front_bin_batch, then front_volume_fraction_batch and front_csf_prepare beside "
+                      "front_curvature_ppic, then front_csf_force_cells_batch and ft_batch_cell_ranges; "
+                      "front_interp_velocity_batch beside all of them" if a.batch_fork else
                       "one CUDA graph per step: front_bin_batch, front_volume_fraction_batch, "
                       "front_curvature_ppic, front_csf_force_batch, ft_batch_cell_ranges, "
                       "front_interp_velocity_batch"),
@@ -1083,6 +1089,7 @@ def run_batched(a, dev, local, flush):
                 sa.wait_stream(cs)
                 with torch.cuda.stream(sa):
                     F.front_volume_fraction_batch(bc.ws)
+                    F.front_csf_prepare(bc.ws)
                 F.front_curvature_ppic(bc.ws, prm, bc.cell_keys, bc.kappa, bc.normal, bc.coeffs, bc.fit_status)
                 cs.wait_stream(sa)
                 F.front_csf_force_cells_batch(bc.ws, prm, bc.kappa, bc.normal)

@@ -220,18 +220,27 @@ int front_curvature_ppic(ft_workspace* ws, const ft_params* p, int64_t cap, uint
 int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                     const double* normal, double* force, void* stream);
 
-/* (a4, split) front_csf_force as two calls, so that the clear of the dense
- * force arrays (the one part of Eq. csf that needs no front data: S_P = 0 in
- * every cell that is neither interfacial nor a face neighbour of one, Sec. 3.3)
- * can run early in the step, beside the binning, instead of after the PPIC fit.
- * front_force_clear sets force (3 x n0*n1*n2 float64, device, caller-owned) to
- * zero; it needs no binning.  front_csf_force_cells writes S_P of
- * front_csf_force in the interfacial cells and their face neighbours and
- * leaves every other cell of force as it is: after front_force_clear (both
- * calls ordered on one stream, or by an event), force holds exactly what
- * front_csf_force writes.  Arguments and errors as for front_csf_force;
- * FT_ERR_ARG on a batch workspace. */
+/* (a4, split) front_csf_force as three calls, so that its parts that need
+ * neither kappa nor alpha can run earlier in the step, off the chain of calls
+ * that the force waits for.  The force of Eq. csf is non-zero only in the
+ * interfacial cells and their face neighbours (Sec. 3.3: the gradient of alpha
+ * vanishes between full or empty cells); the non-interfacial ones among those
+ * neighbours are the "ring" cells, whose curvature is the smoothed one.
+ *   front_force_clear sets force (3 x n0*n1*n2 float64, device, caller-owned)
+ *     to zero; it needs no binning (so it can run beside front_bin).
+ *   front_csf_prepare lists the ring cells of the last front_bin (or
+ *     front_bin_batch) in the workspace; it needs only the binning (so it can
+ *     run beside front_curvature_ppic).  One-front and batch workspaces.
+ *   front_csf_force_cells writes S_P of front_csf_force in the interfacial and
+ *     ring cells and leaves every other cell of force as it is; it reads the
+ *     list of the last front_csf_prepare, which must have been issued after the
+ *     last front_bin (else FT_ERR_STATE).
+ * After front_force_clear and front_csf_prepare (ordered before the cells call
+ * on one stream or by events), force holds exactly what front_csf_force
+ * writes.  Arguments and errors as for front_csf_force; front_force_clear and
+ * front_csf_force_cells give FT_ERR_ARG on a batch workspace. */
 int front_force_clear(ft_workspace* ws, double* force, void* stream);
+int front_csf_prepare(ft_workspace* ws, void* stream);
 int front_csf_force_cells(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                           const double* normal, double* force, void* stream);
 
@@ -431,7 +440,9 @@ int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* ka
                           void* stream);
 
 /* (a4, split) front_force_clear and front_csf_force_cells of every front of
- * the table (the table's force arrays; FT_ERR_STATE before ft_batch_set). */
+ * the table (the table's force arrays; FT_ERR_STATE before ft_batch_set, and
+ * for the cells call without a front_csf_prepare after the last
+ * front_bin_batch). */
 int front_force_clear_batch(ft_workspace* ws, void* stream);
 int front_csf_force_cells_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
                                 void* stream);

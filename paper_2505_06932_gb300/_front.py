@@ -87,6 +87,7 @@ def lib():
                 "front_curvature_ppic": (I32, [P, P, I64, P, P, P, P, P, P]),
                 "front_csf_force": (I32, [P, P, P, P, P, P, P]),
                 "front_force_clear": (I32, [P, P, P]),
+                "front_csf_prepare": (I32, [P, P]),
                 "front_csf_force_cells": (I32, [P, P, P, P, P, P, P]),
                 "front_interp_velocity": (I32, [P, P, P, P, P, I64, P, P]),
                 "ft_probe_fma_rate": (I32, [I32, I32, C.POINTER(C.c_double)]),
@@ -337,9 +338,16 @@ def front_force_clear(ws: Workspace, force, stream=None):
            "front_force_clear")
 
 
+def front_csf_prepare(ws: Workspace, stream=None):
+    """The ring cells of the current binning (one-front or batch workspace),
+    listed ahead of front_csf_force_cells(_batch); needs only the binning."""
+    _check(lib().front_csf_prepare(ws.handle, _stream(stream)), "front_csf_prepare")
+
+
 def front_csf_force_cells(ws: Workspace, params: FtParams, alpha, kappa, normal, force, stream=None):
-    """front_csf_force without the clear: only the cells where the force can be
-    non-zero are written (the rest of force must be zero already)."""
+    """front_csf_force without the clear and the ring list (front_csf_prepare
+    after the last binning): only the cells where the force can be non-zero are
+    written (the rest of force must be zero already)."""
     if force.numel() != 3 * ws.grid.ncells:
         raise FrontError("force must hold 3*n0*n1*n2 values")
     _check(lib().front_csf_force_cells(ws.handle, C.byref(params), _ptr(alpha, torch.float64, "alpha"),

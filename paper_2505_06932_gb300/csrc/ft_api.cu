@@ -349,6 +349,7 @@ int front_bin(ft_workspace* ws, const ft_front* f, const ft_params* p, void* str
     ws->f_tris = f->tris;
     ws->f_nv = f->nv;
     ws->f_nt = f->nt;
+    ws->bin_epoch++;
     cudaError_t e = ft::launch_bin(ws, f, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     ws->binned = (e == cudaSuccess);
@@ -420,7 +421,16 @@ int front_csf_force(ft_workspace* ws, const ft_params* p, const double* alpha, c
     if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || !force) return FT_ERR_ARG;
     if (!ws->binned) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream), true));
+    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream), true, true));
+}
+
+int front_csf_prepare(ft_workspace* ws, void* stream) {
+    if (!ws) return FT_ERR_ARG;
+    if (!ws->binned) return FT_ERR_STATE;
+    if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
+    const cudaError_t e = ft::launch_csf_prepare(ws, as_stream(stream));
+    if (e == cudaSuccess) ws->ring_epoch = ws->bin_epoch;
+    return cuda_err(e);
 }
 
 int front_force_clear(ft_workspace* ws, double* force, void* stream) {
@@ -432,9 +442,9 @@ int front_force_clear(ft_workspace* ws, double* force, void* stream) {
 int front_csf_force_cells(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
                           const double* normal, double* force, void* stream) {
     if (!ws || ws->batch || !params_ok(p) || !alpha || !kappa || !normal || !force) return FT_ERR_ARG;
-    if (!ws->binned) return FT_ERR_STATE;
+    if (!ws->binned || ws->ring_epoch != ws->bin_epoch) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream), false));
+    return cuda_err(ft::launch_csf(ws, p, alpha, kappa, normal, force, as_stream(stream), false, false));
 }
 
 int front_csf_force_compact(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
@@ -477,6 +487,7 @@ int front_bin_batch(ft_workspace* ws, const ft_params* p, void* stream) {
     if (ws->nf < 1) return FT_ERR_STATE;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
     cudaStream_t s = as_stream(stream);
+    ws->bin_epoch++;
     cudaError_t e = ft::launch_bin_batch(ws, p, s);
     if (e == cudaSuccess) e = ft::launch_place_pairs(ws, ws->ncells, s);
     ws->binned = (e == cudaSuccess);
@@ -500,7 +511,7 @@ int front_csf_force_batch(ft_workspace* ws, const ft_params* p, const double* ka
     for (int b = 0; b < ws->nf; b++)
         if (!ws->h_fdesc[b].alpha || !ws->h_fdesc[b].force) return FT_ERR_ARG;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream), true));
+    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream), true, true));
 }
 
 int front_force_clear_batch(ft_workspace* ws, void* stream) {
@@ -515,11 +526,11 @@ int front_force_clear_batch(ft_workspace* ws, void* stream) {
 int front_csf_force_cells_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
                                 void* stream) {
     if (!ws || !ws->batch || !params_ok(p) || !kappa || !normal) return FT_ERR_ARG;
-    if (!ws->binned) return FT_ERR_STATE;
+    if (!ws->binned || ws->ring_epoch != ws->bin_epoch) return FT_ERR_STATE;
     for (int b = 0; b < ws->nf; b++)
         if (!ws->h_fdesc[b].alpha || !ws->h_fdesc[b].force) return FT_ERR_ARG;
     if (cudaSetDevice(ws->device) != cudaSuccess) return FT_ERR_CUDA;
-    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream), false));
+    return cuda_err(ft::launch_csf_batch(ws, p, kappa, normal, as_stream(stream), false, false));
 }
 
 int front_face_force(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,

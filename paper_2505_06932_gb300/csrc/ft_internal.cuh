@@ -96,6 +96,9 @@ struct ft_workspace {
     int last_precision;
     bool sys_fp32;         // the last PPIC call left its normal equations as float pairs
     bool clip32_ok;        // every grid keeps |coordinate| / h within the float32 clip's bounds
+    // binnings issued on this workspace, and the binning the ring list of
+    // front_csf_prepare belongs to (host-side order of the calls)
+    unsigned long long bin_epoch, ring_epoch;
 
     ft_counters* ctr;
     int* idx_map;          // ncells: interfacial index or -1
@@ -197,9 +200,12 @@ cudaError_t launch_alpha(ft_workspace* ws, double* alpha, cudaStream_t s);
 cudaError_t launch_ppic(ft_workspace* ws, const ft_params* p, long long cap, unsigned* cell_keys,
                         double* kappa, double* normal, double* coeffs, int8_t* fit_status,
                         cudaStream_t s);
-// the CSF force; clear: zero the dense arrays first (else the caller has)
+// the CSF force; clear: zero the dense arrays first (else the caller has);
+// list: list the ring cells first (else launch_csf_prepare has, for this binning)
 cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha,
-                       const double* kappa, const double* normal, double* force, cudaStream_t s, bool clear);
+                       const double* kappa, const double* normal, double* force, cudaStream_t s, bool clear,
+                       bool list);
+cudaError_t launch_csf_prepare(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_force_clear(ft_workspace* ws, double* force, cudaStream_t s);
 // compact outputs (one front): force at the interfacial and ring cells with their
 // keys; alpha as a bit per cell (alpha > 1/2) and the interfacial cells' values
@@ -214,7 +220,7 @@ cudaError_t launch_interp(const ft_grid* g, const double* U, const double* V, co
 cudaError_t launch_bin_batch(ft_workspace* ws, const ft_params* p, cudaStream_t s);
 cudaError_t launch_alpha_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
-                             cudaStream_t s, bool clear);
+                             cudaStream_t s, bool clear, bool list);
 cudaError_t launch_force_clear_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_interp_batch(ft_workspace* ws, cudaStream_t s);
 cudaError_t launch_advect(const ft_grid* g, const double* U, const double* V, const double* W,

@@ -8,13 +8,14 @@
 // either side differ only if the front passes through P; so P is interfacial
 // or a face neighbour of an interfacial cell.  Hence:
 //  * the force arrays are zeroed (a memset, or k_zero_force for a batch);
-//  * k_csf_cells -- seven threads per interfacial cell: one writes its own
-//    force sigma kappa grad alpha (central differences, alpha = 0 outside the
-//    grid), each of the others looks at one face neighbour and lists it as a
-//    ring cell when it is not interfacial and this cell is the smallest-key
-//    interfacial face neighbour it has (so it is listed once);
-//  * k_csf_ring -- one thread per ring cell: the smoothed curvature and the
-//    force.
+//  * k_csf_ring_list -- six threads per interfacial cell, each looking at one
+//    face neighbour and listing it as a ring cell when it is not interfacial
+//    and this cell is the smallest-key interfacial face neighbour it has (so
+//    it is listed once); it needs only the binning, so a caller may run it
+//    beside the PPIC fit (front_csf_prepare);
+//  * k_csf_force -- one thread per interfacial cell (its force sigma kappa
+//    grad alpha, central differences, alpha = 0 outside the grid) and per ring
+//    cell (the smoothed curvature and the force), in one launch.
 #include <type_traits>
 
 #include "ft_internal.cuh"
@@ -59,20 +60,19 @@ __global__ void __launch_bounds__(kThreads) k_zero_force(F fr) {
     }
 }
 
-// Seven tasks per interfacial cell (one thread each): task 0 writes the cell's
-// own force; task 1 + e looks at the face neighbour e and lists it as a ring
-// cell when it is not interfacial and this cell is its smallest-key
-// interfacial face neighbour.
+// Six tasks per interfacial cell (one thread each): task e looks at the face
+// neighbour e and lists it as a ring cell when it is not interfacial and this
+// cell is its smallest-key interfacial face neighbour (so that it is listed
+// once).  Needs only the binning.
 template <class F>
-__global__ void __launch_bounds__(kThreads) k_csf_cells(F fr, double sigma, const unsigned* __restrict__ cells,
-                                                        const int* __restrict__ idx_map,
-                                                        const double* __restrict__ kappa,
-                                                        unsigned* __restrict__ ring, unsigned* __restrict__ nring,
-                                                        long long ring_cap, ft_counters* ctr, CsfOut out) {
+__global__ void __launch_bounds__(kThreads) k_csf_ring_list(F fr, const unsigned* __restrict__ cells,
+                                                            const int* __restrict__ idx_map,
+                                                            unsigned* __restrict__ ring, unsigned* __restrict__ nring,
+                                                            long long ring_cap, ft_counters* ctr) {
     const long long M = ctr->M;
-    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < 7 * M; w += (long long)gridDim.x * kThreads) {
-        const long long m = w / 7;
-        const int task = (int)(w - 7 * m);
+    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < 6 * M; w += (long long)gridDim.x * kThreads) {
+        const long long m = w / 6;
+        const int e = (int)(w - 6 * m);
         const long long gkey = cells[m];
         const int b = fr.by_key(gkey);
         const ft_fdesc& D = fr.desc(b);
@@ -84,35 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_csf_cells(F fr, double sigma, cons
         const long long s0 = (long long)n1 * n2, s1 = n2;
         const int c[3] = {(int)i, (int)j, (int)k}, n[3] = {(int)n0, (int)n1, (int)n2};
         const long long st[3] = {s0, s1, 1};
-        if (task == 0) {
-            const long long NC = (long long)n0 * n1 * n2;
-            const double* __restrict__ alpha = D.alpha;
-            double a[6];
-#pragma unroll
-            for (int e = 0; e < 6; e++) {
-                const int ax = e >> 1, sg = (e & 1) ? -1 : 1;
-                a[e] = (c[ax] + sg >= 0 && c[ax] + sg < n[ax]) ? alpha[key + sg * st[ax]] : 0.0;
-            }
-            const double ih2 = 0.5 * D.inv_h;
-            const double f = sigma * kappa[m];
-            const double fx = f * ((a[0] - a[1]) * ih2), fy = f * ((a[2] - a[3]) * ih2),
-                         fz = f * ((a[4] - a[5]) * ih2);
-            if (out.keys) {
-                if (m < out.cap) {
-                    out.keys[m] = key;
-                    out.f[3 * m] = fx;
-                    out.f[3 * m + 1] = fy;
-                    out.f[3 * m + 2] = fz;
-                }
-            } else {
-                double* __restrict__ force = D.force;
-                force[key] = fx;
-                force[NC + key] = fy;
-                force[2 * NC + key] = fz;
-            }
-            continue;
-        }
-        const int e = task - 1, ax = e >> 1, sg = (e & 1) ? -1 : 1;
+        const int ax = e >> 1, sg = (e & 1) ? -1 : 1;
         if (c[ax] + sg < 0 || c[ax] + sg >= n[ax]) continue;
         const long long q = (long long)key + sg * st[ax];
         if (idx_map[kb + q] >= 0) continue;
@@ -135,85 +107,146 @@ __global__ void __launch_bounds__(kThreads) k_csf_cells(F fr, double sigma, cons
     }
 }
 
-// One thread per ring cell.  The 26 index-map lookups are issued together
-// (independent loads) before the float64 smoothing sums, which then run once
-// per cell instead of once per lane of a warp-wide reduction.
+// The force of interfacial cell m: sigma kappa_m grad alpha (central
+// differences, alpha = 0 outside the grid), into slot m or the dense arrays.
 template <class F>
-__global__ void __launch_bounds__(128) k_csf_ring(F fr, double sigma, const int* __restrict__ idx_map,
-                                                  const double* __restrict__ kappa, const double* __restrict__ normal,
-                                                  const unsigned* __restrict__ ring, const unsigned* __restrict__ nring,
-                                                  long long ring_cap, ft_counters* ctr, CsfOut out) {
+__device__ __forceinline__ void cell_force(const F& fr, double sigma, const unsigned* __restrict__ cells,
+                                           const double* __restrict__ kappa, long long m, const CsfOut& out) {
+    const long long gkey = cells[m];
+    const int b = fr.by_key(gkey);
+    const ft_fdesc& D = fr.desc(b);
+    const unsigned n0 = (unsigned)D.g.n[0], n1 = (unsigned)D.g.n[1], n2 = (unsigned)D.g.n[2];
+    const long long kb = fr.key_base(b);
+    const unsigned key = (unsigned)(gkey - kb);
+    const unsigned col = key / n2, k = key - col * n2;
+    const unsigned i = col / n1, j = col - i * n1;
+    const long long s0 = (long long)n1 * n2, s1 = n2;
+    const int c[3] = {(int)i, (int)j, (int)k}, n[3] = {(int)n0, (int)n1, (int)n2};
+    const long long st[3] = {s0, s1, 1};
+    const long long NC = (long long)n0 * n1 * n2;
+    const double* __restrict__ alpha = D.alpha;
+    double a[6];
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        const int ax = e >> 1, sg = (e & 1) ? -1 : 1;
+        a[e] = (c[ax] + sg >= 0 && c[ax] + sg < n[ax]) ? alpha[key + sg * st[ax]] : 0.0;
+    }
+    const double ih2 = 0.5 * D.inv_h;
+    const double f = sigma * kappa[m];
+    const double fx = f * ((a[0] - a[1]) * ih2), fy = f * ((a[2] - a[3]) * ih2), fz = f * ((a[4] - a[5]) * ih2);
+    if (out.keys) {
+        if (m < out.cap) {
+            out.keys[m] = key;
+            out.f[3 * m] = fx;
+            out.f[3 * m + 1] = fy;
+            out.f[3 * m + 2] = fz;
+        }
+    } else {
+        double* __restrict__ force = D.force;
+        force[key] = fx;
+        force[NC + key] = fy;
+        force[2 * NC + key] = fz;
+    }
+}
+
+// The force of ring cell r (slot M + r): the smoothed curvature over its
+// interfacial neighbours times sigma grad alpha.  The 26 index-map lookups are
+// issued together (independent loads) before the float64 smoothing sums, which
+// then run once per cell instead of once per lane of a warp-wide reduction.
+template <class F>
+__device__ __forceinline__ void ring_force(const F& fr, double sigma, const int* __restrict__ idx_map,
+                                           const double* __restrict__ kappa, const double* __restrict__ normal,
+                                           const unsigned* __restrict__ ring, long long r, long long M,
+                                           const CsfOut& out) {
+    const long long gkey = ring[r];
+    const int b = fr.by_key(gkey);
+    const ft_fdesc& D = fr.desc(b);
+    const int n0 = D.g.n[0], n1 = D.g.n[1], n2 = D.g.n[2];
+    const long long NC = (long long)n0 * n1 * n2;
+    const long long s1 = n2, s0 = (long long)n1 * n2;
+    const double* __restrict__ alpha = D.alpha;
+    const long long kb = fr.key_base(b);
+    const long long key = gkey - kb;
+    const unsigned ukey = (unsigned)key, ucol = ukey / (unsigned)n2;
+    const int k = (int)(ukey - ucol * (unsigned)n2);
+    const int i = (int)(ucol / (unsigned)n1);
+    const int j = (int)(ucol - (unsigned)i * (unsigned)n1);
+    int q[26];
+#pragma unroll
+    for (int c = 0; c < 26; c++) {
+        const int code = c < 13 ? c : c + 1;  // the 27 offsets without the centre
+        const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
+        const int ii = i + di, jj = j + dj, kk = k + dk;
+        const bool in = ii >= 0 && ii < n0 && jj >= 0 && jj < n1 && kk >= 0 && kk < n2;
+        q[c] = in ? idx_map[kb + key + (long long)di * s0 + (long long)dj * s1 + dk] : -1;
+    }
+    const double axp = (i + 1 < n0) ? alpha[key + s0] : 0.0;
+    const double axm = (i > 0) ? alpha[key - s0] : 0.0;
+    const double ayp = (j + 1 < n1) ? alpha[key + s1] : 0.0;
+    const double aym = (j > 0) ? alpha[key - s1] : 0.0;
+    const double azp = (k + 1 < n2) ? alpha[key + 1] : 0.0;
+    const double azm = (k > 0) ? alpha[key - 1] : 0.0;
+    double num = 0.0, den = 0.0, ks = 0.0;
+    int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < 26; c++) {
+        if (q[c] < 0) continue;
+        const int code = c < 13 ? c : c + 1;
+        const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
+        const int nsq = di * di + dj * dj + dk * dk;
+        const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
+        const double* nq = normal + 3 * (long long)q[c];
+        const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
+        const double kq = kappa[q[c]];
+        num += kq * w;
+        den += w;
+        ks += kq;
+        cnt++;
+    }
+    const double ih2 = 0.5 * D.inv_h;
+    const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
+    const double kp = (den > 0.0) ? num / den : (cnt ? ks / cnt : 0.0);
+    const double f = sigma * kp;
+    if (out.keys) {
+        const long long slot = M + r;
+        if (slot < out.cap) {
+            out.keys[slot] = ukey;
+            out.f[3 * slot] = f * gx;
+            out.f[3 * slot + 1] = f * gy;
+            out.f[3 * slot + 2] = f * gz;
+        }
+    } else {
+        double* __restrict__ force = D.force;
+        force[key] = f * gx;
+        force[NC + key] = f * gy;
+        force[2 * NC + key] = f * gz;
+    }
+}
+
+// The CSF force of every interfacial cell (items [0, M)) and every listed ring
+// cell (items [M, M + nring)) in one launch, after the PPIC fit; the ring
+// list comes from k_csf_ring_list, which needs only the binning and so can run
+// beside the fit.
+template <class F>
+__global__ void __launch_bounds__(kThreads) k_csf_force(F fr, double sigma, const unsigned* __restrict__ cells,
+                                                        const int* __restrict__ idx_map,
+                                                        const double* __restrict__ kappa,
+                                                        const double* __restrict__ normal,
+                                                        const unsigned* __restrict__ ring,
+                                                        const unsigned* __restrict__ nring, long long ring_cap,
+                                                        ft_counters* ctr, CsfOut out) {
+    const long long M = ctr->M;
     const long long nr = min((long long)*nring, ring_cap);
     if (out.keys && blockIdx.x == 0 && threadIdx.x == 0) {
-        const long long total = ctr->M + nr;
+        const long long total = M + nr;
         *out.count = total;
         if (total > out.cap) ft_flag(ctr, FT_ST_CAPACITY);
     }
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
-         r += (long long)gridDim.x * blockDim.x) {
-        const long long gkey = ring[r];
-        const int b = fr.by_key(gkey);
-        const ft_fdesc& D = fr.desc(b);
-        const int n0 = D.g.n[0], n1 = D.g.n[1], n2 = D.g.n[2];
-        const long long NC = (long long)n0 * n1 * n2;
-        const long long s1 = n2, s0 = (long long)n1 * n2;
-        const double* __restrict__ alpha = D.alpha;
-        const long long kb = fr.key_base(b);
-        const long long key = gkey - kb;
-        const unsigned ukey = (unsigned)key, ucol = ukey / (unsigned)n2;
-        const int k = (int)(ukey - ucol * (unsigned)n2);
-        const int i = (int)(ucol / (unsigned)n1);
-        const int j = (int)(ucol - (unsigned)i * (unsigned)n1);
-        int q[26];
-#pragma unroll
-        for (int c = 0; c < 26; c++) {
-            const int code = c < 13 ? c : c + 1;  // the 27 offsets without the centre
-            const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
-            const int ii = i + di, jj = j + dj, kk = k + dk;
-            const bool in = ii >= 0 && ii < n0 && jj >= 0 && jj < n1 && kk >= 0 && kk < n2;
-            q[c] = in ? idx_map[kb + key + (long long)di * s0 + (long long)dj * s1 + dk] : -1;
-        }
-        const double axp = (i + 1 < n0) ? alpha[key + s0] : 0.0;
-        const double axm = (i > 0) ? alpha[key - s0] : 0.0;
-        const double ayp = (j + 1 < n1) ? alpha[key + s1] : 0.0;
-        const double aym = (j > 0) ? alpha[key - s1] : 0.0;
-        const double azp = (k + 1 < n2) ? alpha[key + 1] : 0.0;
-        const double azm = (k > 0) ? alpha[key - 1] : 0.0;
-        double num = 0.0, den = 0.0, ks = 0.0;
-        int cnt = 0;
-#pragma unroll
-        for (int c = 0; c < 26; c++) {
-            if (q[c] < 0) continue;
-            const int code = c < 13 ? c : c + 1;
-            const int di = code / 9 - 1, dj = (code / 3) % 3 - 1, dk = code % 3 - 1;
-            const int nsq = di * di + dj * dj + dk * dk;
-            const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
-            const double* nq = normal + 3 * (long long)q[c];
-            const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
-            const double kq = kappa[q[c]];
-            num += kq * w;
-            den += w;
-            ks += kq;
-            cnt++;
-        }
-        const double ih2 = 0.5 * D.inv_h;
-        const double gx = (axp - axm) * ih2, gy = (ayp - aym) * ih2, gz = (azp - azm) * ih2;
-        const double kp = (den > 0.0) ? num / den : (cnt ? ks / cnt : 0.0);
-        const double f = sigma * kp;
-        if (out.keys) {
-            const long long slot = ctr->M + r;
-            if (slot < out.cap) {
-                out.keys[slot] = ukey;
-                out.f[3 * slot] = f * gx;
-                out.f[3 * slot + 1] = f * gy;
-                out.f[3 * slot + 2] = f * gz;
-            }
-        } else {
-            double* __restrict__ force = D.force;
-            force[key] = f * gx;
-            force[NC + key] = f * gy;
-            force[2 * NC + key] = f * gz;
-        }
+    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < M + nr; w += (long long)gridDim.x * kThreads) {
+        if (w < M)
+            cell_force(fr, sigma, cells, kappa, w, out);
+        else
+            ring_force(fr, sigma, idx_map, kappa, normal, ring, w - M, M, out);
     }
 }
 
@@ -360,29 +393,37 @@ cudaError_t clear_with(ft_workspace* ws, const F& fr, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// The force in the cells where it can be non-zero, after the dense arrays are
-// cleared here (clear) or by the caller beforehand (!clear); the compact output
-// has no dense array.
+// The ring list of the current binning (the face neighbours of interfacial
+// cells that are not interfacial themselves), in the sort's spare key buffer
+// (max_cand entries, free once the pairs are placed); its length in ctr->pad.
+template <class F>
+cudaError_t ring_with(ft_workspace* ws, const F& fr, cudaStream_t s) {
+    unsigned* nring = &ws->ctr->pad;
+    const cudaError_t e = cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    Trace t(s, "k_csf_ring_list");
+    k_csf_ring_list<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, ws->cells, ws->idx_map, ws->keys[ws->sorted_buf ^ 1],
+                                                             nring, ws->max_cand, ws->ctr);
+    return cudaGetLastError();
+}
+
+// The force in the cells where it can be non-zero: the ring list made here
+// (list) or by the caller beforehand for the same binning (!list), then the
+// dense arrays cleared here (clear) or by the caller beforehand (!clear; the
+// compact output has no dense array), then one launch over the interfacial
+// and ring cells.
 template <class F>
 cudaError_t csf_with(ft_workspace* ws, const F& fr, const ft_params* p, const double* kappa, const double* normal,
-                     cudaStream_t s, bool clear, CsfOut out = CsfOut{nullptr, nullptr, 0, nullptr}) {
-    // the ring list lives in the sort's spare key buffer (max_cand entries)
-    unsigned* ring = ws->keys[ws->sorted_buf ^ 1];
-    unsigned* nring = &ws->ctr->pad;
-    cudaMemsetAsync(nring, 0, sizeof(unsigned), s);
-    if (clear && !out.keys) {
-        const cudaError_t e = clear_with(ws, fr, s);
-        if (e != cudaSuccess) return e;
-    }
-    count_launches(2);
-    {
-        Trace t(s, "k_csf_cells");
-        k_csf_cells<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, p->sigma, ws->cells, ws->idx_map, kappa, ring, nring,
-                                                             ws->max_cand, ws->ctr, out);
-    }
-    Trace t(s, "k_csf_ring");
-    k_csf_ring<F><<<ws->sm_count * 4, 128, 0, s>>>(fr, p->sigma, ws->idx_map, kappa, normal, ring, nring,
-                                                   ws->max_cand, ws->ctr, out);
+                     cudaStream_t s, bool clear, bool list, CsfOut out = CsfOut{nullptr, nullptr, 0, nullptr}) {
+    cudaError_t e = list ? ring_with(ws, fr, s) : cudaSuccess;
+    if (e == cudaSuccess && clear && !out.keys) e = clear_with(ws, fr, s);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    Trace t(s, "k_csf_force");
+    k_csf_force<F><<<ws->sm_count * 4, kThreads, 0, s>>>(fr, p->sigma, ws->cells, ws->idx_map, kappa, normal,
+                                                         ws->keys[ws->sorted_buf ^ 1], &ws->ctr->pad, ws->max_cand,
+                                                         ws->ctr, out);
     return cudaGetLastError();
 }
 
@@ -391,7 +432,7 @@ cudaError_t launch_csf_compact(ft_workspace* ws, const ft_params* p, const doubl
                                cudaStream_t s) {
     FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
     fr.d0.alpha = const_cast<double*>(alpha);  // read only here
-    return csf_with(ws, fr, p, kappa, normal, s, false, CsfOut{keys, force, cap, count});
+    return csf_with(ws, fr, p, kappa, normal, s, false, true, CsfOut{keys, force, cap, count});
 }
 
 cudaError_t launch_alpha_pack(ft_workspace* ws, const double* alpha, long long cap, unsigned* bits, double* acells,
@@ -403,16 +444,21 @@ cudaError_t launch_alpha_pack(ft_workspace* ws, const double* alpha, long long c
 }
 
 cudaError_t launch_csf(ft_workspace* ws, const ft_params* p, const double* alpha, const double* kappa,
-                       const double* normal, double* force, cudaStream_t s, bool clear) {
+                       const double* normal, double* force, cudaStream_t s, bool clear, bool list) {
     FrontsOne fr = ft_one(ws, nullptr, nullptr, 0, 0);
     fr.d0.alpha = const_cast<double*>(alpha);  // read only here
     fr.d0.force = force;
-    return csf_with(ws, fr, p, kappa, normal, s, clear);
+    return csf_with(ws, fr, p, kappa, normal, s, clear, list);
 }
 
 cudaError_t launch_csf_batch(ft_workspace* ws, const ft_params* p, const double* kappa, const double* normal,
-                             cudaStream_t s, bool clear) {
-    return csf_with(ws, ft_many(ws), p, kappa, normal, s, clear);
+                             cudaStream_t s, bool clear, bool list) {
+    return csf_with(ws, ft_many(ws), p, kappa, normal, s, clear, list);
+}
+
+cudaError_t launch_csf_prepare(ft_workspace* ws, cudaStream_t s) {
+    if (ws->batch) return ring_with(ws, ft_many(ws), s);
+    return ring_with(ws, ft_one(ws, nullptr, nullptr, 0, 0), s);
 }
 
 cudaError_t launch_force_clear(ft_workspace* ws, double* force, cudaStream_t s) {

@@ -83,10 +83,12 @@ def test_compact_force_capacity_flagged():
 
 @pytest.mark.parametrize("precision", [F.FT_FP64, F.FT_FP32C], ids=["fp64", "fp32c"])
 def test_split_force_equals_front_csf_force(precision):
-    """front_force_clear + front_csf_force_cells (the clear on a side stream
-    forked before the binning and joined before the force, as the bench's graph
-    step runs it, captured in a CUDA graph) give front_csf_force's array bit for
-    bit, whatever the array held before."""
+    """front_force_clear + front_csf_prepare + front_csf_force_cells (the clear
+    on a side stream forked before the binning, alpha and the ring list on
+    another beside the fit, both joined before the force, as the bench's graph
+    step runs them, also captured in a CUDA graph) give front_csf_force's array
+    bit for bit, whatever the array held before; the cells call without a ring
+    list for the current binning is a call-order error."""
     w = I.rough_sphere_128(2)
     dev = torch.device("cuda", 0)
     v = torch.from_numpy(w["verts"]).to(dev)
@@ -98,7 +100,7 @@ def test_split_force_equals_front_csf_force(precision):
     torch.cuda.synchronize()
     assert fc.ws.status() == 0
     ref = fc.force.clone()
-    side = torch.cuda.Stream(device=dev)
+    side, side2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def split():
         cs = torch.cuda.current_stream()
@@ -106,9 +108,13 @@ def test_split_force_equals_front_csf_force(precision):
         with torch.cuda.stream(side):
             F.front_force_clear(fc.ws, fc.force)
         F.front_bin(fc.ws, v, t, prm)
-        F.front_volume_fraction(fc.ws, fc.alpha)
+        side2.wait_stream(cs)
+        with torch.cuda.stream(side2):
+            F.front_volume_fraction(fc.ws, fc.alpha)
+            F.front_csf_prepare(fc.ws)  # beside the fit
         F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
         cs.wait_stream(side)
+        cs.wait_stream(side2)
         F.front_csf_force_cells(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
 
     fc.force.fill_(float("nan"))
@@ -123,6 +129,13 @@ def test_split_force_equals_front_csf_force(precision):
     torch.cuda.synchronize()
     assert fc.ws.status() == 0
     assert torch.equal(fc.force.view(torch.int64), ref.view(torch.int64))
+    # a new binning makes the ring list stale: the cells call is refused until
+    # front_csf_prepare lists it again
+    F.front_bin(fc.ws, v, t, prm)
+    with pytest.raises(F.FrontError):
+        F.front_csf_force_cells(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
+    F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
+    F.front_csf_prepare(fc.ws)
     # the cells call alone leaves every cell where the force is zero as it was
     fc.force.fill_(3.0)
     F.front_csf_force_cells(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
@@ -157,6 +170,7 @@ def test_split_force_batch_equals_front_csf_force_batch():
         F.front_force_clear_batch(bc.ws)
     F.front_bin_batch(bc.ws, prm)
     F.front_volume_fraction_batch(bc.ws)
+    F.front_csf_prepare(bc.ws)
     F.front_curvature_ppic(bc.ws, prm, bc.cell_keys, bc.kappa, bc.normal, bc.coeffs, bc.fit_status)
     cs.wait_stream(side)
     F.front_csf_force_cells_batch(bc.ws, prm, bc.kappa, bc.normal)

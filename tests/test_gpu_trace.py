@@ -34,7 +34,7 @@ def test_trace_counts_every_kernel_of_a_step(precision):
     clip = "k_clip32" if precision == F.FT_FP32C else "k_clip"
     acc = "k_ppic_acc<float>" if precision == F.FT_FP32C else "k_ppic_acc<double>"
     for k in ("k_tri_setup", clip, "k_cnt_down", "k_place", "k_cell_order", "k_alpha_fill", acc,
-              "k_ppic_solve", "k_csf_cells", "k_csf_ring", "k_interp"):
+              "k_ppic_solve", "k_csf_ring_list", "k_csf_force", "k_interp"):
         n, ms = tr[k]
         assert n == 3 and ms > 0.0, k
     # nothing traced once the trace is closed, and a second stop is an error
