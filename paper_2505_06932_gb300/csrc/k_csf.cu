@@ -196,7 +196,26 @@ __device__ __forceinline__ void ring_force(const F& fr, double sigma, const int*
         const int nsq = di * di + dj * dj + dk * dk;
         const double inv_len = nsq == 1 ? 1.0 : (nsq == 2 ? 0.70710678118654752440 : 0.57735026918962576451);
         const double* nq = normal + 3 * (long long)q[c];
-        const double w = fabs(di * nq[0] + dj * nq[1] + dk * nq[2]) * inv_len;
+        // s_Q . n_Q with the offset's zero components left out (c is a
+        // compile-time constant here, so only the non-zero terms are formed:
+        // for a finite normal the sum is the same, term for term, as the full
+        // dot product, whose other products are zeros)
+        double dot = 0.0;
+        bool any = false;
+        if (di != 0) {
+            dot = di > 0 ? nq[0] : -nq[0];
+            any = true;
+        }
+        if (dj != 0) {
+            const double t = dj > 0 ? nq[1] : -nq[1];
+            dot = any ? dot + t : t;
+            any = true;
+        }
+        if (dk != 0) {
+            const double t = dk > 0 ? nq[2] : -nq[2];
+            dot = any ? dot + t : t;
+        }
+        const double w = nsq == 1 ? fabs(dot) : fabs(dot) * inv_len;
         const double kq = kappa[q[c]];
         num += kq * w;
         den += w;
