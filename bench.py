@@ -202,6 +202,9 @@ def parse():
     ap.add_argument("--e2e-upload-streams", type=int, default=1,
                     help="staggered/graph e2e leg: copy streams the face-velocity uploads are spread over "
                          "(round robin over the face arrays; vertices and triangles go first on the first)")
+    ap.add_argument("--e2e-faces", choices=("inplace", "copy"), default="copy",
+                    help="face velocities of the e2e leg: read in place from pinned host memory by the "
+                         "interpolation kernel, or copied to the device every step (the other is measured beside)")
     ap.add_argument("--e2e-outputs", choices=("compact", "dense"), default="compact",
                     help="e2e leg: download alpha and the force in the compact form (front_alpha_pack, "
                          "front_csf_force_compact: the same information) or as dense arrays")
@@ -720,7 +723,9 @@ def run_ours(a):
         e2e_streams = dict(sides=[torch.cuda.Stream(device=dev) for _ in fcs],
                            copies=[torch.cuda.Stream(device=dev) for _ in fcs])
 
-    def e2e_enqueue(cs):
+    def e2e_enqueue(cs, inplace):
+        # inplace: the face velocities stay in the pinned host buffers and the
+        # interpolation reads the values it needs there (no face upload)
         if stag:
             sds, ups, dns = e2e_streams["sds"], e2e_streams["ups"], e2e_streams["dns"]
             sas, sis = e2e_streams["sas"], e2e_streams["sis"]
@@ -736,7 +741,7 @@ def run_ours(a):
             j = 0
             for f, ((hv, ht, hf), (v, t, fa)) in enumerate(zip(hin, dfr)):
                 used = []
-                for dst, src in zip(fa, hf):
+                for dst, src in ([] if inplace else zip(fa, hf)):
                     u = ups[j % len(ups)]
                     j += 1
                     with torch.cuda.stream(u):
@@ -770,7 +775,8 @@ def run_ours(a):
                     si.wait_event(vt_in[f])
                     for ev in faces_in[f]:
                         si.wait_event(ev)
-                    F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+                    fu = hin[f][2] if inplace else fa
+                    F.front_interp_velocity(fc.grid, fu[0], fu[1], fu[2], v, fc.vel[:v.shape[0]])
                     vel_ready.record(si)
                 with torch.cuda.stream(sd):
                     F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
@@ -810,7 +816,7 @@ def run_ours(a):
             for (hv, ht, hf), (v, t, fa), fc, o, c, sd, cp in zip(hin, dfr, fcs, hout, counts, sides, copies):
                 faces_in, alpha_ready = torch.cuda.Event(), torch.cuda.Event()
                 with torch.cuda.stream(cp):
-                    for dst, src in zip(fa, hf):
+                    for dst, src in ([] if inplace else zip(fa, hf)):
                         dst.copy_(src, non_blocking=True)
                     faces_in.record(cp)
                 with torch.cuda.stream(sd):
@@ -822,7 +828,8 @@ def run_ours(a):
                     F.front_curvature_ppic(fc.ws, prm, fc.cell_keys, fc.kappa, fc.normal, fc.coeffs, fc.fit_status)
                     F.front_csf_force(fc.ws, prm, fc.alpha, fc.kappa, fc.normal, fc.force)
                     sd.wait_event(faces_in)
-                    F.front_interp_velocity(fc.grid, fa[0], fa[1], fa[2], v, fc.vel[:v.shape[0]])
+                    fu = hf if inplace else fa
+                    F.front_interp_velocity(fc.grid, fu[0], fu[1], fu[2], v, fc.vel[:v.shape[0]])
                     M = c["M"]
                     o["force"].copy_(fc.force, non_blocking=True)
                     o["kappa"].copy_(fc.kappa[:M], non_blocking=True)
@@ -835,28 +842,36 @@ def run_ours(a):
                 cs.wait_stream(sd)
                 cs.wait_stream(cp)
 
-    e2e_graph = None
-    if a.e2e_mode == "graph":
-        # the step above captured once (copies from and to the same pinned host
-        # buffers, which a caller refills between steps) and replayed every step
-        e2e_graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(e2e_graph):
-            e2e_enqueue(torch.cuda.current_stream())
-        torch.cuda.synchronize()
-    e2e_ms = 0.0
-    for _ in range(a.e2e_steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        if e2e_graph is not None:
-            e2e_graph.replay()
-        else:
-            e2e_enqueue(stream)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
-    e2e_max = allmax(ws, e2e_ms)
-    e2e_value = allsum(ws, cells_per_step * a.e2e_steps) / (e2e_max * 1e-3)
+    def time_e2e(inplace):
+        e2e_graph = None
+        if a.e2e_mode == "graph":
+            # the step above captured once (copies from and to the same pinned host
+            # buffers, which a caller refills between steps) and replayed every step
+            e2e_graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(e2e_graph):
+                e2e_enqueue(torch.cuda.current_stream(), inplace)
+            torch.cuda.synchronize()
+        e2e_ms = 0.0
+        for _ in range(a.e2e_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if e2e_graph is not None:
+                e2e_graph.replay()
+            else:
+                e2e_enqueue(stream, inplace)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+        return allsum(ws, cells_per_step * a.e2e_steps) / (allmax(ws, e2e_ms) * 1e-3)
+
+    # the main e2e number reads the faces in place (a.e2e_faces); the other way
+    # is measured beside it
+    faces_inplace = a.e2e_faces == "inplace"
+    e2e_value = time_e2e(faces_inplace)
+    e2e_other = time_e2e(not faces_inplace)
+    h2d_faces = sum(f.numel() * 8 for _, _, hf in hin for f in hf)
+    nv_all = sum(hv.shape[0] for hv, _, _ in hin)
 
     # the paper's own indicator on the same fits: alpha_P, surface-averaged kappa and normal
     parab = measure_paraboloid(fcs, counts, a.paraboloid_reps, flush, stream) if a.paraboloid_reps > 0 else None
@@ -894,8 +909,16 @@ def run_ours(a):
         "same_workload_as_one_batch": one_batch,
         "other_configs": configs,
         "paraboloid": parab,
-        "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": round(e2e_value, 1), "unit": "interfacial cells/s",
+                "h2d_bytes_per_step": h2d - (h2d_faces if faces_inplace else 0),
                 "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
+                "faces": ("left in the pinned host buffers and read in place by the interpolation kernel (at most "
+                          f"54 face values, 432 B, per vertex: {432 * nv_all} B per step at most; "
+                          f"{h2d_faces} B of face arrays in host memory)" if faces_inplace else
+                          f"copied to the device every step ({h2d_faces} B)"),
+                ("faces_copied" if faces_inplace else "faces_in_place"): {
+                    "value": round(e2e_other, 1),
+                    "h2d_bytes_per_step": h2d - (0 if faces_inplace else h2d_faces)},
                 "mode": a.e2e_mode, "outputs": a.e2e_outputs + (
                     ": alpha as one bit per cell plus the interfacial values, the CSF force at its non-zero cells "
                     "with their keys, kappa, normal, vertex velocities" if compact else
@@ -906,7 +929,8 @@ def run_ours(a):
                              "the fronts one after the other on one compute stream (the first front's outputs go "
                              "down while the second is computed), ") +
                             "each front's calls as the DAG of the graph step, one upload stream (vertices and "
-                            "triangles of every front first, then the face velocities), a download stream per front"
+                            "triangles of every front" + ("" if faces_inplace else " first, then the face velocities")
+                            + "), a download stream per front"
                             if stag else
                             "per front a compute stream and a copy stream (faces up and alpha down overlap the "
                             "binning and the fit), the two fronts concurrently"))},

@@ -318,7 +318,14 @@ int front_volume_fraction_ppic(ft_workspace* ws, const double* coeffs, int64_t c
  * face velocities U (n0+1,n1,n2), V (n0,n1+1,n2), W (n0,n1,n2+1) to the nv
  * points verts (nv x 3) into vel (nv x 3).  The cell is floor((x - origin)/h)
  * clamped to the grid; transverse face gradients are central differences,
- * one-sided on the first and last face rows.  Needs no workspace. */
+ * one-sided on the first and last face rows.  Needs no workspace.
+ * U, V and W may be device arrays or page-locked host memory mapped into the
+ * device's address space (cudaHostAlloc or cudaHostRegister; with unified
+ * addressing the host pointer is the device pointer): the kernel then reads
+ * in place only the face values around the points (at most 54 per point; on
+ * GB300 over NVLink-C2C), so a caller whose face field lives on the host need
+ * not copy the whole field.  The result is the same bit for bit.  verts and vel
+ * are device arrays. */
 int front_interp_velocity(const ft_grid* g, const double* U, const double* V, const double* W,
                           const double* verts, int64_t nv, double* vel, void* stream);
 

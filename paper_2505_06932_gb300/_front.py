@@ -158,6 +158,18 @@ def _ptr(t: torch.Tensor, dtype, what: str):
     return C.c_void_p(t.data_ptr())
 
 
+def _ptr_faces(t: torch.Tensor, what: str):
+    """A face array: a CUDA tensor, or a page-locked host tensor that the
+    kernel reads in place (mapped host memory)."""
+    if t is not None and not t.is_cuda:
+        if not t.is_pinned():
+            raise FrontError(f"{what} must be a CUDA tensor or pinned host memory")
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise FrontError(f"{what} must be contiguous float64")
+        return C.c_void_p(t.data_ptr())
+    return _ptr(t, torch.float64, what)
+
+
 def make_grid(g) -> FtGrid:
     s = FtGrid()
     for d in range(3):
@@ -445,8 +457,8 @@ def front_interp_velocity(grid, U, V, W, verts, vel, stream=None):
     if tuple(U.shape) != (n[0] + 1, n[1], n[2]) or tuple(V.shape) != (n[0], n[1] + 1, n[2]) \
             or tuple(W.shape) != (n[0], n[1], n[2] + 1):
         raise FrontError("face arrays have the wrong shapes")
-    _check(lib().front_interp_velocity(C.byref(g), _ptr(U, torch.float64, "U"), _ptr(V, torch.float64, "V"),
-                                       _ptr(W, torch.float64, "W"), _ptr(verts, torch.float64, "verts"),
+    _check(lib().front_interp_velocity(C.byref(g), _ptr_faces(U, "U"), _ptr_faces(V, "V"),
+                                       _ptr_faces(W, "W"), _ptr(verts, torch.float64, "verts"),
                                        verts.shape[0], _ptr(vel, torch.float64, "vel"), _stream(stream)),
            "front_interp_velocity")
 
