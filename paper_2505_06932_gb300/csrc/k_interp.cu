@@ -51,7 +51,16 @@ __device__ __forceinline__ void interp_at(const ft_fdesc& D, const FaceArr (&F)[
     double lo[3], hi[3];
     int c[3];
     for (int d = 0; d < 3; d++) {
-        const double f = floor(__ddiv_rn(__dsub_rn(x[d], g.origin[d]), h));
+        // floor((x - origin) / h) with the quotient rounded once: the product with
+        // the rounded 1/h is within 3.4e-16 |q| of that quotient (three
+        // roundings), under 4e-7 for |q| < 2^30, so its floor is the same unless
+        // q lies within 1e-6 of an integer (or is that large), where the
+        // division itself decides
+        const double dx = __dsub_rn(x[d], g.origin[d]);
+        const double q = __dmul_rn(dx, ih);
+        double f = floor(q);
+        const double r = q - f;
+        if (!(r > 1e-6 && r < 1.0 - 1e-6 && fabs(q) < 1073741824.0)) f = floor(__ddiv_rn(dx, h));
         const int n = g.n[d];
         c[d] = (f >= 0.0) ? ((f <= (double)(n - 1)) ? (int)f : n - 1) : 0;
         lo[d] = ft_plane(g.origin[d], h, c[d]);
