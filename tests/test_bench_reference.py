@@ -41,3 +41,30 @@ def test_cpu_baseline_one_core():
     cb = bench.cpu_baseline([I.laplace_droplet_32(1)], budget_s=0.0, one_core_budget_s=0.1)
     one = cb["one_core"]
     assert one["cores"] == 1 and one["value"] > 0 and one["kind"] == "oracle"
+
+
+def test_every_traced_kernel_has_a_work_model():
+    """Each name the library traces (Trace(stream, "name") in csrc) has an
+    algorithmic work model in bench.kernel_work, or a stated reason in
+    bench.NO_MODEL, so that every kernel of the step gets a roofline entry."""
+    import re
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = os.path.join(ROOT, "paper_2505_06932_gb300", "csrc")
+    names = set()
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".cuh")):
+            names |= set(re.findall(r'Trace\s+\w+\(\s*[\w>.\-]+\s*,\s*"([^"]+)"\s*\)', open(os.path.join(csrc, f)).read()))
+    assert {"k_ppic_acc<float>", "k_clip32", "k_csf_force", "k_csf_ring_list"} <= names
+    w = dict(T=1000, V=500, N=64 ** 3, C=5000, P=4000, M=300, ring=350, fit_pairs=120000, clip_f64=20)
+    missing = []
+    for n in sorted(names):
+        models = [bench.kernel_work(n, w, fp32) for fp32 in (False, True)]
+        if n in bench.NO_MODEL:
+            continue
+        if any(m is None for m in models):
+            missing.append(n)
+            continue
+        for bound, work, text in models:
+            assert bound in ("hbm", "fp32", "fp64") and work > 0 and text, n
+    assert not missing, missing
